@@ -1,0 +1,173 @@
+"""FP64 CPU checker for the batched quadrotor step -- TEST INFRASTRUCTURE ONLY.
+
+This package is the slow, obviously-correct definition the CUDA library is
+tested against.  Only ``tests/``, the smoke check and the bench's CPU-baseline
+leg import it; the product path never does.  It shares no code with the CUDA
+library: the model lives in ``quad_model.hpp`` (C++, FP64, agent by agent,
+written from the equations of Sec. III-B of arXiv 2308.12698), compiled into
+``liboracle.so`` and reached through ctypes.
+
+Parity status: the rigid-body equations, rotor model, allocation and RK4
+are pinned by closed forms and invariants in ``tests/test_oracle_pins.py``.
+The cascaded controller is the build's own reading (the paper defers it to a
+reference it does not include); it is pinned by hand-solved special cases and
+by the closed-loop spectrum at hover, not by any printed value, so its parity
+against the paper itself is unpinned.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_SOURCES = ("oracle.cpp", "quad_model.hpp", "scalar_types.hpp")
+
+NX = 17
+NPARAM = 25
+NTHETA = 16
+OPEN_LOOP = 0
+CLOSED_LOOP = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with g++ (-O2, FP64, no fast-math)."""
+    src_m = max(os.path.getmtime(os.path.join(_HERE, s)) for s in _SOURCES)
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= src_m:
+        return LIB_PATH
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-pthread",
+           os.path.join(_HERE, "oracle.cpp"), "-o", LIB_PATH + ".tmp"]
+    subprocess.run(cmd, check=True)
+    os.replace(LIB_PATH + ".tmp", LIB_PATH)
+    return LIB_PATH
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.c_void_p
+        L.oracle_rollout.argtypes = [P, ctypes.c_int, P, ctypes.c_int64, P, P, ctypes.c_double,
+                                     ctypes.c_int64, ctypes.c_int, ctypes.c_int, P]
+        L.oracle_grad.argtypes = [P, ctypes.c_int, P, ctypes.c_int64, P, P, ctypes.c_double,
+                                  ctypes.c_int64, ctypes.c_int, P, ctypes.c_double, ctypes.c_int, P, P, P]
+        L.oracle_derivative.argtypes = [P, P, P, P]
+        L.oracle_controller.argtypes = [P, P, P, P]
+        L.oracle_allocation.argtypes = [P, P, P, P]
+        L.oracle_shepperd.argtypes = [P, P]
+        L.oracle_count_ops.argtypes = [P, P, P, ctypes.c_double, ctypes.c_int, P]
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def pack_group(g: dict) -> np.ndarray:
+    """Packed FP64 parameter group: m Jxx Jyy Jzz L alpha kt kq tau_m c_d omega_max g kp kd katt krate a_max."""
+    v = [g["m"], g["Jxx"], g["Jyy"], g["Jzz"], g["L"], g["alpha"], g["kt"], g["kq"], g["tau_m"], g["c_d"],
+         g["omega_max"], g["g"], *g["kp"], *g["kd"], *g["katt"], *g["krate"], g["a_max"]]
+    a = np.asarray(v, dtype=np.float64)
+    assert a.size == NPARAM
+    return a
+
+
+def pack_groups(groups) -> np.ndarray:
+    return np.ascontiguousarray(np.concatenate([pack_group(g) for g in groups]))
+
+
+def _threads(nthreads):
+    return nthreads if nthreads else (os.cpu_count() or 1)
+
+
+def rollout(groups, gid, x0, cmd, h, nsteps, mode, nthreads=None, with_cost=False):
+    """Advance every agent nsteps RK4 steps; returns the (n, 17) FP64 final state
+    (and the per-agent running sum of Omega^2 over step ends when asked)."""
+    x = np.ascontiguousarray(np.asarray(x0, dtype=np.float64)).copy()
+    n = x.shape[0]
+    c = np.ascontiguousarray(np.asarray(cmd, dtype=np.float64))
+    gi = np.ascontiguousarray(np.asarray(gid, dtype=np.int32))
+    pg = pack_groups(groups)
+    rc = np.zeros(n, dtype=np.float64)
+    rcode = lib().oracle_rollout(_p(pg), len(groups), _p(gi), n, _p(x), _p(c), float(h), int(nsteps), int(mode),
+                                 _threads(nthreads), _p(rc))
+    if rcode != 0:
+        raise ValueError("oracle_rollout rejected its arguments")
+    return (x, rc) if with_cost else x
+
+
+def grad(groups, gid, x0, cmd, h, nsteps, mode, goal, w_omega, nthreads=None):
+    """Per-agent loss, dL/dx0 (n, 17) and dL/dtheta (n, 16) by FP64 reverse mode."""
+    x = np.ascontiguousarray(np.asarray(x0, dtype=np.float64))
+    n = x.shape[0]
+    c = np.ascontiguousarray(np.asarray(cmd, dtype=np.float64))
+    gi = np.ascontiguousarray(np.asarray(gid, dtype=np.int32))
+    gl = np.ascontiguousarray(np.asarray(goal, dtype=np.float64))
+    pg = pack_groups(groups)
+    loss = np.zeros(n)
+    dx0 = np.zeros((n, NX))
+    dth = np.zeros((n, NTHETA))
+    rcode = lib().oracle_grad(_p(pg), len(groups), _p(gi), n, _p(x), _p(c), float(h), int(nsteps), int(mode),
+                              _p(gl), float(w_omega), _threads(nthreads), _p(loss), _p(dx0), _p(dth))
+    if rcode != 0:
+        raise ValueError("oracle_grad rejected its arguments")
+    return loss, dx0, dth
+
+
+def loss(groups, gid, x0, cmd, h, nsteps, mode, goal, w_omega, nthreads=None):
+    """Per-agent loss |p_T - goal|^2 + w_omega * sum_{n=1..T} sum_i Omega_{n,i}^2 (FP64)."""
+    xT, rc = rollout(groups, gid, x0, cmd, h, nsteps, mode, nthreads, with_cost=True)
+    d = xT[:, 0:3] - np.asarray(goal, dtype=np.float64)
+    return (d * d).sum(axis=1) + w_omega * rc
+
+
+def derivative(group, x, w):
+    pg = pack_group(group)
+    xx = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    ww = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    dx = np.zeros(NX)
+    lib().oracle_derivative(_p(pg), _p(xx), _p(ww), _p(dx))
+    return dx
+
+
+def controller(group, x, cmd):
+    pg = pack_group(group)
+    xx = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    cc = np.ascontiguousarray(np.asarray(cmd, dtype=np.float64))
+    w = np.zeros(4)
+    lib().oracle_controller(_p(pg), _p(xx), _p(cc), _p(w))
+    return w
+
+
+def allocation(group):
+    pg = pack_group(group)
+    G = np.zeros(16)
+    Gi = np.zeros(16)
+    tm = np.zeros(3)
+    lib().oracle_allocation(_p(pg), _p(G), _p(Gi), _p(tm))
+    return G.reshape(4, 4), Gi.reshape(4, 4), tm
+
+
+def shepperd(R):
+    RR = np.ascontiguousarray(np.asarray(R, dtype=np.float64).reshape(9))
+    q = np.zeros(4)
+    lib().oracle_shepperd(_p(RR), _p(q))
+    return q
+
+
+def count_ops(group, x, cmd, h, mode):
+    """Non-trivial FP64 operations of one step: dict(add, mul, div, sqrt, trig, cmp)."""
+    pg = pack_group(group)
+    xx = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    cc = np.ascontiguousarray(np.asarray(cmd, dtype=np.float64))
+    out = np.zeros(6, dtype=np.int64)
+    lib().oracle_count_ops(_p(pg), _p(xx), _p(cc), float(h), int(mode), _p(out))
+    return dict(zip(("add", "mul", "div", "sqrt", "trig", "cmp"), out.tolist()))

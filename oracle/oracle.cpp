@@ -1,0 +1,215 @@
+// TEST INFRASTRUCTURE ONLY: C entry points of the FP64 checker (built into
+// oracle/liboracle.so).  Used by tests, the smoke check and the bench's CPU
+// baseline; never by the CUDA library.
+//
+// Layouts: states are agent-major (n x 17 doubles: p v q omega Omega),
+// commands n x 4, parameter groups n_groups x 25 doubles in the packed order
+// of unpack_group(), group ids int32.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "quad_model.hpp"
+
+namespace orc {
+thread_local Tape* g_tape = nullptr;
+thread_local OpCount g_count;
+}  // namespace orc
+
+using namespace orc;
+
+namespace {
+
+template <class F>
+void parallel_for(int64_t n, int nthreads, F&& body) {
+  if (nthreads <= 1 || n < 2) {
+    body(0, n);
+    return;
+  }
+  nthreads = (int)std::min<int64_t>(nthreads, n);
+  std::vector<std::thread> pool;
+  const int64_t chunk = (n + nthreads - 1) / nthreads;
+  for (int t = 0; t < nthreads; ++t) {
+    const int64_t lo = t * chunk, hi = std::min<int64_t>(n, lo + chunk);
+    if (lo >= hi) break;
+    pool.emplace_back([&body, lo, hi] { body(lo, hi); });
+  }
+  for (auto& th : pool) th.join();
+}
+
+struct GroupSet {
+  std::vector<Group<double>> P;
+  std::vector<Fixed> F;
+  GroupSet(const double* packed, int n_groups) {
+    for (int g = 0; g < n_groups; ++g) {
+      P.push_back(unpack_group(packed + (int64_t)g * NPARAM));
+      F.push_back(make_fixed(P.back()));
+    }
+  }
+};
+
+// Running cost term of one step end: sum_i Omega_i^2.
+inline double omega_sq(const double* x) {
+  return x[13] * x[13] + x[14] * x[14] + x[15] * x[15] + x[16] * x[16];
+}
+
+}  // namespace
+
+extern "C" {
+
+int oracle_nparam() { return NPARAM; }
+
+// Allocation matrix of Eq. 3 (row-major 4x4), its inverse and the per-axis
+// torque limits for one packed parameter group.
+int oracle_allocation(const double* group, double* G, double* Ginv, double* taumax) {
+  const Fixed F = make_fixed(unpack_group(group));
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      G[i * 4 + j] = F.G[i][j];
+      Ginv[i * 4 + j] = F.Ginv[i][j];
+    }
+  for (int i = 0; i < 3; ++i) taumax[i] = F.taumax[i];
+  return 0;
+}
+
+// dx = f(x, w) for one agent.
+int oracle_derivative(const double* group, const double* x, const double* w, double* dx) {
+  const Group<double> P = unpack_group(group);
+  const Fixed F = make_fixed(P);
+  derivative(P, F, x, w, dx);
+  return 0;
+}
+
+// Rotor-speed commands of the cascaded controller for one agent.
+int oracle_controller(const double* group, const double* x, const double* cmd, double* w) {
+  const Group<double> P = unpack_group(group);
+  const Fixed F = make_fixed(P);
+  controller(P, F, x, cmd, w);
+  return 0;
+}
+
+// Unit quaternion of a row-major 3x3 rotation matrix (Shepperd).
+int oracle_shepperd(const double* R9, double* q) {
+  double R[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) R[i][j] = R9[i * 3 + j];
+  shepperd(R, q);
+  return 0;
+}
+
+// Advance n agents by nsteps RK4 steps of length h in place.  run_cost (may
+// be NULL) receives, per agent, sum over step ends n = 1..nsteps of
+// sum_i Omega_i^2.
+int oracle_rollout(const double* groups, int n_groups, const int32_t* gid, int64_t n, double* x,
+                   const double* cmd, double h, int64_t nsteps, int mode, int nthreads, double* run_cost) {
+  if (n < 0 || nsteps < 0 || n_groups < 1) return -1;
+  const GroupSet S(groups, n_groups);
+  parallel_for(n, nthreads, [&](int64_t lo, int64_t hi) {
+    for (int64_t a = lo; a < hi; ++a) {
+      const int g = gid ? gid[a] : 0;
+      double cur[NX], nxt[NX];
+      std::memcpy(cur, x + a * NX, sizeof(cur));
+      double rc = 0.0;
+      for (int64_t s = 0; s < nsteps; ++s) {
+        rk4_step(S.P[g], S.F[g], mode, cur, cmd + a * 4, h, nxt);
+        std::memcpy(cur, nxt, sizeof(cur));
+        rc += omega_sq(cur);
+      }
+      std::memcpy(x + a * NX, cur, sizeof(cur));
+      if (run_cost) run_cost[a] = rc;
+    }
+  });
+  return 0;
+}
+
+// Per-agent loss L_a = |p_T - goal_a|^2 + w_omega * sum_{n=1..T} sum_i Omega_{n,i}^2
+// and its exact discrete gradient by reverse mode: dL/dx0 (n x 17) and
+// dL/dtheta (n x 16, order kp kd katt krate m Jxx Jyy Jzz) of the agent's
+// own group parameters.  The forward states are stored; each step is then
+// re-taped on its own and swept backwards with the incoming adjoint.
+int oracle_grad(const double* groups, int n_groups, const int32_t* gid, int64_t n, const double* x0,
+                const double* cmd, double h, int64_t nsteps, int mode, const double* goal, double w_omega,
+                int nthreads, double* loss, double* dx0, double* dtheta) {
+  if (n < 0 || nsteps < 0 || n_groups < 1) return -1;
+  const GroupSet S(groups, n_groups);
+  parallel_for(n, nthreads, [&](int64_t lo, int64_t hi) {
+    Tape tape;
+    g_tape = &tape;
+    std::vector<double> xs((nsteps + 1) * NX);
+    std::vector<double> adj;
+    for (int64_t a = lo; a < hi; ++a) {
+      const int g = gid ? gid[a] : 0;
+      const Group<double>& Pd = S.P[g];
+      const Fixed& F = S.F[g];
+      const double* c = cmd + a * 4;
+      std::memcpy(xs.data(), x0 + a * NX, NX * sizeof(double));
+      double rc = 0.0;
+      for (int64_t s = 0; s < nsteps; ++s) {
+        rk4_step(Pd, F, mode, xs.data() + s * NX, c, h, xs.data() + (s + 1) * NX);
+        rc += omega_sq(xs.data() + (s + 1) * NX);
+      }
+      const double* xT = xs.data() + nsteps * NX;
+      double L = w_omega * rc;
+      double lam[NX] = {0};
+      for (int i = 0; i < 3; ++i) {
+        const double d = xT[i] - goal[a * 3 + i];
+        L += d * d;
+        lam[i] = 2.0 * d;
+      }
+      if (nsteps > 0)
+        for (int i = 0; i < 4; ++i) lam[13 + i] = 2.0 * w_omega * xT[13 + i];
+      double th[NTHETA] = {0};
+      for (int64_t s = nsteps - 1; s >= 0; --s) {
+        tape.clear();
+        Group<Var> Pv = cast_group<Var>(Pd);
+        for (int i = 0; i < 3; ++i) Pv.kp[i] = Var::leaf(Pd.kp[i]);
+        for (int i = 0; i < 3; ++i) Pv.kd[i] = Var::leaf(Pd.kd[i]);
+        for (int i = 0; i < 3; ++i) Pv.katt[i] = Var::leaf(Pd.katt[i]);
+        for (int i = 0; i < 3; ++i) Pv.krate[i] = Var::leaf(Pd.krate[i]);
+        Pv.m = Var::leaf(Pd.m);
+        for (int i = 0; i < 3; ++i) Pv.J[i] = Var::leaf(Pd.J[i]);
+        Var xv[NX], xn[NX];
+        for (int i = 0; i < NX; ++i) xv[i] = Var::leaf(xs[s * NX + i]);
+        rk4_step(Pv, F, mode, xv, c, h, xn);
+        adj.assign(tape.nodes.size(), 0.0);
+        for (int i = 0; i < NX; ++i)
+          if (xn[i].idx >= 0) adj[xn[i].idx] += lam[i];
+        tape.backprop(adj);
+        // theta leaves were created first, in theta order (indices 0..15)
+        for (int k = 0; k < NTHETA; ++k) th[k] += adj[k];
+        for (int i = 0; i < NX; ++i) lam[i] = adj[xv[i].idx];
+        if (s >= 1)
+          for (int i = 0; i < 4; ++i) lam[13 + i] += 2.0 * w_omega * xs[s * NX + 13 + i];
+      }
+      loss[a] = L;
+      if (dx0) std::memcpy(dx0 + a * NX, lam, sizeof(lam));
+      if (dtheta) std::memcpy(dtheta + a * NTHETA, th, sizeof(th));
+    }
+    g_tape = nullptr;
+  });
+  return 0;
+}
+
+// Non-trivial FP64 operations of one step for one agent:
+// counts = {add/sub, mul, div, sqrt, sin/cos, comparisons}.
+int oracle_count_ops(const double* group, const double* x, const double* cmd, double h, int mode,
+                     int64_t* counts) {
+  const Group<double> Pd = unpack_group(group);
+  const Fixed F = make_fixed(Pd);
+  const Group<Cnt> P = cast_group<Cnt>(Pd);
+  Cnt xc[NX], xn[NX];
+  for (int i = 0; i < NX; ++i) xc[i] = Cnt(x[i]);
+  g_count = OpCount();
+  rk4_step(P, F, mode, xc, cmd, h, xn);
+  counts[0] = g_count.add;
+  counts[1] = g_count.mul;
+  counts[2] = g_count.div;
+  counts[3] = g_count.sqrt;
+  counts[4] = g_count.trig;
+  counts[5] = g_count.cmp;
+  return 0;
+}
+
+}  // extern "C"
