@@ -1,0 +1,488 @@
+#!/usr/bin/env python
+"""Throughput of the batched quadrotor step on B300.
+
+Workload (one bench step): a closed-loop swarm of 1,000,000 quadrotors of the
+reference airframe (1.5 kg X-frame, cascaded controller, rotor lag, RK4 with
+dt = 1 ms) advanced 1000 physics steps, replayed as a CUDA graph of fused
+K-substep launches.  Inputs are seeded synthetic (positions U[-10,10]^3,
+waypoints U[-50,50]^3, tilts <= 10 deg) and resident in HBM before timing;
+L2 is flushed (256 MB write) and the initial state restored, both untimed,
+before every timed step.
+
+Metric: agent-steps/s (agents x physics steps / device time), whole job over
+all ranks.  Beside it: the plain one-step-per-launch kernel, the checkpointed
+forward + adjoint rollout and the heterogeneous 8-group batch, each in
+agent-steps/s on the same GPU, the roofline of the dominant kernel, clocks
+sampled during the timed region, an end-to-end figure through the host-buffer
+C-ABI call, and the FP64 checker timed on host cores on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "agent-steps/s at 1M quadrotors (fwd; fwd+adjoint) vs plain kernel, % roofline"
+UNIT = "agent-steps/s"
+N_AGENTS = 1_000_000
+T_STEPS = 1000
+DT = 1e-3
+
+#: Non-trivial floating operations (add/sub, mul, div, sqrt) of one
+#: closed-loop agent-step in the checker's definition, the minimum over the
+#: bench workload's states (748..762; operands that are exactly 0 or 1 are not
+#: counted); tests pin it to the checker's operation counter.
+FLOPS_PER_AGENT_STEP = 748
+#: Bytes one plain step moves per agent: state 68 read + 68 written, command
+#: 16, group id 1, status 1.
+BYTES_PER_AGENT_STEP_PLAIN = 154
+#: FP32 lanes per SM (Blackwell) and the largest SM clock of the part.
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2032.0
+L2_FLUSH_BYTES = 256 << 20
+KERNEL_SOURCES = ("paper_2308_12698_b300/csrc/quadsim.cu", "paper_2308_12698_b300/csrc/model.cuh")
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """dram bytes per launch from a committed ncu summary, if taken on the current kernel source."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    sha = kernel_sha()
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.endswith(".md"):
+            continue
+        txt = open(os.path.join(pdir, fn)).read()
+        m = re.search(r"^bench_traffic:\s*kernel=(\S+)\s+workload=(\S+)\s+source_sha=(\w+)\s+bytes_per_launch=([\d.eE+]+)",
+                      txt, re.M)
+        if m and m.group(1) == kernel and m.group(2) == workload and m.group(3) == sha:
+            return float(m.group(4))
+    return None
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"quadsim_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(p[1]), smax=float(p[2]), power=float(p[3]), hw=p[5], hwt=p[6], swt=p[7],
+                                 pcap=p[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [r for r in rows if r["power"] > 200.0] or rows
+        sm = sorted(r["sm"] for r in loaded)
+        reasons = []
+        for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                          ("pcap", "sw_power_cap")):
+            if any(r[key].lower() == "active" for r in loaded):
+                reasons.append(name)
+        os.unlink(self.path)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r["smax"] for r in rows), "reasons": reasons,
+                "samples": len(rows), "samples_under_load": len(loaded),
+                "power_w_max": max(r["power"] for r in rows)}
+
+
+# ------------------------------------------------------------- distributed --
+
+def dist_setup(gpus: int):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world: int):
+    import torch
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# -------------------------------------------------------------- CPU legs --
+
+_WL_CACHE = {}
+
+
+def oracle_rate(n_agents: int, nsteps: int, threads: int):
+    """The FP64 checker, as it stands, on n_agents x nsteps of the bench workload."""
+    import oracle
+    from paper_2308_12698_b300 import workload as W
+    if "wl" not in _WL_CACHE:
+        _WL_CACHE["wl"] = W.scale_sweep(N_AGENTS)
+    wl = _WL_CACHE["wl"]
+    sel = slice(0, n_agents)
+    t0 = time.perf_counter()
+    oracle.rollout(wl.groups, wl.gid[sel], wl.x0[sel], wl.cmd[sel], wl.dt, nsteps, wl.mode, nthreads=threads)
+    dt = time.perf_counter() - t0
+    return n_agents * nsteps / dt, dt
+
+
+def cpu_sample_size(target_s: float, threads: int, nsteps: int) -> int:
+    """Agents of a sample that keeps the checker busy about target_s seconds."""
+    rate, _ = oracle_rate(64 * threads, 200, threads)
+    n = int(rate * target_s / nsteps)
+    return max(256, min(N_AGENTS, n))
+
+
+def cpu_baseline(target_s: float = 10.0) -> dict:
+    threads = os.cpu_count() or 1
+    n = cpu_sample_size(target_s, threads, T_STEPS)
+    rate, secs = oracle_rate(n, T_STEPS, threads)
+    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {n} agents of the 1e6-agent workload x {T_STEPS} steps, FP64 C++ checker, "
+                      f"std::thread over {threads} host cores, {secs:.1f} s"}
+
+
+def run_reference(args, world: int, rank: int):
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    # each step: a bounded sample sized so the whole run stays within ~2-3 minutes
+    per_step_s = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    n = cpu_sample_size(per_step_s, threads, T_STEPS)
+    for _ in range(args.warmup):
+        oracle_rate(n, T_STEPS, threads)
+    times = []
+    for _ in range(args.steps):
+        _, s = oracle_rate(n, T_STEPS, threads)
+        times.append(s)
+    total = sum(times)
+    value = n * T_STEPS * len(times) / total
+    sample = (f"first {n} agents of the 1e6-agent workload x {T_STEPS} steps per bench step, FP64 C++ checker "
+              f"on {threads} host cores")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": workload_config(None),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(tuned) -> dict:
+    c = {"workload": "closed-loop quadrotor swarm: 1,000,000 reference quadrotors (1.5 kg X-frame, cascaded "
+                     "PD/attitude/rate controller, rotor lag, linear drag), 1000 RK4 steps of 1 ms per bench step",
+         "n_agents_per_gpu": N_AGENTS, "physics_steps_per_bench_step": T_STEPS, "dt_s": DT,
+         "inputs": "seeded synthetic, resident in HBM",
+         "l2": "flushed (256 MB write) and initial state restored before every timed step, untimed",
+         "parallelism": "agent data parallel, one rank per GPU, no collective on the forward path"}
+    if tuned:
+        c.update(tuned)
+    return c
+
+
+# ------------------------------------------------------------ GPU legs --
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-extra", action="store_true", help="headline only (no side measurements)")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--agents", type=int, default=N_AGENTS, help="agents per GPU (profiling cases)")
+    ap.add_argument("--physics-steps", type=int, default=T_STEPS, help="physics steps per bench step")
+    ap.add_argument("--K", type=int, default=0, help="fix the fused steps per launch (skips the tuner)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2308_12698_b300 import autotune
+    from paper_2308_12698_b300 import workload as W
+    from paper_2308_12698_b300.sim import Sim, planar
+
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+
+    NA, TS = args.agents, args.physics_steps
+    wl = W.scale_sweep(NA, nsteps=TS)
+    x0 = planar(torch.from_numpy(wl.x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).reshape(-1).to(dev)
+    x = x0.clone()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    if args.K:
+        sim.set_launch(K=args.K)
+        tune = {"block": sim.launch()["block"], "K": args.K, "tuned": False}
+    else:
+        tune = autotune.tune_step(sim, x0, cmd, DT, TS)
+    K = tune["K"]
+    graph = sim.graph(x, cmd, DT, TS, K=K)
+    launches = graph.launches_per_replay
+
+    def timed_steps(run, n, reset=None):
+        """Per-step device times (ms) with untimed reset + L2 flush before each."""
+        out = []
+        for _ in range(n):
+            if reset:
+                reset()
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            run()
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+        return out
+
+    reset = lambda: x.copy_(x0)  # noqa: E731
+    timed_steps(graph.launch, args.warmup, reset)
+    barrier(world)
+    with ClockSampler(local) as clk:
+        times = timed_steps(graph.launch, args.steps, reset)
+        barrier(world)
+    total_ms = max_over_ranks(sum(times), world)
+    ms_step = total_ms / args.steps
+    value = world * NA * TS * args.steps / (total_ms / 1e3)
+    clocks = clk.summary()
+
+    # roofline of the dominant kernel: the fused step kernel, FP32-ALU bound
+    launch_s = (sum(times) / args.steps / launches) / 1e3
+    flops_launch = FLOPS_PER_AGENT_STEP * NA * min(K, TS)
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops_launch / launch_s / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+            "traffic": profiled_traffic("step_kernel<1,false>", f"closed-loop-{NA}-K{K}"),
+            "kernel": f"step_kernel<closed loop, one group>, K={K} fused steps, block {tune['block']}",
+            "flops_per_agent_step": FLOPS_PER_AGENT_STEP,
+            "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 (FMA) x {SM_MAX_MHZ:.0f} MHz max clock",
+            "avg_launch_us": launch_s * 1e6}
+    if clocks.get("sm_mhz"):
+        roof["frac_at_measured_clock"] = achieved / (peak_tflops * clocks["sm_mhz"] / SM_MAX_MHZ)
+
+    # end to end through the host-buffer C-ABI call
+    h_state0 = planar(torch.from_numpy(wl.x0)).pin_memory()
+    h_state = h_state0.clone().pin_memory()
+    h_cmd = torch.from_numpy(wl.cmd).reshape(-1).contiguous().pin_memory()
+    d_state = torch.empty_like(x0)
+    d_cmd = torch.empty_like(cmd)
+    for _ in range(args.warmup):
+        h_state.copy_(h_state0)
+        sim.step_host(h_state, h_cmd, d_state, d_cmd, DT, TS, K=K)
+    barrier(world)
+    e2e_s = 0.0
+    for _ in range(args.steps):
+        h_state.copy_(h_state0)
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.step_host(h_state, h_cmd, d_state, d_cmd, DT, TS, K=K)
+        e2e_s += time.perf_counter() - t0
+    e2e_s = max_over_ranks(e2e_s, world)
+    e2e = {"value": world * NA * TS * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(h_state.numel() * 4 + h_cmd.numel() * 4),
+           "d2h_bytes_per_step": int(h_state.numel() * 4),
+           "call": "sim_step_host (pinned host state+cmd in, state out, stream wait)"}
+
+    extra = {}
+    if not args.no_extra and NA == N_AGENTS and TS == T_STEPS:
+        extra = side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_steps, sms)
+
+    peaks = measured_peaks()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config({"K": K, "block": tune["block"], "graph_launches_per_step": launches,
+                                       "n_agents_per_gpu": NA, "physics_steps_per_bench_step": TS}),
+            "roofline": roof, "clocks": clocks, "e2e": e2e, "gpu_launches": launches * args.steps}
+    line.update(extra)
+    if "hbm_gbs" in peaks and "plain" in line:
+        line["plain"]["roofline"]["peak"] = peaks["hbm_gbs"]
+        line["plain"]["roofline"]["frac"] = line["plain"]["roofline"]["achieved"] / peaks["hbm_gbs"]
+    if world == 1 and rank == 0:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    graph.close()
+    sim.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_steps, sms) -> dict:
+    """Plain kernel, fwd+adjoint and heterogeneous batch on the same GPU (3 timed reps each)."""
+    import torch
+
+    from paper_2308_12698_b300 import autotune
+    from paper_2308_12698_b300 import workload as W
+    from paper_2308_12698_b300.sim import Sim, planar
+    reps = 3
+    out = {}
+    reset = lambda: x.copy_(x0)  # noqa: E731
+
+    # plain one-step kernel: 1000 launches per bench step (graph), HBM bound
+    g1 = sim.graph(x, cmd, DT, T_STEPS, K=1)
+    timed_steps(g1.launch, 2, reset)
+    t = timed_steps(g1.launch, reps, reset)
+    ms = max_over_ranks(sum(t), world) / reps
+    launch_s = ms / 1e3 / T_STEPS
+    gbs = BYTES_PER_AGENT_STEP_PLAIN * N_AGENTS / launch_s / 1e9
+    out["plain"] = {"value": world * N_AGENTS * T_STEPS / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                    "roofline": {"bound": "hbm", "achieved": gbs, "peak": None, "unit": "GB/s", "frac": None,
+                                 "bytes_per_agent_step": BYTES_PER_AGENT_STEP_PLAIN,
+                                 "note": "1e6-agent state (68 MB) + commands fit in the 126 MB L2 between launches"}}
+    g1.close()
+
+    # checkpointed forward + adjoint, 1e6 agents x 1000 steps, loss |p_T - goal|^2 + w sum Omega^2
+    cfg = autotune.tune_adjoint(sim, x0, cmd, DT, T_STEPS)
+    C = cfg["C"]
+    S = sim.n_segments(T_STEPS, C)
+    ckpt = torch.empty((S + 1, 17 * sim.n), dtype=torch.float32, device=x0.device)
+    rc = torch.empty(sim.n, dtype=torch.float32, device=x0.device)
+    gT = torch.zeros(17 * sim.n, dtype=torch.float32, device=x0.device)
+    gT[: 3 * sim.n] = 1.0
+    w = torch.full((sim.n,), 1e-6, dtype=torch.float32, device=x0.device)
+    ws = torch.empty(max(sim.workspace_bytes(C), 1), dtype=torch.uint8, device=x0.device)
+
+    def fwd_adj():
+        sim.rollout_forward(x0, cmd, DT, T_STEPS, C=C, ckpt=ckpt, run_cost=rc)
+        sim.rollout_backward(ckpt, cmd, DT, T_STEPS, gT, w, C=C, workspace=ws)
+
+    timed_steps(fwd_adj, 2)
+    t = timed_steps(fwd_adj, reps)
+    ms = max_over_ranks(sum(t), world) / reps
+    out["fwd_adjoint"] = {"value": world * N_AGENTS * T_STEPS / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                          "C": C, "block_adj": cfg["block"], "workspace_MB": ws.numel() / 1e6,
+                          "checkpoint_MB": ckpt.numel() * 4 / 1e6,
+                          "flops_per_agent_step_fwd_equiv": FLOPS_PER_AGENT_STEP}
+    del ckpt, ws
+
+    # heterogeneous: 8 groups, uneven sizes (600k), one persistent launch per K steps, graph
+    hw = W.heterogeneous(nsteps=T_STEPS, shuffle=False)
+    gid = torch.from_numpy(hw.gid).to(x0.device)
+    hs = Sim(hw.groups, hw.n, hw.mode, gid=gid)
+    hx0 = planar(torch.from_numpy(hw.x0)).to(x0.device)
+    hcmd = torch.from_numpy(hw.cmd).reshape(-1).to(x0.device)
+    hx = hx0.clone()
+    ht = autotune.tune_step(hs, hx0, hcmd, DT, T_STEPS)
+    hg = hs.graph(hx, hcmd, DT, T_STEPS, K=ht["K"])
+    hreset = lambda: hx.copy_(hx0)  # noqa: E731
+    timed_steps(hg.launch, 2, hreset)
+    t = timed_steps(hg.launch, reps, hreset)
+    ms = max_over_ranks(sum(t), world) / reps
+    out["hetero"] = {"value": world * hw.n * T_STEPS / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                     "n_agents": hw.n, "groups": len(hw.groups), "sizes": list(W.HETERO_SIZES), "K": ht["K"],
+                     "block": ht["block"]}
+    hg.close()
+    hs.close()
+
+    # the paper's own measurement point: 1000 quadrotors, per-round time (context only)
+    pw = W.scale_sweep(1000, nsteps=T_STEPS)
+    ps = Sim(pw.groups, pw.n, pw.mode)
+    px0 = planar(torch.from_numpy(pw.x0)).to(x0.device)
+    pcmd = torch.from_numpy(pw.cmd).reshape(-1).to(x0.device)
+    px = px0.clone()
+    pt = autotune.tune_step(ps, px0, pcmd, DT, T_STEPS)
+    pg = ps.graph(px, pcmd, DT, T_STEPS, K=pt["K"])
+    preset = lambda: px.copy_(px0)  # noqa: E731
+    timed_steps(pg.launch, 2, preset)
+    t = timed_steps(pg.launch, reps, preset)
+    ms = sum(t) / reps
+    out["n1000"] = {"value": 1000 * T_STEPS / (ms / 1e3), "unit": UNIT, "us_per_physics_step": ms,
+                    "K": pt["K"], "note": "latency bound: 1000 agents fill 4 of the SMs"}
+    pg.close()
+    ps.close()
+    return out
+
+
+if __name__ == "__main__":
+    main()

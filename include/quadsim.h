@@ -1,0 +1,179 @@
+/*
+ * quadsim.h -- C ABI of the batched quadrotor simulator (libquadsim.so).
+ *
+ * One step of a swarm of N nonlinear quadrotors, computed on the GPU, one
+ * thread per agent:
+ *   - rigid-body dynamics, Eq. (qd1)-(qd4) of arXiv 2308.12698, Sec. III-B:
+ *       p' = v,  v' = R(q)[0,0,f_c]/m - (c_d/m) v + [0,0,-g],
+ *       q' = 1/2 q o [0, omega],  omega' = I^-1(-omega x I omega + tau);
+ *   - rotor thrust/torque, Eq. (2): f_i = kt Omega_i^2, tau_i = kq Omega_i^2;
+ *   - allocation, Eq. (3): [f_c, tau_x, tau_y, tau_z] = G [f_1..f_4], with G
+ *     rows (1,1,1,1), L sin(a)(1,-1,-1,1), L cos(a)(-1,-1,1,1), kq/kt(1,-1,1,-1);
+ *   - first-order rotor lag Omega' = (Omega_cmd - Omega)/tau_m;
+ *   - classical RK4 with the command held over the four stages (Sec. III-B,
+ *     last paragraph);
+ *   - closed loop: a cascaded controller evaluated once per step (position PD
+ *     with per-axis acceleration clamp and gravity feed-forward -> desired
+ *     attitude from thrust direction and heading -> attitude P on the error
+ *     quaternion -> body-rate P scaled by the axis torque limit -> G^-1 ->
+ *     per-rotor clamp of Omega^2 to [0, omega_max^2] -> sqrt).  The paper
+ *     names only the inner body-rate loop (Sec. III-B); the cascade above is
+ *     this library's definition of it.
+ *
+ * Conventions
+ *   State of one agent, 17 floats: p(3) v(3) q(4: w,x,y,z, Hamilton,
+ *   body->inertial) omega(3, body) Omega(4, rad/s).  Frames ENU / FLU.
+ *   Rotors: 1 front-left, 2 front-right, 3 rear-right, 4 rear-left.
+ *
+ *   State buffers are PLANAR ("SoA of float4"): for N agents, 17*N floats,
+ *     plane k = 0..3 : N float4 holding components 4k..4k+3 of every agent,
+ *                      at float offset 4*k*N;
+ *     plane 4        : N floats holding component 16, at float offset 16*N.
+ *   The base pointer must be 16-byte aligned.
+ *   Commands: N float4 (16-byte aligned).  Closed loop: waypoint x, y, z and
+ *   heading psi (rad).  Open loop: the four rotor speed commands (rad/s).
+ *
+ * Execution and ownership
+ *   Every pointer named d_* is device memory owned by the caller; h_* is host
+ *   memory owned by the caller.  The library owns only the handle, its device
+ *   copy of the parameter groups and a per-agent status byte array, all
+ *   allocated in sim_create and freed in sim_destroy.  Calls that take a
+ *   stream enqueue asynchronous work on it and return without synchronising
+ *   (unless stated) and allocate nothing, so sim_step can be captured in a
+ *   CUDA graph.  A stream argument is a cudaStream_t passed as void*
+ *   (NULL = the legacy default stream).
+ *
+ * Errors
+ *   Every int-returning call returns SIM_OK (0) or a negative SIM_ERR_*.
+ *   Arguments are checked on the host before anything is enqueued.  No call
+ *   raises, traps or asserts on the device.  An agent whose state becomes
+ *   non-finite is marked dead in the status array and left at its last
+ *   finite state; dead agents are skipped by every later call (cf. Sec.
+ *   III-A: agents marked dead are excluded from the system).
+ */
+#ifndef QUADSIM_H
+#define QUADSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SIM_OK 0
+#define SIM_ERR_ARG (-1)       /* bad pointer, size, alignment or value */
+#define SIM_ERR_CUDA (-2)      /* a CUDA runtime call failed */
+#define SIM_ERR_WORKSPACE (-3) /* workspace too small */
+#define SIM_ERR_TIMEOUT (-4)   /* a bounded host wait ran out */
+#define SIM_ERR_GROUP (-5)     /* a group id >= n_groups was found */
+
+#define SIM_OPEN_LOOP 0
+#define SIM_CLOSED_LOOP 1
+
+#define SIM_MAX_GROUPS 32 /* parameter groups per handle */
+#define SIM_NTHETA 16     /* differentiable parameters per group */
+
+/* One parameter group (homogeneous airframe + controller).  Units SI, rad. */
+typedef struct {
+  float m, Jxx, Jyy, Jzz;               /* kg; principal inertias kg m^2 (Eq. qd4) */
+  float L, alpha;                       /* arm length m; arm angle from body x (Eq. 3) */
+  float kt, kq;                         /* Eq. 2 coefficients N/(rad/s)^2, N m/(rad/s)^2 */
+  float tau_m, c_d, omega_max, g;       /* rotor lag s; drag N s/m; rotor clamp rad/s; m/s^2 */
+  float kp[3], kd[3], katt[3], krate[3]; /* position PD, attitude P, normalised rate P */
+  float a_max;                          /* per-axis acceleration clamp m/s^2 (INFINITY = off) */
+} sim_group_params_t;
+
+typedef struct sim_s* sim_handle_t;
+typedef struct sim_graph_s* sim_graph_t;
+
+/* Create a simulator for n_agents agents in n_groups parameter groups.
+ * d_group_id: device array of n_agents uint8 group ids, or NULL when
+ * n_groups == 1.  The handle keeps the pointer (the caller keeps the buffer
+ * alive and unchanged); sim_create checks every id once (synchronously) and
+ * returns SIM_ERR_GROUP if one is out of range.  mode: SIM_OPEN_LOOP or
+ * SIM_CLOSED_LOOP.  Runs on the current CUDA device. */
+int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents, const uint8_t* d_group_id,
+               int mode, sim_handle_t* out);
+
+/* Replace the parameter groups (same count).  Synchronous. */
+int sim_set_params(sim_handle_t h, const sim_group_params_t* groups, int n_groups);
+
+/* Advance every live agent nsteps RK4 steps of length dt, in place.
+ * substeps_K: steps fused per launch (state stays in registers between
+ * them and touches HBM once per launch); 0 = the handle's tuned value.
+ * nsteps % K remainder steps run as one shorter launch. */
+int sim_step(sim_handle_t h, float* d_state, const float* d_cmd, float dt, int64_t nsteps, int substeps_K,
+             void* stream);
+
+/* sim_step for callers whose state lives in host memory: copies h_state and
+ * h_cmd into the caller's device buffers d_state / d_cmd, steps, copies the
+ * state back into h_state, then waits for the stream.  Host buffers should
+ * be pinned for asynchronous copies. */
+int sim_step_host(sim_handle_t h, float* h_state, const float* h_cmd, float* d_state, float* d_cmd, float dt,
+                  int64_t nsteps, int substeps_K, void* stream);
+
+/* Forward rollout with checkpoints, one launch.  Reads d_state0, writes
+ * S+1 planar states into d_ckpt (S = ceil(nsteps/ckpt_C)): x_0, x_C, ...,
+ * x_{(S-1)C}, then x_nsteps last.  d_ckpt holds (S+1)*17*N floats.
+ * d_run_cost (N floats, may be NULL) receives, per agent, the sum over step
+ * ends n = 1..nsteps of sum_i Omega_{n,i}^2. */
+int sim_rollout_forward(sim_handle_t h, const float* d_state0, const float* d_cmd, float dt, int64_t nsteps,
+                        int ckpt_C, float* d_ckpt, float* d_run_cost, void* stream);
+
+/* Bytes of workspace sim_rollout_backward needs for this handle, its
+ * current launch configuration and checkpoint interval ckpt_C. */
+size_t sim_workspace_bytes(sim_handle_t h, int ckpt_C);
+
+/* Discrete adjoint of the rollout of sim_rollout_forward (same dt, nsteps,
+ * ckpt_C, d_cmd).  For the loss L = l(x_T) + sum_a w_a * run_cost_a it takes
+ *   d_dL_dxT : planar 17*N, dl/dx_T;
+ *   d_w_run  : N floats, w_a (NULL = no running cost);
+ * and writes
+ *   d_dL_dx0          : planar 17*N, dL/dx_0;
+ *   d_dL_dtheta       : n_groups*16 floats, dL/dtheta per group, theta =
+ *                       (kp[3], kd[3], katt[3], krate[3], m, Jxx, Jyy, Jzz);
+ *   d_dL_dtheta_agent : N*16 floats of per-agent contributions, or NULL.
+ * Segments are recomputed from the checkpoints into the workspace and swept
+ * backwards.  Subgradients: clamps pass the gradient on their closed
+ * interval, sqrt(0) has derivative 0, branch choices are constants.  The
+ * per-group sums are deterministic (fixed reduction order, no atomics).
+ * d_workspace must hold sim_workspace_bytes(h, ckpt_C) bytes, 256-byte
+ * aligned. */
+int sim_rollout_backward(sim_handle_t h, const float* d_ckpt, const float* d_cmd, float dt, int64_t nsteps,
+                         int ckpt_C, const float* d_dL_dxT, const float* d_w_run, float* d_dL_dx0,
+                         float* d_dL_dtheta, float* d_dL_dtheta_agent, void* d_workspace, size_t ws_bytes,
+                         void* stream);
+
+/* Launch configuration: threads per block of the forward kernels (a
+ * multiple of 32, <= 256) and of the adjoint kernel (a multiple of 32,
+ * <= 128), and the defaults used when a call passes 0 for the steps fused
+ * per launch (K) or the checkpoint interval (C).  A 0 argument leaves that
+ * value unchanged; anything else out of range returns SIM_ERR_ARG. */
+int sim_set_launch(sim_handle_t h, int block_fwd, int block_adj, int K, int C);
+int sim_get_launch(sim_handle_t h, int* block_fwd, int* block_adj, int* K, int* C);
+
+/* Number of agents marked dead (non-finite state).  Synchronises the stream
+ * with a bounded wait (SIM_ERR_TIMEOUT after timeout_ms). */
+int sim_status(sim_handle_t h, int64_t* n_dead, int timeout_ms, void* stream);
+/* Marks every agent alive again. */
+int sim_reset_status(sim_handle_t h, void* stream);
+
+/* Capture ceil(nsteps/K) sim_step launches on d_state/d_cmd into a CUDA
+ * graph (stream capture on `stream`, which must not be the legacy default
+ * stream); sim_graph_launch replays them on any stream. */
+int sim_graph_create(sim_handle_t h, float* d_state, const float* d_cmd, float dt, int64_t nsteps, int substeps_K,
+                     void* stream, sim_graph_t* out);
+int sim_graph_launch(sim_graph_t g, void* stream);
+void sim_graph_destroy(sim_graph_t g);
+
+/* Number of kernel launches one sim_step call makes for these arguments. */
+int64_t sim_step_launches(sim_handle_t h, int64_t nsteps, int substeps_K);
+
+void sim_destroy(sim_handle_t h);
+const char* sim_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QUADSIM_H */

@@ -63,6 +63,8 @@ def lib():
         L.oracle_allocation.argtypes = [P, P, P, P]
         L.oracle_shepperd.argtypes = [P, P]
         L.oracle_count_ops.argtypes = [P, P, P, ctypes.c_double, ctypes.c_int, P]
+        L.oracle_clamp_margins.argtypes = [P, ctypes.c_int, P, ctypes.c_int64, P, P, ctypes.c_double, ctypes.c_int64,
+                                           ctypes.c_int, P]
         _lib = L
     return _lib
 
@@ -127,6 +129,22 @@ def loss(groups, gid, x0, cmd, h, nsteps, mode, goal, w_omega, nthreads=None):
     xT, rc = rollout(groups, gid, x0, cmd, h, nsteps, mode, nthreads, with_cost=True)
     d = xT[:, 0:3] - np.asarray(goal, dtype=np.float64)
     return (d * d).sum(axis=1) + w_omega * rc
+
+
+def clamp_margins(groups, gid, x0, cmd, h, nsteps, nthreads=None):
+    """(n, 3) minima over a closed-loop trajectory of: |S|/omega_max^2 (rotor demand near the
+    sqrt kink at 0), |S - omega_max^2|/omega_max^2 (rotor ceiling), ||ar| - a_max|/a_max
+    (acceleration clamp)."""
+    x = np.ascontiguousarray(np.asarray(x0, dtype=np.float64))
+    n = x.shape[0]
+    c = np.ascontiguousarray(np.asarray(cmd, dtype=np.float64))
+    gi = np.ascontiguousarray(np.asarray(gid, dtype=np.int32))
+    pg = pack_groups(groups)
+    out = np.zeros((n, 3))
+    if lib().oracle_clamp_margins(_p(pg), len(groups), _p(gi), n, _p(x), _p(c), float(h), int(nsteps),
+                                  _threads(nthreads), _p(out)) != 0:
+        raise ValueError("oracle_clamp_margins rejected its arguments")
+    return out
 
 
 def derivative(group, x, w):

@@ -6,6 +6,7 @@
 // commands n x 4, parameter groups n_groups x 25 doubles in the packed order
 // of unpack_group(), group ids int32.
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <thread>
@@ -188,6 +189,45 @@ int oracle_grad(const double* groups, int n_groups, const int32_t* gid, int64_t 
       if (dtheta) std::memcpy(dtheta + a * NTHETA, th, sizeof(th));
     }
     g_tape = nullptr;
+  });
+  return 0;
+}
+
+// Distance of each agent's closed-loop trajectory from the kinks of the
+// controller, minimised over the nsteps step starts: out[a*3 + 0] = min over
+// rotors of |S_i| / omega_max^2 (S = unclamped Omega_cmd^2; sqrt has an
+// unbounded derivative at 0), out[a*3 + 1] = min |S_i - omega_max^2| /
+// omega_max^2 (rotor ceiling), out[a*3 + 2] = min ||ar_i| - a_max| / a_max
+// (acceleration clamp).  Gradients of agents with a small margin are
+// ill-conditioned: a perturbation at rounding level moves them by a finite
+// amount.
+int oracle_clamp_margins(const double* groups, int n_groups, const int32_t* gid, int64_t n, const double* x0,
+                         const double* cmd, double h, int64_t nsteps, int nthreads, double* out) {
+  if (n < 0 || nsteps < 0 || n_groups < 1) return -1;
+  const GroupSet S(groups, n_groups);
+  parallel_for(n, nthreads, [&](int64_t lo, int64_t hi) {
+    for (int64_t a = lo; a < hi; ++a) {
+      const int g = gid ? gid[a] : 0;
+      const Group<double>& P = S.P[g];
+      double cur[NX], nxt[NX];
+      std::memcpy(cur, x0 + a * NX, sizeof(cur));
+      const double om2 = P.omega_max * P.omega_max;
+      double m0 = 1e300, m1 = 1e300, m2 = 1e300;
+      for (int64_t s = 0; s < nsteps; ++s) {
+        double ar[3], Sd[4], w[4];
+        controller(P, S.F[g], cur, cmd + a * 4, w, ar, Sd);
+        for (int i = 0; i < 4; ++i) {
+          m0 = std::min(m0, std::fabs(Sd[i]) / om2);
+          m1 = std::min(m1, std::fabs(Sd[i] - om2) / om2);
+        }
+        for (int i = 0; i < 3; ++i) m2 = std::min(m2, std::fabs(std::fabs(ar[i]) - P.a_max) / P.a_max);
+        rk4_step(P, S.F[g], CLOSED_LOOP, cur, cmd + a * 4, h, nxt);
+        std::memcpy(cur, nxt, sizeof(cur));
+      }
+      out[a * 3 + 0] = m0;
+      out[a * 3 + 1] = m1;
+      out[a * 3 + 2] = m2;
+    }
   });
   return 0;
 }

@@ -270,8 +270,12 @@ void derivative(const Group<T>& P, const Fixed& F, const T x[NX], const T w[4], 
 }
 
 // Cascaded controller: state and waypoint command -> rotor speed commands.
+// Optional diagnostics (no effect on the result): the unclamped acceleration
+// demand ar[3] and the unclamped rotor demand S[4] = Omega_cmd^2 before the
+// clamp to [0, omega_max^2].
 template <class T>
-void controller(const Group<T>& P, const Fixed& F, const T x[NX], const double cmd[4], T w[4]) {
+void controller(const Group<T>& P, const Fixed& F, const T x[NX], const double cmd[4], T w[4],
+                double* ar_out = nullptr, double* S_out = nullptr) {
   const T* p = x;
   const T* v = x + 3;
   const T* q = x + 6;
@@ -280,7 +284,9 @@ void controller(const Group<T>& P, const Fixed& F, const T x[NX], const double c
   T Fd[3];
   for (int i = 0; i < 3; ++i) {
     const T e = T(cmd[i]) - p[i];
-    const T a = clampv(P.kp[i] * e - P.kd[i] * v[i], -val(P.a_max), val(P.a_max));
+    const T ar = P.kp[i] * e - P.kd[i] * v[i];
+    if (ar_out) ar_out[i] = val(ar);
+    const T a = clampv(ar, -val(P.a_max), val(P.a_max));
     Fd[i] = P.m * (i == 2 ? a + P.g : a);
   }
   // collective thrust: desired force projected on the current body z axis
@@ -323,7 +329,9 @@ void controller(const Group<T>& P, const Fixed& F, const T x[NX], const double c
   for (int i = 0; i < 4; ++i) {
     T fi = T(F.Ginv[i][0]) * u[0];
     for (int j = 1; j < 4; ++j) fi = fi + T(F.Ginv[i][j]) * u[j];
-    w[i] = sqrt(clampv(fi / P.kt, 0.0, om2max));
+    const T S = fi / P.kt;
+    if (S_out) S_out[i] = val(S);
+    w[i] = sqrt(clampv(S, 0.0, om2max));
   }
 }
 

@@ -1,0 +1,744 @@
+// libquadsim.so: the C ABI of include/quadsim.h and the sm_103a kernels
+// behind it.  One thread per agent; state in planar float4 SoA; parameter
+// groups in kernel parameters (one group) or shared memory (several groups,
+// indexed by a per-agent uint8 id); grid-stride loops over a grid of one
+// resident wave (blocks per SM x SMs).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <thread>
+
+#include "../../include/quadsim.h"
+#include "model.cuh"
+
+using namespace qs;
+
+namespace {
+
+constexpr int kDefaultBlockFwd = 256;
+constexpr int kDefaultBlockAdj = 128;
+constexpr int kDefaultK = 10;
+constexpr int kDefaultC = 100;
+
+// --------------------------------------------------------------- kernels --
+
+struct StepArgs {
+  float* state;
+  const float4* cmd;
+  const uint8_t* gid;
+  uint8_t* status;
+  int64_t n;
+  int K;
+  int n_groups;
+  StepH H;
+  const DevGroup* groups;  // device table (several groups)
+};
+
+__device__ __forceinline__ bool all_finite(const St& x) {
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < NX; ++i) s += x.a[i];
+  return isfinite(s);
+}
+
+template <bool HETERO>
+__device__ __forceinline__ void load_groups(DevGroup* sg, const DevGroup* src, int n_groups) {
+  if (HETERO) {
+    const float4* s = reinterpret_cast<const float4*>(src);
+    float4* d = reinterpret_cast<float4*>(sg);
+    for (int i = threadIdx.x; i < n_groups * (int)(sizeof(DevGroup) / 16); i += blockDim.x) d[i] = s[i];
+    __syncthreads();
+  }
+}
+
+// K fused RK4 steps per launch; the state touches HBM once per launch.
+template <int MODE, bool HETERO>
+__global__ void __launch_bounds__(256) step_kernel(StepArgs A, const DevGroup P0) {
+  extern __shared__ float4 smem4[];
+  DevGroup* sg = reinterpret_cast<DevGroup*>(smem4);
+  load_groups<HETERO>(sg, A.groups, A.n_groups);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) {
+    if (A.status[i]) continue;  // dead agents are frozen
+    St x;
+    load_state(A.state, A.n, i, x);
+    const float4 c = A.cmd[i];
+    float ch = 0.f, sh = 0.f;
+    if (MODE == 1) sincosf(c.w, &sh, &ch);
+    if (HETERO) {
+      const DevGroup P = sg[A.gid[i]];
+      for (int k = 0; k < A.K; ++k) step<MODE>(P, x, c, ch, sh, A.H);
+    } else {
+      for (int k = 0; k < A.K; ++k) step<MODE>(P0, x, c, ch, sh, A.H);
+    }
+    if (all_finite(x)) {
+      store_state(A.state, A.n, i, x);
+    } else {
+      A.status[i] = 1;  // keep the last finite state
+    }
+  }
+}
+
+struct CkptArgs {
+  const float* x0;
+  float* ckpt;
+  float* run_cost;
+  const float4* cmd;
+  const uint8_t* gid;
+  uint8_t* status;
+  int64_t n;
+  int64_t nsteps;
+  int C;
+  int S;
+  int n_groups;
+  StepH H;
+  const DevGroup* groups;
+};
+
+// Whole forward rollout in one launch, checkpoint every C steps.
+template <int MODE, bool HETERO>
+__global__ void __launch_bounds__(256) ckpt_kernel(CkptArgs A, const DevGroup P0) {
+  extern __shared__ float4 smem4[];
+  DevGroup* sg = reinterpret_cast<DevGroup*>(smem4);
+  load_groups<HETERO>(sg, A.groups, A.n_groups);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t plane = (int64_t)NX * A.n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) {
+    St x;
+    load_state(A.x0, A.n, i, x);
+    store_state(A.ckpt, A.n, i, x);
+    if (A.status[i]) {  // frozen: every checkpoint is the current state
+      for (int s = 1; s <= A.S; ++s) store_state(A.ckpt + s * plane, A.n, i, x);
+      if (A.run_cost) A.run_cost[i] = 0.f;
+      continue;
+    }
+    const float4 c = A.cmd[i];
+    float ch = 0.f, sh = 0.f;
+    if (MODE == 1) sincosf(c.w, &sh, &ch);
+    const DevGroup P = HETERO ? sg[A.gid[i]] : P0;
+    float rc = 0.f;
+    for (int s = 0; s < A.S; ++s) {
+      const int len = (int)min((int64_t)A.C, A.nsteps - (int64_t)s * A.C);
+      for (int k = 0; k < len; ++k) {
+        step<MODE>(P, x, c, ch, sh, A.H);
+        rc += (x.a[OM] * x.a[OM] + x.a[OM + 1] * x.a[OM + 1]) + (x.a[OM + 2] * x.a[OM + 2] + x.a[OM + 3] * x.a[OM + 3]);
+      }
+      store_state(A.ckpt + (s + 1) * plane, A.n, i, x);
+    }
+    if (A.run_cost) A.run_cost[i] = rc;
+    if (!all_finite(x)) A.status[i] = 1;
+  }
+}
+
+struct AdjArgs {
+  const float* ckpt;
+  const float4* cmd;
+  const uint8_t* gid;
+  const uint8_t* status;
+  const float* dLdxT;
+  const float* w_run;
+  float* dLdx0;
+  float* th_agent;
+  float* partials;  // [gridDim.x][n_groups][16]
+  float* scratch;   // [C][17 planes][grid threads]
+  int64_t n;
+  int64_t nsteps;
+  int C;
+  int S;
+  int n_groups;
+  StepH H;
+  const DevGroup* groups;
+};
+
+// Discrete adjoint: per agent, segments in reverse; each segment is
+// recomputed from its checkpoint into this thread's scratch column, then
+// swept backwards step by step.  Per-agent theta cotangents are reduced per
+// group inside each warp (fixed butterfly order), accumulated per warp in
+// shared memory, and written as one partial per block.
+template <int MODE>
+__global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
+  extern __shared__ float4 smem4[];
+  DevGroup* sg = reinterpret_cast<DevGroup*>(smem4);
+  float* wacc = reinterpret_cast<float*>(sg + A.n_groups);
+  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int e = threadIdx.x; e < nw * A.n_groups * NTH; e += blockDim.x) wacc[e] = 0.f;
+  load_groups<true>(sg, A.groups, A.n_groups);
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t sstep = (int64_t)NX * nthreads;
+  const int64_t plane = (int64_t)NX * A.n;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < A.n; base += nthreads) {
+    const int64_t i = base + threadIdx.x;
+    float tb[NTH];
+#pragma unroll
+    for (int q = 0; q < NTH; ++q) tb[q] = 0.f;
+    int g = -1;
+    if (i < A.n && A.status[i] == 0) {
+      g = A.gid ? (int)A.gid[i] : 0;
+      const DevGroup P = sg[g];
+      const float4 c = A.cmd[i];
+      float ch = 0.f, sh = 0.f;
+      if (MODE == 1) sincosf(c.w, &sh, &ch);
+      const float w = A.w_run ? A.w_run[i] : 0.f;
+      St lam, x;
+      load_state(A.dLdxT, A.n, i, lam);
+      load_state(A.ckpt + (int64_t)A.S * plane, A.n, i, x);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) lam.a[OM + q] += 2.f * w * x.a[OM + q];
+      for (int s = A.S - 1; s >= 0; --s) {
+        const int64_t n0 = (int64_t)s * A.C;
+        const int len = (int)min((int64_t)A.C, A.nsteps - n0);
+        load_state(A.ckpt + (int64_t)s * plane, A.n, i, x);
+        for (int j = 0; j < len; ++j) {
+          store_state(A.scratch + j * sstep, nthreads, slot, x);
+          if (j + 1 < len) step<MODE>(P, x, c, ch, sh, A.H);
+        }
+        for (int j = len - 1; j >= 0; --j) {
+          load_state(A.scratch + j * sstep, nthreads, slot, x);
+          step_vjp<MODE>(P, x, c, ch, sh, A.H, lam, tb);
+          if (n0 + j >= 1) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) lam.a[OM + q] += 2.f * w * x.a[OM + q];
+          }
+        }
+      }
+      store_state(A.dLdx0, A.n, i, lam);
+      if (A.th_agent) {
+#pragma unroll
+        for (int q = 0; q < NTH; ++q) A.th_agent[i * NTH + q] = tb[q];
+      }
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, g >= 0);
+    while (todo) {
+      const int leader = __ffs(todo) - 1;
+      const int gl = __shfl_sync(0xffffffffu, g, leader);
+      const bool mine = (g == gl);
+      todo &= ~__ballot_sync(0xffffffffu, mine);
+#pragma unroll
+      for (int q = 0; q < NTH; ++q) {
+        float v = mine ? tb[q] : 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) wacc[(warp * A.n_groups + gl) * NTH + q] += v;
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < A.n_groups * NTH; e += blockDim.x) {
+    float s = 0.f;
+    for (int w = 0; w < nw; ++w) s += wacc[w * A.n_groups * NTH + e];
+    A.partials[(int64_t)blockIdx.x * A.n_groups * NTH + e] = s;
+  }
+}
+
+// out[e] = sum over blocks b of partials[b][e], fixed order: each thread sums
+// a strided subset in increasing b, then a fixed shared-memory tree.
+__global__ void __launch_bounds__(256) reduce_partials(const float* partials, int nblocks, int width, float* out) {
+  __shared__ float buf[256];
+  const int e = blockIdx.x;
+  float s = 0.f;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partials[(int64_t)b * width + e];
+  buf[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = blockDim.x >> 1; off > 0; off >>= 1) {
+    if (threadIdx.x < off) buf[threadIdx.x] += buf[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[e] = buf[0];
+}
+
+__global__ void max_gid_kernel(const uint8_t* gid, int64_t n, unsigned int* out) {
+  unsigned int m = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (unsigned int)gid[i]);
+  for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+__global__ void count_dead_kernel(const uint8_t* status, int64_t n, unsigned long long* out) {
+  unsigned long long c = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    c += status[i] != 0;
+  for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+// ------------------------------------------------------------ host side --
+
+DevGroup derive(const sim_group_params_t& p) {
+  DevGroup d;
+  std::memset(&d, 0, sizeof(d));
+  const double m = p.m, Jx = p.Jxx, Jy = p.Jyy, Jz = p.Jzz, kt = p.kt, kq = p.kq;
+  const double Ls = (double)p.L * std::sin((double)p.alpha), Lc = (double)p.L * std::cos((double)p.alpha);
+  const double om2 = (double)p.omega_max * p.omega_max;
+  d.m = p.m; d.inv_m = (float)(1.0 / m); d.g = p.g; d.cd_m = (float)(p.c_d / m);
+  d.Jx = p.Jxx; d.Jy = p.Jyy; d.Jz = p.Jzz; d.inv_tau = (float)(1.0 / p.tau_m);
+  d.iJx = (float)(1.0 / Jx); d.iJy = (float)(1.0 / Jy); d.iJz = (float)(1.0 / Jz); d.om2max = (float)om2;
+  d.gx = (float)((Jy - Jz) / Jx); d.gy = (float)((Jz - Jx) / Jy); d.gz = (float)((Jx - Jy) / Jz); d.c_d = p.c_d;
+  d.kf = p.kt; d.kfLs = (float)(kt * Ls); d.kfLc = (float)(kt * Lc); d.km = p.kq;
+  const double taumax[3] = {2.0 * Ls * kt * om2, 2.0 * Lc * kt * om2, 2.0 * kq * om2};
+  for (int i = 0; i < 3; ++i) {
+    d.kp[i] = p.kp[i];
+    d.kd[i] = p.kd[i];
+    d.katt2[i] = (float)(2.0 * p.katt[i]);
+    d.krt[i] = (float)(p.krate[i] * taumax[i]);
+    d.krate[i] = p.krate[i];
+    d.taumax[i] = (float)taumax[i];
+  }
+  d.a_max = p.a_max;
+  d.mix0 = (float)(1.0 / (4.0 * kt));
+  d.mix1 = (float)(1.0 / (4.0 * kt * Ls));
+  d.mix2 = (float)(1.0 / (4.0 * kt * Lc));
+  d.mix3 = (float)(1.0 / (4.0 * kq));
+  return d;
+}
+
+bool valid_params(const sim_group_params_t& p) {
+  const float pos[] = {p.m, p.Jxx, p.Jyy, p.Jzz, p.L, p.kt, p.kq, p.tau_m, p.omega_max};
+  for (float v : pos)
+    if (!(std::isfinite(v) && v > 0.f)) return false;
+  if (!(std::isfinite(p.c_d) && p.c_d >= 0.f) || !std::isfinite(p.g)) return false;
+  if (!(std::sin((double)p.alpha) > 0.0 && std::cos((double)p.alpha) > 0.0)) return false;
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(p.kp[i]) || !std::isfinite(p.kd[i]) || !std::isfinite(p.katt[i]) ||
+        !std::isfinite(p.krate[i]))
+      return false;
+  return p.a_max >= 0.f;  // +inf allowed (no clamp)
+}
+
+StepH make_h(float dt) {
+  StepH H;
+  H.h = dt;
+  H.h2 = (float)(0.5 * (double)dt);
+  H.h6 = (float)((double)dt / 6.0);
+  return H;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+template <class F>
+int occupancy(F kernel, int block, size_t smem) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, smem) != cudaSuccess) return 1;
+  return std::max(nb, 1);
+}
+
+}  // namespace
+
+struct sim_s {
+  int device = 0;
+  int sms = 1;
+  int n_groups = 1;
+  int64_t n = 0;
+  int mode = SIM_CLOSED_LOOP;
+  const uint8_t* gid = nullptr;  // borrowed
+  uint8_t* status = nullptr;     // owned
+  DevGroup* d_groups = nullptr;  // owned
+  DevGroup host_group0;
+  int block_fwd = kDefaultBlockFwd;
+  int block_adj = kDefaultBlockAdj;
+  int K = kDefaultK;
+  int C = kDefaultC;
+};
+
+struct sim_graph_s {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+bool hetero(const sim_s* h) { return h->n_groups > 1; }
+
+size_t group_smem(const sim_s* h) { return hetero(h) ? sizeof(DevGroup) * h->n_groups : 0; }
+
+int fwd_grid(const sim_s* h, size_t smem) {
+  // one resident wave of blocks, grid-stride over the agents
+  int occ;
+  if (h->mode == SIM_CLOSED_LOOP)
+    occ = hetero(h) ? occupancy(step_kernel<1, true>, h->block_fwd, smem)
+                    : occupancy(step_kernel<1, false>, h->block_fwd, smem);
+  else
+    occ = hetero(h) ? occupancy(step_kernel<0, true>, h->block_fwd, smem)
+                    : occupancy(step_kernel<0, false>, h->block_fwd, smem);
+  const int64_t need = (h->n + h->block_fwd - 1) / h->block_fwd;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)occ * h->sms));
+}
+
+size_t adj_smem(const sim_s* h) {
+  return sizeof(DevGroup) * h->n_groups + (size_t)(h->block_adj / 32) * h->n_groups * NTH * sizeof(float);
+}
+
+int adj_grid(const sim_s* h) {
+  const size_t smem = adj_smem(h);
+  const int occ = h->mode == SIM_CLOSED_LOOP ? occupancy(adjoint_kernel<1>, h->block_adj, smem)
+                                             : occupancy(adjoint_kernel<0>, h->block_adj, smem);
+  const int64_t need = (h->n + h->block_adj - 1) / h->block_adj;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)occ * h->sms));
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t scratch_bytes(const sim_s* h, int C, int grid) {
+  return align256((size_t)C * NX * sizeof(float) * (size_t)grid * h->block_adj);
+}
+
+int launch_step(sim_s* h, float* d_state, const float* d_cmd, StepH H, int K, cudaStream_t st) {
+  StepArgs A;
+  A.state = d_state;
+  A.cmd = reinterpret_cast<const float4*>(d_cmd);
+  A.gid = h->gid;
+  A.status = h->status;
+  A.n = h->n;
+  A.K = K;
+  A.n_groups = h->n_groups;
+  A.H = H;
+  A.groups = h->d_groups;
+  const size_t smem = group_smem(h);
+  const int grid = fwd_grid(h, smem);
+  const DevGroup& P0 = h->host_group0;
+  if (h->mode == SIM_CLOSED_LOOP) {
+    if (hetero(h)) step_kernel<1, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
+    else step_kernel<1, false><<<grid, h->block_fwd, smem, st>>>(A, P0);
+  } else {
+    if (hetero(h)) step_kernel<0, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
+    else step_kernel<0, false><<<grid, h->block_fwd, smem, st>>>(A, P0);
+  }
+  return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ERR_CUDA;
+}
+
+int wait_stream(cudaStream_t st, int timeout_ms) {
+  cudaEvent_t ev;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return SIM_ERR_CUDA;
+  if (cudaEventRecord(ev, st) != cudaSuccess) {
+    cudaEventDestroy(ev);
+    return SIM_ERR_CUDA;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  int rc = SIM_OK;
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) {
+      rc = SIM_ERR_CUDA;
+      break;
+    }
+    const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+    if (timeout_ms >= 0 && ms.count() > timeout_ms) {
+      rc = SIM_ERR_TIMEOUT;
+      break;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  cudaEventDestroy(ev);
+  return rc;
+}
+
+
+}  // namespace
+
+extern "C" {
+
+const char* sim_error_string(int code) {
+  switch (code) {
+    case SIM_OK: return "ok";
+    case SIM_ERR_ARG: return "invalid argument";
+    case SIM_ERR_CUDA: return "CUDA runtime error";
+    case SIM_ERR_WORKSPACE: return "workspace too small";
+    case SIM_ERR_TIMEOUT: return "timed out waiting for the stream";
+    case SIM_ERR_GROUP: return "group id out of range";
+    default: return "unknown error";
+  }
+}
+
+int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents, const uint8_t* d_group_id, int mode,
+               sim_handle_t* out) {
+  if (!out) return SIM_ERR_ARG;
+  *out = nullptr;
+  if (!groups || n_groups < 1 || n_groups > SIM_MAX_GROUPS || n_agents < 0) return SIM_ERR_ARG;
+  if (mode != SIM_OPEN_LOOP && mode != SIM_CLOSED_LOOP) return SIM_ERR_ARG;
+  if (n_groups > 1 && !d_group_id && n_agents > 0) return SIM_ERR_ARG;
+  for (int g = 0; g < n_groups; ++g)
+    if (!valid_params(groups[g])) return SIM_ERR_ARG;
+  sim_s* h = new (std::nothrow) sim_s();
+  if (!h) return SIM_ERR_ARG;
+  h->n_groups = n_groups;
+  h->n = n_agents;
+  h->mode = mode;
+  h->gid = d_group_id;
+  h->host_group0 = derive(groups[0]);
+  int rc = SIM_OK;
+  DevGroup tbl[SIM_MAX_GROUPS];
+  for (int g = 0; g < n_groups; ++g) tbl[g] = derive(groups[g]);
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
+      cudaMalloc(&h->d_groups, sizeof(DevGroup) * n_groups) != cudaSuccess ||
+      cudaMemcpy(h->d_groups, tbl, sizeof(DevGroup) * n_groups, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMalloc(&h->status, std::max<int64_t>(n_agents, 1)) != cudaSuccess ||
+      cudaMemset(h->status, 0, std::max<int64_t>(n_agents, 1)) != cudaSuccess) {
+    rc = SIM_ERR_CUDA;
+  }
+  if (rc == SIM_OK && n_groups > 1 && n_agents > 0) {
+    unsigned int* d_max = nullptr;
+    unsigned int mx = 0;
+    if (cudaMalloc(&d_max, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(d_max, 0, sizeof(unsigned int)) != cudaSuccess) {
+      rc = SIM_ERR_CUDA;
+    } else {
+      max_gid_kernel<<<std::min<int64_t>((n_agents + 255) / 256, 4096), 256>>>(d_group_id, n_agents, d_max);
+      if (cudaGetLastError() != cudaSuccess ||
+          cudaMemcpy(&mx, d_max, sizeof(unsigned int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = SIM_ERR_CUDA;
+      else if ((int)mx >= n_groups)
+        rc = SIM_ERR_GROUP;
+    }
+    if (d_max) cudaFree(d_max);
+  }
+  if (rc != SIM_OK) {
+    sim_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return SIM_OK;
+}
+
+int sim_set_params(sim_handle_t h, const sim_group_params_t* groups, int n_groups) {
+  if (!h || !groups || n_groups != h->n_groups) return SIM_ERR_ARG;
+  DevGroup tbl[SIM_MAX_GROUPS];
+  for (int g = 0; g < n_groups; ++g) {
+    if (!valid_params(groups[g])) return SIM_ERR_ARG;
+    tbl[g] = derive(groups[g]);
+  }
+  if (cudaMemcpy(h->d_groups, tbl, sizeof(DevGroup) * n_groups, cudaMemcpyHostToDevice) != cudaSuccess)
+    return SIM_ERR_CUDA;
+  h->host_group0 = tbl[0];
+  return SIM_OK;
+}
+
+int sim_set_launch(sim_handle_t h, int block_fwd, int block_adj, int K, int C) {
+  if (!h || block_fwd < 0 || block_adj < 0 || K < 0 || C < 0) return SIM_ERR_ARG;
+  if (block_fwd && (block_fwd % 32 || block_fwd > 256)) return SIM_ERR_ARG;
+  if (block_adj && (block_adj % 32 || block_adj > 128)) return SIM_ERR_ARG;
+  if (block_fwd) h->block_fwd = block_fwd;
+  if (block_adj) h->block_adj = block_adj;
+  if (K) h->K = K;
+  if (C) h->C = C;
+  return SIM_OK;
+}
+
+int sim_get_launch(sim_handle_t h, int* block_fwd, int* block_adj, int* K, int* C) {
+  if (!h) return SIM_ERR_ARG;
+  if (block_fwd) *block_fwd = h->block_fwd;
+  if (block_adj) *block_adj = h->block_adj;
+  if (K) *K = h->K;
+  if (C) *C = h->C;
+  return SIM_OK;
+}
+
+int64_t sim_step_launches(sim_handle_t h, int64_t nsteps, int substeps_K) {
+  if (!h || nsteps <= 0 || h->n == 0) return 0;
+  const int64_t K = substeps_K > 0 ? substeps_K : h->K;
+  return (nsteps + K - 1) / K;
+}
+
+int sim_step(sim_handle_t h, float* d_state, const float* d_cmd, float dt, int64_t nsteps, int substeps_K,
+             void* stream) {
+  if (!h || nsteps < 0 || substeps_K < 0 || !(dt > 0.f) || !std::isfinite(dt)) return SIM_ERR_ARG;
+  if (h->n == 0 || nsteps == 0) return SIM_OK;
+  if (!d_state || !d_cmd || !aligned16(d_state) || !aligned16(d_cmd)) return SIM_ERR_ARG;
+  const int K = substeps_K > 0 ? substeps_K : h->K;
+  const StepH H = make_h(dt);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int64_t done = 0;
+  while (done < nsteps) {
+    const int k = (int)std::min<int64_t>(K, nsteps - done);
+    const int rc = launch_step(h, d_state, d_cmd, H, k, st);
+    if (rc != SIM_OK) return rc;
+    done += k;
+  }
+  return SIM_OK;
+}
+
+int sim_step_host(sim_handle_t h, float* h_state, const float* h_cmd, float* d_state, float* d_cmd, float dt,
+                  int64_t nsteps, int substeps_K, void* stream) {
+  if (!h || !h_state || !h_cmd || !d_state || !d_cmd) return SIM_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t sb = (size_t)NX * h->n * sizeof(float), cb = (size_t)4 * h->n * sizeof(float);
+  if (cudaMemcpyAsync(d_state, h_state, sb, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(d_cmd, h_cmd, cb, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return SIM_ERR_CUDA;
+  int rc = sim_step(h, d_state, d_cmd, dt, nsteps, substeps_K, stream);
+  if (rc != SIM_OK) return rc;
+  if (cudaMemcpyAsync(h_state, d_state, sb, cudaMemcpyDeviceToHost, st) != cudaSuccess) return SIM_ERR_CUDA;
+  return wait_stream(st, 600000);
+}
+
+int sim_rollout_forward(sim_handle_t h, const float* d_state0, const float* d_cmd, float dt, int64_t nsteps,
+                        int ckpt_C, float* d_ckpt, float* d_run_cost, void* stream) {
+  if (!h || nsteps < 1 || ckpt_C < 0 || !(dt > 0.f) || !std::isfinite(dt)) return SIM_ERR_ARG;
+  if (h->n == 0) return SIM_OK;
+  if (!d_state0 || !d_cmd || !d_ckpt || !aligned16(d_state0) || !aligned16(d_cmd) || !aligned16(d_ckpt))
+    return SIM_ERR_ARG;
+  const int C = ckpt_C > 0 ? ckpt_C : h->C;
+  CkptArgs A;
+  A.x0 = d_state0;
+  A.ckpt = d_ckpt;
+  A.run_cost = d_run_cost;
+  A.cmd = reinterpret_cast<const float4*>(d_cmd);
+  A.gid = h->gid;
+  A.status = h->status;
+  A.n = h->n;
+  A.nsteps = nsteps;
+  A.C = C;
+  A.S = (int)((nsteps + C - 1) / C);
+  A.n_groups = h->n_groups;
+  A.H = make_h(dt);
+  A.groups = h->d_groups;
+  const size_t smem = group_smem(h);
+  const int grid = fwd_grid(h, smem);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const DevGroup& P0 = h->host_group0;
+  if (h->mode == SIM_CLOSED_LOOP) {
+    if (hetero(h)) ckpt_kernel<1, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
+    else ckpt_kernel<1, false><<<grid, h->block_fwd, smem, st>>>(A, P0);
+  } else {
+    if (hetero(h)) ckpt_kernel<0, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
+    else ckpt_kernel<0, false><<<grid, h->block_fwd, smem, st>>>(A, P0);
+  }
+  return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ERR_CUDA;
+}
+
+size_t sim_workspace_bytes(sim_handle_t h, int ckpt_C) {
+  if (!h || ckpt_C < 0) return 0;
+  const int C = ckpt_C > 0 ? ckpt_C : h->C;
+  const int grid = adj_grid(h);
+  return scratch_bytes(h, C, grid) + align256((size_t)grid * h->n_groups * NTH * sizeof(float));
+}
+
+int sim_rollout_backward(sim_handle_t h, const float* d_ckpt, const float* d_cmd, float dt, int64_t nsteps,
+                         int ckpt_C, const float* d_dL_dxT, const float* d_w_run, float* d_dL_dx0,
+                         float* d_dL_dtheta, float* d_dL_dtheta_agent, void* d_workspace, size_t ws_bytes,
+                         void* stream) {
+  if (!h || nsteps < 1 || ckpt_C < 0 || !(dt > 0.f) || !std::isfinite(dt)) return SIM_ERR_ARG;
+  if (!d_dL_dtheta) return SIM_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (h->n == 0) {
+    return cudaMemsetAsync(d_dL_dtheta, 0, sizeof(float) * h->n_groups * NTH, st) == cudaSuccess ? SIM_OK
+                                                                                                : SIM_ERR_CUDA;
+  }
+  if (!d_ckpt || !d_cmd || !d_dL_dxT || !d_dL_dx0 || !d_workspace) return SIM_ERR_ARG;
+  if (!aligned16(d_ckpt) || !aligned16(d_cmd) || !aligned16(d_dL_dxT) || !aligned16(d_dL_dx0) ||
+      (reinterpret_cast<uintptr_t>(d_workspace) & 255u))
+    return SIM_ERR_ARG;
+  const int C = ckpt_C > 0 ? ckpt_C : h->C;
+  const int grid = adj_grid(h);
+  const size_t sbytes = scratch_bytes(h, C, grid);
+  const size_t need = sbytes + align256((size_t)grid * h->n_groups * NTH * sizeof(float));
+  if (ws_bytes < need) return SIM_ERR_WORKSPACE;
+  AdjArgs A;
+  A.ckpt = d_ckpt;
+  A.cmd = reinterpret_cast<const float4*>(d_cmd);
+  A.gid = h->n_groups > 1 ? h->gid : nullptr;
+  A.status = h->status;
+  A.dLdxT = d_dL_dxT;
+  A.w_run = d_w_run;
+  A.dLdx0 = d_dL_dx0;
+  A.th_agent = d_dL_dtheta_agent;
+  A.scratch = static_cast<float*>(d_workspace);
+  A.partials = reinterpret_cast<float*>(static_cast<char*>(d_workspace) + sbytes);
+  A.n = h->n;
+  A.nsteps = nsteps;
+  A.C = C;
+  A.S = (int)((nsteps + C - 1) / C);
+  A.n_groups = h->n_groups;
+  A.H = make_h(dt);
+  A.groups = h->d_groups;
+  const size_t smem = adj_smem(h);
+  if (h->mode == SIM_CLOSED_LOOP) adjoint_kernel<1><<<grid, h->block_adj, smem, st>>>(A);
+  else adjoint_kernel<0><<<grid, h->block_adj, smem, st>>>(A);
+  if (cudaGetLastError() != cudaSuccess) return SIM_ERR_CUDA;
+  reduce_partials<<<h->n_groups * NTH, 256, 0, st>>>(A.partials, grid, h->n_groups * NTH, d_dL_dtheta);
+  return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ERR_CUDA;
+}
+
+int sim_status(sim_handle_t h, int64_t* n_dead, int timeout_ms, void* stream) {
+  if (!h || !n_dead) return SIM_ERR_ARG;
+  *n_dead = 0;
+  if (h->n == 0) return SIM_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  unsigned long long* d = nullptr;
+  unsigned long long v = 0;
+  if (cudaMalloc(&d, sizeof(v)) != cudaSuccess) return SIM_ERR_CUDA;
+  int rc = SIM_OK;
+  if (cudaMemsetAsync(d, 0, sizeof(v), st) != cudaSuccess) rc = SIM_ERR_CUDA;
+  if (rc == SIM_OK) {
+    count_dead_kernel<<<std::min<int64_t>((h->n + 255) / 256, 4096), 256, 0, st>>>(h->status, h->n, d);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&v, d, sizeof(v), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      rc = SIM_ERR_CUDA;
+  }
+  if (rc == SIM_OK) rc = wait_stream(st, timeout_ms);
+  if (rc == SIM_OK) *n_dead = (int64_t)v;
+  if (rc != SIM_ERR_TIMEOUT) cudaFree(d);
+  return rc;
+}
+
+int sim_reset_status(sim_handle_t h, void* stream) {
+  if (!h) return SIM_ERR_ARG;
+  if (h->n == 0) return SIM_OK;
+  return cudaMemsetAsync(h->status, 0, h->n, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? SIM_OK
+                                                                                                   : SIM_ERR_CUDA;
+}
+
+int sim_graph_create(sim_handle_t h, float* d_state, const float* d_cmd, float dt, int64_t nsteps, int substeps_K,
+                     void* stream, sim_graph_t* out) {
+  if (!h || !out || !stream) return SIM_ERR_ARG;
+  *out = nullptr;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  sim_graph_s* g = new (std::nothrow) sim_graph_s();
+  if (!g) return SIM_ERR_ARG;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    delete g;
+    return SIM_ERR_CUDA;
+  }
+  const int rc = sim_step(h, d_state, d_cmd, dt, nsteps, substeps_K, stream);
+  const cudaError_t e = cudaStreamEndCapture(st, &g->graph);
+  if (rc != SIM_OK || e != cudaSuccess) {
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return rc != SIM_OK ? rc : SIM_ERR_CUDA;
+  }
+  if (cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) {
+    cudaGraphDestroy(g->graph);
+    delete g;
+    return SIM_ERR_CUDA;
+  }
+  *out = g;
+  return SIM_OK;
+}
+
+int sim_graph_launch(sim_graph_t g, void* stream) {
+  if (!g) return SIM_ERR_ARG;
+  return cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? SIM_OK : SIM_ERR_CUDA;
+}
+
+void sim_graph_destroy(sim_graph_t g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+}
+
+void sim_destroy(sim_handle_t h) {
+  if (!h) return;
+  if (h->status) cudaFree(h->status);
+  if (h->d_groups) cudaFree(h->d_groups);
+  delete h;
+}
+
+}  // extern "C"

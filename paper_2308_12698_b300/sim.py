@@ -1,0 +1,275 @@
+"""Python face of libquadsim.so: a handle class, a CUDA-graph wrapper and a
+torch.autograd.Function over the hand-written adjoint.
+
+PyTorch only provides device memory and the stream; every step of the
+simulation runs in the library's kernels.  State tensors are flat float32
+CUDA tensors in the planar layout of include/quadsim.h (17 N floats).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import SimError, check, group_struct, lib
+
+THETA_FIELDS = (("kp", 0), ("kp", 1), ("kp", 2), ("kd", 0), ("kd", 1), ("kd", 2), ("katt", 0), ("katt", 1),
+                ("katt", 2), ("krate", 0), ("krate", 1), ("krate", 2), ("m", None), ("Jxx", None), ("Jyy", None),
+                ("Jzz", None))
+
+
+def _ptr(t) -> ctypes.c_void_p | None:
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_f32(t: torch.Tensor, numel: int, name: str):
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == numel):
+        raise SimError(f"{name}: expected a contiguous float32 CUDA tensor of {numel} elements")
+
+
+def theta_of(group: dict) -> list[float]:
+    """The 16 differentiable parameters of a group, in the library's order."""
+    return [float(group[k][i] if i is not None else group[k]) for k, i in THETA_FIELDS]
+
+
+def with_theta(group: dict, theta) -> dict:
+    g = {k: (list(v) if isinstance(v, (list, tuple)) else v) for k, v in group.items()}
+    for (k, i), v in zip(THETA_FIELDS, theta):
+        if i is None:
+            g[k] = float(v)
+        else:
+            g[k][i] = float(v)
+    return g
+
+
+class Sim:
+    """One swarm: n agents, parameter groups, per-agent uint8 group ids.
+
+    gid: a uint8 CUDA tensor of n ids (kept alive by the handle), or None
+    for a single group.
+    """
+
+    def __init__(self, groups: list[dict], n: int, mode: int, gid: torch.Tensor | None = None):
+        L = lib()
+        self.groups = [dict(g) for g in groups]
+        self.n = int(n)
+        self.mode = int(mode)
+        if gid is not None:
+            if not (gid.is_cuda and gid.dtype == torch.uint8 and gid.is_contiguous() and gid.numel() == n):
+                raise SimError("gid: expected a contiguous uint8 CUDA tensor of n elements")
+        self.gid = gid
+        arr = (_lib.GroupParams * len(groups))(*[group_struct(g) for g in groups])
+        h = ctypes.c_void_p()
+        rc = L.sim_create(arr, len(groups), self.n, _ptr(gid) if len(groups) > 1 else None, self.mode,
+                          ctypes.byref(h))
+        check(rc, "sim_create")
+        self._h = h
+
+    # -- lifecycle --
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sim_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def n_groups(self) -> int:
+        return len(self.groups)
+
+    # -- configuration --
+    def set_params(self, groups: list[dict]):
+        arr = (_lib.GroupParams * len(groups))(*[group_struct(g) for g in groups])
+        check(lib().sim_set_params(self._h, arr, len(groups)), "sim_set_params")
+        self.groups = [dict(g) for g in groups]
+
+    def set_theta(self, theta: np.ndarray):
+        """Replace the 16 differentiable parameters of every group ((G, 16) array)."""
+        theta = np.asarray(theta, dtype=np.float64).reshape(self.n_groups, 16)
+        self.set_params([with_theta(g, t) for g, t in zip(self.groups, theta)])
+
+    def theta(self) -> np.ndarray:
+        return np.array([theta_of(g) for g in self.groups], dtype=np.float32)
+
+    def set_launch(self, block: int = 0, K: int = 0, C: int = 0, block_adj: int = 0):
+        check(lib().sim_set_launch(self._h, int(block), int(block_adj), int(K), int(C)), "sim_set_launch")
+
+    def launch(self) -> dict:
+        """Current launch configuration: block, block_adj, K, C."""
+        v = [ctypes.c_int() for _ in range(4)]
+        check(lib().sim_get_launch(self._h, *[ctypes.byref(x) for x in v]), "sim_get_launch")
+        return dict(zip(("block", "block_adj", "K", "C"), (x.value for x in v)))
+
+    # -- forward --
+    def step(self, state: torch.Tensor, cmd: torch.Tensor, dt: float, nsteps: int, K: int = 0, stream=None):
+        _check_f32(state, 17 * self.n, "state")
+        _check_f32(cmd, 4 * self.n, "cmd")
+        check(lib().sim_step(self._h, _ptr(state), _ptr(cmd), float(dt), int(nsteps), int(K), _stream(stream)),
+              "sim_step")
+
+    def step_host(self, h_state: torch.Tensor, h_cmd: torch.Tensor, d_state: torch.Tensor, d_cmd: torch.Tensor,
+                  dt: float, nsteps: int, K: int = 0, stream=None):
+        """Host-resident state: copy in, step, copy out, wait (pinned host tensors)."""
+        for t, m in ((h_state, 17), (h_cmd, 4)):
+            if t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or t.numel() != m * self.n:
+                raise SimError("host buffers: expected contiguous float32 CPU tensors")
+        _check_f32(d_state, 17 * self.n, "d_state")
+        _check_f32(d_cmd, 4 * self.n, "d_cmd")
+        check(lib().sim_step_host(self._h, _ptr(h_state), _ptr(h_cmd), _ptr(d_state), _ptr(d_cmd), float(dt),
+                                  int(nsteps), int(K), _stream(stream)), "sim_step_host")
+
+    def launches(self, nsteps: int, K: int = 0) -> int:
+        return int(lib().sim_step_launches(self._h, int(nsteps), int(K)))
+
+    def n_segments(self, nsteps: int, C: int = 0) -> int:
+        C = C or self.launch()["C"]
+        return (int(nsteps) + C - 1) // C
+
+    def rollout_forward(self, x0: torch.Tensor, cmd: torch.Tensor, dt: float, nsteps: int, C: int = 0,
+                        ckpt: torch.Tensor | None = None, run_cost: torch.Tensor | None = None, stream=None):
+        """Returns (ckpt, run_cost): ckpt is (S+1, 17 N), ckpt[-1] the final state."""
+        _check_f32(x0, 17 * self.n, "x0")
+        _check_f32(cmd, 4 * self.n, "cmd")
+        S = self.n_segments(nsteps, C)
+        if ckpt is None:
+            ckpt = torch.empty((S + 1, 17 * self.n), dtype=torch.float32, device=x0.device)
+        if run_cost is None:
+            run_cost = torch.empty(self.n, dtype=torch.float32, device=x0.device)
+        check(lib().sim_rollout_forward(self._h, _ptr(x0), _ptr(cmd), float(dt), int(nsteps), int(C), _ptr(ckpt),
+                                        _ptr(run_cost), _stream(stream)), "sim_rollout_forward")
+        return ckpt, run_cost
+
+    # -- adjoint --
+    def workspace_bytes(self, C: int = 0) -> int:
+        return int(lib().sim_workspace_bytes(self._h, int(C)))
+
+    def rollout_backward(self, ckpt: torch.Tensor, cmd: torch.Tensor, dt: float, nsteps: int, dL_dxT: torch.Tensor,
+                         w_run: torch.Tensor | None = None, C: int = 0, per_agent: bool = False,
+                         workspace: torch.Tensor | None = None, stream=None):
+        """Returns (dL/dx0 planar, dL/dtheta (G, 16), per-agent (N, 16) or None)."""
+        _check_f32(dL_dxT, 17 * self.n, "dL_dxT")
+        if w_run is not None:
+            _check_f32(w_run, self.n, "w_run")
+        dev = ckpt.device
+        ws = self.workspace_bytes(C)
+        if workspace is None or workspace.numel() < ws:
+            workspace = torch.empty(max(ws, 1), dtype=torch.uint8, device=dev)
+        dx0 = torch.empty(17 * self.n, dtype=torch.float32, device=dev)
+        dth = torch.empty((self.n_groups, 16), dtype=torch.float32, device=dev)
+        dth_a = torch.empty((self.n, 16), dtype=torch.float32, device=dev) if per_agent else None
+        check(lib().sim_rollout_backward(self._h, _ptr(ckpt), _ptr(cmd), float(dt), int(nsteps), int(C),
+                                         _ptr(dL_dxT), _ptr(w_run), _ptr(dx0), _ptr(dth), _ptr(dth_a),
+                                         _ptr(workspace), ws, _stream(stream)), "sim_rollout_backward")
+        return dx0, dth, dth_a
+
+    # -- status --
+    def n_dead(self, timeout_ms: int = 60000, stream=None) -> int:
+        v = ctypes.c_int64()
+        check(lib().sim_status(self._h, ctypes.byref(v), int(timeout_ms), _stream(stream)), "sim_status")
+        return int(v.value)
+
+    def reset_status(self, stream=None):
+        check(lib().sim_reset_status(self._h, _stream(stream)), "sim_reset_status")
+
+    # -- graphs --
+    def graph(self, state: torch.Tensor, cmd: torch.Tensor, dt: float, nsteps: int, K: int = 0) -> "Graph":
+        return Graph(self, state, cmd, dt, nsteps, K)
+
+
+class Graph:
+    """ceil(nsteps/K) sim_step launches captured once, replayed by launch()."""
+
+    def __init__(self, sim: Sim, state: torch.Tensor, cmd: torch.Tensor, dt: float, nsteps: int, K: int = 0):
+        _check_f32(state, 17 * sim.n, "state")
+        _check_f32(cmd, 4 * sim.n, "cmd")
+        self.sim = sim
+        self._bufs = (state, cmd)
+        self.launches_per_replay = sim.launches(nsteps, K)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        g = ctypes.c_void_p()
+        check(lib().sim_graph_create(sim.handle, _ptr(state), _ptr(cmd), float(dt), int(nsteps), int(K),
+                                     ctypes.c_void_p(side.cuda_stream), ctypes.byref(g)), "sim_graph_create")
+        torch.cuda.current_stream().wait_stream(side)
+        self._g = g
+
+    def launch(self, stream=None):
+        check(lib().sim_graph_launch(self._g, _stream(stream)), "sim_graph_launch")
+
+    def close(self):
+        if getattr(self, "_g", None):
+            lib().sim_graph_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class QuadRollout(torch.autograd.Function):
+    """(theta (G, 16), x0 planar) -> (x_T planar, run_cost (N,)).
+
+    theta = per group (kp[3], kd[3], katt[3], krate[3], m, Jxx, Jyy, Jzz);
+    run_cost_a = sum_{n=1..T} sum_i Omega_{n,i}^2.  The backward pass is the
+    library's discrete adjoint with checkpoints every C steps; it returns
+    gradients for theta and x0.
+    """
+
+    @staticmethod
+    def forward(ctx, theta, x0, sim: Sim, cmd, dt: float, nsteps: int, C: int = 0):
+        th = theta.detach().cpu().numpy()
+        if not np.array_equal(th.astype(np.float32), sim.theta()):
+            sim.set_theta(th)
+        ckpt, rc = sim.rollout_forward(x0.detach().contiguous(), cmd, dt, nsteps, C)
+        ctx.sim, ctx.cmd, ctx.dt, ctx.nsteps, ctx.C = sim, cmd, dt, nsteps, C
+        ctx.theta_device = theta.device
+        ctx.save_for_backward(ckpt)
+        return ckpt[-1].clone(), rc
+
+    @staticmethod
+    def backward(ctx, g_xT, g_rc):
+        (ckpt,) = ctx.saved_tensors
+        sim = ctx.sim
+        if g_xT is None:
+            g_xT = torch.zeros(17 * sim.n, dtype=torch.float32, device=ckpt.device)
+        w = None if g_rc is None else g_rc.contiguous().float()
+        dx0, dth, _ = sim.rollout_backward(ckpt, ctx.cmd, ctx.dt, ctx.nsteps, g_xT.contiguous().float(), w, ctx.C)
+        return dth.to(ctx.theta_device), dx0, None, None, None, None, None
+
+
+def planar(x: torch.Tensor) -> torch.Tensor:
+    """(N, 17) -> flat planar layout (data movement only)."""
+    n = x.shape[0]
+    out = torch.empty(17 * n, dtype=x.dtype, device=x.device)
+    for k in range(4):
+        out[4 * k * n: 4 * k * n + 4 * n] = x[:, 4 * k:4 * k + 4].reshape(-1)
+    out[16 * n:] = x[:, 16]
+    return out
+
+
+def unplanar(flat: torch.Tensor, n: int) -> torch.Tensor:
+    """flat planar layout -> (N, 17)."""
+    x = torch.empty((n, 17), dtype=flat.dtype, device=flat.device)
+    for k in range(4):
+        x[:, 4 * k:4 * k + 4] = flat[4 * k * n: 4 * k * n + 4 * n].reshape(n, 4)
+    x[:, 16] = flat[16 * n: 17 * n]
+    return x

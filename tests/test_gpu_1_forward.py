@@ -1,0 +1,242 @@
+"""Forward path on the GPU (through the C ABI) against the FP64 checker.
+
+Tolerances (FP32 device vs FP64 checker, same FP32 inputs upcast):
+  * one step: |x_gpu - x_ref| <= 1e-5 max(|x_ref|, floor), floors 1 m, 1 m/s,
+    1 (quaternion), 1 rad/s, 100 rad/s;
+  * 1000 closed- or open-loop steps: |p_gpu - p_ref|_inf <= 1e-3 m and the
+    attitude angle 2 acos|<q_gpu, q_ref>| <= 1e-3 rad (quaternions normalised
+    for the metric only).
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2308_12698_b300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+FLOOR = np.array([1.0] * 3 + [1.0] * 3 + [1.0] * 4 + [1.0] * 3 + [100.0] * 4)
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch.device("cuda:0")
+
+
+def gpu_run(wl, dev, nsteps, K=0, x0=None, gid=True, sim_kw=None, block=0):
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    g = torch.from_numpy(wl.gid).to(dev) if (gid and len(wl.groups) > 1) else None
+    sim = Sim(wl.groups, wl.n, wl.mode, gid=g)
+    if block:
+        sim.set_launch(block=block)
+    x = planar(torch.from_numpy(wl.x0 if x0 is None else x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    sim.step(x, cmd, wl.dt, nsteps, K=K)
+    torch.cuda.synchronize()
+    out = unplanar(x, wl.n).cpu().numpy()
+    sim.close()
+    return out
+
+
+def ref_run(orc, wl, nsteps, x0=None):
+    return orc.rollout(wl.groups, wl.gid, wl.x0 if x0 is None else x0, wl.cmd, wl.dt, nsteps, wl.mode)
+
+
+def attitude_err(qa, qb):
+    qa = qa / np.linalg.norm(qa, axis=1, keepdims=True)
+    qb = qb / np.linalg.norm(qb, axis=1, keepdims=True)
+    d = np.clip(np.abs(np.sum(qa * qb, axis=1)), 0.0, 1.0)
+    return 2.0 * np.arccos(d)
+
+
+def check_one_step(got, ref):
+    tol = 1e-5 * np.maximum(np.abs(ref), FLOOR)
+    bad = np.abs(got.astype(np.float64) - ref) > tol
+    assert not bad.any(), (np.argwhere(bad)[:5], (np.abs(got - ref) / tol).max())
+
+
+def check_traj(got, ref, tol=1e-3):
+    perr = np.abs(got[:, 0:3].astype(np.float64) - ref[:, 0:3]).max()
+    aerr = attitude_err(got[:, 6:10].astype(np.float64), ref[:, 6:10]).max()
+    assert perr <= tol and aerr <= tol, (perr, aerr)
+    return perr, aerr
+
+
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 4097])
+@pytest.mark.parametrize("mode", ["open", "closed"])
+def test_one_step(dev, orc, n, mode):
+    wl = W.open_loop(n=n) if mode == "open" else W.closed_loop(n=n)
+    check_one_step(gpu_run(wl, dev, 1, K=1), ref_run(orc, wl, 1))
+
+
+def test_one_step_from_advanced_states(dev, orc):
+    """One step from states deep in a closed-loop transient (tilted, saturated rotors)."""
+    wl = W.closed_loop(n=2000, nsteps=1500)
+    xs = ref_run(orc, wl, 1500).astype(np.float32)
+    check_one_step(gpu_run(wl, dev, 1, K=1, x0=xs), ref_run(orc, wl, 1, x0=xs))
+
+
+def test_open_loop_1000_steps(dev, orc):
+    wl = W.open_loop(n=64, nsteps=1000)
+    check_traj(gpu_run(wl, dev, 1000, K=1), ref_run(orc, wl, 1000))
+
+
+@pytest.mark.parametrize("K", [1, 10, 100])
+def test_closed_loop_1000_steps(dev, orc, K):
+    wl = W.closed_loop(n=5000, nsteps=1000)
+    check_traj(gpu_run(wl, dev, 1000, K=K), ref_run(orc, wl, 1000))
+
+
+def test_fused_substeps_are_bitwise_plain_steps(dev):
+    wl = W.closed_loop(n=3001, nsteps=120)
+    a = gpu_run(wl, dev, 120, K=1)
+    b = gpu_run(wl, dev, 120, K=120)
+    c = gpu_run(wl, dev, 120, K=7)  # 17 launches of 7 + a tail of 1
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(a, c)
+
+
+@pytest.mark.parametrize("shuffle", [False, True])
+def test_heterogeneous_parity(dev, orc, shuffle):
+    wl = W.heterogeneous(sizes=(3, 40, 700, 1200, 33, 5, 2000, 17), nsteps=1000, shuffle=shuffle)
+    check_traj(gpu_run(wl, dev, 1000, K=50), ref_run(orc, wl, 1000))
+
+
+def test_heterogeneous_one_launch_is_bitwise_each_group_alone(dev):
+    wl = W.heterogeneous(sizes=(100, 900, 5000, 64), nsteps=200, shuffle=True)
+    both = gpu_run(wl, dev, 200, K=20)
+    for gi, grp in enumerate(wl.groups):
+        idx = np.nonzero(wl.gid == gi)[0]
+        sub = W.Workload("g", wl.mode, [grp], np.zeros(idx.size, np.uint8), wl.x0[idx], wl.cmd[idx], wl.dt, 200)
+        alone = gpu_run(sub, dev, 200, K=20)
+        np.testing.assert_array_equal(both[idx], alone)
+
+
+def test_one_group_with_ids_is_bitwise_homogeneous(dev):
+    wl = W.closed_loop(n=777, nsteps=50)
+    a = gpu_run(wl, dev, 50, K=10)
+    # the same single group listed twice, every agent in group 1: heterogeneous kernel
+    wl2 = W.Workload("g", wl.mode, [wl.groups[0], wl.groups[0]], np.ones(wl.n, np.uint8), wl.x0, wl.cmd, wl.dt, 50)
+    b = gpu_run(wl2, dev, 50, K=10)
+    np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("block", [32, 64, 128, 256])
+def test_block_sizes_agree(dev, block):
+    wl = W.closed_loop(n=1000, nsteps=30)
+    ref = gpu_run(wl, dev, 30, K=10, block=256)
+    np.testing.assert_array_equal(gpu_run(wl, dev, 30, K=10, block=block), ref)
+
+
+def test_graph_replay_matches_direct(dev):
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    wl = W.closed_loop(n=2048, nsteps=100)
+    direct = gpu_run(wl, dev, 300, K=10)
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    x = planar(torch.from_numpy(wl.x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    g = sim.graph(x, cmd, wl.dt, 100, K=10)
+    assert g.launches_per_replay == 10
+    for _ in range(3):
+        g.launch()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(unplanar(x, wl.n).cpu().numpy(), direct)
+    g.close()
+    sim.close()
+
+
+def test_host_entry_matches_device_entry(dev):
+    from paper_2308_12698_b300.sim import Sim, planar
+    wl = W.closed_loop(n=1500, nsteps=100)
+    direct = gpu_run(wl, dev, 100, K=25)
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    h_state = planar(torch.from_numpy(wl.x0)).pin_memory()
+    h_cmd = torch.from_numpy(wl.cmd).reshape(-1).pin_memory()
+    d_state = torch.empty(17 * wl.n, device=dev)
+    d_cmd = torch.empty(4 * wl.n, device=dev)
+    sim.step_host(h_state, h_cmd, d_state, d_cmd, wl.dt, 100, K=25)
+    from paper_2308_12698_b300.sim import unplanar
+    np.testing.assert_array_equal(unplanar(h_state, wl.n).numpy(), direct)
+    sim.close()
+
+
+def test_full_size_sampled_parity(dev, orc):
+    """1e6 agents, 1000 closed-loop steps in the bench's launch shape; 4096 sampled agents checked."""
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    wl = W.scale_sweep(1_000_000)
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    x = planar(torch.from_numpy(wl.x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    sim.step(x, cmd, wl.dt, 1000, K=100)
+    torch.cuda.synchronize()
+    got = unplanar(x, wl.n).cpu().numpy()
+    idx = np.random.default_rng(0).choice(wl.n, 4096, replace=False)
+    idx = np.concatenate([idx, [0, wl.n - 1]])
+    ref = orc.rollout(wl.groups, wl.gid[idx], wl.x0[idx], wl.cmd[idx], wl.dt, 1000, wl.mode)
+    check_traj(got[idx], ref)
+    assert sim.n_dead() == 0
+    sim.close()
+
+
+def test_nonfinite_agent_is_frozen_and_counted(dev):
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    wl = W.closed_loop(n=500, nsteps=10)
+    x0 = wl.x0.copy()
+    x0[17, 4] = np.nan
+    x0[300, 13] = np.inf
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    x = planar(torch.from_numpy(x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    sim.step(x, cmd, wl.dt, 10, K=5)
+    out = unplanar(x, wl.n).cpu().numpy()
+    assert sim.n_dead() == 2
+    np.testing.assert_array_equal(out[[17, 300]], x0[[17, 300]])
+    ok = np.setdiff1d(np.arange(wl.n), [17, 300])
+    ref = gpu_run(W.Workload("c", wl.mode, wl.groups, wl.gid[ok], wl.x0[ok], wl.cmd[ok], wl.dt, 10), dev, 10, K=5)
+    np.testing.assert_array_equal(out[ok], ref)
+    sim.reset_status()
+    assert sim.n_dead() == 0
+    sim.close()
+
+
+def test_device_argument_errors(dev):
+    import ctypes
+    from paper_2308_12698_b300 import _lib
+    from paper_2308_12698_b300.sim import Sim, SimError
+    L = _lib.lib()
+    wl = W.heterogeneous(sizes=(10, 10), nsteps=1)
+    bad = torch.from_numpy(np.array([0] * 19 + [2], np.uint8)).to(dev)
+    with pytest.raises(SimError, match="group id"):
+        Sim(wl.groups, wl.n, wl.mode, gid=bad)
+    sim = Sim(wl.groups[:1], wl.n, wl.mode)
+    x = torch.zeros(17 * wl.n + 1, device=dev)
+    cmd = torch.zeros(4 * wl.n + 4, device=dev)
+    h = sim.handle
+    assert L.sim_step(h, ctypes.c_void_p(x.data_ptr() + 4), ctypes.c_void_p(cmd.data_ptr()), 1e-3, 1, 1,
+                      None) == _lib.SIM_ERR_ARG  # misaligned
+    assert L.sim_step(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(cmd.data_ptr()), 0.0, 1, 1,
+                      None) == _lib.SIM_ERR_ARG  # dt <= 0
+    assert L.sim_step(h, None, ctypes.c_void_p(cmd.data_ptr()), 1e-3, 1, 1, None) == _lib.SIM_ERR_ARG
+    assert L.sim_set_launch(h, 48, 0, 0, 0) == _lib.SIM_ERR_ARG
+    assert L.sim_set_launch(h, 0, 256, 0, 0) == _lib.SIM_ERR_ARG
+    ws = sim.workspace_bytes(10)
+    buf = torch.empty(ws, dtype=torch.uint8, device=dev)
+    th = torch.empty(16, device=dev)
+    assert L.sim_rollout_backward(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(cmd.data_ptr()), 1e-3, 10, 10,
+                                  ctypes.c_void_p(x.data_ptr()), None, ctypes.c_void_p(x.data_ptr()),
+                                  ctypes.c_void_p(th.data_ptr()), None, ctypes.c_void_p(buf.data_ptr()), ws - 1,
+                                  None) == _lib.SIM_ERR_WORKSPACE
+    sim.close()
+
+
+def test_empty_swarm(dev):
+    from paper_2308_12698_b300.sim import Sim
+    sim = Sim([W.base_group()], 0, 1)
+    x = torch.zeros(0, device=dev)
+    sim.step(x, torch.zeros(0, device=dev), 1e-3, 10)
+    assert sim.n_dead() == 0
+    sim.close()

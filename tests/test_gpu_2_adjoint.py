@@ -1,0 +1,255 @@
+"""Differentiable rollout on the GPU: the hand-written FP32 adjoint against the
+checker's FP64 reverse mode and FP64 central differences.
+
+Loss = sum_a |p_T - goal_a|^2 + w sum_a sum_{n=1..T} sum_i Omega_{n,i}^2.
+Acceptance per gradient block (theta of one agent or group: 16 values;
+dL/dx0 of one agent: 17 values): cosine >= 0.9999, and every component within
+1e-3 of itself plus 1e-4 of the block's largest component.  The floor is the
+FP32 accumulation bound: a 2000-step adjoint of ~1e3 operations per step
+carries a random-walk rounding error of order sqrt(2e6) * 6e-8 ~ 1e-4 of the
+block's scale, which a purely component-relative bar would charge to its
+smallest components.
+
+Agents whose trajectory passes next to a kink of the controller are flagged
+(from the FP64 trajectory): a rotor demand S = Omega_cmd^2 within 1e-3
+Omega_max^2 of 0 (sqrt has an unbounded derivative there and S is a difference
+of terms ~Omega_max^2, so rounding-level state noise moves that step's
+contribution by ~eps Omega_max^2 / S), or within 1e-5 of the rotor ceiling or
+of the acceleration clamp.  Flagged agents are reported separately and held
+to a conditioning bar (cosine >= 0.999, components within 2e-2 of themselves
+plus 2e-3 of the block's largest); unflagged agents to the bar above.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2308_12698_b300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch.device("cuda:0")
+
+
+SQRT_MARGIN, CLAMP_MARGIN = 1e-3, 1e-5
+
+
+def flagged(orc, wl, idx=None):
+    sel = slice(None) if idx is None else idx
+    m = orc.clamp_margins(wl.groups, wl.gid[sel], wl.x0[sel], wl.cmd[sel], wl.dt, wl.nsteps)
+    return (m[:, 0] < SQRT_MARGIN) | (m[:, 1] < CLAMP_MARGIN) | (m[:, 2] < CLAMP_MARGIN)
+
+
+def check_loose(got, ref, what):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    cos = got @ ref / (np.linalg.norm(got) * np.linalg.norm(ref) + 1e-300)
+    err = np.abs(got - ref)
+    tol = 2e-2 * np.abs(ref) + 2e-3 * np.abs(ref).max()
+    assert cos >= 0.999 and np.all(err <= tol), (what, cos, err / tol)
+
+
+def check_block(got, ref, what):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    cos = got @ ref / (np.linalg.norm(got) * np.linalg.norm(ref) + 1e-300)
+    err = np.abs(got - ref)
+    tol = 1e-3 * np.abs(ref) + 1e-4 * np.abs(ref).max()
+    worst = int(np.argmax(err / tol))
+    assert cos >= 0.9999 and np.all(err <= tol), (what, cos, worst, err[worst] / tol[worst], got[worst], ref[worst])
+
+
+def gpu_grad(wl, dev, C, per_agent=True, run=1):
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    gid = torch.from_numpy(wl.gid).to(dev)
+    sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
+    x0 = planar(torch.from_numpy(wl.x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    ckpt, rc = sim.rollout_forward(x0, cmd, wl.dt, wl.nsteps, C=C)
+    xT = unplanar(ckpt[-1], wl.n)
+    goal = torch.from_numpy(wl.goal).to(dev)
+    d = xT[:, 0:3] - goal
+    loss = (d * d).sum(dim=1) + wl.w_omega * rc
+    g = torch.zeros_like(xT)
+    g[:, 0:3] = 2 * d
+    w = torch.full((wl.n,), wl.w_omega, device=dev)
+    outs = []
+    for _ in range(run):
+        dx0, dth, dth_a = sim.rollout_backward(ckpt, cmd, wl.dt, wl.nsteps, planar(g), w, C=C, per_agent=per_agent)
+        torch.cuda.synchronize()
+        outs.append((unplanar(dx0, wl.n).cpu().numpy(), dth.cpu().numpy(),
+                     None if dth_a is None else dth_a.cpu().numpy()))
+    res = dict(loss=loss.cpu().numpy(), rc=rc.cpu().numpy(), xT=xT.cpu().numpy(), outs=outs)
+    sim.close()
+    return res
+
+
+def test_adjoint_matches_fp64_reverse_mode(dev, orc):
+    wl = W.differentiable(n_per_group=8, n_groups=4, nsteps=2000)
+    r = gpu_grad(wl, dev, C=100)
+    dx0, dth, dth_a = r["outs"][0]
+    loss, rdx0, rdth = orc.grad(wl.groups, wl.gid, wl.x0, wl.cmd, wl.dt, wl.nsteps, wl.mode, wl.goal, wl.w_omega)
+    np.testing.assert_allclose(r["loss"], loss, rtol=2e-4, atol=1e-6)
+    fl = flagged(orc, wl)
+    assert (~fl).sum() >= 8, fl.sum()
+    for a in range(wl.n):
+        chk = check_loose if fl[a] else check_block
+        chk(dth_a[a], rdth[a], f"theta agent {a}")
+        chk(dx0[a], rdx0[a], f"x0 agent {a}")
+    for gi in range(len(wl.groups)):
+        check_loose(dth[gi], rdth[wl.gid == gi].sum(axis=0), f"theta group {gi}")
+
+
+def test_adjoint_gentle_rollout_every_agent_strict(dev, orc):
+    """Start at rest, level, at the commanded heading, 0.1 m from the goal, headings over all of
+    [-pi, pi) (every Shepperd branch of the desired attitude): no agent comes near a kink, so
+    every agent meets the strict bar."""
+    base = W.differentiable(n_per_group=64, n_groups=2, nsteps=400)
+    rng = np.random.default_rng(11)
+    goal = (base.x0[:, 0:3] + rng.uniform(-0.1, 0.1, (base.n, 3))).astype(np.float32)
+    cmd = base.cmd.copy()
+    cmd[:, 0:3] = goal
+    cmd[:, 3] = np.linspace(-np.pi, np.pi, base.n, endpoint=False).astype(np.float32)
+    x0 = base.x0.copy()
+    half = cmd[:, 3].astype(np.float64) / 2  # start level at the commanded heading
+    x0[:, 6:10] = np.stack([np.cos(half), 0 * half, 0 * half, np.sin(half)], 1).astype(np.float32)
+    x0[:, 3:6] = 0.0
+    x0[:, 10:13] = 0.0
+    wl = W.Workload("gentle", base.mode, base.groups, base.gid, x0, cmd, base.dt, base.nsteps, goal=goal,
+                    w_omega=1e-6)
+    assert not flagged(orc, wl).any()
+    r = gpu_grad(wl, dev, C=50)
+    dx0, dth, dth_a = r["outs"][0]
+    _, rdx0, rdth = orc.grad(wl.groups, wl.gid, wl.x0, wl.cmd, wl.dt, wl.nsteps, wl.mode, wl.goal, wl.w_omega)
+    for a in range(wl.n):
+        check_block(dth_a[a], rdth[a], f"theta agent {a}")
+        check_block(dx0[a], rdx0[a], f"x0 agent {a}")
+    for gi in range(len(wl.groups)):
+        check_block(dth[gi], rdth[wl.gid == gi].sum(axis=0), f"theta group {gi}")
+
+
+def test_running_cost_matches(dev, orc):
+    wl = W.differentiable(n_per_group=16, n_groups=2, nsteps=500)
+    r = gpu_grad(wl, dev, C=50, per_agent=False)
+    xT, rc = orc.rollout(wl.groups, wl.gid, wl.x0, wl.cmd, wl.dt, wl.nsteps, wl.mode, with_cost=True)
+    np.testing.assert_allclose(r["rc"], rc, rtol=1e-5)
+    np.testing.assert_allclose(r["xT"][:, 0:3], xT[:, 0:3], rtol=0, atol=1e-3)
+
+
+@pytest.mark.parametrize("nsteps,C", [(250, 100), (37, 5), (100, 1), (64, 200)])
+def test_segment_tails(dev, orc, nsteps, C):
+    wl = W.differentiable(n_per_group=4, n_groups=2, nsteps=nsteps)
+    r = gpu_grad(wl, dev, C=C)
+    dx0, dth, dth_a = r["outs"][0]
+    _, rdx0, rdth = orc.grad(wl.groups, wl.gid, wl.x0, wl.cmd, wl.dt, wl.nsteps, wl.mode, wl.goal, wl.w_omega)
+    fl = flagged(orc, wl)
+    for a in range(wl.n):
+        chk = check_loose if fl[a] else check_block
+        chk(dth_a[a], rdth[a], f"theta agent {a}")
+        chk(dx0[a], rdx0[a], f"x0 agent {a}")
+
+
+def test_open_loop_adjoint(dev, orc):
+    base = W.open_loop(n=16, nsteps=300)
+    goal = base.x0[:, 0:3] + 1.0
+    wl = W.Workload("ol", base.mode, base.groups, base.gid, base.x0, base.cmd, base.dt, 300, goal=goal,
+                    w_omega=1e-6)
+    r = gpu_grad(wl, dev, C=30)
+    dx0, dth, dth_a = r["outs"][0]
+    _, rdx0, rdth = orc.grad(wl.groups, wl.gid, wl.x0, wl.cmd, wl.dt, wl.nsteps, wl.mode, wl.goal, wl.w_omega)
+    assert np.all(dth_a[:, :12] == 0)  # gains do not act open loop
+    for a in range(wl.n):
+        check_block(dth_a[a, 12:], rdth[a, 12:], f"m,J agent {a}")
+        check_block(dx0[a], rdx0[a], f"x0 agent {a}")
+
+
+def test_adjoint_is_deterministic(dev):
+    wl = W.differentiable(n_per_group=300, n_groups=3, nsteps=200)
+    r = gpu_grad(wl, dev, C=50, run=2)
+    (a0, b0, c0), (a1, b1, c1) = r["outs"]
+    np.testing.assert_array_equal(a0, a1)
+    np.testing.assert_array_equal(b0, b1)
+    np.testing.assert_array_equal(c0, c1)
+    # group sums are the per-agent contributions summed
+    for gi in range(3):
+        np.testing.assert_allclose(b0[gi], c0[wl.gid == gi].astype(np.float64).sum(axis=0), rtol=1e-4,
+                                   atol=1e-6 * np.abs(b0[gi]).max())
+
+
+def _fd_theta(orc, wl, agents, h=1e-6):
+    """FP64 central differences of each sampled agent's loss w.r.t. its 16 group parameters."""
+    from paper_2308_12698_b300.sim import theta_of, with_theta
+    groups, gid, x0, cmd, goal, meta = [], [], [], [], [], []
+    for a in agents:
+        g0 = wl.groups[wl.gid[a]]
+        th = np.array(theta_of(g0))
+        for k in range(16):
+            for s in (+1, -1):
+                t = th.copy()
+                t[k] += s * h * abs(th[k])
+                groups.append(with_theta(g0, t))
+                gid.append(len(groups) - 1)
+                x0.append(wl.x0[a])
+                cmd.append(wl.cmd[a])
+                goal.append(wl.goal[a])
+                meta.append((a, k, s, h * abs(th[k])))
+    L = orc.loss(groups, np.array(gid), np.array(x0), np.array(cmd), wl.dt, wl.nsteps, wl.mode, np.array(goal),
+                 wl.w_omega)
+    out = np.zeros((len(agents), 16))
+    for j in range(0, len(meta), 2):
+        a, k, _, step = meta[j]
+        out[list(agents).index(a), k] = (L[j] - L[j + 1]) / (2 * step)
+    return out
+
+
+def test_full_size_adjoint_sampled_against_fd(dev, orc):
+    """4096 agents in 4 groups, 2000 steps, C = 100; 16 sampled agents checked against FP64
+    reverse mode (theta and x0) and FP64 central differences (theta)."""
+    wl = W.differentiable()
+    r = gpu_grad(wl, dev, C=100)
+    dx0, dth, dth_a = r["outs"][0]
+    # 16 agents: the first 8 unflagged and the first 8 flagged of a seeded permutation
+    perm = np.random.default_rng(5).permutation(wl.n)[:256]
+    fl = flagged(orc, wl, perm)
+    agents = np.concatenate([perm[~fl][:8], perm[fl][:8]])
+    fla = np.concatenate([np.zeros(8, bool), np.ones(len(agents) - 8, bool)])
+    sub = lambda v: v[agents]  # noqa: E731
+    groups_sub = wl.groups
+    _, rdx0, rdth = orc.grad(groups_sub, sub(wl.gid), sub(wl.x0), sub(wl.cmd), wl.dt, wl.nsteps, wl.mode,
+                             sub(wl.goal), wl.w_omega)
+    fd = _fd_theta(orc, wl, agents)
+    for j, a in enumerate(agents):
+        if fla[j]:
+            # FD itself straddles the kink for these; reverse mode is the reference
+            check_loose(dth_a[a], rdth[j], f"theta agent {a} vs reverse (flagged)")
+            check_loose(dx0[a], rdx0[j], f"x0 agent {a} vs reverse (flagged)")
+        else:
+            check_block(dth_a[a], rdth[j], f"theta agent {a} vs reverse")
+            check_block(dx0[a], rdx0[j], f"x0 agent {a} vs reverse")
+            check_block(dth_a[a], fd[j], f"theta agent {a} vs FD")
+
+
+def test_autograd_function(dev):
+    from paper_2308_12698_b300.sim import QuadRollout, Sim, planar, unplanar
+    wl = W.differentiable(n_per_group=64, n_groups=2, nsteps=300)
+    gid = torch.from_numpy(wl.gid).to(dev)
+    sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
+    theta = torch.tensor(sim.theta(), requires_grad=True)
+    x0 = planar(torch.from_numpy(wl.x0)).to(dev).requires_grad_(True)
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    goal = torch.from_numpy(wl.goal).to(dev)
+    xT, rc = QuadRollout.apply(theta, x0, sim, cmd, wl.dt, wl.nsteps, 30)
+    p = unplanar(xT, wl.n)[:, 0:3]
+    loss = ((p - goal) ** 2).sum() + wl.w_omega * rc.sum()
+    loss.backward()
+    ref = gpu_grad(wl, dev, C=30, per_agent=False)
+    dx0, dth, _ = ref["outs"][0]
+    np.testing.assert_allclose(theta.grad.cpu().numpy(), dth, rtol=1e-5, atol=1e-6 * np.abs(dth).max())
+    np.testing.assert_allclose(unplanar(x0.grad, wl.n).cpu().numpy(), dx0, rtol=1e-5, atol=1e-7)
+    sim.close()
