@@ -201,10 +201,15 @@ def oracle_rate(n_agents: int, nsteps: int, threads: int):
 
 
 def cpu_sample_size(target_s: float, threads: int, nsteps: int) -> int:
-    """Agents of a sample that keeps the checker busy about target_s seconds."""
-    rate, _ = oracle_rate(64 * threads, 200, threads)
-    n = int(rate * target_s / nsteps)
-    return max(256, min(N_AGENTS, n))
+    """Agents of a sample that keeps the checker busy about target_s seconds
+    (calibrated on samples grown until one takes at least 0.3 s)."""
+    n = 16 * threads
+    while True:
+        rate, secs = oracle_rate(n, nsteps, threads)
+        if secs >= 0.3 or n >= N_AGENTS:
+            break
+        n = min(N_AGENTS, n * 4)
+    return max(256, min(N_AGENTS, int(rate * target_s / nsteps)))
 
 
 def cpu_baseline(target_s: float = 10.0) -> dict:
@@ -259,7 +264,7 @@ def workload_config(tuned) -> dict:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-extra", action="store_true", help="headline only (no side measurements)")

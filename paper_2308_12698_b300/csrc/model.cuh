@@ -1,45 +1,77 @@
 // Device model of one quadrotor step, one thread per agent, FP32 in registers.
 //
-//   derivative   Eq. (qd1)-(qd4), Eq. (2), Eq. (3) of arXiv 2308.12698 Sec. III-B,
-//                plus first-order rotor lag and linear drag
-//   controller   cascaded position PD -> attitude P -> normalised rate P ->
-//                G^-1 -> rotor clamp (the paper's inner body-rate loop,
-//                Sec. III-B, completed as documented in quadsim.h)
-//   rk4          classical RK4, command held over the stages (Sec. III-B)
-//   *_vjp        hand-written vector-Jacobian products of the above for the
-//                discrete adjoint
+//   rb_derivative   Eq. (qd1)-(qd4), Eq. (2), Eq. (3) of arXiv 2308.12698 Sec. III-B,
+//                   plus linear drag, for the 13 rigid-body components
+//   rotor lag       Omega' = (Omega_cmd - Omega)/tau_m; linear and decoupled, so
+//                   its four RK4 stages and the RK4 update are applied through
+//                   their exact coefficients (LagCoef) instead of four
+//                   derivative evaluations -- the same RK4 map, fewer operations
+//   controller      cascaded position PD -> attitude P -> normalised rate P ->
+//                   G^-1 -> rotor clamp (the paper's inner body-rate loop,
+//                   Sec. III-B, completed as documented in quadsim.h)
+//   rk4             classical RK4, command held over the stages (Sec. III-B)
+//   *_vjp           hand-written vector-Jacobian products for the discrete adjoint
 //
-// State vector index map (17 floats): p 0-2, v 3-5, q 6-9 (w x y z),
-// omega 10-12, Omega 13-16.
+// State index map (17 floats): p 0-2, v 3-5, q 6-9 (w x y z), omega 10-12,
+// Omega 13-16.  rb_derivative returns 2 q' for the quaternion (q o [0, w]),
+// and the RK4 coefficients of those four components are halved to match.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace qs {
 
-enum { PX = 0, VX = 3, QW = 6, QX = 7, QY = 8, QZ = 9, WX = 10, OM = 13, NX = 17 };
+enum { PX = 0, VX = 3, QW = 6, QX = 7, QY = 8, QZ = 9, WX = 10, OM = 13, NX = 17, NRB = 13 };
 enum { TH_KP = 0, TH_KD = 3, TH_KATT = 6, TH_KRATE = 9, TH_M = 12, TH_J = 13, NTH = 16 };
 
 // Per-group constants, derived on the host in double from the public
-// parameters and rounded once to float.  44 floats, float4-aligned rows.
+// parameters and rounded once to float.  Rows of four floats.
 struct __align__(16) DevGroup {
-  float m, inv_m, g, cd_m;        // mass, 1/m, gravity, c_d/m
-  float Jx, Jy, Jz, inv_tau;      // principal inertias, 1/tau_m
-  float iJx, iJy, iJz, om2max;    // 1/J, omega_max^2
-  float gx, gy, gz, c_d;          // (Jy-Jz)/Jx, (Jz-Jx)/Jy, (Jx-Jy)/Jz, drag
-  float kf, kfLs, kfLc, km;       // kt, kt L sin(a), kt L cos(a), kq
+  // forward: dynamics
+  float T2c, cd_m, g, inv_tau;  // 2 kt / m, c_d / m, gravity, 1 / tau_m
+  float txc, tyc, tzc, om2max;  // kt L sin(a) / Jx, kt L cos(a) / Jy, kq / Jz, omega_max^2
+  float gx, gy, gz, m;          // (Jy - Jz)/Jx, (Jz - Jx)/Jy, (Jx - Jy)/Jz, mass
+  // forward: controller
   float kp[3], a_max;
-  float kd[3], mix0;              // mix0 = 1/(4 kt)
-  float katt2[3], mix1;           // 2 katt; mix1 = 1/(4 kt L sin a)
-  float krt[3], mix2;             // krate*taumax; mix2 = 1/(4 kt L cos a)
-  float krate[3], mix3;           // mix3 = 1/(4 kq)
-  float taumax[3], pad;
+  float kd[3], f0c;             // f0c = m / (4 kt): collective thrust demand -> Omega^2 per rotor
+  float qa[3], pad0;            // mix_i krate_i taumax_i 2 katt_i: error-quaternion component -> Omega^2
+  float wa[3], pad1;            // mix_i krate_i taumax_i: body rate -> Omega^2
+  // adjoint
+  float inv_m, Jx, Jy, Jz;
+  float iJx, iJy, iJz, mix0;    // mix0 = 1 / (4 kt)
+  float krate[3], pad2;
+  float katt2[3], pad3;         // 2 katt
+  float mt[3], pad4;            // mix_i taumax_i  (mix = 1/(4 kt L sin a), 1/(4 kt L cos a), 1/(4 kq))
 };
-static_assert(sizeof(DevGroup) == 44 * 4, "DevGroup layout");
+static_assert(sizeof(DevGroup) == 48 * 4, "DevGroup layout");
 
 struct St {
   float a[NX];
 };
+
+// Step-size constants rounded once on the host.  q components use halved
+// coefficients because rb_derivative returns 2 q'.
+struct StepH {
+  float h, h2, h6;      // h, h/2, h/6
+  float hq, h2q, h6q;   // h/2, h/4, h/12
+};
+
+__device__ __forceinline__ float coef(int i, float a, float aq) { return (i >= QW && i <= QZ) ? aq : a; }
+
+// Exact RK4 coefficients of Omega' = (u - Omega)/tau: stage k sees
+// Omega + c_k (u - Omega) (c_1 = 0), and the step ends at Omega + c5 (u - Omega).
+struct LagCoef {
+  float c2, c3, c4, c5;
+};
+
+__device__ __forceinline__ LagCoef lag_coef(float inv_tau, const StepH& H) {
+  LagCoef L;
+  L.c2 = H.h2 * inv_tau;
+  L.c3 = L.c2 * (1.f - L.c2);
+  L.c4 = H.h * inv_tau * (1.f - L.c3);
+  L.c5 = H.h6 * inv_tau * ((3.f - 2.f * L.c2) + (3.f - 2.f * L.c3 - L.c4));
+  return L;
+}
 
 // ------------------------------------------------------------ planar I/O --
 // Plane k (0..3) holds float4 of components 4k..4k+3, plane 4 component 16.
@@ -65,79 +97,73 @@ __device__ __forceinline__ void store_state(float* __restrict__ base, int64_t n,
 
 __device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
 
-// Body z axis in the inertial frame: third column of R(q).
-__device__ __forceinline__ void body_z(const St& x, float& bx, float& by, float& bz) {
-  const float w = x.a[QW], qx = x.a[QX], qy = x.a[QY], qz = x.a[QZ];
-  bx = 2.f * (qx * qz + w * qy);
-  by = 2.f * (qy * qz - w * qx);
-  bz = 1.f - 2.f * (qx * qx + qy * qy);
-}
-
-// --------------------------------------------------------- the derivative --
-__device__ __forceinline__ void derivative(const DevGroup& P, const St& y, const float u[4], St& d) {
-  const float s1 = y.a[OM] * y.a[OM], s2 = y.a[OM + 1] * y.a[OM + 1];
-  const float s3 = y.a[OM + 2] * y.a[OM + 2], s4 = y.a[OM + 3] * y.a[OM + 3];
-  // Eq. (2)-(3): collective thrust and body torques from the lagged rotor speeds
-  const float fc = P.kf * ((s1 + s2) + (s3 + s4));
-  const float tx = P.kfLs * ((s1 - s2) + (s4 - s3));
-  const float ty = P.kfLc * ((s3 + s4) - (s1 + s2));
-  const float tz = P.km * ((s1 - s2) + (s3 - s4));
-  float bx, by, bz;
-  body_z(y, bx, by, bz);
-  const float T = fc * P.inv_m;
+// ---------------------------------------------------- rigid-body derivative --
+// y: the 13 rigid-body components at a stage; Om: the stage's rotor speeds.
+// d[0..2] = v, d[3..5] = v', d[6..9] = 2 q', d[10..12] = omega'.
+__device__ __forceinline__ void rb_derivative(const DevGroup& P, const float* y, const float Om[4], float* d) {
+  const float s1 = Om[0] * Om[0], s2 = Om[1] * Om[1], s3 = Om[2] * Om[2], s4 = Om[3] * Om[3];
+  // Eq. (2)-(3): collective thrust (as 2 f_c / m) and body torques (as tau / J)
+  const float T2 = P.T2c * ((s1 + s2) + (s3 + s4));
+  const float tx = P.txc * ((s1 - s2) + (s4 - s3));
+  const float ty = P.tyc * ((s3 + s4) - (s1 + s2));
+  const float tz = P.tzc * ((s1 - s2) + (s3 - s4));
+  const float w = y[QW], qx = y[QX], qy = y[QY], qz = y[QZ];
+  const float wx = y[WX], wy = y[WX + 1], wz = y[WX + 2];
+  // R(q) e3 = (2 bx, 2 by, 1 - 2 bxy)
+  const float bx = qx * qz + w * qy, by = qy * qz - w * qx, bxy = qx * qx + qy * qy;
   // Eq. (qd1)
-  d.a[0] = y.a[VX]; d.a[1] = y.a[VX + 1]; d.a[2] = y.a[VX + 2];
+  d[0] = y[VX]; d[1] = y[VX + 1]; d[2] = y[VX + 2];
   // Eq. (qd2) with linear drag
-  d.a[3] = bx * T - P.cd_m * y.a[VX];
-  d.a[4] = by * T - P.cd_m * y.a[VX + 1];
-  d.a[5] = bz * T - P.cd_m * y.a[VX + 2] - P.g;
-  // Eq. (qd3): 1/2 q o [0, omega]
-  const float w = y.a[QW], qx = y.a[QX], qy = y.a[QY], qz = y.a[QZ];
-  const float wx = y.a[WX], wy = y.a[WX + 1], wz = y.a[WX + 2];
-  d.a[QW] = 0.5f * (-qx * wx - qy * wy - qz * wz);
-  d.a[QX] = 0.5f * (w * wx + qy * wz - qz * wy);
-  d.a[QY] = 0.5f * (w * wy + qz * wx - qx * wz);
-  d.a[QZ] = 0.5f * (w * wz + qx * wy - qy * wx);
+  d[3] = T2 * bx - P.cd_m * y[VX];
+  d[4] = T2 * by - P.cd_m * y[VX + 1];
+  d[5] = (0.5f * T2 - P.g) - T2 * bxy - P.cd_m * y[VX + 2];
+  // Eq. (qd3), doubled: q o [0, omega]
+  d[QW] = -qx * wx - qy * wy - qz * wz;
+  d[QX] = w * wx + qy * wz - qz * wy;
+  d[QY] = w * wy + qz * wx - qx * wz;
+  d[QZ] = w * wz + qx * wy - qy * wx;
   // Eq. (qd4): omega' = I^-1 (tau - omega x I omega), diagonal I
-  d.a[WX] = P.gx * (wy * wz) + tx * P.iJx;
-  d.a[WX + 1] = P.gy * (wz * wx) + ty * P.iJy;
-  d.a[WX + 2] = P.gz * (wx * wy) + tz * P.iJz;
-  // rotor lag
-#pragma unroll
-  for (int i = 0; i < 4; ++i) d.a[OM + i] = (u[i] - y.a[OM + i]) * P.inv_tau;
+  d[WX] = P.gx * (wy * wz) + tx;
+  d[WX + 1] = P.gy * (wz * wx) + ty;
+  d[WX + 2] = P.gz * (wx * wy) + tz;
 }
 
 // ---------------------------------------------------------- the controller --
-// Forward intermediates shared by the controller and its VJP.
 struct Ctl {
   float e[3], a[3];
-  bool pass[3];          // acceleration clamp passes the gradient
-  float F[3], b3[3], fc;
+  bool pass[3];  // acceleration clamp passes the gradient
+  float F[3];    // desired acceleration plus gravity (the desired force / m)
+  float b3[3], fc;
   float rn, zd[3];
   float ry, yd[3], xd[3];
-  int branch;            // Shepperd branch 0:w 1:x 2:y 3:z
-  float k;               // 0.5 / sqrt(t) of the branch
+  int branch;    // Shepperd branch 0:w 1:x 2:y 3:z
+  float k;       // 0.5 / sqrt(t) of the branch
   float qd[4];
-  float sgn;             // sign that makes qe.w >= 0
-  float qe[4];           // after the sign fix
-  float wd[3];
-  float S[4];            // Omega^2 demanded by the mixer, before the clamp
+  float sgn;     // sign that makes qe.w >= 0
+  float qe[4];   // after the sign fix
+  float S[4];    // Omega^2 demanded by the mixer, before the clamp
 };
 
-__device__ __forceinline__ void controller_fwd(const DevGroup& P, const St& x, const float4 c, float ch, float sh,
+__device__ __forceinline__ void controller_fwd(const DevGroup& P, const float* x, const float4 c, float ch, float sh,
                                                Ctl& C, float u[4]) {
   const float cc[3] = {c.x, c.y, c.z};
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    C.e[i] = cc[i] - x.a[PX + i];
-    const float ar = P.kp[i] * C.e[i] - P.kd[i] * x.a[VX + i];
+    C.e[i] = cc[i] - x[PX + i];
+    const float ar = P.kp[i] * C.e[i] - P.kd[i] * x[VX + i];
     C.pass[i] = (ar >= -P.a_max) && (ar <= P.a_max);
     C.a[i] = clampf(ar, -P.a_max, P.a_max);
   }
-  C.F[0] = P.m * C.a[0];
-  C.F[1] = P.m * C.a[1];
-  C.F[2] = P.m * (C.a[2] + P.g);
-  body_z(x, C.b3[0], C.b3[1], C.b3[2]);
+  // desired force direction (a + g e3) and its projection on the body z axis
+  C.F[0] = C.a[0];
+  C.F[1] = C.a[1];
+  C.F[2] = C.a[2] + P.g;
+  {
+    const float w = x[QW], qx = x[QX], qy = x[QY], qz = x[QZ];
+    C.b3[0] = 2.f * (qx * qz + w * qy);
+    C.b3[1] = 2.f * (qy * qz - w * qx);
+    C.b3[2] = 1.f - 2.f * (qx * qx + qy * qy);
+  }
   C.fc = C.F[0] * C.b3[0] + C.F[1] * C.b3[1] + C.F[2] * C.b3[2];
   // desired body z along the force, body y from the heading, x = y cross z
   C.rn = rsqrtf(C.F[0] * C.F[0] + C.F[1] * C.F[1] + C.F[2] * C.F[2]);
@@ -178,24 +204,22 @@ __device__ __forceinline__ void controller_fwd(const DevGroup& P, const St& x, c
   } else {
     C.qd[3] = 0.5f * r; C.qd[0] = (R10 - R01) * C.k; C.qd[1] = (R02 + R20) * C.k; C.qd[2] = (R12 + R21) * C.k;
   }
-  // q_e = conj(q) o q_d
-  const float w = x.a[QW], qx = x.a[QX], qy = x.a[QY], qz = x.a[QZ];
+  // q_e = conj(q) o q_d, shortest way round
+  const float w = x[QW], qx = x[QX], qy = x[QY], qz = x[QZ];
   const float dw = C.qd[0], dx = C.qd[1], dy = C.qd[2], dz = C.qd[3];
-  float ew = w * dw + qx * dx + qy * dy + qz * dz;
-  float ex = w * dx - dw * qx - qy * dz + qz * dy;
-  float ey = w * dy - dw * qy - qz * dx + qx * dz;
-  float ez = w * dz - dw * qz - qx * dy + qy * dx;
+  const float ew = w * dw + qx * dx + qy * dy + qz * dz;
+  const float ex = w * dx - dw * qx - qy * dz + qz * dy;
+  const float ey = w * dy - dw * qy - qz * dx + qx * dz;
+  const float ez = w * dz - dw * qz - qx * dy + qy * dx;
   C.sgn = ew < 0.f ? -1.f : 1.f;
   C.qe[0] = C.sgn * ew; C.qe[1] = C.sgn * ex; C.qe[2] = C.sgn * ey; C.qe[3] = C.sgn * ez;
-  // attitude P, then rate P scaled by the axis torque limit
-  float tau[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    C.wd[i] = P.katt2[i] * C.qe[1 + i];
-    tau[i] = P.krt[i] * (C.wd[i] - x.a[WX + i]);
-  }
-  // G^-1 by the orthogonal rows of G, in Omega^2 units
-  const float f0 = P.mix0 * C.fc, f1 = P.mix1 * tau[0], f2 = P.mix2 * tau[1], f3 = P.mix3 * tau[2];
+  // attitude P and normalised rate P, already in Omega^2 units per rotor:
+  // mix_i tau_i = mix_i krate_i taumax_i (2 katt_i qe_i - omega_i)
+  const float f0 = P.f0c * C.fc;
+  const float f1 = P.qa[0] * C.qe[1] - P.wa[0] * x[WX];
+  const float f2 = P.qa[1] * C.qe[2] - P.wa[1] * x[WX + 1];
+  const float f3 = P.qa[2] * C.qe[3] - P.wa[2] * x[WX + 2];
+  // G^-1 by the orthogonal rows of G
   C.S[0] = (f0 + f1) + (f3 - f2);
   C.S[1] = (f0 - f1) - (f2 + f3);
   C.S[2] = (f0 - f1) + (f2 + f3);
@@ -207,115 +231,110 @@ __device__ __forceinline__ void controller_fwd(const DevGroup& P, const St& x, c
   }
 }
 
-__device__ __forceinline__ void controller(const DevGroup& P, const St& x, const float4 c, float ch, float sh,
+__device__ __forceinline__ void controller(const DevGroup& P, const float* x, const float4 c, float ch, float sh,
                                            float u[4]) {
   Ctl C;
   controller_fwd(P, x, c, ch, sh, C, u);
 }
 
 // ------------------------------------------------------------------ RK4 --
-struct StepH {
-  float h, h2, h6;  // h, h/2, h/6 (rounded once on the host)
-};
-
-__device__ __forceinline__ void rk4(const DevGroup& P, St& x, const float u[4], const StepH& H) {
-  St k, y, acc;
-  derivative(P, x, u, k);
+__device__ __forceinline__ void rk4(const DevGroup& P, St& x, const float u[4], const StepH& H, const LagCoef& L) {
+  float dOm[4], Om[4];
 #pragma unroll
-  for (int i = 0; i < NX; ++i) { acc.a[i] = k.a[i]; y.a[i] = x.a[i] + H.h2 * k.a[i]; }
-  derivative(P, y, u, k);
+  for (int i = 0; i < 4; ++i) dOm[i] = u[i] - x.a[OM + i];
+  float k[NRB], y[NRB], acc[NRB];
+  rb_derivative(P, x.a, x.a + OM, k);
 #pragma unroll
-  for (int i = 0; i < NX; ++i) { acc.a[i] += 2.f * k.a[i]; y.a[i] = x.a[i] + H.h2 * k.a[i]; }
-  derivative(P, y, u, k);
+  for (int i = 0; i < NRB; ++i) { acc[i] = k[i]; y[i] = x.a[i] + coef(i, H.h2, H.h2q) * k[i]; }
 #pragma unroll
-  for (int i = 0; i < NX; ++i) { acc.a[i] += 2.f * k.a[i]; y.a[i] = x.a[i] + H.h * k.a[i]; }
-  derivative(P, y, u, k);
+  for (int i = 0; i < 4; ++i) Om[i] = x.a[OM + i] + L.c2 * dOm[i];
+  rb_derivative(P, y, Om, k);
 #pragma unroll
-  for (int i = 0; i < NX; ++i) { acc.a[i] += k.a[i]; x.a[i] = x.a[i] + H.h6 * acc.a[i]; }
+  for (int i = 0; i < NRB; ++i) { acc[i] += 2.f * k[i]; y[i] = x.a[i] + coef(i, H.h2, H.h2q) * k[i]; }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) Om[i] = x.a[OM + i] + L.c3 * dOm[i];
+  rb_derivative(P, y, Om, k);
+#pragma unroll
+  for (int i = 0; i < NRB; ++i) { acc[i] += 2.f * k[i]; y[i] = x.a[i] + coef(i, H.h, H.hq) * k[i]; }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) Om[i] = x.a[OM + i] + L.c4 * dOm[i];
+  rb_derivative(P, y, Om, k);
+#pragma unroll
+  for (int i = 0; i < NRB; ++i) { acc[i] += k[i]; x.a[i] = x.a[i] + coef(i, H.h6, H.h6q) * acc[i]; }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) x.a[OM + i] = x.a[OM + i] + L.c5 * dOm[i];
 }
 
 template <int MODE>
-__device__ __forceinline__ void step(const DevGroup& P, St& x, const float4 c, float ch, float sh, const StepH& H) {
+__device__ __forceinline__ void step(const DevGroup& P, St& x, const float4 c, float ch, float sh, const StepH& H,
+                                     const LagCoef& L) {
   float u[4];
   if (MODE == 1) {
-    controller(P, x, c, ch, sh, u);
+    controller(P, x.a, c, ch, sh, u);
   } else {
     u[0] = c.x; u[1] = c.y; u[2] = c.z; u[3] = c.w;
   }
-  rk4(P, x, u, H);
+  rk4(P, x, u, H, L);
 }
 
 // ------------------------------------------------------------------ VJPs --
-// Accumulates into yb (state cotangent), ub (rotor command cotangent) and
-// tb (theta cotangent) the products of g with the Jacobians of derivative().
-__device__ __forceinline__ void derivative_vjp(const DevGroup& P, const St& y, const St& g, St& yb, float ub[4],
-                                               float tb[NTH]) {
-  const float O1 = y.a[OM], O2 = y.a[OM + 1], O3 = y.a[OM + 2], O4 = y.a[OM + 3];
-  const float s1 = O1 * O1, s2 = O2 * O2, s3 = O3 * O3, s4 = O4 * O4;
-  const float fc = P.kf * ((s1 + s2) + (s3 + s4));
-  const float tx = P.kfLs * ((s1 - s2) + (s4 - s3));
-  const float ty = P.kfLc * ((s3 + s4) - (s1 + s2));
-  const float tz = P.km * ((s1 - s2) + (s3 - s4));
-  const float w = y.a[QW], qx = y.a[QX], qy = y.a[QY], qz = y.a[QZ];
-  const float wx = y.a[WX], wy = y.a[WX + 1], wz = y.a[WX + 2];
-  float bx, by, bz;
-  body_z(y, bx, by, bz);
-  const float T = fc * P.inv_m;
-  const float gvx = g.a[3], gvy = g.a[4], gvz = g.a[5];
-  // p' = v
-  yb.a[VX] += g.a[0]; yb.a[VX + 1] += g.a[1]; yb.a[VX + 2] += g.a[2];
-  // v' = b3 T - cd_m v - g e3
-  yb.a[VX] -= P.cd_m * gvx; yb.a[VX + 1] -= P.cd_m * gvy; yb.a[VX + 2] -= P.cd_m * gvz;
-  const float Tb = gvx * bx + gvy * by + gvz * bz;
-  const float fcb = Tb * P.inv_m;
-  const float gv_v = gvx * y.a[VX] + gvy * y.a[VX + 1] + gvz * y.a[VX + 2];
-  tb[TH_M] += -Tb * T * P.inv_m + gv_v * P.cd_m * P.inv_m;
-  const float bbx = gvx * T, bby = gvy * T, bbz = gvz * T;
-  float qbw = 2.f * (qy * bbx - qx * bby);
-  float qbx = 2.f * (qz * bbx - w * bby) - 4.f * qx * bbz;
-  float qby = 2.f * (w * bbx + qz * bby) - 4.f * qy * bbz;
-  float qbz = 2.f * (qx * bbx + qy * bby);
-  // q' = 1/2 q o [0, omega]
-  const float gw = 0.5f * g.a[QW], gx = 0.5f * g.a[QX], gy = 0.5f * g.a[QY], gz = 0.5f * g.a[QZ];
+// Adds to yb (13), Omb (stage rotor speeds, 4) and tb (theta) the products of
+// g (13) with the Jacobians of rb_derivative at (y, Om).
+__device__ __forceinline__ void rb_derivative_vjp(const DevGroup& P, const float* y, const float Om[4], const float* g,
+                                                  float* yb, float Omb[4], float tb[NTH]) {
+  const float s1 = Om[0] * Om[0], s2 = Om[1] * Om[1], s3 = Om[2] * Om[2], s4 = Om[3] * Om[3];
+  const float T2 = P.T2c * ((s1 + s2) + (s3 + s4));
+  const float Dx = (s1 - s2) + (s4 - s3), Dy = (s3 + s4) - (s1 + s2), Dz = (s1 - s2) + (s3 - s4);
+  const float w = y[QW], qx = y[QX], qy = y[QY], qz = y[QZ];
+  const float wx = y[WX], wy = y[WX + 1], wz = y[WX + 2];
+  const float bx = qx * qz + w * qy, by = qy * qz - w * qx, bxy = qx * qx + qy * qy;
+  const float gvx = g[3], gvy = g[4], gvz = g[5];
+  // p' = v ; v' = T2 (bx, by, 1/2 - bxy) - cd_m v - g e3
+  yb[VX] += g[0] - P.cd_m * gvx;
+  yb[VX + 1] += g[1] - P.cd_m * gvy;
+  yb[VX + 2] += g[2] - P.cd_m * gvz;
+  const float T2b = gvx * bx + gvy * by + gvz * (0.5f - bxy);
+  const float gv_v = gvx * y[VX] + gvy * y[VX + 1] + gvz * y[VX + 2];
+  tb[TH_M] += (gv_v * P.cd_m - T2b * T2) * P.inv_m;
+  const float bbx = gvx * T2, bby = gvy * T2, bbxy = -gvz * T2;
+  float qbw = qy * bbx - qx * bby;
+  float qbx = qz * bbx - w * bby + 2.f * qx * bbxy;
+  float qby = w * bbx + qz * bby + 2.f * qy * bbxy;
+  float qbz = qx * bbx + qy * bby;
+  // 2 q' = q o [0, omega]
+  const float gw = g[QW], gx = g[QX], gy = g[QY], gz = g[QZ];
   qbw += gx * wx + gy * wy + gz * wz;
   qbx += -gw * wx - gy * wz + gz * wy;
   qby += -gw * wy + gx * wz - gz * wx;
   qbz += -gw * wz - gx * wy + gy * wx;
-  yb.a[QW] += qbw; yb.a[QX] += qbx; yb.a[QY] += qby; yb.a[QZ] += qbz;
+  yb[QW] += qbw; yb[QX] += qbx; yb[QY] += qby; yb[QZ] += qbz;
   float wbx = -gw * qx + gx * w + gy * qz - gz * qy;
   float wby = -gw * qy - gx * qz + gy * w + gz * qx;
   float wbz = -gw * qz + gx * qy - gy * qx + gz * w;
-  // omega'_x = ((Jy - Jz) wy wz + tx) / Jx, and cyclic
-  const float nbx = g.a[WX] * P.iJx, nby = g.a[WX + 1] * P.iJy, nbz = g.a[WX + 2] * P.iJz;
-  const float cx = P.Jy - P.Jz, cy = P.Jz - P.Jx, cz = P.Jx - P.Jy;
-  const float dwx = (cx * (wy * wz) + tx) * P.iJx;
-  const float dwy = (cy * (wz * wx) + ty) * P.iJy;
-  const float dwz = (cz * (wx * wy) + tz) * P.iJz;
-  tb[TH_J] += -nbx * dwx - nby * (wz * wx) + nbz * (wx * wy);
-  tb[TH_J + 1] += nbx * (wy * wz) - nby * dwy - nbz * (wx * wy);
-  tb[TH_J + 2] += -nbx * (wy * wz) + nby * (wz * wx) - nbz * dwz;
-  wbx += nby * cy * wz + nbz * cz * wy;
-  wby += nbx * cx * wz + nbz * cz * wx;
-  wbz += nbx * cx * wy + nby * cy * wx;
-  yb.a[WX] += wbx; yb.a[WX + 1] += wby; yb.a[WX + 2] += wbz;
-  // rotors: thrust/torque rows of G on s_i = Omega_i^2, then the lag
-  const float a0 = P.kf * fcb, a1 = P.kfLs * nbx, a2 = P.kfLc * nby, a3 = P.km * nbz;
-  const float sb1 = (a0 + a1) + (a3 - a2);
-  const float sb2 = (a0 - a1) - (a2 + a3);
-  const float sb3 = (a0 - a1) + (a2 + a3);
-  const float sb4 = (a0 + a1) + (a2 - a3);
-  const float gO1 = g.a[OM] * P.inv_tau, gO2 = g.a[OM + 1] * P.inv_tau;
-  const float gO3 = g.a[OM + 2] * P.inv_tau, gO4 = g.a[OM + 3] * P.inv_tau;
-  yb.a[OM] += 2.f * O1 * sb1 - gO1;
-  yb.a[OM + 1] += 2.f * O2 * sb2 - gO2;
-  yb.a[OM + 2] += 2.f * O3 * sb3 - gO3;
-  yb.a[OM + 3] += 2.f * O4 * sb4 - gO4;
-  ub[0] += gO1; ub[1] += gO2; ub[2] += gO3; ub[3] += gO4;
+  // omega'_x = ((Jy - Jz) wy wz + kt L sin(a) Dx) / Jx, and cyclic
+  const float nx = g[WX], ny = g[WX + 1], nz = g[WX + 2];
+  const float dwx = P.gx * (wy * wz) + P.txc * Dx;
+  const float dwy = P.gy * (wz * wx) + P.tyc * Dy;
+  const float dwz = P.gz * (wx * wy) + P.tzc * Dz;
+  const float ax = nx * P.iJx, ay = ny * P.iJy, az = nz * P.iJz;
+  tb[TH_J] += -ax * dwx - ay * (wz * wx) + az * (wx * wy);
+  tb[TH_J + 1] += ax * (wy * wz) - ay * dwy - az * (wx * wy);
+  tb[TH_J + 2] += -ax * (wy * wz) + ay * (wz * wx) - az * dwz;
+  wbx += ny * P.gy * wz + nz * P.gz * wy;
+  wby += nx * P.gx * wz + nz * P.gz * wx;
+  wbz += nx * P.gx * wy + ny * P.gy * wx;
+  yb[WX] += wbx; yb[WX + 1] += wby; yb[WX + 2] += wbz;
+  // rotors: s_i = Omega_i^2 through the thrust and torque rows of G
+  const float a0 = P.T2c * T2b, a1 = P.txc * nx, a2 = P.tyc * ny, a3 = P.tzc * nz;
+  Omb[0] += 2.f * Om[0] * ((a0 + a1) + (a3 - a2));
+  Omb[1] += 2.f * Om[1] * ((a0 - a1) - (a2 + a3));
+  Omb[2] += 2.f * Om[2] * ((a0 - a1) + (a2 + a3));
+  Omb[3] += 2.f * Om[3] * ((a0 + a1) + (a2 - a3));
 }
 
 // Cotangent of the controller: ub (rotor commands) -> xb (state), tb (theta).
-__device__ __forceinline__ void controller_vjp(const DevGroup& P, const St& x, const float4 c, float ch, float sh,
-                                               const float ub[4], St& xb, float tb[NTH]) {
+__device__ __forceinline__ void controller_vjp(const DevGroup& P, const float* x, const float4 c, float ch, float sh,
+                                               const float ub[4], float* xb, float tb[NTH]) {
   Ctl C;
   float u[4];
   controller_fwd(P, x, c, ch, sh, C, u);
@@ -326,31 +345,29 @@ __device__ __forceinline__ void controller_vjp(const DevGroup& P, const St& x, c
     const float s = C.S[i];
     Sb[i] = (s > 0.f && s <= P.om2max) ? ub[i] * 0.5f * rsqrtf(s) : 0.f;
   }
-  const float fcb = P.mix0 * ((Sb[0] + Sb[1]) + (Sb[2] + Sb[3]));
-  float taub[3];
-  taub[0] = P.mix1 * ((Sb[0] - Sb[1]) + (Sb[3] - Sb[2]));
-  taub[1] = P.mix2 * ((Sb[2] + Sb[3]) - (Sb[0] + Sb[1]));
-  taub[2] = P.mix3 * ((Sb[0] - Sb[1]) + (Sb[2] - Sb[3]));
-  // tau = krate taumax (wd - omega), wd = 2 katt qe
+  const float f0b = (Sb[0] + Sb[1]) + (Sb[2] + Sb[3]);
+  float fb[3];
+  fb[0] = (Sb[0] - Sb[1]) + (Sb[3] - Sb[2]);
+  fb[1] = (Sb[2] + Sb[3]) - (Sb[0] + Sb[1]);
+  fb[2] = (Sb[0] - Sb[1]) + (Sb[2] - Sb[3]);
+  // f_i = mt_i krate_i (2 katt_i qe_i - omega_i)
   float qeb[4];
   qeb[0] = 0.f;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const float err = C.wd[i] - x.a[WX + i];
-    tb[TH_KRATE + i] += taub[i] * P.taumax[i] * err;
-    const float wdb = taub[i] * P.krt[i];
-    xb.a[WX + i] -= wdb;
-    tb[TH_KATT + i] += wdb * 2.f * C.qe[1 + i];
-    qeb[1 + i] = wdb * P.katt2[i] * C.sgn;  // through the sign fix
+    tb[TH_KRATE + i] += fb[i] * P.mt[i] * (P.katt2[i] * C.qe[1 + i] - x[WX + i]);
+    tb[TH_KATT + i] += fb[i] * P.wa[i] * 2.f * C.qe[1 + i];
+    xb[WX + i] -= fb[i] * P.wa[i];
+    qeb[1 + i] = fb[i] * P.qa[i] * C.sgn;  // through the sign fix
   }
   // qe = conj(q) o qd
-  const float w = x.a[QW], qx = x.a[QX], qy = x.a[QY], qz = x.a[QZ];
+  const float w = x[QW], qx = x[QX], qy = x[QY], qz = x[QZ];
   const float dw = C.qd[0], dx = C.qd[1], dy = C.qd[2], dz = C.qd[3];
   const float Ew = qeb[0], Ex = qeb[1], Ey = qeb[2], Ez = qeb[3];
-  xb.a[QW] += Ew * dw + Ex * dx + Ey * dy + Ez * dz;
-  xb.a[QX] += Ew * dx - Ex * dw + Ey * dz - Ez * dy;
-  xb.a[QY] += Ew * dy - Ex * dz - Ey * dw + Ez * dx;
-  xb.a[QZ] += Ew * dz + Ex * dy - Ey * dx - Ez * dw;
+  float qbw = Ew * dw + Ex * dx + Ey * dy + Ez * dz;
+  float qbx = Ew * dx - Ex * dw + Ey * dz - Ez * dy;
+  float qby = Ew * dy - Ex * dz - Ey * dw + Ez * dx;
+  float qbz = Ew * dz + Ex * dy - Ey * dx - Ez * dw;
   float qdb[4];
   qdb[0] = Ew * w - Ex * qx - Ey * qy - Ez * qz;
   qdb[1] = Ew * qx + Ex * w - Ey * qz + Ez * qy;
@@ -391,7 +408,6 @@ __device__ __forceinline__ void controller_vjp(const DevGroup& P, const St& x, c
     const float tb_ = (0.5f * qdb[3] - k2x2 * kb) * k;
     Rb[0][0] -= tb_; Rb[1][1] -= tb_; Rb[2][2] += tb_;
   }
-  // columns of R_des
   float xdb[3] = {Rb[0][0], Rb[1][0], Rb[2][0]};
   float ydb[3] = {Rb[0][1], Rb[1][1], Rb[2][1]};
   float zdb[3] = {Rb[0][2], Rb[1][2], Rb[2][2]};
@@ -407,30 +423,32 @@ __device__ __forceinline__ void controller_vjp(const DevGroup& P, const St& x, c
   const float yrb0 = (ydb[0] - C.yd[0] * yy) * C.ry;
   const float yrb1 = (ydb[1] - C.yd[1] * yy) * C.ry;
   const float yrb2 = (ydb[2] - C.yd[2] * yy) * C.ry;
-  // yr = zd x (ch, sh, 0):  zdb += (ch, sh, 0) x yrb
+  // yr = zd x (ch, sh, 0)
   zdb[0] += sh * yrb2;
   zdb[1] += -ch * yrb2;
   zdb[2] += ch * yrb1 - sh * yrb0;
-  // zd = F / |F|
+  // zd = F / |F|; f0 = f0c (F . b3), f0c = m / (4 kt)
+  const float fcb = f0b * P.f0c;
+  tb[TH_M] += f0b * C.fc * P.mix0;
   const float zz = C.zd[0] * zdb[0] + C.zd[1] * zdb[1] + C.zd[2] * zdb[2];
   float Fb[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) Fb[i] = (zdb[i] - C.zd[i] * zz) * C.rn + fcb * C.b3[i];
-  // fc = F . b3  ->  b3 -> q
+  // b3 = R(q) e3 -> q
   const float bbx = fcb * C.F[0], bby = fcb * C.F[1], bbz = fcb * C.F[2];
-  xb.a[QW] += 2.f * (qy * bbx - qx * bby);
-  xb.a[QX] += 2.f * (qz * bbx - w * bby) - 4.f * qx * bbz;
-  xb.a[QY] += 2.f * (w * bbx + qz * bby) - 4.f * qy * bbz;
-  xb.a[QZ] += 2.f * (qx * bbx + qy * bby);
-  // F = m (a + g e3)
-  tb[TH_M] += Fb[0] * C.a[0] + Fb[1] * C.a[1] + Fb[2] * (C.a[2] + P.g);
+  qbw += 2.f * (qy * bbx - qx * bby);
+  qbx += 2.f * (qz * bbx - w * bby) - 4.f * qx * bbz;
+  qby += 2.f * (w * bbx + qz * bby) - 4.f * qy * bbz;
+  qbz += 2.f * (qx * bbx + qy * bby);
+  xb[QW] += qbw; xb[QX] += qbx; xb[QY] += qby; xb[QZ] += qbz;
+  // F = a + g e3, a = clamp(kp e - kd v)
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const float arb = C.pass[i] ? P.m * Fb[i] : 0.f;
+    const float arb = C.pass[i] ? Fb[i] : 0.f;
     tb[TH_KP + i] += arb * C.e[i];
-    tb[TH_KD + i] -= arb * x.a[VX + i];
-    xb.a[PX + i] -= P.kp[i] * arb;
-    xb.a[VX + i] -= P.kd[i] * arb;
+    tb[TH_KD + i] -= arb * x[VX + i];
+    xb[PX + i] -= P.kp[i] * arb;
+    xb[VX + i] -= P.kd[i] * arb;
   }
 }
 
@@ -438,46 +456,71 @@ __device__ __forceinline__ void controller_vjp(const DevGroup& P, const St& x, c
 // tb += (d x_{n+1} / d theta)^T lam.  x is the step-start state.
 template <int MODE>
 __device__ __forceinline__ void step_vjp(const DevGroup& P, const St& x, const float4 c, float ch, float sh,
-                                         const StepH& H, St& lam, float tb[NTH]) {
+                                         const StepH& H, const LagCoef& L, St& lam, float tb[NTH]) {
   float u[4];
   if (MODE == 1) {
-    controller(P, x, c, ch, sh, u);
+    controller(P, x.a, c, ch, sh, u);
   } else {
     u[0] = c.x; u[1] = c.y; u[2] = c.z; u[3] = c.w;
   }
-  St k, y2, y3, y4;
-  derivative(P, x, u, k);
+  float dOm[4], Om2[4], Om3[4], Om4[4];
 #pragma unroll
-  for (int i = 0; i < NX; ++i) y2.a[i] = x.a[i] + H.h2 * k.a[i];
-  derivative(P, y2, u, k);
+  for (int i = 0; i < 4; ++i) {
+    dOm[i] = u[i] - x.a[OM + i];
+    Om2[i] = x.a[OM + i] + L.c2 * dOm[i];
+    Om3[i] = x.a[OM + i] + L.c3 * dOm[i];
+    Om4[i] = x.a[OM + i] + L.c4 * dOm[i];
+  }
+  float k[NRB], y2[NRB], y3[NRB], y4[NRB];
+  rb_derivative(P, x.a, x.a + OM, k);
 #pragma unroll
-  for (int i = 0; i < NX; ++i) y3.a[i] = x.a[i] + H.h2 * k.a[i];
-  derivative(P, y3, u, k);
+  for (int i = 0; i < NRB; ++i) y2[i] = x.a[i] + coef(i, H.h2, H.h2q) * k[i];
+  rb_derivative(P, y2, Om2, k);
 #pragma unroll
-  for (int i = 0; i < NX; ++i) y4.a[i] = x.a[i] + H.h * k.a[i];
-  const float h3 = 2.f * H.h6;
-  float ub[4] = {0.f, 0.f, 0.f, 0.f};
-  St xb = lam, g, yb;
-  // k4 at y4 = x + h k3
+  for (int i = 0; i < NRB; ++i) y3[i] = x.a[i] + coef(i, H.h2, H.h2q) * k[i];
+  rb_derivative(P, y3, Om3, k);
 #pragma unroll
-  for (int i = 0; i < NX; ++i) { g.a[i] = H.h6 * lam.a[i]; yb.a[i] = 0.f; }
-  derivative_vjp(P, y4, g, yb, ub, tb);
-  // k3 at y3 = x + h/2 k2
+  for (int i = 0; i < NRB; ++i) y4[i] = x.a[i] + coef(i, H.h, H.hq) * k[i];
+  float xb[NX], g[NRB], yb[NRB];
+  float Ob1[4] = {0.f, 0.f, 0.f, 0.f}, Ob2[4] = {0.f, 0.f, 0.f, 0.f};
+  float Ob3[4] = {0.f, 0.f, 0.f, 0.f}, Ob4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-  for (int i = 0; i < NX; ++i) { xb.a[i] += yb.a[i]; g.a[i] = h3 * lam.a[i] + H.h * yb.a[i]; yb.a[i] = 0.f; }
-  derivative_vjp(P, y3, g, yb, ub, tb);
-  // k2 at y2 = x + h/2 k1
+  for (int i = 0; i < NRB; ++i) { xb[i] = lam.a[i]; g[i] = coef(i, H.h6, H.h6q) * lam.a[i]; yb[i] = 0.f; }
+  rb_derivative_vjp(P, y4, Om4, g, yb, Ob4, tb);
 #pragma unroll
-  for (int i = 0; i < NX; ++i) { xb.a[i] += yb.a[i]; g.a[i] = h3 * lam.a[i] + H.h2 * yb.a[i]; yb.a[i] = 0.f; }
-  derivative_vjp(P, y2, g, yb, ub, tb);
-  // k1 at x
+  for (int i = 0; i < NRB; ++i) {
+    xb[i] += yb[i];
+    g[i] = 2.f * coef(i, H.h6, H.h6q) * lam.a[i] + coef(i, H.h, H.hq) * yb[i];
+    yb[i] = 0.f;
+  }
+  rb_derivative_vjp(P, y3, Om3, g, yb, Ob3, tb);
 #pragma unroll
-  for (int i = 0; i < NX; ++i) { xb.a[i] += yb.a[i]; g.a[i] = H.h6 * lam.a[i] + H.h2 * yb.a[i]; yb.a[i] = 0.f; }
-  derivative_vjp(P, x, g, yb, ub, tb);
+  for (int i = 0; i < NRB; ++i) {
+    xb[i] += yb[i];
+    g[i] = 2.f * coef(i, H.h6, H.h6q) * lam.a[i] + coef(i, H.h2, H.h2q) * yb[i];
+    yb[i] = 0.f;
+  }
+  rb_derivative_vjp(P, y2, Om2, g, yb, Ob2, tb);
 #pragma unroll
-  for (int i = 0; i < NX; ++i) xb.a[i] += yb.a[i];
-  if (MODE == 1) controller_vjp(P, x, c, ch, sh, ub, xb, tb);
-  lam = xb;
+  for (int i = 0; i < NRB; ++i) {
+    xb[i] += yb[i];
+    g[i] = coef(i, H.h6, H.h6q) * lam.a[i] + coef(i, H.h2, H.h2q) * yb[i];
+    yb[i] = 0.f;
+  }
+  rb_derivative_vjp(P, x.a, x.a + OM, g, yb, Ob1, tb);
+#pragma unroll
+  for (int i = 0; i < NRB; ++i) xb[i] += yb[i];
+  // rotor lag: stage k sees Omega + c_k (u - Omega); the step ends at Omega + c5 (u - Omega)
+  float ub[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float lO = lam.a[OM + i];
+    ub[i] = L.c5 * lO + L.c2 * Ob2[i] + L.c3 * Ob3[i] + L.c4 * Ob4[i];
+    xb[OM + i] = (lO - ub[i]) + Ob1[i] + Ob2[i] + Ob3[i] + Ob4[i];
+  }
+  if (MODE == 1) controller_vjp(P, x.a, c, ch, sh, ub, xb, tb);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) lam.a[i] = xb[i];
 }
 
 }  // namespace qs

@@ -72,9 +72,11 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs A, const DevGroup P0
     if (MODE == 1) sincosf(c.w, &sh, &ch);
     if (HETERO) {
       const DevGroup P = sg[A.gid[i]];
-      for (int k = 0; k < A.K; ++k) step<MODE>(P, x, c, ch, sh, A.H);
+      const LagCoef L = lag_coef(P.inv_tau, A.H);
+      for (int k = 0; k < A.K; ++k) step<MODE>(P, x, c, ch, sh, A.H, L);
     } else {
-      for (int k = 0; k < A.K; ++k) step<MODE>(P0, x, c, ch, sh, A.H);
+      const LagCoef L = lag_coef(P0.inv_tau, A.H);
+      for (int k = 0; k < A.K; ++k) step<MODE>(P0, x, c, ch, sh, A.H, L);
     }
     if (all_finite(x)) {
       store_state(A.state, A.n, i, x);
@@ -121,11 +123,12 @@ __global__ void __launch_bounds__(256) ckpt_kernel(CkptArgs A, const DevGroup P0
     float ch = 0.f, sh = 0.f;
     if (MODE == 1) sincosf(c.w, &sh, &ch);
     const DevGroup P = HETERO ? sg[A.gid[i]] : P0;
+    const LagCoef L = lag_coef(P.inv_tau, A.H);
     float rc = 0.f;
     for (int s = 0; s < A.S; ++s) {
       const int len = (int)min((int64_t)A.C, A.nsteps - (int64_t)s * A.C);
       for (int k = 0; k < len; ++k) {
-        step<MODE>(P, x, c, ch, sh, A.H);
+        step<MODE>(P, x, c, ch, sh, A.H, L);
         rc += (x.a[OM] * x.a[OM] + x.a[OM + 1] * x.a[OM + 1]) + (x.a[OM + 2] * x.a[OM + 2] + x.a[OM + 3] * x.a[OM + 3]);
       }
       store_state(A.ckpt + (s + 1) * plane, A.n, i, x);
@@ -181,6 +184,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
     if (i < A.n && A.status[i] == 0) {
       g = A.gid ? (int)A.gid[i] : 0;
       const DevGroup P = sg[g];
+      const LagCoef L = lag_coef(P.inv_tau, A.H);
       const float4 c = A.cmd[i];
       float ch = 0.f, sh = 0.f;
       if (MODE == 1) sincosf(c.w, &sh, &ch);
@@ -196,11 +200,11 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
         load_state(A.ckpt + (int64_t)s * plane, A.n, i, x);
         for (int j = 0; j < len; ++j) {
           store_state(A.scratch + j * sstep, nthreads, slot, x);
-          if (j + 1 < len) step<MODE>(P, x, c, ch, sh, A.H);
+          if (j + 1 < len) step<MODE>(P, x, c, ch, sh, A.H, L);
         }
         for (int j = len - 1; j >= 0; --j) {
           load_state(A.scratch + j * sstep, nthreads, slot, x);
-          step_vjp<MODE>(P, x, c, ch, sh, A.H, lam, tb);
+          step_vjp<MODE>(P, x, c, ch, sh, A.H, L, lam, tb);
           if (n0 + j >= 1) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) lam.a[OM + q] += 2.f * w * x.a[OM + q];
@@ -276,25 +280,35 @@ DevGroup derive(const sim_group_params_t& p) {
   const double m = p.m, Jx = p.Jxx, Jy = p.Jyy, Jz = p.Jzz, kt = p.kt, kq = p.kq;
   const double Ls = (double)p.L * std::sin((double)p.alpha), Lc = (double)p.L * std::cos((double)p.alpha);
   const double om2 = (double)p.omega_max * p.omega_max;
-  d.m = p.m; d.inv_m = (float)(1.0 / m); d.g = p.g; d.cd_m = (float)(p.c_d / m);
-  d.Jx = p.Jxx; d.Jy = p.Jyy; d.Jz = p.Jzz; d.inv_tau = (float)(1.0 / p.tau_m);
-  d.iJx = (float)(1.0 / Jx); d.iJy = (float)(1.0 / Jy); d.iJz = (float)(1.0 / Jz); d.om2max = (float)om2;
-  d.gx = (float)((Jy - Jz) / Jx); d.gy = (float)((Jz - Jx) / Jy); d.gz = (float)((Jx - Jy) / Jz); d.c_d = p.c_d;
-  d.kf = p.kt; d.kfLs = (float)(kt * Ls); d.kfLc = (float)(kt * Lc); d.km = p.kq;
   const double taumax[3] = {2.0 * Ls * kt * om2, 2.0 * Lc * kt * om2, 2.0 * kq * om2};
+  const double mix[3] = {1.0 / (4.0 * kt * Ls), 1.0 / (4.0 * kt * Lc), 1.0 / (4.0 * kq)};
+  d.T2c = (float)(2.0 * kt / m);
+  d.cd_m = (float)(p.c_d / m);
+  d.g = p.g;
+  d.inv_tau = (float)(1.0 / p.tau_m);
+  d.txc = (float)(kt * Ls / Jx);
+  d.tyc = (float)(kt * Lc / Jy);
+  d.tzc = (float)(kq / Jz);
+  d.om2max = (float)om2;
+  d.gx = (float)((Jy - Jz) / Jx);
+  d.gy = (float)((Jz - Jx) / Jy);
+  d.gz = (float)((Jx - Jy) / Jz);
+  d.m = p.m;
   for (int i = 0; i < 3; ++i) {
     d.kp[i] = p.kp[i];
     d.kd[i] = p.kd[i];
-    d.katt2[i] = (float)(2.0 * p.katt[i]);
-    d.krt[i] = (float)(p.krate[i] * taumax[i]);
+    d.qa[i] = (float)(mix[i] * p.krate[i] * taumax[i] * 2.0 * p.katt[i]);
+    d.wa[i] = (float)(mix[i] * p.krate[i] * taumax[i]);
     d.krate[i] = p.krate[i];
-    d.taumax[i] = (float)taumax[i];
+    d.katt2[i] = (float)(2.0 * p.katt[i]);
+    d.mt[i] = (float)(mix[i] * taumax[i]);
   }
   d.a_max = p.a_max;
+  d.f0c = (float)(m / (4.0 * kt));
+  d.inv_m = (float)(1.0 / m);
+  d.Jx = p.Jxx; d.Jy = p.Jyy; d.Jz = p.Jzz;
+  d.iJx = (float)(1.0 / Jx); d.iJy = (float)(1.0 / Jy); d.iJz = (float)(1.0 / Jz);
   d.mix0 = (float)(1.0 / (4.0 * kt));
-  d.mix1 = (float)(1.0 / (4.0 * kt * Ls));
-  d.mix2 = (float)(1.0 / (4.0 * kt * Lc));
-  d.mix3 = (float)(1.0 / (4.0 * kq));
   return d;
 }
 
@@ -316,6 +330,9 @@ StepH make_h(float dt) {
   H.h = dt;
   H.h2 = (float)(0.5 * (double)dt);
   H.h6 = (float)((double)dt / 6.0);
+  H.hq = (float)(0.5 * (double)dt);
+  H.h2q = (float)(0.25 * (double)dt);
+  H.h6q = (float)((double)dt / 12.0);
   return H;
 }
 
