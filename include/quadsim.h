@@ -145,6 +145,35 @@ int sim_rollout_backward(sim_handle_t h, const float* d_ckpt, const float* d_cmd
                          float* d_dL_dtheta, float* d_dL_dtheta_agent, void* d_workspace, size_t ws_bytes,
                          void* stream);
 
+/* Workspace-free variant of sim_rollout_backward (the paper has no
+ * counterpart; it exists for this library's callers).  Some callers may not
+ * allocate device memory once they are running -- for example a real-time
+ * control loop that reserves all of its memory at start-up, or a plug-in
+ * whose host application owns every device allocation and hands out no
+ * workspace -- so they cannot provide the workspace sim_rollout_backward
+ * needs.  This entry point takes the same arguments minus the workspace and
+ * allocates nothing (no cudaMalloc, no cudaFree, no allocating library
+ * call): its scratch is a fixed array of SIM_NOALLOC_SCRATCH_BYTES (32 MiB)
+ * inside the library, which every GPU that loads the library holds until the
+ * process exits.
+ *   - The grid is capped so that its scratch fits in the array; the results
+ *     equal sim_rollout_backward's (per-agent outputs bit for bit, the group
+ *     sums up to the order of the final reduction), possibly slower.
+ *   - SIM_ERR_WORKSPACE if even one block does not fit, i.e. when
+ *     ckpt_C * 68 B * (adjoint block size) + n_groups * 64 B exceeds
+ *     32 MiB (ckpt_C above about 3,800 with the default 128-thread adjoint
+ *     block).
+ *   - The first call on a device looks up the array's device address for
+ *     that device (cudaGetSymbolAddress); make that first call before any
+ *     stream capture.
+ *   - Every call shares the one array: calls whose work overlaps on the GPU
+ *     (other streams, other threads) race and corrupt each other's results.
+ *     Serialise them. */
+#define SIM_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+int sim_rollout_backward_noalloc(sim_handle_t h, const float* d_ckpt, const float* d_cmd, float dt, int64_t nsteps,
+                                 int ckpt_C, const float* d_dL_dxT, const float* d_w_run, float* d_dL_dx0,
+                                 float* d_dL_dtheta, float* d_dL_dtheta_agent, void* stream);
+
 /* Launch configuration: threads per block of the forward kernels (a
  * multiple of 32, <= 256) and of the adjoint kernel (a multiple of 32,
  * <= 128), and the defaults used when a call passes 0 for the steps fused

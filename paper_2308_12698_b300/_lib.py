@@ -17,12 +17,13 @@ SIM_OPEN_LOOP = 0
 SIM_CLOSED_LOOP = 1
 SIM_MAX_GROUPS = 32
 SIM_NTHETA = 16
+SIM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 #: Every entry point include/quadsim.h declares.
 EXPORTS = ("sim_create", "sim_set_params", "sim_step", "sim_step_host", "sim_rollout_forward",
            "sim_workspace_bytes", "sim_rollout_backward", "sim_set_launch", "sim_get_launch", "sim_status",
            "sim_reset_status", "sim_graph_create", "sim_graph_launch", "sim_graph_destroy", "sim_step_launches",
-           "sim_destroy", "sim_error_string")
+           "sim_destroy", "sim_error_string", "sim_rollout_backward_noalloc")
 
 
 class GroupParams(ctypes.Structure):
@@ -67,6 +68,7 @@ def lib():
         "sim_rollout_forward": (I, [P, P, P, F, I64, I, P, P, P]),
         "sim_workspace_bytes": (SZ, [P, I]),
         "sim_rollout_backward": (I, [P, P, P, F, I64, I, P, P, P, P, P, P, SZ, P]),
+        "sim_rollout_backward_noalloc": (I, [P, P, P, F, I64, I, P, P, P, P, P, P]),
         "sim_set_launch": (I, [P, I, I, I, I]),
         "sim_get_launch": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
         "sim_status": (I, [P, ctypes.POINTER(I64), I, P]),

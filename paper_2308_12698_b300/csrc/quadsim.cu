@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <thread>
 
@@ -668,6 +669,97 @@ int sim_rollout_backward(sim_handle_t h, const float* d_ckpt, const float* d_cmd
   A.th_agent = d_dL_dtheta_agent;
   A.scratch = static_cast<float*>(d_workspace);
   A.partials = reinterpret_cast<float*>(static_cast<char*>(d_workspace) + sbytes);
+  A.n = h->n;
+  A.nsteps = nsteps;
+  A.C = C;
+  A.S = (int)((nsteps + C - 1) / C);
+  A.n_groups = h->n_groups;
+  A.H = make_h(dt);
+  A.groups = h->d_groups;
+  const size_t smem = adj_smem(h);
+  if (h->mode == SIM_CLOSED_LOOP) adjoint_kernel<1><<<grid, h->block_adj, smem, st>>>(A);
+  else adjoint_kernel<0><<<grid, h->block_adj, smem, st>>>(A);
+  if (cudaGetLastError() != cudaSuccess) return SIM_ERR_CUDA;
+  reduce_partials<<<h->n_groups * NTH, 256, 0, st>>>(A.partials, grid, h->n_groups * NTH, d_dL_dtheta);
+  return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ERR_CUDA;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------ workspace-free adjoint --
+// Scratch for sim_rollout_backward_noalloc: a fixed array in the module's own
+// device memory, present on every GPU that loads the library until exit.
+// Device code could name it directly; host code needs its device address,
+// which cudaGetSymbolAddress returns per device (the host-side symbol is only
+// a stand-in).  Every call shares it: scratch is written before it is read
+// and the per-block partials are written in full, so nothing is cleared.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SIM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on `device`, looked up once per device
+// with that device current.
+int noalloc_scratch(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices) return SIM_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return SIM_ERR_CUDA;
+    if (cur != device && cudaSetDevice(device) != cudaSuccess) return SIM_ERR_CUDA;
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (cur != device) cudaSetDevice(cur);
+    if (e != cudaSuccess || !p) return SIM_ERR_CUDA;
+    g_noalloc_ptr[device] = p;
+  }
+  *out = g_noalloc_ptr[device];
+  return SIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sim_rollout_backward_noalloc(sim_handle_t h, const float* d_ckpt, const float* d_cmd, float dt, int64_t nsteps,
+                                 int ckpt_C, const float* d_dL_dxT, const float* d_w_run, float* d_dL_dx0,
+                                 float* d_dL_dtheta, float* d_dL_dtheta_agent, void* stream) {
+  if (!h || nsteps < 1 || ckpt_C < 0 || !(dt > 0.f) || !std::isfinite(dt)) return SIM_ERR_ARG;
+  if (!d_dL_dtheta) return SIM_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (h->n == 0) {
+    return cudaMemsetAsync(d_dL_dtheta, 0, sizeof(float) * h->n_groups * NTH, st) == cudaSuccess ? SIM_OK
+                                                                                                : SIM_ERR_CUDA;
+  }
+  if (!d_ckpt || !d_cmd || !d_dL_dxT || !d_dL_dx0) return SIM_ERR_ARG;
+  if (!aligned16(d_ckpt) || !aligned16(d_cmd) || !aligned16(d_dL_dxT) || !aligned16(d_dL_dx0)) return SIM_ERR_ARG;
+  const int C = ckpt_C > 0 ? ckpt_C : h->C;
+  // as many resident blocks as the usual grid, but no more than the fixed
+  // scratch holds: per block, C step-start states per thread plus one partial
+  const size_t per_block = (size_t)C * NX * sizeof(float) * h->block_adj + (size_t)h->n_groups * NTH * sizeof(float);
+  const size_t fit = (SIM_NOALLOC_SCRATCH_BYTES - 512) / per_block;
+  if (fit < 1) return SIM_ERR_WORKSPACE;
+  const int grid = (int)std::min<size_t>((size_t)adj_grid(h), fit);
+  const size_t sbytes = scratch_bytes(h, C, grid);
+  if (sbytes + align256((size_t)grid * h->n_groups * NTH * sizeof(float)) > SIM_NOALLOC_SCRATCH_BYTES)
+    return SIM_ERR_WORKSPACE;
+  void* base = nullptr;
+  const int rc = noalloc_scratch(h->device, &base);
+  if (rc != SIM_OK) return rc;
+  AdjArgs A;
+  A.ckpt = d_ckpt;
+  A.cmd = reinterpret_cast<const float4*>(d_cmd);
+  A.gid = h->n_groups > 1 ? h->gid : nullptr;
+  A.status = h->status;
+  A.dLdxT = d_dL_dxT;
+  A.w_run = d_w_run;
+  A.dLdx0 = d_dL_dx0;
+  A.th_agent = d_dL_dtheta_agent;
+  A.scratch = static_cast<float*>(base);
+  A.partials = reinterpret_cast<float*>(static_cast<char*>(base) + sbytes);
   A.n = h->n;
   A.nsteps = nsteps;
   A.C = C;
