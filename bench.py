@@ -43,6 +43,13 @@ DT = 1e-3
 #: bench workload's states (748..762; operands that are exactly 0 or 1 are not
 #: counted); tests pin it to the checker's operation counter.
 FLOPS_PER_AGENT_STEP = 748
+#: Tape edges of one closed-loop step in the checker's reverse mode (minimum
+#: over the workload's states, 1348..1367); sweeping one costs a multiply and
+#: an add.  Algorithmic work of forward + adjoint per agent-step: the forward
+#: step, the step again to linearise it, and the reverse sweep.  The extra
+#: forward recomputation that checkpointing adds is not counted.
+ADJ_TAPE_EDGES_PER_AGENT_STEP = 1348
+FWD_ADJ_FLOPS_PER_AGENT_STEP = 2 * FLOPS_PER_AGENT_STEP + 2 * ADJ_TAPE_EDGES_PER_AGENT_STEP
 #: Bytes one plain step moves per agent: state 68 read + 68 written, command
 #: 16, group id 1, status 1.
 BYTES_PER_AGENT_STEP_PLAIN = 154
@@ -50,7 +57,9 @@ BYTES_PER_AGENT_STEP_PLAIN = 154
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2032.0
 L2_FLUSH_BYTES = 256 << 20
-KERNEL_SOURCES = ("paper_2308_12698_b300/csrc/quadsim.cu", "paper_2308_12698_b300/csrc/model.cuh")
+#: The sources that define the step kernel: a committed ncu figure is used
+#: only while their fingerprint is the one it was taken on.
+KERNEL_SOURCES = ("paper_2308_12698_b300/csrc/model_fwd.cuh", "paper_2308_12698_b300/csrc/step_kernel.cuh")
 
 
 def kernel_sha() -> str:
@@ -272,6 +281,9 @@ def main():
     ap.add_argument("--agents", type=int, default=N_AGENTS, help="agents per GPU (profiling cases)")
     ap.add_argument("--physics-steps", type=int, default=T_STEPS, help="physics steps per bench step")
     ap.add_argument("--K", type=int, default=0, help="fix the fused steps per launch (skips the tuner)")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="time only the checkpointed forward + adjoint (profiling case)")
+    ap.add_argument("--C", type=int, default=0, help="fix the checkpoint interval (with --adjoint-only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -293,6 +305,9 @@ def main():
 
     world, rank, local = dist_setup(args.gpus)
     dev = torch.device("cuda", local)
+    if args.adjoint_only:
+        run_adjoint_only(args, world, rank, dev)
+        return
     stream = torch.cuda.current_stream()
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
@@ -403,6 +418,50 @@ def main():
         dist.destroy_process_group()
 
 
+def run_adjoint_only(args, world, rank, dev):
+    """Checkpointed forward + adjoint on --agents x --physics-steps, --C (or tuned)."""
+    import torch
+
+    from paper_2308_12698_b300 import autotune
+    from paper_2308_12698_b300 import workload as W
+    from paper_2308_12698_b300.sim import Sim, planar
+    NA, TS = args.agents, args.physics_steps
+    wl = W.scale_sweep(NA, nsteps=TS)
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    x0 = planar(torch.from_numpy(wl.x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).reshape(-1).to(dev)
+    if args.C:
+        C = args.C
+    else:
+        C = autotune.tune_adjoint(sim, x0, cmd, DT, TS)["C"]
+    S = sim.n_segments(TS, C)
+    ckpt = torch.empty((S + 1, 17 * sim.n), dtype=torch.float32, device=dev)
+    rc = torch.empty(sim.n, dtype=torch.float32, device=dev)
+    gT = torch.zeros(17 * sim.n, dtype=torch.float32, device=dev)
+    gT[: 3 * sim.n] = 1.0
+    w = torch.full((sim.n,), 1e-6, dtype=torch.float32, device=dev)
+    ws = torch.empty(max(sim.workspace_bytes(C), 1), dtype=torch.uint8, device=dev)
+
+    def run():
+        sim.rollout_forward(x0, cmd, DT, TS, C=C, ckpt=ckpt, run_cost=rc)
+        sim.rollout_backward(ckpt, cmd, DT, TS, gT, w, C=C, workspace=ws)
+
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        run()
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    if rank == 0:
+        print(json.dumps({"leg": "fwd_adjoint", "agents": NA, "physics_steps": TS, "C": C, "ms_per_step": ms,
+                          "value": NA * TS / (ms / 1e3), "unit": UNIT, "launch": sim.launch()}), flush=True)
+    sim.close()
+
+
 def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_steps, sms) -> dict:
     """Plain kernel, fwd+adjoint and heterogeneous batch on the same GPU (3 timed reps each)."""
     import torch
@@ -445,10 +504,16 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     timed_steps(fwd_adj, 2)
     t = timed_steps(fwd_adj, reps)
     ms = max_over_ranks(sum(t), world) / reps
-    out["fwd_adjoint"] = {"value": world * N_AGENTS * T_STEPS / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+    rate = N_AGENTS * T_STEPS / (ms / 1e3)
+    peak_tf = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    out["fwd_adjoint"] = {"value": world * rate, "unit": UNIT, "ms_per_step": ms,
                           "C": C, "block_adj": cfg["block"], "workspace_MB": ws.numel() / 1e6,
                           "checkpoint_MB": ckpt.numel() * 4 / 1e6,
-                          "flops_per_agent_step_fwd_equiv": FLOPS_PER_AGENT_STEP}
+                          "roofline": {"bound": "alu", "achieved": FWD_ADJ_FLOPS_PER_AGENT_STEP * rate / 1e12,
+                                       "peak": peak_tf, "unit": "TFLOP/s",
+                                       "frac": FWD_ADJ_FLOPS_PER_AGENT_STEP * rate / 1e12 / peak_tf,
+                                       "flops_per_agent_step": FWD_ADJ_FLOPS_PER_AGENT_STEP,
+                                       "basis": "forward + linearised forward + reverse sweep (2 flops per tape edge)"}}
     del ckpt, ws
 
     # heterogeneous: 8 groups, uneven sizes (600k), one persistent launch per K steps, graph
@@ -469,6 +534,53 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
                      "block": ht["block"]}
     hg.close()
     hs.close()
+
+    # collision detection: 1e6 agents at 2 m mean spacing, 1 % planted near pairs
+    cw = W.collision_field(N_AGENTS)
+    cs = Sim(cw.groups, cw.n, cw.mode)
+    cx = planar(torch.from_numpy(cw.x0)).to(x0.device)
+    cws = torch.empty(max(cs.collide_workspace_bytes(), 1), dtype=torch.uint8, device=x0.device)
+    crun = lambda: cs.collide(cx, 1.0, cws)  # noqa: E731
+    timed_steps(crun, 2, cs.reset_status)
+    t = timed_steps(crun, reps, cs.reset_status)
+    ms = max_over_ranks(sum(t), world) / reps
+    hits = int((cs.status() == 2).sum().item())
+    out["collide"] = {"value": world * cw.n / (ms / 1e3), "unit": "agents/s", "ms_per_call": ms,
+                      "n_agents": cw.n, "collided": hits, "table_and_lists_MB": cws.numel() / 1e6,
+                      "method": "spatial hash, linked lists, 27-cell search"}
+    cs.close()
+    del cx, cws
+
+    # scale sweep 1e3 .. 1e7 agents, 1000 closed-loop steps: plain K = 1 and fused (tuned K)
+    sweep = []
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    hbm = measured_peaks().get("hbm_gbs")
+    for n in (1_000, 10_000, 100_000, 1_000_000, 10_000_000):
+        sw = W.scale_sweep(n, nsteps=T_STEPS)
+        ss = Sim(sw.groups, sw.n, sw.mode)
+        sx0 = planar(torch.from_numpy(sw.x0)).to(x0.device)
+        scmd = torch.from_numpy(sw.cmd).reshape(-1).to(x0.device)
+        sx = sx0.clone()
+        st = autotune.tune_step(ss, sx0, scmd, DT, T_STEPS)
+        sreset = lambda: sx.copy_(sx0)  # noqa: E731
+        row = {"n_agents": n}
+        for label, k in (("plain", 1), ("fused", st["K"])):
+            gr = ss.graph(sx, scmd, DT, T_STEPS, K=k)
+            timed_steps(gr.launch, 1, sreset)
+            t = timed_steps(gr.launch, 2, sreset)
+            ms = sum(t) / len(t)
+            rate = n * T_STEPS / (ms / 1e3)
+            row[label] = {"value": rate, "unit": UNIT, "ms_per_1000_steps": ms, "K": k,
+                          "tflops": FLOPS_PER_AGENT_STEP * rate / 1e12,
+                          "alu_frac": FLOPS_PER_AGENT_STEP * rate / 1e12 / peak_tflops}
+            if k == 1:
+                row[label]["hbm_gbs"] = BYTES_PER_AGENT_STEP_PLAIN * rate / 1e9
+                row[label]["hbm_frac"] = (BYTES_PER_AGENT_STEP_PLAIN * rate / 1e9 / hbm) if hbm else None
+            gr.close()
+        ss.close()
+        sweep.append(row)
+        del sx0, sx, scmd
+    out["sweep"] = sweep
 
     # the paper's own measurement point: 1000 quadrotors, per-round time (context only)
     pw = W.scale_sweep(1000, nsteps=T_STEPS)

@@ -174,6 +174,29 @@ int sim_rollout_backward_noalloc(sim_handle_t h, const float* d_ckpt, const floa
                                  int ckpt_C, const float* d_dL_dxT, const float* d_w_run, float* d_dL_dx0,
                                  float* d_dL_dtheta, float* d_dL_dtheta_agent, void* stream);
 
+/* Collision detection (Sec. III-A: the collision/detection module marks
+ * colliding agents as dead and excludes them from the whole system).  Two
+ * live agents collide when their centres are closer than the sum of their
+ * bounding radii, radius = (arm length L of the agent's group) *
+ * radius_scale; the decision is taken in FP32 as d2 < (r_i + r_j)^2 with
+ * d2 = (dx*dx + dy*dy) + dz*dz, each operation rounded separately.  Every
+ * colliding live agent is marked dead (status 2) and frozen by later calls.
+ * Method: a uniform grid of cells of side > 2 max radius, hashed into a
+ * power-of-two table (spatial hash of Teschner et al., 2003), one linked list
+ * per bucket built with atomic exchanges, then a 27-cell neighbour search per
+ * agent.  The outcome does not depend on the order of the lists.
+ * d_state: planar state (only positions are read).  d_workspace:
+ * sim_collide_workspace_bytes(h) bytes, 256-byte aligned.  radius_scale > 0.
+ * Up to 2^31 - 1 agents.  The call may run on a stream other than the
+ * stepping stream ("outside the main loop"): an agent marked while a step is
+ * in flight is frozen from the next launch on. */
+size_t sim_collide_workspace_bytes(sim_handle_t h);
+int sim_collide(sim_handle_t h, const float* d_state, float radius_scale, void* d_workspace, size_t ws_bytes,
+                void* stream);
+/* Copies the per-agent status bytes (0 alive, 1 non-finite, 2 collided) into
+ * the caller's device buffer of n_agents bytes. */
+int sim_copy_status(sim_handle_t h, uint8_t* d_status_out, void* stream);
+
 /* Launch configuration: threads per block of the forward kernels (a
  * multiple of 32, <= 256) and of the adjoint kernel (a multiple of 32,
  * <= 128), and the defaults used when a call passes 0 for the steps fused

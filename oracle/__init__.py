@@ -63,6 +63,8 @@ def lib():
         L.oracle_allocation.argtypes = [P, P, P, P]
         L.oracle_shepperd.argtypes = [P, P]
         L.oracle_count_ops.argtypes = [P, P, P, ctypes.c_double, ctypes.c_int, P]
+        L.oracle_count_adjoint_edges.argtypes = [P, P, P, ctypes.c_double, ctypes.c_int, P]
+        L.oracle_collisions.argtypes = [P, P, P, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int, P]
         L.oracle_clamp_margins.argtypes = [P, ctypes.c_int, P, ctypes.c_int64, P, P, ctypes.c_double, ctypes.c_int64,
                                            ctypes.c_int, P]
         _lib = L
@@ -147,6 +149,27 @@ def clamp_margins(groups, gid, x0, cmd, h, nsteps, nthreads=None):
     return out
 
 
+def collisions(p, radius, alive, idx=None, nthreads=None):
+    """uint8 flags: 1 where a live agent is closer than r_i + r_j to another live agent.
+
+    Decided in FP32 without fused multiply-adds (the precision the kernel decides in):
+    d2 = (dx*dx + dy*dy) + dz*dz < (r_i + r_j)^2.  With idx, only those agents are decided."""
+    pp = np.ascontiguousarray(np.asarray(p, dtype=np.float32).reshape(-1, 3))
+    n = pp.shape[0]
+    rr = np.ascontiguousarray(np.asarray(radius, dtype=np.float32).reshape(n))
+    al = np.ascontiguousarray(np.asarray(alive, dtype=np.uint8).reshape(n))
+    if idx is None:
+        out = np.zeros(n, dtype=np.uint8)
+        rc = lib().oracle_collisions(_p(pp), _p(rr), _p(al), n, None, -1, _threads(nthreads), _p(out))
+    else:
+        ii = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+        out = np.zeros(ii.size, dtype=np.uint8)
+        rc = lib().oracle_collisions(_p(pp), _p(rr), _p(al), n, _p(ii), ii.size, _threads(nthreads), _p(out))
+    if rc != 0:
+        raise ValueError("oracle_collisions rejected its arguments")
+    return out
+
+
 def derivative(group, x, w):
     pg = pack_group(group)
     xx = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
@@ -179,6 +202,16 @@ def shepperd(R):
     q = np.zeros(4)
     lib().oracle_shepperd(_p(RR), _p(q))
     return q
+
+
+def count_adjoint_edges(group, x, cmd, h, mode):
+    """Edges of the one-step reverse-mode tape (each costs a multiply and an add to sweep)."""
+    pg = pack_group(group)
+    xx = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    cc = np.ascontiguousarray(np.asarray(cmd, dtype=np.float64))
+    out = np.zeros(1, dtype=np.int64)
+    lib().oracle_count_adjoint_edges(_p(pg), _p(xx), _p(cc), float(h), int(mode), _p(out))
+    return int(out[0])
 
 
 def count_ops(group, x, cmd, h, mode):

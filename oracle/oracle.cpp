@@ -232,6 +232,75 @@ int oracle_clamp_margins(const double* groups, int n_groups, const int32_t* gid,
   return 0;
 }
 
+// Collision test of one ordered pair, as a plain definition: live agents i
+// and j (i != j) collide when their centres are closer than the sum of their
+// bounding radii.  The decision is taken in FP32 with every operation rounded
+// on its own (the checker is built without floating contraction): dx = p_j - p_i per axis,
+// d2 = (dx*dx + dy*dy) + dz*dz, thr = (r_i + r_j)^2, collide if d2 < thr.
+static inline bool pair_collides(const float* pi, float ri, const float* pj, float rj) {
+  const float dx = pj[0] - pi[0], dy = pj[1] - pi[1], dz = pj[2] - pi[2];
+  const float xx = dx * dx, yy = dy * dy, zz = dz * dz;
+  const float s = xx + yy;
+  const float d2 = s + zz;
+  const float rs = ri + rj;
+  const float thr = rs * rs;
+  return d2 < thr;
+}
+
+// Marks hit[a] = 1 for every live agent a (alive[a] != 0) that collides with
+// another live agent, by brute force over all pairs (Sec. III-A: colliding
+// agents are marked dead and excluded).  p: n x 3 float positions; radius:
+// n floats.  With m >= 0 and idx given, only agents idx[0..m) are decided
+// (each against all n), and hit is indexed like idx.
+int oracle_collisions(const float* p, const float* radius, const uint8_t* alive, int64_t n, const int64_t* idx,
+                      int64_t m, int nthreads, uint8_t* hit) {
+  if (n < 0) return -1;
+  const int64_t count = idx ? m : n;
+  parallel_for(count, nthreads, [&](int64_t lo, int64_t hi) {
+    for (int64_t k = lo; k < hi; ++k) {
+      const int64_t a = idx ? idx[k] : k;
+      uint8_t h = 0;
+      if (alive[a]) {
+        for (int64_t b = 0; b < n && !h; ++b) {
+          if (b == a || !alive[b]) continue;
+          if (pair_collides(p + 3 * a, radius[a], p + 3 * b, radius[b])) h = 1;
+        }
+      }
+      hit[k] = h;
+    }
+  });
+  return 0;
+}
+
+// Reverse-sweep work of one step in the checker's reverse mode: the number of
+// tape edges of a closed- or open-loop step taped with respect to the 17
+// states and the 16 differentiated parameters.  Sweeping backwards costs one
+// multiply and one add per edge.
+int oracle_count_adjoint_edges(const double* group, const double* x, const double* cmd, double h, int mode,
+                               int64_t* edges) {
+  const Group<double> Pd = unpack_group(group);
+  const Fixed F = make_fixed(Pd);
+  Tape tape;
+  g_tape = &tape;
+  Group<Var> Pv = cast_group<Var>(Pd);
+  for (int i = 0; i < 3; ++i) {
+    Pv.kp[i] = Var::leaf(Pd.kp[i]);
+    Pv.kd[i] = Var::leaf(Pd.kd[i]);
+    Pv.katt[i] = Var::leaf(Pd.katt[i]);
+    Pv.krate[i] = Var::leaf(Pd.krate[i]);
+    Pv.J[i] = Var::leaf(Pd.J[i]);
+  }
+  Pv.m = Var::leaf(Pd.m);
+  Var xv[NX], xn[NX];
+  for (int i = 0; i < NX; ++i) xv[i] = Var::leaf(x[i]);
+  rk4_step(Pv, F, mode, xv, cmd, h, xn);
+  int64_t e = 0;
+  for (const Node& n : tape.nodes) e += (n.a >= 0) + (n.b >= 0);
+  *edges = e;
+  g_tape = nullptr;
+  return 0;
+}
+
 // Non-trivial FP64 operations of one step for one agent:
 // counts = {add/sub, mul, div, sqrt, sin/cos, comparisons}.
 int oracle_count_ops(const double* group, const double* x, const double* cmd, double h, int mode,

@@ -23,7 +23,8 @@ SIM_NOALLOC_SCRATCH_BYTES = 32 << 20
 EXPORTS = ("sim_create", "sim_set_params", "sim_step", "sim_step_host", "sim_rollout_forward",
            "sim_workspace_bytes", "sim_rollout_backward", "sim_set_launch", "sim_get_launch", "sim_status",
            "sim_reset_status", "sim_graph_create", "sim_graph_launch", "sim_graph_destroy", "sim_step_launches",
-           "sim_destroy", "sim_error_string", "sim_rollout_backward_noalloc")
+           "sim_destroy", "sim_error_string", "sim_rollout_backward_noalloc",
+           "sim_collide_workspace_bytes", "sim_collide", "sim_copy_status")
 
 
 class GroupParams(ctypes.Structure):
@@ -69,6 +70,9 @@ def lib():
         "sim_workspace_bytes": (SZ, [P, I]),
         "sim_rollout_backward": (I, [P, P, P, F, I64, I, P, P, P, P, P, P, SZ, P]),
         "sim_rollout_backward_noalloc": (I, [P, P, P, F, I64, I, P, P, P, P, P, P]),
+        "sim_collide_workspace_bytes": (SZ, [P]),
+        "sim_collide": (I, [P, P, F, P, SZ, P]),
+        "sim_copy_status": (I, [P, P, P]),
         "sim_set_launch": (I, [P, I, I, I, I]),
         "sim_get_launch": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
         "sim_status": (I, [P, ctypes.POINTER(I64), I, P]),

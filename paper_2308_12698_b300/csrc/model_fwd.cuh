@@ -10,7 +10,7 @@
 //                   G^-1 -> rotor clamp (the paper's inner body-rate loop,
 //                   Sec. III-B, completed as documented in quadsim.h)
 //   rk4             classical RK4, command held over the stages (Sec. III-B)
-//   *_vjp           hand-written vector-Jacobian products for the discrete adjoint
+//   (the vector-Jacobian products of the adjoint are in model_adj.cuh)
 //
 // State index map (17 floats): p 0-2, v 3-5, q 6-9 (w x y z), omega 10-12,
 // Omega 13-16.  rb_derivative returns 2 q' for the quaternion (q o [0, w]),
@@ -275,252 +275,6 @@ __device__ __forceinline__ void step(const DevGroup& P, St& x, const float4 c, f
     u[0] = c.x; u[1] = c.y; u[2] = c.z; u[3] = c.w;
   }
   rk4(P, x, u, H, L);
-}
-
-// ------------------------------------------------------------------ VJPs --
-// Adds to yb (13), Omb (stage rotor speeds, 4) and tb (theta) the products of
-// g (13) with the Jacobians of rb_derivative at (y, Om).
-__device__ __forceinline__ void rb_derivative_vjp(const DevGroup& P, const float* y, const float Om[4], const float* g,
-                                                  float* yb, float Omb[4], float tb[NTH]) {
-  const float s1 = Om[0] * Om[0], s2 = Om[1] * Om[1], s3 = Om[2] * Om[2], s4 = Om[3] * Om[3];
-  const float T2 = P.T2c * ((s1 + s2) + (s3 + s4));
-  const float Dx = (s1 - s2) + (s4 - s3), Dy = (s3 + s4) - (s1 + s2), Dz = (s1 - s2) + (s3 - s4);
-  const float w = y[QW], qx = y[QX], qy = y[QY], qz = y[QZ];
-  const float wx = y[WX], wy = y[WX + 1], wz = y[WX + 2];
-  const float bx = qx * qz + w * qy, by = qy * qz - w * qx, bxy = qx * qx + qy * qy;
-  const float gvx = g[3], gvy = g[4], gvz = g[5];
-  // p' = v ; v' = T2 (bx, by, 1/2 - bxy) - cd_m v - g e3
-  yb[VX] += g[0] - P.cd_m * gvx;
-  yb[VX + 1] += g[1] - P.cd_m * gvy;
-  yb[VX + 2] += g[2] - P.cd_m * gvz;
-  const float T2b = gvx * bx + gvy * by + gvz * (0.5f - bxy);
-  const float gv_v = gvx * y[VX] + gvy * y[VX + 1] + gvz * y[VX + 2];
-  tb[TH_M] += (gv_v * P.cd_m - T2b * T2) * P.inv_m;
-  const float bbx = gvx * T2, bby = gvy * T2, bbxy = -gvz * T2;
-  float qbw = qy * bbx - qx * bby;
-  float qbx = qz * bbx - w * bby + 2.f * qx * bbxy;
-  float qby = w * bbx + qz * bby + 2.f * qy * bbxy;
-  float qbz = qx * bbx + qy * bby;
-  // 2 q' = q o [0, omega]
-  const float gw = g[QW], gx = g[QX], gy = g[QY], gz = g[QZ];
-  qbw += gx * wx + gy * wy + gz * wz;
-  qbx += -gw * wx - gy * wz + gz * wy;
-  qby += -gw * wy + gx * wz - gz * wx;
-  qbz += -gw * wz - gx * wy + gy * wx;
-  yb[QW] += qbw; yb[QX] += qbx; yb[QY] += qby; yb[QZ] += qbz;
-  float wbx = -gw * qx + gx * w + gy * qz - gz * qy;
-  float wby = -gw * qy - gx * qz + gy * w + gz * qx;
-  float wbz = -gw * qz + gx * qy - gy * qx + gz * w;
-  // omega'_x = ((Jy - Jz) wy wz + kt L sin(a) Dx) / Jx, and cyclic
-  const float nx = g[WX], ny = g[WX + 1], nz = g[WX + 2];
-  const float dwx = P.gx * (wy * wz) + P.txc * Dx;
-  const float dwy = P.gy * (wz * wx) + P.tyc * Dy;
-  const float dwz = P.gz * (wx * wy) + P.tzc * Dz;
-  const float ax = nx * P.iJx, ay = ny * P.iJy, az = nz * P.iJz;
-  tb[TH_J] += -ax * dwx - ay * (wz * wx) + az * (wx * wy);
-  tb[TH_J + 1] += ax * (wy * wz) - ay * dwy - az * (wx * wy);
-  tb[TH_J + 2] += -ax * (wy * wz) + ay * (wz * wx) - az * dwz;
-  wbx += ny * P.gy * wz + nz * P.gz * wy;
-  wby += nx * P.gx * wz + nz * P.gz * wx;
-  wbz += nx * P.gx * wy + ny * P.gy * wx;
-  yb[WX] += wbx; yb[WX + 1] += wby; yb[WX + 2] += wbz;
-  // rotors: s_i = Omega_i^2 through the thrust and torque rows of G
-  const float a0 = P.T2c * T2b, a1 = P.txc * nx, a2 = P.tyc * ny, a3 = P.tzc * nz;
-  Omb[0] += 2.f * Om[0] * ((a0 + a1) + (a3 - a2));
-  Omb[1] += 2.f * Om[1] * ((a0 - a1) - (a2 + a3));
-  Omb[2] += 2.f * Om[2] * ((a0 - a1) + (a2 + a3));
-  Omb[3] += 2.f * Om[3] * ((a0 + a1) + (a2 - a3));
-}
-
-// Cotangent of the controller: ub (rotor commands) -> xb (state), tb (theta).
-__device__ __forceinline__ void controller_vjp(const DevGroup& P, const float* x, const float4 c, float ch, float sh,
-                                               const float ub[4], float* xb, float tb[NTH]) {
-  Ctl C;
-  float u[4];
-  controller_fwd(P, x, c, ch, sh, C, u);
-  // sqrt(clamp(S)): gradient passes on 0 < S <= om2max (sqrt'(0) taken as 0)
-  float Sb[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float s = C.S[i];
-    Sb[i] = (s > 0.f && s <= P.om2max) ? ub[i] * 0.5f * rsqrtf(s) : 0.f;
-  }
-  const float f0b = (Sb[0] + Sb[1]) + (Sb[2] + Sb[3]);
-  float fb[3];
-  fb[0] = (Sb[0] - Sb[1]) + (Sb[3] - Sb[2]);
-  fb[1] = (Sb[2] + Sb[3]) - (Sb[0] + Sb[1]);
-  fb[2] = (Sb[0] - Sb[1]) + (Sb[2] - Sb[3]);
-  // f_i = mt_i krate_i (2 katt_i qe_i - omega_i)
-  float qeb[4];
-  qeb[0] = 0.f;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    tb[TH_KRATE + i] += fb[i] * P.mt[i] * (P.katt2[i] * C.qe[1 + i] - x[WX + i]);
-    tb[TH_KATT + i] += fb[i] * P.wa[i] * 2.f * C.qe[1 + i];
-    xb[WX + i] -= fb[i] * P.wa[i];
-    qeb[1 + i] = fb[i] * P.qa[i] * C.sgn;  // through the sign fix
-  }
-  // qe = conj(q) o qd
-  const float w = x[QW], qx = x[QX], qy = x[QY], qz = x[QZ];
-  const float dw = C.qd[0], dx = C.qd[1], dy = C.qd[2], dz = C.qd[3];
-  const float Ew = qeb[0], Ex = qeb[1], Ey = qeb[2], Ez = qeb[3];
-  float qbw = Ew * dw + Ex * dx + Ey * dy + Ez * dz;
-  float qbx = Ew * dx - Ex * dw + Ey * dz - Ez * dy;
-  float qby = Ew * dy - Ex * dz - Ey * dw + Ez * dx;
-  float qbz = Ew * dz + Ex * dy - Ey * dx - Ez * dw;
-  float qdb[4];
-  qdb[0] = Ew * w - Ex * qx - Ey * qy - Ez * qz;
-  qdb[1] = Ew * qx + Ex * w - Ey * qz + Ez * qy;
-  qdb[2] = Ew * qy + Ex * qz + Ey * w - Ez * qx;
-  qdb[3] = Ew * qz - Ex * qy + Ey * qx + Ez * w;
-  // Shepperd, branch taken
-  float Rb[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-  const float R10 = C.xd[1], R20 = C.xd[2];
-  const float R01 = C.yd[0], R21 = C.yd[2];
-  const float R02 = C.zd[0], R12 = C.zd[1];
-  const float k = C.k, k2x2 = 2.f * C.k * C.k;
-  if (C.branch == 0) {
-    const float kb = qdb[1] * (R21 - R12) + qdb[2] * (R02 - R20) + qdb[3] * (R10 - R01);
-    Rb[2][1] += qdb[1] * k; Rb[1][2] -= qdb[1] * k;
-    Rb[0][2] += qdb[2] * k; Rb[2][0] -= qdb[2] * k;
-    Rb[1][0] += qdb[3] * k; Rb[0][1] -= qdb[3] * k;
-    const float tb_ = (0.5f * qdb[0] - k2x2 * kb) * k;
-    Rb[0][0] += tb_; Rb[1][1] += tb_; Rb[2][2] += tb_;
-  } else if (C.branch == 1) {
-    const float kb = qdb[0] * (R21 - R12) + qdb[2] * (R01 + R10) + qdb[3] * (R02 + R20);
-    Rb[2][1] += qdb[0] * k; Rb[1][2] -= qdb[0] * k;
-    Rb[0][1] += qdb[2] * k; Rb[1][0] += qdb[2] * k;
-    Rb[0][2] += qdb[3] * k; Rb[2][0] += qdb[3] * k;
-    const float tb_ = (0.5f * qdb[1] - k2x2 * kb) * k;
-    Rb[0][0] += tb_; Rb[1][1] -= tb_; Rb[2][2] -= tb_;
-  } else if (C.branch == 2) {
-    const float kb = qdb[0] * (R02 - R20) + qdb[1] * (R01 + R10) + qdb[3] * (R12 + R21);
-    Rb[0][2] += qdb[0] * k; Rb[2][0] -= qdb[0] * k;
-    Rb[0][1] += qdb[1] * k; Rb[1][0] += qdb[1] * k;
-    Rb[1][2] += qdb[3] * k; Rb[2][1] += qdb[3] * k;
-    const float tb_ = (0.5f * qdb[2] - k2x2 * kb) * k;
-    Rb[0][0] -= tb_; Rb[1][1] += tb_; Rb[2][2] -= tb_;
-  } else {
-    const float kb = qdb[0] * (R10 - R01) + qdb[1] * (R02 + R20) + qdb[2] * (R12 + R21);
-    Rb[1][0] += qdb[0] * k; Rb[0][1] -= qdb[0] * k;
-    Rb[0][2] += qdb[1] * k; Rb[2][0] += qdb[1] * k;
-    Rb[1][2] += qdb[2] * k; Rb[2][1] += qdb[2] * k;
-    const float tb_ = (0.5f * qdb[3] - k2x2 * kb) * k;
-    Rb[0][0] -= tb_; Rb[1][1] -= tb_; Rb[2][2] += tb_;
-  }
-  float xdb[3] = {Rb[0][0], Rb[1][0], Rb[2][0]};
-  float ydb[3] = {Rb[0][1], Rb[1][1], Rb[2][1]};
-  float zdb[3] = {Rb[0][2], Rb[1][2], Rb[2][2]};
-  // xd = yd x zd
-  ydb[0] += C.zd[1] * xdb[2] - C.zd[2] * xdb[1];
-  ydb[1] += C.zd[2] * xdb[0] - C.zd[0] * xdb[2];
-  ydb[2] += C.zd[0] * xdb[1] - C.zd[1] * xdb[0];
-  zdb[0] += xdb[1] * C.yd[2] - xdb[2] * C.yd[1];
-  zdb[1] += xdb[2] * C.yd[0] - xdb[0] * C.yd[2];
-  zdb[2] += xdb[0] * C.yd[1] - xdb[1] * C.yd[0];
-  // yd = yr / |yr|
-  const float yy = C.yd[0] * ydb[0] + C.yd[1] * ydb[1] + C.yd[2] * ydb[2];
-  const float yrb0 = (ydb[0] - C.yd[0] * yy) * C.ry;
-  const float yrb1 = (ydb[1] - C.yd[1] * yy) * C.ry;
-  const float yrb2 = (ydb[2] - C.yd[2] * yy) * C.ry;
-  // yr = zd x (ch, sh, 0)
-  zdb[0] += sh * yrb2;
-  zdb[1] += -ch * yrb2;
-  zdb[2] += ch * yrb1 - sh * yrb0;
-  // zd = F / |F|; f0 = f0c (F . b3), f0c = m / (4 kt)
-  const float fcb = f0b * P.f0c;
-  tb[TH_M] += f0b * C.fc * P.mix0;
-  const float zz = C.zd[0] * zdb[0] + C.zd[1] * zdb[1] + C.zd[2] * zdb[2];
-  float Fb[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) Fb[i] = (zdb[i] - C.zd[i] * zz) * C.rn + fcb * C.b3[i];
-  // b3 = R(q) e3 -> q
-  const float bbx = fcb * C.F[0], bby = fcb * C.F[1], bbz = fcb * C.F[2];
-  qbw += 2.f * (qy * bbx - qx * bby);
-  qbx += 2.f * (qz * bbx - w * bby) - 4.f * qx * bbz;
-  qby += 2.f * (w * bbx + qz * bby) - 4.f * qy * bbz;
-  qbz += 2.f * (qx * bbx + qy * bby);
-  xb[QW] += qbw; xb[QX] += qbx; xb[QY] += qby; xb[QZ] += qbz;
-  // F = a + g e3, a = clamp(kp e - kd v)
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const float arb = C.pass[i] ? Fb[i] : 0.f;
-    tb[TH_KP + i] += arb * C.e[i];
-    tb[TH_KD + i] -= arb * x[VX + i];
-    xb[PX + i] -= P.kp[i] * arb;
-    xb[VX + i] -= P.kd[i] * arb;
-  }
-}
-
-// Adjoint of one RK4 step x_n -> x_{n+1}: lam <- (d x_{n+1} / d x_n)^T lam,
-// tb += (d x_{n+1} / d theta)^T lam.  x is the step-start state.
-template <int MODE>
-__device__ __forceinline__ void step_vjp(const DevGroup& P, const St& x, const float4 c, float ch, float sh,
-                                         const StepH& H, const LagCoef& L, St& lam, float tb[NTH]) {
-  float u[4];
-  if (MODE == 1) {
-    controller(P, x.a, c, ch, sh, u);
-  } else {
-    u[0] = c.x; u[1] = c.y; u[2] = c.z; u[3] = c.w;
-  }
-  float dOm[4], Om2[4], Om3[4], Om4[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    dOm[i] = u[i] - x.a[OM + i];
-    Om2[i] = x.a[OM + i] + L.c2 * dOm[i];
-    Om3[i] = x.a[OM + i] + L.c3 * dOm[i];
-    Om4[i] = x.a[OM + i] + L.c4 * dOm[i];
-  }
-  float k[NRB], y2[NRB], y3[NRB], y4[NRB];
-  rb_derivative(P, x.a, x.a + OM, k);
-#pragma unroll
-  for (int i = 0; i < NRB; ++i) y2[i] = x.a[i] + coef(i, H.h2, H.h2q) * k[i];
-  rb_derivative(P, y2, Om2, k);
-#pragma unroll
-  for (int i = 0; i < NRB; ++i) y3[i] = x.a[i] + coef(i, H.h2, H.h2q) * k[i];
-  rb_derivative(P, y3, Om3, k);
-#pragma unroll
-  for (int i = 0; i < NRB; ++i) y4[i] = x.a[i] + coef(i, H.h, H.hq) * k[i];
-  float xb[NX], g[NRB], yb[NRB];
-  float Ob1[4] = {0.f, 0.f, 0.f, 0.f}, Ob2[4] = {0.f, 0.f, 0.f, 0.f};
-  float Ob3[4] = {0.f, 0.f, 0.f, 0.f}, Ob4[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-  for (int i = 0; i < NRB; ++i) { xb[i] = lam.a[i]; g[i] = coef(i, H.h6, H.h6q) * lam.a[i]; yb[i] = 0.f; }
-  rb_derivative_vjp(P, y4, Om4, g, yb, Ob4, tb);
-#pragma unroll
-  for (int i = 0; i < NRB; ++i) {
-    xb[i] += yb[i];
-    g[i] = 2.f * coef(i, H.h6, H.h6q) * lam.a[i] + coef(i, H.h, H.hq) * yb[i];
-    yb[i] = 0.f;
-  }
-  rb_derivative_vjp(P, y3, Om3, g, yb, Ob3, tb);
-#pragma unroll
-  for (int i = 0; i < NRB; ++i) {
-    xb[i] += yb[i];
-    g[i] = 2.f * coef(i, H.h6, H.h6q) * lam.a[i] + coef(i, H.h2, H.h2q) * yb[i];
-    yb[i] = 0.f;
-  }
-  rb_derivative_vjp(P, y2, Om2, g, yb, Ob2, tb);
-#pragma unroll
-  for (int i = 0; i < NRB; ++i) {
-    xb[i] += yb[i];
-    g[i] = coef(i, H.h6, H.h6q) * lam.a[i] + coef(i, H.h2, H.h2q) * yb[i];
-    yb[i] = 0.f;
-  }
-  rb_derivative_vjp(P, x.a, x.a + OM, g, yb, Ob1, tb);
-#pragma unroll
-  for (int i = 0; i < NRB; ++i) xb[i] += yb[i];
-  // rotor lag: stage k sees Omega + c_k (u - Omega); the step ends at Omega + c5 (u - Omega)
-  float ub[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float lO = lam.a[OM + i];
-    ub[i] = L.c5 * lO + L.c2 * Ob2[i] + L.c3 * Ob3[i] + L.c4 * Ob4[i];
-    xb[OM + i] = (lO - ub[i]) + Ob1[i] + Ob2[i] + Ob3[i] + Ob4[i];
-  }
-  if (MODE == 1) controller_vjp(P, x.a, c, ch, sh, ub, xb, tb);
-#pragma unroll
-  for (int i = 0; i < NX; ++i) lam.a[i] = xb[i];
 }
 
 }  // namespace qs

@@ -15,7 +15,9 @@
 #include <thread>
 
 #include "../../include/quadsim.h"
-#include "model.cuh"
+#include "model_adj.cuh"
+#include "model_fwd.cuh"
+#include "step_kernel.cuh"
 
 using namespace qs;
 
@@ -27,65 +29,6 @@ constexpr int kDefaultK = 10;
 constexpr int kDefaultC = 100;
 
 // --------------------------------------------------------------- kernels --
-
-struct StepArgs {
-  float* state;
-  const float4* cmd;
-  const uint8_t* gid;
-  uint8_t* status;
-  int64_t n;
-  int K;
-  int n_groups;
-  StepH H;
-  const DevGroup* groups;  // device table (several groups)
-};
-
-__device__ __forceinline__ bool all_finite(const St& x) {
-  float s = 0.f;
-#pragma unroll
-  for (int i = 0; i < NX; ++i) s += x.a[i];
-  return isfinite(s);
-}
-
-template <bool HETERO>
-__device__ __forceinline__ void load_groups(DevGroup* sg, const DevGroup* src, int n_groups) {
-  if (HETERO) {
-    const float4* s = reinterpret_cast<const float4*>(src);
-    float4* d = reinterpret_cast<float4*>(sg);
-    for (int i = threadIdx.x; i < n_groups * (int)(sizeof(DevGroup) / 16); i += blockDim.x) d[i] = s[i];
-    __syncthreads();
-  }
-}
-
-// K fused RK4 steps per launch; the state touches HBM once per launch.
-template <int MODE, bool HETERO>
-__global__ void __launch_bounds__(256) step_kernel(StepArgs A, const DevGroup P0) {
-  extern __shared__ float4 smem4[];
-  DevGroup* sg = reinterpret_cast<DevGroup*>(smem4);
-  load_groups<HETERO>(sg, A.groups, A.n_groups);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) {
-    if (A.status[i]) continue;  // dead agents are frozen
-    St x;
-    load_state(A.state, A.n, i, x);
-    const float4 c = A.cmd[i];
-    float ch = 0.f, sh = 0.f;
-    if (MODE == 1) sincosf(c.w, &sh, &ch);
-    if (HETERO) {
-      const DevGroup P = sg[A.gid[i]];
-      const LagCoef L = lag_coef(P.inv_tau, A.H);
-      for (int k = 0; k < A.K; ++k) step<MODE>(P, x, c, ch, sh, A.H, L);
-    } else {
-      const LagCoef L = lag_coef(P0.inv_tau, A.H);
-      for (int k = 0; k < A.K; ++k) step<MODE>(P0, x, c, ch, sh, A.H, L);
-    }
-    if (all_finite(x)) {
-      store_state(A.state, A.n, i, x);
-    } else {
-      A.status[i] = 1;  // keep the last finite state
-    }
-  }
-}
 
 struct CkptArgs {
   const float* x0;
@@ -164,7 +107,9 @@ struct AdjArgs {
 // swept backwards step by step.  Per-agent theta cotangents are reduced per
 // group inside each warp (fixed butterfly order), accumulated per warp in
 // shared memory, and written as one partial per block.
-template <int MODE>
+// SMEMS: the segment's step-start states live in shared memory (small C)
+// rather than in the global scratch.
+template <int MODE, bool SMEMS>
 __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
   extern __shared__ float4 smem4[];
   DevGroup* sg = reinterpret_cast<DevGroup*>(smem4);
@@ -172,9 +117,14 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
   const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int e = threadIdx.x; e < nw * A.n_groups * NTH; e += blockDim.x) wacc[e] = 0.f;
   load_groups<true>(sg, A.groups, A.n_groups);
-  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t sstep = (int64_t)NX * nthreads;
+  // shared scratch starts after the accumulators, 16-byte aligned
+  float* sscr = reinterpret_cast<float*>(smem4 + (sizeof(DevGroup) * A.n_groups + 4 * nw * A.n_groups * NTH + 15) / 16);
+  float* const scratch = SMEMS ? sscr : A.scratch;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;  // grid stride over agents
+  // scratch column of this thread: its own slot in the block (shared) or in the grid (global)
+  const int64_t scols = SMEMS ? (int64_t)blockDim.x : nthreads;
+  const int64_t slot = SMEMS ? (int64_t)threadIdx.x : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t sstep = (int64_t)NX * scols;
   const int64_t plane = (int64_t)NX * A.n;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < A.n; base += nthreads) {
     const int64_t i = base + threadIdx.x;
@@ -184,7 +134,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
     int g = -1;
     if (i < A.n && A.status[i] == 0) {
       g = A.gid ? (int)A.gid[i] : 0;
-      const DevGroup P = sg[g];
+      const DevGroup& P = sg[g];  // read from shared memory where used: keeps registers for the adjoint
       const LagCoef L = lag_coef(P.inv_tau, A.H);
       const float4 c = A.cmd[i];
       float ch = 0.f, sh = 0.f;
@@ -200,11 +150,11 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
         const int len = (int)min((int64_t)A.C, A.nsteps - n0);
         load_state(A.ckpt + (int64_t)s * plane, A.n, i, x);
         for (int j = 0; j < len; ++j) {
-          store_state(A.scratch + j * sstep, nthreads, slot, x);
+          store_state(scratch + j * sstep, scols, slot, x);
           if (j + 1 < len) step<MODE>(P, x, c, ch, sh, A.H, L);
         }
         for (int j = len - 1; j >= 0; --j) {
-          load_state(A.scratch + j * sstep, nthreads, slot, x);
+          load_state(scratch + j * sstep, scols, slot, x);
           step_vjp<MODE>(P, x, c, ch, sh, A.H, L, lam, tb);
           if (n0 + j >= 1) {
 #pragma unroll
@@ -271,6 +221,82 @@ __global__ void count_dead_kernel(const uint8_t* status, int64_t n, unsigned lon
     c += status[i] != 0;
   for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+// ------------------------------------------------------------ collisions --
+
+struct CollArgs {
+  const float4* pos;      // plane 0 of the planar state: (px, py, pz, vx)
+  const uint8_t* gid;
+  uint8_t* status;
+  const float* arm;
+  float scale;
+  float inv_cell;
+  uint32_t mask;          // table size - 1 (power of two)
+  int* head;              // [table] first agent of each bucket, -1 if empty
+  int* next;              // [n] next agent in the same bucket, -1 at the end
+  uint8_t* hit;           // [n]
+  int64_t n;
+};
+
+// Spatial hash of an integer cell (Teschner et al., 2003).
+__device__ __forceinline__ uint32_t cell_key(int cx, int cy, int cz, uint32_t mask) {
+  return (((uint32_t)cx * 73856093u) ^ ((uint32_t)cy * 19349663u) ^ ((uint32_t)cz * 83492791u)) & mask;
+}
+
+__device__ __forceinline__ int cell_of(float v, float inv_cell) { return (int)floorf(v * inv_cell); }
+
+__global__ void __launch_bounds__(256) collide_insert(CollArgs A) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) {
+    if (A.status[i]) continue;
+    const float4 p = A.pos[i];
+    const uint32_t k = cell_key(cell_of(p.x, A.inv_cell), cell_of(p.y, A.inv_cell), cell_of(p.z, A.inv_cell), A.mask);
+    A.next[i] = atomicExch(&A.head[k], (int)i);
+  }
+}
+
+// FP32 pair test with every operation rounded separately (no contraction).
+__device__ __forceinline__ bool pair_hit(float4 pi, float ri, float4 pj, float rj) {
+  const float dx = __fsub_rn(pj.x, pi.x), dy = __fsub_rn(pj.y, pi.y), dz = __fsub_rn(pj.z, pi.z);
+  const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+  const float rs = __fadd_rn(ri, rj);
+  return d2 < __fmul_rn(rs, rs);
+}
+
+__global__ void __launch_bounds__(256) collide_query(CollArgs A) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) {
+    uint8_t h = 0;
+    if (A.status[i] == 0) {
+      const float4 pi = A.pos[i];
+      const float ri = __fmul_rn(A.arm[A.gid ? A.gid[i] : 0], A.scale);
+      const int cx = cell_of(pi.x, A.inv_cell), cy = cell_of(pi.y, A.inv_cell), cz = cell_of(pi.z, A.inv_cell);
+      int64_t budget = A.n + 27;  // a list never holds more than n agents
+      for (int dz = -1; dz <= 1 && !h; ++dz)
+        for (int dy = -1; dy <= 1 && !h; ++dy)
+          for (int dx = -1; dx <= 1 && !h; ++dx) {
+            int j = A.head[cell_key(cx + dx, cy + dy, cz + dz, A.mask)];
+            while (j >= 0 && budget-- > 0) {
+              if ((int64_t)j != i) {
+                const float rj = __fmul_rn(A.arm[A.gid ? A.gid[j] : 0], A.scale);
+                if (pair_hit(pi, ri, A.pos[j], rj)) {
+                  h = 1;
+                  break;
+                }
+              }
+              j = A.next[j];
+            }
+          }
+    }
+    A.hit[i] = h;
+  }
+}
+
+__global__ void __launch_bounds__(256) collide_apply(CollArgs A) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride)
+    if (A.hit[i] && A.status[i] == 0) A.status[i] = 2;
 }
 
 // ------------------------------------------------------------ host side --
@@ -357,6 +383,8 @@ struct sim_s {
   const uint8_t* gid = nullptr;  // borrowed
   uint8_t* status = nullptr;     // owned
   DevGroup* d_groups = nullptr;  // owned
+  float* d_arm = nullptr;        // owned: arm length per group (collision radius)
+  float max_arm = 0.f;
   DevGroup host_group0;
   int block_fwd = kDefaultBlockFwd;
   int block_adj = kDefaultBlockAdj;
@@ -388,21 +416,48 @@ int fwd_grid(const sim_s* h, size_t smem) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)occ * h->sms));
 }
 
-size_t adj_smem(const sim_s* h) {
-  return sizeof(DevGroup) * h->n_groups + (size_t)(h->block_adj / 32) * h->n_groups * NTH * sizeof(float);
+// Shared-memory budget per block for the segment scratch (small C).
+constexpr size_t kSmemScratchMax = 96 * 1024;
+
+bool adj_smem_scratch(const sim_s* h, int C) {
+  return (size_t)C * NX * sizeof(float) * h->block_adj <= kSmemScratchMax;
 }
 
-int adj_grid(const sim_s* h) {
-  const size_t smem = adj_smem(h);
-  const int occ = h->mode == SIM_CLOSED_LOOP ? occupancy(adjoint_kernel<1>, h->block_adj, smem)
-                                             : occupancy(adjoint_kernel<0>, h->block_adj, smem);
+size_t adj_smem(const sim_s* h, int C) {
+  size_t b = sizeof(DevGroup) * h->n_groups + (size_t)(h->block_adj / 32) * h->n_groups * NTH * sizeof(float);
+  if (adj_smem_scratch(h, C)) b = ((b + 15) & ~(size_t)15) + (size_t)C * NX * sizeof(float) * h->block_adj;
+  return b;
+}
+
+int adj_grid(const sim_s* h, int C) {
+  const size_t smem = adj_smem(h, C);
+  const bool sm = adj_smem_scratch(h, C);
+  int occ;
+  if (h->mode == SIM_CLOSED_LOOP)
+    occ = sm ? occupancy(adjoint_kernel<1, true>, h->block_adj, smem) : occupancy(adjoint_kernel<1, false>, h->block_adj, smem);
+  else
+    occ = sm ? occupancy(adjoint_kernel<0, true>, h->block_adj, smem) : occupancy(adjoint_kernel<0, false>, h->block_adj, smem);
   const int64_t need = (h->n + h->block_adj - 1) / h->block_adj;
   return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)occ * h->sms));
+}
+
+int launch_adjoint(const sim_s* h, const AdjArgs& A, int C, int grid, cudaStream_t st) {
+  const size_t smem = adj_smem(h, C);
+  const bool sm = adj_smem_scratch(h, C);
+  if (h->mode == SIM_CLOSED_LOOP) {
+    if (sm) adjoint_kernel<1, true><<<grid, h->block_adj, smem, st>>>(A);
+    else adjoint_kernel<1, false><<<grid, h->block_adj, smem, st>>>(A);
+  } else {
+    if (sm) adjoint_kernel<0, true><<<grid, h->block_adj, smem, st>>>(A);
+    else adjoint_kernel<0, false><<<grid, h->block_adj, smem, st>>>(A);
+  }
+  return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ERR_CUDA;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t scratch_bytes(const sim_s* h, int C, int grid) {
+  if (adj_smem_scratch(h, C)) return 0;
   return align256((size_t)C * NX * sizeof(float) * (size_t)grid * h->block_adj);
 }
 
@@ -492,11 +547,18 @@ int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents,
   h->host_group0 = derive(groups[0]);
   int rc = SIM_OK;
   DevGroup tbl[SIM_MAX_GROUPS];
-  for (int g = 0; g < n_groups; ++g) tbl[g] = derive(groups[g]);
+  float arm[SIM_MAX_GROUPS];
+  for (int g = 0; g < n_groups; ++g) {
+    tbl[g] = derive(groups[g]);
+    arm[g] = groups[g].L;
+    h->max_arm = std::max(h->max_arm, arm[g]);
+  }
   if (cudaGetDevice(&h->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
       cudaMalloc(&h->d_groups, sizeof(DevGroup) * n_groups) != cudaSuccess ||
       cudaMemcpy(h->d_groups, tbl, sizeof(DevGroup) * n_groups, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMalloc(&h->d_arm, sizeof(float) * n_groups) != cudaSuccess ||
+      cudaMemcpy(h->d_arm, arm, sizeof(float) * n_groups, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMalloc(&h->status, std::max<int64_t>(n_agents, 1)) != cudaSuccess ||
       cudaMemset(h->status, 0, std::max<int64_t>(n_agents, 1)) != cudaSuccess) {
     rc = SIM_ERR_CUDA;
@@ -517,6 +579,13 @@ int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents,
     }
     if (d_max) cudaFree(d_max);
   }
+  if (rc == SIM_OK) {
+    // allow the shared-memory scratch variant of the adjoint its full size
+    const int big = (int)(kSmemScratchMax + 64 * 1024);
+    if (cudaFuncSetAttribute(adjoint_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) != cudaSuccess ||
+        cudaFuncSetAttribute(adjoint_kernel<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) != cudaSuccess)
+      rc = SIM_ERR_CUDA;
+  }
   if (rc != SIM_OK) {
     sim_destroy(h);
     return rc;
@@ -528,12 +597,18 @@ int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents,
 int sim_set_params(sim_handle_t h, const sim_group_params_t* groups, int n_groups) {
   if (!h || !groups || n_groups != h->n_groups) return SIM_ERR_ARG;
   DevGroup tbl[SIM_MAX_GROUPS];
+  float arm[SIM_MAX_GROUPS];
+  float max_arm = 0.f;
   for (int g = 0; g < n_groups; ++g) {
     if (!valid_params(groups[g])) return SIM_ERR_ARG;
     tbl[g] = derive(groups[g]);
+    arm[g] = groups[g].L;
+    max_arm = std::max(max_arm, arm[g]);
   }
-  if (cudaMemcpy(h->d_groups, tbl, sizeof(DevGroup) * n_groups, cudaMemcpyHostToDevice) != cudaSuccess)
+  if (cudaMemcpy(h->d_groups, tbl, sizeof(DevGroup) * n_groups, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->d_arm, arm, sizeof(float) * n_groups, cudaMemcpyHostToDevice) != cudaSuccess)
     return SIM_ERR_CUDA;
+  h->max_arm = max_arm;
   h->host_group0 = tbl[0];
   return SIM_OK;
 }
@@ -634,7 +709,7 @@ int sim_rollout_forward(sim_handle_t h, const float* d_state0, const float* d_cm
 size_t sim_workspace_bytes(sim_handle_t h, int ckpt_C) {
   if (!h || ckpt_C < 0) return 0;
   const int C = ckpt_C > 0 ? ckpt_C : h->C;
-  const int grid = adj_grid(h);
+  const int grid = adj_grid(h, C);
   return scratch_bytes(h, C, grid) + align256((size_t)grid * h->n_groups * NTH * sizeof(float));
 }
 
@@ -654,7 +729,7 @@ int sim_rollout_backward(sim_handle_t h, const float* d_ckpt, const float* d_cmd
       (reinterpret_cast<uintptr_t>(d_workspace) & 255u))
     return SIM_ERR_ARG;
   const int C = ckpt_C > 0 ? ckpt_C : h->C;
-  const int grid = adj_grid(h);
+  const int grid = adj_grid(h, C);
   const size_t sbytes = scratch_bytes(h, C, grid);
   const size_t need = sbytes + align256((size_t)grid * h->n_groups * NTH * sizeof(float));
   if (ws_bytes < need) return SIM_ERR_WORKSPACE;
@@ -676,10 +751,7 @@ int sim_rollout_backward(sim_handle_t h, const float* d_ckpt, const float* d_cmd
   A.n_groups = h->n_groups;
   A.H = make_h(dt);
   A.groups = h->d_groups;
-  const size_t smem = adj_smem(h);
-  if (h->mode == SIM_CLOSED_LOOP) adjoint_kernel<1><<<grid, h->block_adj, smem, st>>>(A);
-  else adjoint_kernel<0><<<grid, h->block_adj, smem, st>>>(A);
-  if (cudaGetLastError() != cudaSuccess) return SIM_ERR_CUDA;
+  if (launch_adjoint(h, A, C, grid, st) != SIM_OK) return SIM_ERR_CUDA;
   reduce_partials<<<h->n_groups * NTH, 256, 0, st>>>(A.partials, grid, h->n_groups * NTH, d_dL_dtheta);
   return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ERR_CUDA;
 }
@@ -739,10 +811,11 @@ int sim_rollout_backward_noalloc(sim_handle_t h, const float* d_ckpt, const floa
   const int C = ckpt_C > 0 ? ckpt_C : h->C;
   // as many resident blocks as the usual grid, but no more than the fixed
   // scratch holds: per block, C step-start states per thread plus one partial
-  const size_t per_block = (size_t)C * NX * sizeof(float) * h->block_adj + (size_t)h->n_groups * NTH * sizeof(float);
+  const size_t per_block = (adj_smem_scratch(h, C) ? 0 : (size_t)C * NX * sizeof(float) * h->block_adj) +
+                           (size_t)h->n_groups * NTH * sizeof(float);
   const size_t fit = (SIM_NOALLOC_SCRATCH_BYTES - 512) / per_block;
   if (fit < 1) return SIM_ERR_WORKSPACE;
-  const int grid = (int)std::min<size_t>((size_t)adj_grid(h), fit);
+  const int grid = (int)std::min<size_t>((size_t)adj_grid(h, C), fit);
   const size_t sbytes = scratch_bytes(h, C, grid);
   if (sbytes + align256((size_t)grid * h->n_groups * NTH * sizeof(float)) > SIM_NOALLOC_SCRATCH_BYTES)
     return SIM_ERR_WORKSPACE;
@@ -767,12 +840,73 @@ int sim_rollout_backward_noalloc(sim_handle_t h, const float* d_ckpt, const floa
   A.n_groups = h->n_groups;
   A.H = make_h(dt);
   A.groups = h->d_groups;
-  const size_t smem = adj_smem(h);
-  if (h->mode == SIM_CLOSED_LOOP) adjoint_kernel<1><<<grid, h->block_adj, smem, st>>>(A);
-  else adjoint_kernel<0><<<grid, h->block_adj, smem, st>>>(A);
-  if (cudaGetLastError() != cudaSuccess) return SIM_ERR_CUDA;
+  if (launch_adjoint(h, A, C, grid, st) != SIM_OK) return SIM_ERR_CUDA;
   reduce_partials<<<h->n_groups * NTH, 256, 0, st>>>(A.partials, grid, h->n_groups * NTH, d_dL_dtheta);
   return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ERR_CUDA;
+}
+
+}  // extern "C"
+
+namespace {
+
+uint32_t collide_table(int64_t n) {
+  uint64_t t = 1024;
+  while (t < (uint64_t)(2 * n) && t < (1ull << 30)) t <<= 1;
+  return (uint32_t)t;
+}
+
+size_t collide_bytes(const sim_s* h) {
+  return align256((size_t)collide_table(h->n) * sizeof(int)) + align256((size_t)h->n * sizeof(int)) +
+         align256((size_t)h->n);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t sim_collide_workspace_bytes(sim_handle_t h) { return h ? collide_bytes(h) : 0; }
+
+int sim_collide(sim_handle_t h, const float* d_state, float radius_scale, void* d_workspace, size_t ws_bytes,
+                void* stream) {
+  if (!h || !(radius_scale > 0.f) || !std::isfinite(radius_scale)) return SIM_ERR_ARG;
+  if (h->n == 0) return SIM_OK;
+  if (h->n > (int64_t)INT32_MAX) return SIM_ERR_ARG;
+  if (!d_state || !aligned16(d_state) || !d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255u))
+    return SIM_ERR_ARG;
+  if (ws_bytes < collide_bytes(h)) return SIM_ERR_WORKSPACE;
+  const uint32_t table = collide_table(h->n);
+  char* w = static_cast<char*>(d_workspace);
+  CollArgs A;
+  A.pos = reinterpret_cast<const float4*>(d_state);
+  A.gid = h->n_groups > 1 ? h->gid : nullptr;
+  A.status = h->status;
+  A.arm = h->d_arm;
+  A.scale = radius_scale;
+  // cells a little wider than the largest collision distance, so a colliding
+  // pair is never more than one cell apart on any axis after rounding
+  A.inv_cell = (float)(1.0 / (2.0 * (double)h->max_arm * radius_scale * 1.001));
+  A.mask = table - 1;
+  A.head = reinterpret_cast<int*>(w);
+  A.next = reinterpret_cast<int*>(w + align256((size_t)table * sizeof(int)));
+  A.hit = reinterpret_cast<uint8_t*>(w + align256((size_t)table * sizeof(int)) + align256((size_t)h->n * sizeof(int)));
+  A.n = h->n;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(A.head, 0xff, (size_t)table * sizeof(int), st) != cudaSuccess) return SIM_ERR_CUDA;
+  const int grid = (int)std::min<int64_t>((h->n + 255) / 256, (int64_t)h->sms * 8);
+  collide_insert<<<grid, 256, 0, st>>>(A);
+  collide_query<<<grid, 256, 0, st>>>(A);
+  collide_apply<<<grid, 256, 0, st>>>(A);
+  return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ERR_CUDA;
+}
+
+int sim_copy_status(sim_handle_t h, uint8_t* d_status_out, void* stream) {
+  if (!h) return SIM_ERR_ARG;
+  if (h->n == 0) return SIM_OK;
+  if (!d_status_out) return SIM_ERR_ARG;
+  return cudaMemcpyAsync(d_status_out, h->status, (size_t)h->n, cudaMemcpyDeviceToDevice,
+                         reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? SIM_OK
+             : SIM_ERR_CUDA;
 }
 
 int sim_status(sim_handle_t h, int64_t* n_dead, int timeout_ms, void* stream) {
@@ -847,6 +981,7 @@ void sim_destroy(sim_handle_t h) {
   if (!h) return;
   if (h->status) cudaFree(h->status);
   if (h->d_groups) cudaFree(h->d_groups);
+  if (h->d_arm) cudaFree(h->d_arm);
   delete h;
 }
 

@@ -1,0 +1,71 @@
+// The fused forward kernel: K RK4 steps per launch, one thread per agent,
+// state in registers between steps and in HBM (planar float4 SoA) between
+// launches; one parameter group in kernel parameters or several in shared
+// memory indexed by a per-agent uint8 id; grid-stride over a resident wave.
+// Agents with a nonzero status byte are skipped; an agent whose state turns
+// non-finite keeps its last finite state and is marked (status 1).
+#pragma once
+#include "model_fwd.cuh"
+
+namespace qs {
+
+struct StepArgs {
+  float* state;
+  const float4* cmd;
+  const uint8_t* gid;
+  uint8_t* status;
+  int64_t n;
+  int K;
+  int n_groups;
+  StepH H;
+  const DevGroup* groups;  // device table (several groups)
+};
+
+__device__ __forceinline__ bool all_finite(const St& x) {
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < NX; ++i) s += x.a[i];
+  return isfinite(s);
+}
+
+template <bool HETERO>
+__device__ __forceinline__ void load_groups(DevGroup* sg, const DevGroup* src, int n_groups) {
+  if (HETERO) {
+    const float4* s = reinterpret_cast<const float4*>(src);
+    float4* d = reinterpret_cast<float4*>(sg);
+    for (int i = threadIdx.x; i < n_groups * (int)(sizeof(DevGroup) / 16); i += blockDim.x) d[i] = s[i];
+    __syncthreads();
+  }
+}
+
+// K fused RK4 steps per launch; the state touches HBM once per launch.
+template <int MODE, bool HETERO>
+__global__ void __launch_bounds__(256) step_kernel(StepArgs A, const DevGroup P0) {
+  extern __shared__ float4 smem4[];
+  DevGroup* sg = reinterpret_cast<DevGroup*>(smem4);
+  load_groups<HETERO>(sg, A.groups, A.n_groups);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) {
+    if (A.status[i]) continue;  // dead agents are frozen
+    St x;
+    load_state(A.state, A.n, i, x);
+    const float4 c = A.cmd[i];
+    float ch = 0.f, sh = 0.f;
+    if (MODE == 1) sincosf(c.w, &sh, &ch);
+    if (HETERO) {
+      const DevGroup P = sg[A.gid[i]];
+      const LagCoef L = lag_coef(P.inv_tau, A.H);
+      for (int k = 0; k < A.K; ++k) step<MODE>(P, x, c, ch, sh, A.H, L);
+    } else {
+      const LagCoef L = lag_coef(P0.inv_tau, A.H);
+      for (int k = 0; k < A.K; ++k) step<MODE>(P0, x, c, ch, sh, A.H, L);
+    }
+    if (all_finite(x)) {
+      store_state(A.state, A.n, i, x);
+    } else {
+      A.status[i] = 1;  // keep the last finite state
+    }
+  }
+}
+
+}  // namespace qs

@@ -179,6 +179,26 @@ class Sim:
                                          _ptr(workspace), ws, _stream(stream)), "sim_rollout_backward")
         return dx0, dth, dth_a
 
+    # -- collisions --
+    def collide_workspace_bytes(self) -> int:
+        return int(lib().sim_collide_workspace_bytes(self._h))
+
+    def collide(self, state: torch.Tensor, radius_scale: float = 1.0, workspace: torch.Tensor | None = None,
+                stream=None):
+        """Marks agents closer than the sum of their arm lengths (x radius_scale) dead (status 2)."""
+        _check_f32(state, 17 * self.n, "state")
+        ws = self.collide_workspace_bytes()
+        if workspace is None or workspace.numel() < ws:
+            workspace = torch.empty(max(ws, 1), dtype=torch.uint8, device=state.device)
+        check(lib().sim_collide(self._h, _ptr(state), float(radius_scale), _ptr(workspace), ws, _stream(stream)),
+              "sim_collide")
+
+    def status(self, stream=None) -> torch.Tensor:
+        """Per-agent status bytes (0 alive, 1 non-finite, 2 collided) as a uint8 CUDA tensor."""
+        out = torch.empty(max(self.n, 0), dtype=torch.uint8, device=torch.device("cuda", torch.cuda.current_device()))
+        check(lib().sim_copy_status(self._h, _ptr(out) if self.n else None, _stream(stream)), "sim_copy_status")
+        return out
+
     # -- status --
     def n_dead(self, timeout_ms: int = 60000, stream=None) -> int:
         v = ctypes.c_int64()

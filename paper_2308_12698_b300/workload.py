@@ -250,3 +250,32 @@ def from_planes(flat: np.ndarray, n: int) -> np.ndarray:
         x[:, 4 * k:4 * k + 4] = flat[4 * k * n: 4 * k * n + 4 * n].reshape(n, 4)
     x[:, 16] = flat[16 * n: 17 * n]
     return x
+
+
+def collision_field(n: int, spacing: float = 2.0, planted: float = 0.01, seed: int = BASE_SEED + 5,
+                    nsteps: int = 1, dt: float = 1e-3) -> Workload:
+    """Reference quadrotors spread uniformly over a cube of side spacing * n^(1/3) (mean spacing
+    `spacing` m), with a fraction `planted` of agents moved next to another one at a distance
+    U[0.2, 0.6] m along a random direction (two reference airframes collide below 0.45 m).
+    Waypoints are the agents' own positions (hover); heading held."""
+    rng = np.random.default_rng(seed)
+    groups = [base_group()]
+    gid = np.zeros(n, dtype=np.uint8)
+    wh = _hover_per_agent(groups, gid)
+    x0, psi = _initial_states(rng, n, wh)
+    side = spacing * max(n, 1) ** (1.0 / 3.0)
+    pos = rng.uniform(-side / 2, side / 2, (n, 3))
+    k = int(planted * n)
+    if k and n > 1:
+        a = rng.choice(n, k, replace=False)
+        b = rng.integers(0, n, k)
+        b = np.where(b == a, (b + 1) % n, b)
+        u = rng.normal(size=(k, 3))
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        pos[a] = pos[b] + u * rng.uniform(0.2, 0.6, (k, 1))
+    x0[:, 0:3] = pos.astype(np.float32)
+    cmd = np.zeros((n, 4), dtype=np.float32)
+    cmd[:, 0:3] = x0[:, 0:3]
+    cmd[:, 3] = psi
+    return Workload("collision-field", CLOSED_LOOP, groups, gid, x0, cmd, dt, nsteps,
+                    extra=dict(side=side, planted=k))

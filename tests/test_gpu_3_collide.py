@@ -1,0 +1,126 @@
+"""Collision detection on the GPU (spatial hash) against the checker's brute force.
+
+The decision is integer (a flag per agent), taken in FP32 on both sides with
+the same rounding, so the flags must agree bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2308_12698_b300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch.device("cuda:0")
+
+
+def _radii(wl, scale=1.0):
+    arm = np.array([np.float32(g["L"]) for g in wl.groups], np.float32)
+    return (arm[wl.gid] * np.float32(scale)).astype(np.float32)
+
+
+def gpu_collide(wl, dev, scale=1.0, x0=None, runs=1):
+    from paper_2308_12698_b300.sim import Sim, planar
+    g = torch.from_numpy(wl.gid).to(dev) if len(wl.groups) > 1 else None
+    sim = Sim(wl.groups, wl.n, wl.mode, gid=g)
+    x = planar(torch.from_numpy(wl.x0 if x0 is None else x0)).to(dev)
+    outs = []
+    for _ in range(runs):
+        sim.reset_status()
+        sim.collide(x, scale)
+        outs.append(sim.status().cpu().numpy())
+    torch.cuda.synchronize()
+    sim.close()
+    return outs if runs > 1 else outs[0]
+
+
+@pytest.mark.parametrize("n", [1, 2, 33, 1000, 50_000])
+def test_flags_bit_exact(dev, orc, n):
+    wl = W.collision_field(n, planted=0.05)
+    st = gpu_collide(wl, dev)
+    ref = orc.collisions(wl.x0[:, 0:3], _radii(wl), np.ones(wl.n))
+    np.testing.assert_array_equal((st == 2).astype(np.uint8), ref)
+    if n >= 1000:
+        assert ref.sum() > 0
+
+
+def test_two_agents_at_and_inside_threshold(dev, orc):
+    wl = W.collision_field(4, planted=0.0)
+    x0 = wl.x0.copy()
+    x0[:, 0:3] = [[0, 0, 0], [0.45, 0, 0], [5, 5, 5], [5.449, 5, 5]]
+    st = gpu_collide(wl, dev, x0=x0)
+    ref = orc.collisions(x0[:, 0:3], _radii(wl), np.ones(4))
+    np.testing.assert_array_equal((st == 2).astype(np.uint8), ref)
+
+
+def test_heterogeneous_radii_and_scale(dev, orc):
+    wl = W.heterogeneous(sizes=(300, 700, 2000), nsteps=1, shuffle=True)
+    x0 = wl.x0.copy()
+    rng = np.random.default_rng(2)
+    x0[:, 0:3] = rng.uniform(-6, 6, (wl.n, 3))
+    for scale in (0.5, 1.0, 2.0):
+        st = gpu_collide(wl, dev, scale=scale, x0=x0)
+        ref = orc.collisions(x0[:, 0:3], _radii(wl, scale), np.ones(wl.n))
+        np.testing.assert_array_equal((st == 2).astype(np.uint8), ref)
+
+
+def test_dead_agents_are_excluded(dev, orc):
+    from paper_2308_12698_b300.sim import Sim, planar
+    wl = W.collision_field(5000, planted=0.05)
+    x0 = wl.x0.copy()
+    dead = np.arange(0, wl.n, 7)
+    x0[dead, 3] = np.nan  # non-finite velocity: the first step marks these dead
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    x = planar(torch.from_numpy(x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).reshape(-1).to(dev)
+    sim.step(x, cmd, wl.dt, 1, K=1)
+    st0 = sim.status().cpu().numpy()
+    assert set(np.nonzero(st0)[0]) == set(dead)
+    sim.collide(x, 1.0)
+    st = sim.status().cpu().numpy()
+    from paper_2308_12698_b300.sim import unplanar
+    pos = unplanar(x, wl.n).cpu().numpy()[:, 0:3]
+    alive = (st0 == 0).astype(np.uint8)
+    ref = orc.collisions(pos, _radii(wl), alive)
+    np.testing.assert_array_equal((st == 2).astype(np.uint8), ref)
+    assert np.all(st[dead] == 1)
+    sim.close()
+
+
+def test_collided_agents_are_frozen(dev):
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    wl = W.collision_field(2000, planted=0.05)
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    x = planar(torch.from_numpy(wl.x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).reshape(-1).to(dev)
+    sim.collide(x, 1.0)
+    before = unplanar(x, wl.n).cpu().numpy()
+    st = sim.status().cpu().numpy()
+    sim.step(x, cmd, wl.dt, 20, K=5)
+    after = unplanar(x, wl.n).cpu().numpy()
+    hit = st == 2
+    assert hit.any() and (~hit).any()
+    np.testing.assert_array_equal(after[hit], before[hit])
+    assert np.any(after[~hit] != before[~hit])
+    assert sim.n_dead() == int(hit.sum())
+    sim.close()
+
+
+def test_deterministic_and_full_size_sampled(dev, orc):
+    """1e6 agents in the bench's launch shape: two runs agree, 4096 sampled agents match brute force."""
+    wl = W.collision_field(1_000_000)
+    a, b = gpu_collide(wl, dev, runs=2)
+    np.testing.assert_array_equal(a, b)
+    idx = np.random.default_rng(4).choice(wl.n, 4096, replace=False)
+    planted_hits = np.nonzero(a == 2)[0][:512]
+    idx = np.unique(np.concatenate([idx, planted_hits]))
+    ref = orc.collisions(wl.x0[:, 0:3], _radii(wl), np.ones(wl.n), idx=idx)
+    np.testing.assert_array_equal((a[idx] == 2).astype(np.uint8), ref)
+    assert ref.sum() >= 256
