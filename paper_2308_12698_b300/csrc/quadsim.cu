@@ -384,8 +384,12 @@ struct sim_s {
   uint8_t* status = nullptr;     // owned
   DevGroup* d_groups = nullptr;  // owned
   float* d_arm = nullptr;        // owned: arm length per group (collision radius)
+  unsigned long long* d_count = nullptr;  // owned: counter for sim_status
   float max_arm = 0.f;
   DevGroup host_group0;
+  // host-buffer pipeline (sim_step_host): created on first use
+  cudaStream_t s_h2d = nullptr, s_d2h = nullptr, s_comp[2] = {nullptr, nullptr};
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr, ev_in[8] = {}, ev_done[8] = {};
   int block_fwd = kDefaultBlockFwd;
   int block_adj = kDefaultBlockAdj;
   int K = kDefaultK;
@@ -403,7 +407,7 @@ bool hetero(const sim_s* h) { return h->n_groups > 1; }
 
 size_t group_smem(const sim_s* h) { return hetero(h) ? sizeof(DevGroup) * h->n_groups : 0; }
 
-int fwd_grid(const sim_s* h, size_t smem) {
+int fwd_grid(const sim_s* h, size_t smem, int64_t count) {
   // one resident wave of blocks, grid-stride over the agents
   int occ;
   if (h->mode == SIM_CLOSED_LOOP)
@@ -461,19 +465,22 @@ size_t scratch_bytes(const sim_s* h, int C, int grid) {
   return align256((size_t)C * NX * sizeof(float) * (size_t)grid * h->block_adj);
 }
 
-int launch_step(sim_s* h, float* d_state, const float* d_cmd, StepH H, int K, cudaStream_t st) {
+int launch_step(sim_s* h, float* d_state, const float* d_cmd, StepH H, int K, cudaStream_t st, int64_t first,
+                int64_t count) {
   StepArgs A;
   A.state = d_state;
   A.cmd = reinterpret_cast<const float4*>(d_cmd);
   A.gid = h->gid;
   A.status = h->status;
   A.n = h->n;
+  A.first = first;
+  A.count = count;
   A.K = K;
   A.n_groups = h->n_groups;
   A.H = H;
   A.groups = h->d_groups;
   const size_t smem = group_smem(h);
-  const int grid = fwd_grid(h, smem);
+  const int grid = fwd_grid(h, smem, count);
   const DevGroup& P0 = h->host_group0;
   if (h->mode == SIM_CLOSED_LOOP) {
     if (hetero(h)) step_kernel<1, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
@@ -558,6 +565,7 @@ int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents,
       cudaMalloc(&h->d_groups, sizeof(DevGroup) * n_groups) != cudaSuccess ||
       cudaMemcpy(h->d_groups, tbl, sizeof(DevGroup) * n_groups, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMalloc(&h->d_arm, sizeof(float) * n_groups) != cudaSuccess ||
+      cudaMalloc(&h->d_count, sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemcpy(h->d_arm, arm, sizeof(float) * n_groups, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMalloc(&h->status, std::max<int64_t>(n_agents, 1)) != cudaSuccess ||
       cudaMemset(h->status, 0, std::max<int64_t>(n_agents, 1)) != cudaSuccess) {
@@ -650,7 +658,7 @@ int sim_step(sim_handle_t h, float* d_state, const float* d_cmd, float dt, int64
   int64_t done = 0;
   while (done < nsteps) {
     const int k = (int)std::min<int64_t>(K, nsteps - done);
-    const int rc = launch_step(h, d_state, d_cmd, H, k, st);
+    const int rc = launch_step(h, d_state, d_cmd, H, k, st, 0, h->n);
     if (rc != SIM_OK) return rc;
     done += k;
   }
@@ -659,15 +667,66 @@ int sim_step(sim_handle_t h, float* d_state, const float* d_cmd, float dt, int64
 
 int sim_step_host(sim_handle_t h, float* h_state, const float* h_cmd, float* d_state, float* d_cmd, float dt,
                   int64_t nsteps, int substeps_K, void* stream) {
-  if (!h || !h_state || !h_cmd || !d_state || !d_cmd) return SIM_ERR_ARG;
+  if (!h || !h_state || !h_cmd || !d_state || !d_cmd || nsteps < 0 || substeps_K < 0 || !(dt > 0.f) ||
+      !std::isfinite(dt))
+    return SIM_ERR_ARG;
+  if (!aligned16(d_state) || !aligned16(d_cmd)) return SIM_ERR_ARG;
+  const int64_t n = h->n;
+  if (n == 0) return SIM_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const size_t sb = (size_t)NX * h->n * sizeof(float), cb = (size_t)4 * h->n * sizeof(float);
-  if (cudaMemcpyAsync(d_state, h_state, sb, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(d_cmd, h_cmd, cb, cudaMemcpyHostToDevice, st) != cudaSuccess)
+  if (!h->s_h2d) {
+    for (cudaStream_t* p : {&h->s_h2d, &h->s_d2h, &h->s_comp[0], &h->s_comp[1]})
+      if (cudaStreamCreateWithFlags(p, cudaStreamNonBlocking) != cudaSuccess) return SIM_ERR_CUDA;
+    for (cudaEvent_t* e : {&h->ev_start, &h->ev_end})
+      if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return SIM_ERR_CUDA;
+    for (int c = 0; c < 8; ++c)
+      if (cudaEventCreateWithFlags(&h->ev_in[c], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->ev_done[c], cudaEventDisableTiming) != cudaSuccess)
+        return SIM_ERR_CUDA;
+  }
+  // Chunks of agents flow through H2D copy -> steps -> D2H copy on separate
+  // streams, so the copies of one chunk overlap the steps of the others and
+  // two compute streams let one chunk's last wave overlap the next chunk.
+  const int m = (int)std::max<int64_t>(1, std::min<int64_t>(8, n / 65536));
+  const int64_t chunk = (n + m - 1) / m;
+  const int K = substeps_K > 0 ? substeps_K : h->K;
+  const StepH H = make_h(dt);
+  const size_t fs = sizeof(float);
+  if (cudaEventRecord(h->ev_start, st) != cudaSuccess) return SIM_ERR_CUDA;
+  for (cudaStream_t s2 : {h->s_h2d, h->s_d2h, h->s_comp[0], h->s_comp[1]})
+    if (cudaStreamWaitEvent(s2, h->ev_start, 0) != cudaSuccess) return SIM_ERR_CUDA;
+  auto copy_planes = [&](float* dst, const float* src, int64_t a0, int64_t cnt, cudaMemcpyKind kind,
+                         cudaStream_t s2) -> bool {
+    for (int k = 0; k < 4; ++k) {
+      const size_t off = (size_t)4 * k * n + (size_t)4 * a0;
+      if (cudaMemcpyAsync(dst + off, src + off, (size_t)4 * cnt * fs, kind, s2) != cudaSuccess) return false;
+    }
+    const size_t off = (size_t)16 * n + (size_t)a0;
+    return cudaMemcpyAsync(dst + off, src + off, (size_t)cnt * fs, kind, s2) == cudaSuccess;
+  };
+  for (int c = 0; c < m; ++c) {
+    const int64_t a0 = c * chunk, cnt = std::min<int64_t>(chunk, n - a0);
+    if (cnt <= 0) break;
+    if (!copy_planes(d_state, h_state, a0, cnt, cudaMemcpyHostToDevice, h->s_h2d) ||
+        cudaMemcpyAsync(d_cmd + 4 * a0, h_cmd + 4 * a0, (size_t)4 * cnt * fs, cudaMemcpyHostToDevice, h->s_h2d) !=
+            cudaSuccess ||
+        cudaEventRecord(h->ev_in[c], h->s_h2d) != cudaSuccess)
+      return SIM_ERR_CUDA;
+    cudaStream_t sc = h->s_comp[c & 1];
+    if (cudaStreamWaitEvent(sc, h->ev_in[c], 0) != cudaSuccess) return SIM_ERR_CUDA;
+    for (int64_t done = 0; done < nsteps;) {
+      const int k = (int)std::min<int64_t>(K, nsteps - done);
+      const int rc = launch_step(h, d_state, d_cmd, H, k, sc, a0, cnt);
+      if (rc != SIM_OK) return rc;
+      done += k;
+    }
+    if (cudaEventRecord(h->ev_done[c], sc) != cudaSuccess ||
+        cudaStreamWaitEvent(h->s_d2h, h->ev_done[c], 0) != cudaSuccess ||
+        !copy_planes(h_state, d_state, a0, cnt, cudaMemcpyDeviceToHost, h->s_d2h))
+      return SIM_ERR_CUDA;
+  }
+  if (cudaEventRecord(h->ev_end, h->s_d2h) != cudaSuccess || cudaStreamWaitEvent(st, h->ev_end, 0) != cudaSuccess)
     return SIM_ERR_CUDA;
-  int rc = sim_step(h, d_state, d_cmd, dt, nsteps, substeps_K, stream);
-  if (rc != SIM_OK) return rc;
-  if (cudaMemcpyAsync(h_state, d_state, sb, cudaMemcpyDeviceToHost, st) != cudaSuccess) return SIM_ERR_CUDA;
   return wait_stream(st, 600000);
 }
 
@@ -693,7 +752,7 @@ int sim_rollout_forward(sim_handle_t h, const float* d_state0, const float* d_cm
   A.H = make_h(dt);
   A.groups = h->d_groups;
   const size_t smem = group_smem(h);
-  const int grid = fwd_grid(h, smem);
+  const int grid = fwd_grid(h, smem, h->n);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const DevGroup& P0 = h->host_group0;
   if (h->mode == SIM_CLOSED_LOOP) {
@@ -914,20 +973,14 @@ int sim_status(sim_handle_t h, int64_t* n_dead, int timeout_ms, void* stream) {
   *n_dead = 0;
   if (h->n == 0) return SIM_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  unsigned long long* d = nullptr;
   unsigned long long v = 0;
-  if (cudaMalloc(&d, sizeof(v)) != cudaSuccess) return SIM_ERR_CUDA;
-  int rc = SIM_OK;
-  if (cudaMemsetAsync(d, 0, sizeof(v), st) != cudaSuccess) rc = SIM_ERR_CUDA;
-  if (rc == SIM_OK) {
-    count_dead_kernel<<<std::min<int64_t>((h->n + 255) / 256, 4096), 256, 0, st>>>(h->status, h->n, d);
-    if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpyAsync(&v, d, sizeof(v), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-      rc = SIM_ERR_CUDA;
-  }
-  if (rc == SIM_OK) rc = wait_stream(st, timeout_ms);
+  if (cudaMemsetAsync(h->d_count, 0, sizeof(v), st) != cudaSuccess) return SIM_ERR_CUDA;
+  count_dead_kernel<<<std::min<int64_t>((h->n + 255) / 256, 4096), 256, 0, st>>>(h->status, h->n, h->d_count);
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&v, h->d_count, sizeof(v), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return SIM_ERR_CUDA;
+  const int rc = wait_stream(st, timeout_ms);
   if (rc == SIM_OK) *n_dead = (int64_t)v;
-  if (rc != SIM_ERR_TIMEOUT) cudaFree(d);
   return rc;
 }
 
@@ -979,9 +1032,18 @@ void sim_graph_destroy(sim_graph_t g) {
 
 void sim_destroy(sim_handle_t h) {
   if (!h) return;
+  for (cudaStream_t st : {h->s_h2d, h->s_d2h, h->s_comp[0], h->s_comp[1]})
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t e : {h->ev_start, h->ev_end})
+    if (e) cudaEventDestroy(e);
+  for (int c = 0; c < 8; ++c) {
+    if (h->ev_in[c]) cudaEventDestroy(h->ev_in[c]);
+    if (h->ev_done[c]) cudaEventDestroy(h->ev_done[c]);
+  }
   if (h->status) cudaFree(h->status);
   if (h->d_groups) cudaFree(h->d_groups);
   if (h->d_arm) cudaFree(h->d_arm);
+  if (h->d_count) cudaFree(h->d_count);
   delete h;
 }
 

@@ -14,7 +14,9 @@ struct StepArgs {
   const float4* cmd;
   const uint8_t* gid;
   uint8_t* status;
-  int64_t n;
+  int64_t n;      // agents in the buffers (the plane stride)
+  int64_t first;  // this launch steps agents [first, first + count)
+  int64_t count;
   int K;
   int n_groups;
   StepH H;
@@ -45,7 +47,8 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs A, const DevGroup P0
   DevGroup* sg = reinterpret_cast<DevGroup*>(smem4);
   load_groups<HETERO>(sg, A.groups, A.n_groups);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) {
+  const int64_t end = A.first + A.count;
+  for (int64_t i = A.first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end; i += stride) {
     if (A.status[i]) continue;  // dead agents are frozen
     St x;
     load_state(A.state, A.n, i, x);
