@@ -535,6 +535,25 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     hg.close()
     hs.close()
 
+    # decision rounds: commands from pinned host memory every M steps, positions back after
+    # each round, both overlapped with the physics (1000 steps per bench step)
+    rounds = {}
+    for M in (10, 100):
+        R = T_STEPS // M
+        h_cmds = torch.from_numpy(wl.cmd).reshape(1, -1).repeat(R, 1).contiguous().pin_memory()
+        h_obs = torch.empty((R, 4 * N_AGENTS), dtype=torch.float32).pin_memory()
+        cmd2 = torch.empty(8 * N_AGENTS, dtype=torch.float32, device=x0.device)
+        obs2 = torch.empty(8 * N_AGENTS, dtype=torch.float32, device=x0.device)
+        Kr = min(sim.launch()["K"], M)
+        rrun = lambda: sim.run_rounds(x, h_cmds, M, DT, K=Kr, h_obs=h_obs, cmd2=cmd2, obs2=obs2)  # noqa: E731
+        timed_steps(rrun, 2, reset)
+        t = timed_steps(rrun, reps, reset)
+        ms = max_over_ranks(sum(t), world) / reps
+        rounds[f"M{M}"] = {"value": world * N_AGENTS * T_STEPS / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                           "rounds": R, "K": Kr, "h2d_bytes_per_round": 16 * N_AGENTS,
+                           "d2h_bytes_per_round": 16 * N_AGENTS}
+    out["decision_rounds"] = rounds
+
     # collision detection: 1e6 agents at 2 m mean spacing, 1 % planted near pairs
     cw = W.collision_field(N_AGENTS)
     cs = Sim(cw.groups, cw.n, cw.mode)

@@ -117,6 +117,21 @@ int sim_step(sim_handle_t h, float* d_state, const float* d_cmd, float dt, int64
 int sim_step_host(sim_handle_t h, float* h_state, const float* h_cmd, float* d_state, float* d_cmd, float dt,
                   int64_t nsteps, int substeps_K, void* stream);
 
+/* Decision rounds with the algorithm side outside the physics loop (Sec.
+ * III-A: the physical world runs on between decisions).  Runs `rounds` rounds
+ * of steps_per_round RK4 steps (substeps_K fused per launch; 0 = tuned).
+ * Round r uses the commands h_cmds + r * 4 N (pinned host memory, float4 per
+ * agent): they are copied into one of the two device command planes of
+ * d_cmd2 (2 * 4 N floats) on a library copy stream while round r - 1 runs.
+ * After round r the positions plane (plane 0: px, py, pz, vx per agent) is
+ * snapshotted into one of the two planes of d_obs2 (2 * 4 N floats, may be
+ * NULL with h_obs NULL) and copied to h_obs + r * 4 N on another copy stream
+ * while round r + 1 runs.  d_state is updated in place.  The call is ordered
+ * after earlier work on `stream` and returns when the last round and its
+ * observations are done (bounded wait).  Not capturable (it waits). */
+int sim_run_rounds(sim_handle_t h, float* d_state, float* d_cmd2, const float* h_cmds, float* d_obs2, float* h_obs,
+                   float dt, int64_t steps_per_round, int64_t rounds, int substeps_K, void* stream);
+
 /* Forward rollout with checkpoints, one launch.  Reads d_state0, writes
  * S+1 planar states into d_ckpt (S = ceil(nsteps/ckpt_C)): x_0, x_C, ...,
  * x_{(S-1)C}, then x_nsteps last.  d_ckpt holds (S+1)*17*N floats.

@@ -390,6 +390,8 @@ struct sim_s {
   // host-buffer pipeline (sim_step_host): created on first use
   cudaStream_t s_h2d = nullptr, s_d2h = nullptr, s_comp[2] = {nullptr, nullptr};
   cudaEvent_t ev_start = nullptr, ev_end = nullptr, ev_in[8] = {}, ev_done[8] = {};
+  // decision rounds (sim_run_rounds): per command plane and observation plane
+  cudaEvent_t ev_cmd[2] = {}, ev_cmd_free[2] = {}, ev_obs[2] = {}, ev_obs_free[2] = {};
   int block_fwd = kDefaultBlockFwd;
   int block_adj = kDefaultBlockAdj;
   int K = kDefaultK;
@@ -490,6 +492,23 @@ int launch_step(sim_s* h, float* d_state, const float* d_cmd, StepH H, int K, cu
     else step_kernel<0, false><<<grid, h->block_fwd, smem, st>>>(A, P0);
   }
   return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ERR_CUDA;
+}
+
+// Library-owned streams and events of the host pipelines, created on first use.
+int pipeline_streams(sim_s* h) {
+  if (h->s_h2d) return SIM_OK;
+  for (cudaStream_t* p : {&h->s_h2d, &h->s_d2h, &h->s_comp[0], &h->s_comp[1]})
+    if (cudaStreamCreateWithFlags(p, cudaStreamNonBlocking) != cudaSuccess) return SIM_ERR_CUDA;
+  for (cudaEvent_t* e : {&h->ev_start, &h->ev_end})
+    if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return SIM_ERR_CUDA;
+  for (int c = 0; c < 8; ++c)
+    if (cudaEventCreateWithFlags(&h->ev_in[c], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_done[c], cudaEventDisableTiming) != cudaSuccess)
+      return SIM_ERR_CUDA;
+  for (int b = 0; b < 2; ++b)
+    for (cudaEvent_t* e : {&h->ev_cmd[b], &h->ev_cmd_free[b], &h->ev_obs[b], &h->ev_obs_free[b]})
+      if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return SIM_ERR_CUDA;
+  return SIM_OK;
 }
 
 int wait_stream(cudaStream_t st, int timeout_ms) {
@@ -674,16 +693,7 @@ int sim_step_host(sim_handle_t h, float* h_state, const float* h_cmd, float* d_s
   const int64_t n = h->n;
   if (n == 0) return SIM_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (!h->s_h2d) {
-    for (cudaStream_t* p : {&h->s_h2d, &h->s_d2h, &h->s_comp[0], &h->s_comp[1]})
-      if (cudaStreamCreateWithFlags(p, cudaStreamNonBlocking) != cudaSuccess) return SIM_ERR_CUDA;
-    for (cudaEvent_t* e : {&h->ev_start, &h->ev_end})
-      if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return SIM_ERR_CUDA;
-    for (int c = 0; c < 8; ++c)
-      if (cudaEventCreateWithFlags(&h->ev_in[c], cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventCreateWithFlags(&h->ev_done[c], cudaEventDisableTiming) != cudaSuccess)
-        return SIM_ERR_CUDA;
-  }
+  if (pipeline_streams(h) != SIM_OK) return SIM_ERR_CUDA;
   // Chunks of agents flow through H2D copy -> steps -> D2H copy on separate
   // streams, so the copies of one chunk overlap the steps of the others and
   // two compute streams let one chunk's last wave overlap the next chunk.
@@ -726,6 +736,64 @@ int sim_step_host(sim_handle_t h, float* h_state, const float* h_cmd, float* d_s
       return SIM_ERR_CUDA;
   }
   if (cudaEventRecord(h->ev_end, h->s_d2h) != cudaSuccess || cudaStreamWaitEvent(st, h->ev_end, 0) != cudaSuccess)
+    return SIM_ERR_CUDA;
+  return wait_stream(st, 600000);
+}
+
+int sim_run_rounds(sim_handle_t h, float* d_state, float* d_cmd2, const float* h_cmds, float* d_obs2, float* h_obs,
+                   float dt, int64_t steps_per_round, int64_t rounds, int substeps_K, void* stream) {
+  if (!h || !d_state || !d_cmd2 || !h_cmds || steps_per_round < 1 || rounds < 0 || substeps_K < 0 ||
+      !(dt > 0.f) || !std::isfinite(dt))
+    return SIM_ERR_ARG;
+  if ((h_obs == nullptr) != (d_obs2 == nullptr)) return SIM_ERR_ARG;
+  if (!aligned16(d_state) || !aligned16(d_cmd2) || (d_obs2 && !aligned16(d_obs2))) return SIM_ERR_ARG;
+  const int64_t n = h->n;
+  if (n == 0 || rounds == 0) return SIM_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (pipeline_streams(h) != SIM_OK) return SIM_ERR_CUDA;
+  const size_t plane = (size_t)4 * n;  // floats in one command or observation plane
+  const StepH H = make_h(dt);
+  const int K = substeps_K > 0 ? substeps_K : h->K;
+  if (cudaEventRecord(h->ev_start, st) != cudaSuccess || cudaStreamWaitEvent(h->s_h2d, h->ev_start, 0) != cudaSuccess ||
+      cudaStreamWaitEvent(h->s_d2h, h->ev_start, 0) != cudaSuccess)
+    return SIM_ERR_CUDA;
+  auto push = [&](int64_t r) -> bool {  // commands of round r into plane r % 2
+    const int b = (int)(r & 1);
+    float* dst = d_cmd2 + b * plane;
+    if (r >= 2 && cudaStreamWaitEvent(h->s_h2d, h->ev_cmd_free[b], 0) != cudaSuccess) return false;
+    return cudaMemcpyAsync(dst, h_cmds + (size_t)r * plane, plane * sizeof(float), cudaMemcpyHostToDevice,
+                           h->s_h2d) == cudaSuccess &&
+           cudaEventRecord(h->ev_cmd[b], h->s_h2d) == cudaSuccess;
+  };
+  if (!push(0)) return SIM_ERR_CUDA;
+  for (int64_t r = 0; r < rounds; ++r) {
+    const int b = (int)(r & 1);
+    if (r + 1 < rounds && !push(r + 1)) return SIM_ERR_CUDA;
+    if (cudaStreamWaitEvent(st, h->ev_cmd[b], 0) != cudaSuccess) return SIM_ERR_CUDA;
+    const float* cmd = d_cmd2 + b * plane;
+    for (int64_t done = 0; done < steps_per_round;) {
+      const int k = (int)std::min<int64_t>(K, steps_per_round - done);
+      const int rc = launch_step(h, d_state, cmd, H, k, st, 0, n);
+      if (rc != SIM_OK) return rc;
+      done += k;
+    }
+    if (cudaEventRecord(h->ev_cmd_free[b], st) != cudaSuccess) return SIM_ERR_CUDA;
+    if (d_obs2) {
+      float* snap = d_obs2 + b * plane;
+      if (r >= 2 && cudaStreamWaitEvent(st, h->ev_obs_free[b], 0) != cudaSuccess) return SIM_ERR_CUDA;
+      if (cudaMemcpyAsync(snap, d_state, plane * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+          cudaEventRecord(h->ev_obs[b], st) != cudaSuccess ||
+          cudaStreamWaitEvent(h->s_d2h, h->ev_obs[b], 0) != cudaSuccess ||
+          cudaMemcpyAsync(h_obs + (size_t)r * plane, snap, plane * sizeof(float), cudaMemcpyDeviceToHost, h->s_d2h) !=
+              cudaSuccess ||
+          cudaEventRecord(h->ev_obs_free[b], h->s_d2h) != cudaSuccess)
+        return SIM_ERR_CUDA;
+    }
+  }
+  if (cudaEventRecord(h->ev_end, h->s_d2h) != cudaSuccess || cudaStreamWaitEvent(st, h->ev_end, 0) != cudaSuccess)
+    return SIM_ERR_CUDA;
+  // the copy stream may still hold the last command copies' completion: order them too
+  if (cudaEventRecord(h->ev_start, h->s_h2d) != cudaSuccess || cudaStreamWaitEvent(st, h->ev_start, 0) != cudaSuccess)
     return SIM_ERR_CUDA;
   return wait_stream(st, 600000);
 }
@@ -1040,6 +1108,9 @@ void sim_destroy(sim_handle_t h) {
     if (h->ev_in[c]) cudaEventDestroy(h->ev_in[c]);
     if (h->ev_done[c]) cudaEventDestroy(h->ev_done[c]);
   }
+  for (int b = 0; b < 2; ++b)
+    for (cudaEvent_t e : {h->ev_cmd[b], h->ev_cmd_free[b], h->ev_obs[b], h->ev_obs_free[b]})
+      if (e) cudaEventDestroy(e);
   if (h->status) cudaFree(h->status);
   if (h->d_groups) cudaFree(h->d_groups);
   if (h->d_arm) cudaFree(h->d_arm);

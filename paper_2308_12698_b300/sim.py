@@ -135,6 +135,28 @@ class Sim:
         check(lib().sim_step_host(self._h, _ptr(h_state), _ptr(h_cmd), _ptr(d_state), _ptr(d_cmd), float(dt),
                                   int(nsteps), int(K), _stream(stream)), "sim_step_host")
 
+    def run_rounds(self, state: torch.Tensor, h_cmds: torch.Tensor, steps_per_round: int, dt: float, K: int = 0,
+                   h_obs: torch.Tensor | None = None, cmd2: torch.Tensor | None = None,
+                   obs2: torch.Tensor | None = None, stream=None):
+        """Decision rounds: h_cmds (rounds, 4 N) pinned host commands, one set per round; the
+        positions plane after each round lands in h_obs (rounds, 4 N) pinned host memory."""
+        _check_f32(state, 17 * self.n, "state")
+        rounds = h_cmds.shape[0]
+        if h_cmds.is_cuda or h_cmds.dtype != torch.float32 or not h_cmds.is_contiguous() or \
+                h_cmds.numel() != rounds * 4 * self.n:
+            raise SimError("h_cmds: expected a contiguous float32 CPU tensor (rounds, 4 N)")
+        if h_obs is not None and (h_obs.is_cuda or h_obs.dtype != torch.float32 or not h_obs.is_contiguous() or
+                                  h_obs.numel() != rounds * 4 * self.n):
+            raise SimError("h_obs: expected a contiguous float32 CPU tensor (rounds, 4 N)")
+        dev = state.device
+        if cmd2 is None:
+            cmd2 = torch.empty(8 * self.n, dtype=torch.float32, device=dev)
+        if h_obs is not None and obs2 is None:
+            obs2 = torch.empty(8 * self.n, dtype=torch.float32, device=dev)
+        check(lib().sim_run_rounds(self._h, _ptr(state), _ptr(cmd2), _ptr(h_cmds), _ptr(obs2) if h_obs is not None
+                                   else None, _ptr(h_obs), float(dt), int(steps_per_round), int(rounds), int(K),
+                                   _stream(stream)), "sim_run_rounds")
+
     def launches(self, nsteps: int, K: int = 0) -> int:
         return int(lib().sim_step_launches(self._h, int(nsteps), int(K)))
 

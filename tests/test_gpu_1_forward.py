@@ -192,6 +192,40 @@ def test_pipelined_host_entry_over_chunks(dev):
     ref_sim.close()
 
 
+def test_decision_rounds(dev, orc):
+    """Waypoints change every 25 steps (12 rounds): the double-buffered rounds equal per-round
+    sim_step calls bit for bit, follow the checker run round by round, and report each round's
+    positions."""
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    wl = W.closed_loop(n=3000, nsteps=300)
+    R, M = 12, 25
+    rng = np.random.default_rng(7)
+    cmds = np.repeat(wl.cmd[None], R, axis=0).copy()
+    cmds[:, :, 0:3] += rng.uniform(-3, 3, (R, wl.n, 3)).astype(np.float32)
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    x = planar(torch.from_numpy(wl.x0)).to(dev)
+    h_cmds = torch.from_numpy(cmds.reshape(R, -1)).pin_memory()
+    h_obs = torch.zeros((R, 4 * wl.n)).pin_memory()
+    sim.run_rounds(x, h_cmds, M, wl.dt, K=10, h_obs=h_obs)
+    got = unplanar(x, wl.n).cpu().numpy()
+    # per-round device steps
+    y = planar(torch.from_numpy(wl.x0)).to(dev)
+    obs_dev = []
+    for r in range(R):
+        sim.step(y, torch.from_numpy(cmds[r]).reshape(-1).to(dev), wl.dt, M, K=10)
+        obs_dev.append(y[: 4 * wl.n].cpu().numpy().copy())
+    np.testing.assert_array_equal(unplanar(y, wl.n).cpu().numpy(), got)
+    np.testing.assert_array_equal(h_obs.numpy(), np.stack(obs_dev))
+    # the checker, round by round
+    xr = wl.x0.astype(np.float64)
+    for r in range(R):
+        xr = orc.rollout(wl.groups, wl.gid, xr, cmds[r], wl.dt, M, wl.mode)
+        pos = h_obs[r].numpy().reshape(wl.n, 4)[:, 0:3]
+        assert np.abs(pos - xr[:, 0:3]).max() <= 1e-3
+    check_traj(got, xr)
+    sim.close()
+
+
 def test_full_size_sampled_parity(dev, orc):
     """1e6 agents, 1000 closed-loop steps in the bench's launch shape; 4096 sampled agents checked."""
     from paper_2308_12698_b300.sim import Sim, planar, unplanar
