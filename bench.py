@@ -284,6 +284,7 @@ def main():
     ap.add_argument("--adjoint-only", action="store_true",
                     help="time only the checkpointed forward + adjoint (profiling case)")
     ap.add_argument("--C", type=int, default=0, help="fix the checkpoint interval (with --adjoint-only)")
+    ap.add_argument("--block-adj", type=int, default=0, help="fix the adjoint block size (with --adjoint-only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -430,6 +431,8 @@ def run_adjoint_only(args, world, rank, dev):
     sim = Sim(wl.groups, wl.n, wl.mode)
     x0 = planar(torch.from_numpy(wl.x0)).to(dev)
     cmd = torch.from_numpy(wl.cmd).reshape(-1).to(dev)
+    if args.block_adj:
+        sim.set_launch(block_adj=args.block_adj)
     if args.C:
         C = args.C
     else:

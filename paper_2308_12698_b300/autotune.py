@@ -16,7 +16,7 @@ from .sim import Sim
 
 BLOCKS = (64, 128, 256)
 KS = (10, 50, 100, 250, 1000)
-CS = (4, 8, 16, 25, 50, 100)
+CS = (2, 4, 8, 16, 25, 50, 100)
 
 
 def _cache_path() -> str:

@@ -244,6 +244,60 @@ def test_full_size_sampled_parity(dev, orc):
     sim.close()
 
 
+def test_ten_million_sampled_parity(dev, orc):
+    """1e7 agents (the top of the scale sweep), 1000 steps at K = 1000; 2048 sampled agents."""
+    from paper_2308_12698_b300.sim import Sim, planar
+    wl = W.scale_sweep(10_000_000)
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    x = planar(torch.from_numpy(wl.x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    sim.step(x, cmd, wl.dt, 1000, K=1000)
+    torch.cuda.synchronize()
+    idx = np.concatenate([np.random.default_rng(9).choice(wl.n, 2048, replace=False), [0, wl.n - 1]])
+    from paper_2308_12698_b300.sim import unplanar
+    got = unplanar(x, wl.n)[torch.from_numpy(idx).to(dev)].cpu().numpy()
+    ref = orc.rollout(wl.groups, wl.gid[idx], wl.x0[idx], wl.cmd[idx], wl.dt, 1000, wl.mode)
+    check_traj(got, ref)
+    assert sim.n_dead() == 0
+    sim.close()
+
+
+def test_heterogeneous_graph_replay_matches_direct(dev):
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    wl = W.heterogeneous(sizes=(1000, 5000, 300, 20000), nsteps=200, shuffle=True)
+    direct = gpu_run(wl, dev, 400, K=40)
+    gid = torch.from_numpy(wl.gid).to(dev)
+    sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
+    x = planar(torch.from_numpy(wl.x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    g = sim.graph(x, cmd, wl.dt, 200, K=40)
+    g.launch()
+    g.launch()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(unplanar(x, wl.n).cpu().numpy(), direct)
+    g.close()
+    sim.close()
+
+
+def test_autotuner_pick_is_bitwise_any_other(dev, tmp_path, monkeypatch):
+    from paper_2308_12698_b300 import autotune
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    monkeypatch.setenv("XDG_CACHE_HOME", str(tmp_path))
+    wl = W.closed_loop(n=50_000, nsteps=100)
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    x0 = planar(torch.from_numpy(wl.x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    cfg = autotune.tune_step(sim, x0, cmd, wl.dt, 100, blocks=(64, 256), ks=(10, 100))
+    assert cfg["block"] in (64, 256) and cfg["K"] in (10, 100)
+    assert sim.launch()["block"] == cfg["block"] and sim.launch()["K"] == cfg["K"]
+    cached = autotune.tune_step(sim, x0, cmd, wl.dt, 100, blocks=(64, 256), ks=(10, 100))
+    assert cached["block"] == cfg["block"] and cached["K"] == cfg["K"]
+    x = x0.clone()
+    sim.step(x, cmd, wl.dt, 100)  # the tuned configuration
+    np.testing.assert_array_equal(unplanar(x, wl.n).cpu().numpy(), gpu_run(wl, dev, 100, K=1))
+    sim.close()
+
+
 def test_nonfinite_agent_is_frozen_and_counted(dev):
     from paper_2308_12698_b300.sim import Sim, planar, unplanar
     wl = W.closed_loop(n=500, nsteps=10)
