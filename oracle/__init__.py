@@ -23,7 +23,9 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "liboracle.so")
+#: ORACLE_LIB points the wrapper at another build of the same source (the
+#: mutation test loads deliberately broken copies this way).
+LIB_PATH = os.environ.get("ORACLE_LIB") or os.path.join(_HERE, "liboracle.so")
 _SOURCES = ("oracle.cpp", "quad_model.hpp", "scalar_types.hpp")
 
 NX = 17
@@ -51,7 +53,8 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        build()
+        if not os.environ.get("ORACLE_LIB"):
+            build()
         L = ctypes.CDLL(LIB_PATH)
         P = ctypes.c_void_p
         L.oracle_rollout.argtypes = [P, ctypes.c_int, P, ctypes.c_int64, P, P, ctypes.c_double,

@@ -264,6 +264,25 @@ def test_controller_roll_error(orc):
     np.testing.assert_allclose(w, np.sqrt(f / g["kt"]), rtol=1e-12)
 
 
+@pytest.mark.parametrize("psi", [0.0, 0.9, -2.5])
+def test_controller_roll_error_under_heading(orc, psi):
+    """Yawed to the commanded heading psi, then rolled by th about the body x axis: the error is a
+    pure body-x roll whatever psi is (q_e = q^* o q_d is the body-frame error), so the rotor
+    commands equal the unyawed roll case."""
+    g = W.base_group()
+    th = 0.2
+    qy = np.array([math.cos(psi / 2), 0, 0, math.sin(psi / 2)])
+    qr = np.array([math.cos(th / 2), math.sin(th / 2), 0, 0])
+    x0 = _state(q=_quat_mul(qy, qr))
+    w = orc.controller(g, x0, [0, 0, 0, psi])
+    Ls = g["L"] * math.sin(g["alpha"])
+    taumax = 2 * Ls * g["kt"] * g["omega_max"] ** 2
+    tx = g["krate"][0] * taumax * (-2 * g["katt"][0] * math.sin(th / 2))
+    fc = g["m"] * g["g"] * math.cos(th)
+    f = fc / 4 + np.array([1, -1, -1, 1]) * tx / (4 * Ls)
+    np.testing.assert_allclose(w, np.sqrt(f / g["kt"]), rtol=1e-10)
+
+
 def test_controller_yaw_error(orc):
     """Level, yawed by phi, heading 0: q_e = (cos phi/2, 0, 0, -sin phi/2)."""
     g = W.base_group()
