@@ -16,7 +16,7 @@ from .sim import Sim
 
 BLOCKS = (64, 128, 256)
 KS = (10, 50, 100, 250, 1000)
-CS = (2, 4, 8, 16, 25, 50, 100)
+CS = (1, 2, 4, 8, 16, 25, 50, 100)
 
 
 def _cache_path() -> str:
@@ -110,8 +110,15 @@ def tune_adjoint(sim: Sim, x0: torch.Tensor, cmd: torch.Tensor, dt: float, nstep
                     ckpt, _ = sim.rollout_forward(x0, cmd, dt, nsteps, C=c)
                     sim.rollout_backward(ckpt, cmd, dt, nsteps, g, None, C=c, workspace=ws)
 
+                # checkpoints cost (T/C + 1) states: skip intervals whose checkpoints would
+                # take more than half of the free device memory
+                free, _ = torch.cuda.mem_get_info()
+                if (nsteps // c + 2) * 17 * 4 * sim.n > free // 2:
+                    del ws
+                    continue
                 results.append((_time(run, reps=2), b, c))
                 del ws
+                torch.cuda.empty_cache()
         ms, b, c = min(results)
         cfg = dict(block=b, C=c, ms=ms, candidates=[list(r) for r in results])
         cache[key] = cfg
