@@ -174,20 +174,28 @@ def dist_setup(gpus: int):
 
 def barrier(world: int):
     import torch
-    torch.cuda.synchronize()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
 
 
 def max_over_ranks(x: float, world: int) -> float:
+    """The largest of the ranks' values (NCCL on GPUs, gloo on CPU)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    on_gpu = dist.get_backend() == "nccl"
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if on_gpu else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(world: int, agents_per_rank: int, physics_steps: int, bench_steps: int, max_ms: float) -> float:
+    """Whole-job agent-steps/s: every rank's agents and steps over the slowest rank's time."""
+    return world * agents_per_rank * physics_steps * bench_steps / (max_ms / 1e3)
 
 
 # -------------------------------------------------------------- CPU legs --
@@ -352,8 +360,13 @@ def main():
         barrier(world)
     total_ms = max_over_ranks(sum(times), world)
     ms_step = total_ms / args.steps
-    value = world * NA * TS * args.steps / (total_ms / 1e3)
+    value = job_rate(world, NA, TS, args.steps, total_ms)
     clocks = clk.summary()
+    # the paper's method (Sec. IV): three repeats, mean and standard deviation
+    reps3 = [times[i::3] for i in range(3)] if args.steps >= 3 else [times]
+    rates = [world * NA * TS * len(r) / (sum(r) / 1e3) for r in reps3 if r]
+    spread = {"repeats": len(rates), "mean": float(np.mean(rates)), "sd": float(np.std(rates, ddof=1)) if
+              len(rates) > 1 else 0.0, "unit": UNIT}
 
     # roofline of the dominant kernel: the fused step kernel, FP32-ALU bound
     launch_s = (sum(times) / args.steps / launches) / 1e3
@@ -403,7 +416,8 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config({"K": K, "block": tune["block"], "graph_launches_per_step": launches,
                                        "n_agents_per_gpu": NA, "physics_steps_per_bench_step": TS}),
-            "roofline": roof, "clocks": clocks, "e2e": e2e, "gpu_launches": launches * args.steps}
+            "roofline": roof, "clocks": clocks, "e2e": e2e, "gpu_launches": launches * args.steps,
+            "repeat_spread": spread}
     line.update(extra)
     if "hbm_gbs" in peaks and "plain" in line:
         line["plain"]["roofline"]["peak"] = peaks["hbm_gbs"]
