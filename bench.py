@@ -97,19 +97,74 @@ def measured_peaks() -> dict:
 
 # ------------------------------------------------------------------ clocks --
 
+class _Nvml:
+    """Read-only NVML queries through the driver's libnvidia-ml (ctypes): SM clock (MHz),
+    power (W) and the current clock-event reason bits (0x4 sw power cap, 0x8 hw slowdown,
+    0x20 sw thermal, 0x40 hw thermal)."""
+
+    def __init__(self, index: int):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.dev = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.dev)) != 0:
+            raise RuntimeError("no NVML device")
+        self.reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def max_sm_mhz(self) -> int:
+        v = self.ct.c_uint()
+        if self.lib.nvmlDeviceGetMaxClockInfo(self.dev, 1, self.ct.byref(v)) != 0:
+            raise RuntimeError("nvmlDeviceGetMaxClockInfo failed")
+        return v.value
+
+    def sample(self):
+        sm, mw, rs = self.ct.c_uint(), self.ct.c_uint(), self.ct.c_ulonglong()
+        if (self.lib.nvmlDeviceGetClockInfo(self.dev, 1, self.ct.byref(sm)) != 0 or
+                self.lib.nvmlDeviceGetPowerUsage(self.dev, self.ct.byref(mw)) != 0 or
+                self.reasons(self.dev, self.ct.byref(rs)) != 0):
+            raise RuntimeError("NVML read failed")
+        return sm.value, mw.value / 1000.0, rs.value
+
+    def close(self):
+        try:
+            self.lib.nvmlShutdown()
+        except Exception:
+            pass
+
+
 class ClockSampler:
-    """nvidia-smi samples (200 ms) while the timed region runs."""
+    """SM clock, power and throttle reasons sampled while the timed region runs.
+
+    In-process NVML reads every 5 ms on a background thread (enough samples even
+    for a timed region of a tenth of a second); nvidia-smi at 200 ms if the NVML
+    library cannot be loaded.  Reads only: no setting is changed."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_s: float = 0.005):
         self.index = index
+        self.period = period_s
         self.proc = None
+        self.rows = []
+        self.nvml = None
         self.path = os.path.join("/tmp", f"quadsim_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
+        try:
+            import threading
+            self.nvml = _Nvml(self.index)
+            self.smax = self.nvml.max_sm_mhz()
+            self.stop = threading.Event()
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return self
+        except Exception:
+            self.nvml = None
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
@@ -119,7 +174,22 @@ class ClockSampler:
             self.proc = None
         return self
 
+    def _poll(self):
+        nv = self.nvml
+        while not self.stop.is_set():
+            try:
+                sm, pw, rs = nv.sample()
+                self.rows.append(dict(sm=float(sm), smax=float(self.smax), power=pw, hw=bool(rs & 0x8),
+                                      hwt=bool(rs & 0x40), swt=bool(rs & 0x20), pcap=bool(rs & 0x4)))
+            except Exception:
+                pass
+            self.stop.wait(self.period)
+
     def __exit__(self, *exc):
+        if self.nvml is not None:
+            self.stop.set()
+            self.thread.join(timeout=5)
+            self.nvml.close()
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -127,33 +197,31 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
             self.fh.close()
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    self.rows.append(dict(sm=float(p[1]), smax=float(p[2]), power=float(p[3]),
+                                          hw=p[5].lower() == "active", hwt=p[6].lower() == "active",
+                                          swt=p[7].lower() == "active", pcap=p[8].lower() == "active"))
+                except ValueError:
+                    continue
+            os.unlink(self.path)
 
     def summary(self) -> dict:
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        rows = []
-        for line in open(self.path):
-            p = [x.strip() for x in line.split(",")]
-            if len(p) < 9:
-                continue
-            try:
-                rows.append(dict(sm=float(p[1]), smax=float(p[2]), power=float(p[3]), hw=p[5], hwt=p[6], swt=p[7],
-                                 pcap=p[8]))
-            except ValueError:
-                continue
+        rows = self.rows
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
         loaded = [r for r in rows if r["power"] > 200.0] or rows
         sm = sorted(r["sm"] for r in loaded)
-        reasons = []
-        for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
-                          ("pcap", "sw_power_cap")):
-            if any(r[key].lower() == "active" for r in loaded):
-                reasons.append(name)
-        os.unlink(self.path)
+        reasons = [name for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                                          ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap"))
+                   if any(r[key] for r in loaded)]
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r["smax"] for r in rows), "reasons": reasons,
                 "samples": len(rows), "samples_under_load": len(loaded),
-                "power_w_max": max(r["power"] for r in rows)}
+                "power_w_max": max(r["power"] for r in rows),
+                "source": "nvml" if self.nvml is not None else "nvidia-smi"}
 
 
 # ------------------------------------------------------------- distributed --
