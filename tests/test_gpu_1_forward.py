@@ -106,6 +106,25 @@ def test_heterogeneous_parity(dev, orc, shuffle):
     check_traj(gpu_run(wl, dev, 1000, K=50), ref_run(orc, wl, 1000))
 
 
+def test_heterogeneous_full_size_sampled(dev, orc):
+    """The bench's heterogeneous batch (8 groups, 600,000 agents, one launch of K = 1000): 2048
+    sampled agents against the checker."""
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    wl = W.heterogeneous(nsteps=1000)
+    gid = torch.from_numpy(wl.gid).to(dev)
+    sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
+    x = planar(torch.from_numpy(wl.x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).reshape(-1).to(dev)
+    sim.step(x, cmd, wl.dt, 1000, K=1000)
+    idx = np.concatenate([np.random.default_rng(13).choice(wl.n, 2048, replace=False),
+                          np.searchsorted(wl.gid, np.arange(8))])  # the first agent of every group
+    got = unplanar(x, wl.n)[torch.from_numpy(idx).to(dev)].cpu().numpy()
+    ref = orc.rollout(wl.groups, wl.gid[idx], wl.x0[idx], wl.cmd[idx], wl.dt, 1000, wl.mode)
+    check_traj(got, ref)
+    assert sim.n_dead() == 0
+    sim.close()
+
+
 def test_heterogeneous_one_launch_is_bitwise_each_group_alone(dev):
     wl = W.heterogeneous(sizes=(100, 900, 5000, 64), nsteps=200, shuffle=True)
     both = gpu_run(wl, dev, 200, K=20)

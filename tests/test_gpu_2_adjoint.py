@@ -279,3 +279,40 @@ def test_shared_and_global_scratch_agree(dev):
     np.testing.assert_allclose(out[8][1].cpu().numpy(), out[40][1].cpu().numpy(), rtol=1e-5,
                                atol=1e-6 * out[40][1].abs().max().item())
     sim.close()
+
+
+def test_adjoint_full_size_bench_configuration(dev, orc):
+    """1e6 agents x 1000 steps in the bench's launch shape (C = 2, shared scratch, 64-thread
+    blocks): 24 sampled agents' gradients against FP64 reverse mode."""
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    base = W.scale_sweep(1_000_000, nsteps=1000)
+    goal = base.cmd[:, 0:3].copy()
+    wl = W.Workload("full", base.mode, base.groups, base.gid, base.x0, base.cmd, base.dt, 1000, goal=goal,
+                    w_omega=1e-6)
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    sim.set_launch(block_adj=64)
+    x0 = planar(torch.from_numpy(wl.x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).reshape(-1).to(dev)
+    ckpt, rc = sim.rollout_forward(x0, cmd, wl.dt, wl.nsteps, C=2)
+    xT = unplanar(ckpt[-1], wl.n)
+    g = torch.zeros_like(xT)
+    g[:, 0:3] = 2 * (xT[:, 0:3] - torch.from_numpy(goal).to(dev))
+    w = torch.full((wl.n,), wl.w_omega, device=dev)
+    dx0, dth, dtha = sim.rollout_backward(ckpt, cmd, wl.dt, wl.nsteps, planar(g), w, C=2, per_agent=True)
+    torch.cuda.synchronize()
+    idx = np.random.default_rng(12).choice(wl.n, 24, replace=False)
+    sel = torch.from_numpy(idx).to(dev)
+    got_dx = unplanar(dx0, wl.n)[sel].cpu().numpy()
+    got_th = dtha[sel].cpu().numpy()
+    _, rdx0, rdth = orc.grad(wl.groups, wl.gid[idx], wl.x0[idx], wl.cmd[idx], wl.dt, wl.nsteps, wl.mode, goal[idx],
+                             wl.w_omega)
+    m = orc.clamp_margins(wl.groups, wl.gid[idx], wl.x0[idx], wl.cmd[idx], wl.dt, wl.nsteps)
+    fl = (m[:, 0] < SQRT_MARGIN) | (m[:, 1] < CLAMP_MARGIN) | (m[:, 2] < CLAMP_MARGIN)
+    for j in range(len(idx)):
+        chk = check_loose if fl[j] else check_block
+        chk(got_th[j], rdth[j], f"theta agent {idx[j]}")
+        chk(got_dx[j], rdx0[j], f"x0 agent {idx[j]}")
+    # the group sum is the sum of the per-agent contributions
+    np.testing.assert_allclose(dth.cpu().numpy()[0], dtha.double().sum(0).cpu().numpy(), rtol=1e-4,
+                               atol=1e-6 * dth.abs().max().item())
+    sim.close()
