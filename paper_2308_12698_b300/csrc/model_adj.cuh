@@ -1,8 +1,8 @@
 // Hand-written vector-Jacobian products of the device model (model_fwd.cuh)
 // for the discrete adjoint of the RK4 rollout: rb_derivative_vjp,
 // controller_vjp and step_vjp.  Subgradients: clamps pass the gradient on
-// their closed interval, sqrt has derivative 0 at 0, branch choices (Shepperd
-// branch, sign of q_e.w) are constants.
+// their closed interval, sqrt has derivative 0 at 0, branch choices (the roll
+// half-angle formula, sign of q_e.w) are constants.
 #pragma once
 #include "model_fwd.cuh"
 
@@ -65,11 +65,11 @@ __device__ __forceinline__ void rb_derivative_vjp(const DevGroup& P, const float
 }
 
 // Cotangent of the controller: ub (rotor commands) -> xb (state), tb (theta).
-__device__ __forceinline__ void controller_vjp(const DevGroup& P, const float* x, const float4 c, float ch, float sh,
+__device__ __forceinline__ void controller_vjp(const DevGroup& P, const float* x, const float4 c, const Hd& hd,
                                                const float ub[4], float* xb, float tb[NTH]) {
   Ctl C;
   float u[4];
-  controller_fwd(P, x, c, ch, sh, C, u);
+  controller_fwd(P, x, c, hd, C, u);
   // sqrt(clamp(S)): gradient passes on 0 < S <= om2max (sqrt'(0) taken as 0)
   float Sb[4];
 #pragma unroll
@@ -82,90 +82,57 @@ __device__ __forceinline__ void controller_vjp(const DevGroup& P, const float* x
   fb[0] = (Sb[0] - Sb[1]) + (Sb[3] - Sb[2]);
   fb[1] = (Sb[2] + Sb[3]) - (Sb[0] + Sb[1]);
   fb[2] = (Sb[0] - Sb[1]) + (Sb[2] - Sb[3]);
-  // f_i = mt_i krate_i (2 katt_i qe_i - omega_i)
-  float qeb[4];
-  qeb[0] = 0.f;
+  // f_i = mt_i krate_i (2 katt_i qe_i - omega_i); qe = s E, s = sign(E_w) / |Q|
+  float Eb[4], kap = 0.f;
+  Eb[0] = 0.f;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     tb[TH_KRATE + i] += fb[i] * P.mt[i] * (P.katt2[i] * C.qe[1 + i] - x[WX + i]);
     tb[TH_KATT + i] += fb[i] * P.wa[i] * 2.f * C.qe[1 + i];
     xb[WX + i] -= fb[i] * P.wa[i];
-    qeb[1 + i] = fb[i] * P.qa[i] * C.sgn;  // through the sign fix
+    const float qeb = fb[i] * P.qa[i];
+    kap += qeb * C.qe[1 + i];
+    Eb[1 + i] = qeb * C.s;
   }
-  // qe = conj(q) o qd
+  // E = conj(q) o Q
   const float w = x[QW], qx = x[QX], qy = x[QY], qz = x[QZ];
-  const float dw = C.qd[0], dx = C.qd[1], dy = C.qd[2], dz = C.qd[3];
-  const float Ew = qeb[0], Ex = qeb[1], Ey = qeb[2], Ez = qeb[3];
+  const float dw = C.Q[0], dx = C.Q[1], dy = C.Q[2], dz = C.Q[3];
+  const float Ew = Eb[0], Ex = Eb[1], Ey = Eb[2], Ez = Eb[3];
   float qbw = Ew * dw + Ex * dx + Ey * dy + Ez * dz;
   float qbx = Ew * dx - Ex * dw + Ey * dz - Ez * dy;
   float qby = Ew * dy - Ex * dz - Ey * dw + Ez * dx;
   float qbz = Ew * dz + Ex * dy - Ey * dx - Ez * dw;
-  float qdb[4];
-  qdb[0] = Ew * w - Ex * qx - Ey * qy - Ez * qz;
-  qdb[1] = Ew * qx + Ex * w - Ey * qz + Ez * qy;
-  qdb[2] = Ew * qy + Ex * qz + Ey * w - Ez * qx;
-  qdb[3] = Ew * qz - Ex * qy + Ey * qx + Ez * w;
-  // Shepperd, branch taken
-  float Rb[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-  const float R10 = C.xd[1], R20 = C.xd[2];
-  const float R01 = C.yd[0], R21 = C.yd[2];
-  const float R02 = C.zd[0], R12 = C.zd[1];
-  const float k = C.k, k2x2 = 2.f * C.k * C.k;
-  if (C.branch == 0) {
-    const float kb = qdb[1] * (R21 - R12) + qdb[2] * (R02 - R20) + qdb[3] * (R10 - R01);
-    Rb[2][1] += qdb[1] * k; Rb[1][2] -= qdb[1] * k;
-    Rb[0][2] += qdb[2] * k; Rb[2][0] -= qdb[2] * k;
-    Rb[1][0] += qdb[3] * k; Rb[0][1] -= qdb[3] * k;
-    const float tb_ = (0.5f * qdb[0] - k2x2 * kb) * k;
-    Rb[0][0] += tb_; Rb[1][1] += tb_; Rb[2][2] += tb_;
-  } else if (C.branch == 1) {
-    const float kb = qdb[0] * (R21 - R12) + qdb[2] * (R01 + R10) + qdb[3] * (R02 + R20);
-    Rb[2][1] += qdb[0] * k; Rb[1][2] -= qdb[0] * k;
-    Rb[0][1] += qdb[2] * k; Rb[1][0] += qdb[2] * k;
-    Rb[0][2] += qdb[3] * k; Rb[2][0] += qdb[3] * k;
-    const float tb_ = (0.5f * qdb[1] - k2x2 * kb) * k;
-    Rb[0][0] += tb_; Rb[1][1] -= tb_; Rb[2][2] -= tb_;
-  } else if (C.branch == 2) {
-    const float kb = qdb[0] * (R02 - R20) + qdb[1] * (R01 + R10) + qdb[3] * (R12 + R21);
-    Rb[0][2] += qdb[0] * k; Rb[2][0] -= qdb[0] * k;
-    Rb[0][1] += qdb[1] * k; Rb[1][0] += qdb[1] * k;
-    Rb[1][2] += qdb[3] * k; Rb[2][1] += qdb[3] * k;
-    const float tb_ = (0.5f * qdb[2] - k2x2 * kb) * k;
-    Rb[0][0] -= tb_; Rb[1][1] += tb_; Rb[2][2] -= tb_;
-  } else {
-    const float kb = qdb[0] * (R10 - R01) + qdb[1] * (R02 + R20) + qdb[2] * (R12 + R21);
-    Rb[1][0] += qdb[0] * k; Rb[0][1] -= qdb[0] * k;
-    Rb[0][2] += qdb[1] * k; Rb[2][0] += qdb[1] * k;
-    Rb[1][2] += qdb[2] * k; Rb[2][1] += qdb[2] * k;
-    const float tb_ = (0.5f * qdb[3] - k2x2 * kb) * k;
-    Rb[0][0] -= tb_; Rb[1][1] -= tb_; Rb[2][2] += tb_;
-  }
-  float xdb[3] = {Rb[0][0], Rb[1][0], Rb[2][0]};
-  float ydb[3] = {Rb[0][1], Rb[1][1], Rb[2][1]};
-  float zdb[3] = {Rb[0][2], Rb[1][2], Rb[2][2]};
-  // xd = yd x zd
-  ydb[0] += C.zd[1] * xdb[2] - C.zd[2] * xdb[1];
-  ydb[1] += C.zd[2] * xdb[0] - C.zd[0] * xdb[2];
-  ydb[2] += C.zd[0] * xdb[1] - C.zd[1] * xdb[0];
-  zdb[0] += xdb[1] * C.yd[2] - xdb[2] * C.yd[1];
-  zdb[1] += xdb[2] * C.yd[0] - xdb[0] * C.yd[2];
-  zdb[2] += xdb[0] * C.yd[1] - xdb[1] * C.yd[0];
-  // yd = yr / |yr|
-  const float yy = C.yd[0] * ydb[0] + C.yd[1] * ydb[1] + C.yd[2] * ydb[2];
-  const float yrb0 = (ydb[0] - C.yd[0] * yy) * C.ry;
-  const float yrb1 = (ydb[1] - C.yd[1] * yy) * C.ry;
-  const float yrb2 = (ydb[2] - C.yd[2] * yy) * C.ry;
-  // yr = zd x (ch, sh, 0)
-  zdb[0] += sh * yrb2;
-  zdb[1] += -ch * yrb2;
-  zdb[2] += ch * yrb1 - sh * yrb0;
-  // zd = F / |F|; f0 = f0c (F . b3), f0c = m / (4 kt)
+  // |Q|^-1 enters qe: d(1/|Q|)/dQ = -Q / |Q|^3
+  const float G = -kap * C.s * C.s;
+  float Qb[4];
+  Qb[0] = Ew * w - Ex * qx - Ey * qy - Ez * qz + G * dw;
+  Qb[1] = Ew * qx + Ex * w - Ey * qz + Ez * qy + G * dx;
+  Qb[2] = Ew * qy + Ex * qz + Ey * w - Ez * qx + G * dy;
+  Qb[3] = Ew * qz - Ex * qy + Ey * qx + Ez * w + G * dz;
+  // Q = q_z(psi) o (X0 Y0, X1 Y0, X0 Y1, X1 Y1)
+  const float P0b = hd.c2 * Qb[0] + hd.s2 * Qb[3];
+  const float P1b = hd.c2 * Qb[1] + hd.s2 * Qb[2];
+  const float P2b = hd.c2 * Qb[2] - hd.s2 * Qb[1];
+  const float P3b = hd.c2 * Qb[3] - hd.s2 * Qb[0];
+  const float X0b = P0b * C.Y[0] + P2b * C.Y[1], X1b = P1b * C.Y[0] + P3b * C.Y[1];
+  const float Y0b = P0b * C.X[0] + P1b * C.X[1], Y1b = P2b * C.X[0] + P3b * C.X[1];
+  // Y = (M + N, A); X = (N + F_z, -B) or (-B, N - F_z)
+  float Nb = Y0b, Ab = Y1b, Bb, Fzb;
+  if (C.up) { Nb += X0b; Fzb = X0b; Bb = -X1b; }
+  else { Nb += X1b; Fzb = -X1b; Bb = -X0b; }
+  // M = sqrt(A^2 + N^2), N = sqrt(B^2 + F_z^2)
+  const float M2b = 0.5f * Y0b * C.rM;
+  Ab += 2.f * C.A * M2b;
+  const float N2b = M2b + 0.5f * Nb * C.rN;
+  Bb += 2.f * C.B * N2b;
+  Fzb += 2.f * C.F[2] * N2b;
+  // (A, B) = heading rotation of (F_x, F_y); f0 = f0c (F . b3), f0c = m / (4 kt)
   const float fcb = f0b * P.f0c;
   tb[TH_M] += f0b * C.fc * P.mix0;
-  const float zz = C.zd[0] * zdb[0] + C.zd[1] * zdb[1] + C.zd[2] * zdb[2];
   float Fb[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) Fb[i] = (zdb[i] - C.zd[i] * zz) * C.rn + fcb * C.b3[i];
+  Fb[0] = hd.c * Ab - hd.s * Bb + fcb * C.b3[0];
+  Fb[1] = hd.s * Ab + hd.c * Bb + fcb * C.b3[1];
+  Fb[2] = Fzb + fcb * C.b3[2];
   // b3 = R(q) e3 -> q
   const float bbx = fcb * C.F[0], bby = fcb * C.F[1], bbz = fcb * C.F[2];
   qbw += 2.f * (qy * bbx - qx * bby);
@@ -187,11 +154,11 @@ __device__ __forceinline__ void controller_vjp(const DevGroup& P, const float* x
 // Adjoint of one RK4 step x_n -> x_{n+1}: lam <- (d x_{n+1} / d x_n)^T lam,
 // tb += (d x_{n+1} / d theta)^T lam.  x is the step-start state.
 template <int MODE>
-__device__ __forceinline__ void step_vjp(const DevGroup& P, const St& x, const float4 c, float ch, float sh,
+__device__ __forceinline__ void step_vjp(const DevGroup& P, const St& x, const float4 c, const Hd& hd,
                                          const StepH& H, const LagCoef& L, St& lam, float tb[NTH]) {
   float u[4];
   if (MODE == 1) {
-    controller(P, x.a, c, ch, sh, u);
+    controller(P, x.a, c, hd, u);
   } else {
     u[0] = c.x; u[1] = c.y; u[2] = c.z; u[3] = c.w;
   }
@@ -269,7 +236,7 @@ __device__ __forceinline__ void step_vjp(const DevGroup& P, const St& x, const f
   for (int i = 0; i < 4; ++i) xb[OM + i] += Ob[i];
 #pragma unroll
   for (int i = 0; i < NRB; ++i) xb[i] += yb[i];
-  if (MODE == 1) controller_vjp(P, x.a, c, ch, sh, ub, xb, tb);
+  if (MODE == 1) controller_vjp(P, x.a, c, hd, ub, xb, tb);
 #pragma unroll
   for (int i = 0; i < NX; ++i) lam.a[i] = xb[i];
 }

@@ -8,7 +8,13 @@
 //                   derivative evaluations -- the same RK4 map, fewer operations
 //   controller      cascaded position PD -> attitude P -> normalised rate P ->
 //                   G^-1 -> rotor clamp (the paper's inner body-rate loop,
-//                   Sec. III-B, completed as documented in quadsim.h)
+//                   Sec. III-B, completed as documented in quadsim.h).  The
+//                   desired attitude (body z along the demanded force, body y
+//                   normal to it and to the heading) is the rotation
+//                   Rz(psi) Rx(phi) Ry(theta); its quaternion is formed from
+//                   unnormalised half-angle pairs and normalised once -- the
+//                   same rotation as building the matrix and converting it
+//                   (Shepperd), without the matrix or the branch
 //   rk4             classical RK4, command held over the stages (Sec. III-B)
 //   (the vector-Jacobian products of the adjoint are in model_adj.cuh)
 //
@@ -48,6 +54,18 @@ static_assert(sizeof(DevGroup) == 48 * 4, "DevGroup layout");
 struct St {
   float a[NX];
 };
+
+// Commanded heading psi: cos, sin of psi and of psi / 2.
+struct Hd {
+  float c, s, c2, s2;
+};
+
+__device__ __forceinline__ Hd heading(float psi) {
+  Hd h;
+  sincosf(psi, &h.s, &h.c);
+  sincosf(0.5f * psi, &h.s2, &h.c2);
+  return h;
+}
 
 // Step-size constants rounded once on the host.  q components use halved
 // coefficients because rb_derivative returns 2 q'.
@@ -134,17 +152,20 @@ struct Ctl {
   bool pass[3];  // acceleration clamp passes the gradient
   float F[3];    // desired acceleration plus gravity (the desired force / m)
   float b3[3], fc;
-  float rn, zd[3];
-  float ry, yd[3], xd[3];
-  int branch;    // Shepperd branch 0:w 1:x 2:y 3:z
-  float k;       // 0.5 / sqrt(t) of the branch
-  float qd[4];
-  float sgn;     // sign that makes qe.w >= 0
-  float qe[4];   // after the sign fix
+  float A, B;    // F in the heading frame: along and across (cos psi, sin psi, 0)
+  float N, rN;   // |(B, F_z)| and its reciprocal
+  float M, rM;   // |F| and its reciprocal
+  bool up;       // F_z >= 0: which half-angle formula of the roll
+  float X[2];    // roll half-angle (cos, sin), unnormalised
+  float Y[2];    // pitch half-angle (cos, sin), unnormalised
+  float Q[4];    // q_d unnormalised
+  float E[4];    // conj(q) o Q
+  float s;       // sign(E_w) / |Q|
+  float qe[4];
   float S[4];    // Omega^2 demanded by the mixer, before the clamp
 };
 
-__device__ __forceinline__ void controller_fwd(const DevGroup& P, const float* x, const float4 c, float ch, float sh,
+__device__ __forceinline__ void controller_fwd(const DevGroup& P, const float* x, const float4 c, const Hd& hd,
                                                Ctl& C, float u[4]) {
   const float cc[3] = {c.x, c.y, c.z};
 #pragma unroll
@@ -154,72 +175,50 @@ __device__ __forceinline__ void controller_fwd(const DevGroup& P, const float* x
     C.pass[i] = (ar >= -P.a_max) && (ar <= P.a_max);
     C.a[i] = clampf(ar, -P.a_max, P.a_max);
   }
-  // desired force direction (a + g e3) and its projection on the body z axis
   C.F[0] = C.a[0];
   C.F[1] = C.a[1];
   C.F[2] = C.a[2] + P.g;
-  {
-    const float w = x[QW], qx = x[QX], qy = x[QY], qz = x[QZ];
-    C.b3[0] = 2.f * (qx * qz + w * qy);
-    C.b3[1] = 2.f * (qy * qz - w * qx);
-    C.b3[2] = 1.f - 2.f * (qx * qx + qy * qy);
-  }
-  C.fc = C.F[0] * C.b3[0] + C.F[1] * C.b3[1] + C.F[2] * C.b3[2];
-  // desired body z along the force, body y from the heading, x = y cross z
-  C.rn = rsqrtf(C.F[0] * C.F[0] + C.F[1] * C.F[1] + C.F[2] * C.F[2]);
-  C.zd[0] = C.F[0] * C.rn; C.zd[1] = C.F[1] * C.rn; C.zd[2] = C.F[2] * C.rn;
-  const float yr0 = -C.zd[2] * sh, yr1 = C.zd[2] * ch, yr2 = C.zd[0] * sh - C.zd[1] * ch;
-  C.ry = rsqrtf(yr0 * yr0 + yr1 * yr1 + yr2 * yr2);
-  C.yd[0] = yr0 * C.ry; C.yd[1] = yr1 * C.ry; C.yd[2] = yr2 * C.ry;
-  C.xd[0] = C.yd[1] * C.zd[2] - C.yd[2] * C.zd[1];
-  C.xd[1] = C.yd[2] * C.zd[0] - C.yd[0] * C.zd[2];
-  C.xd[2] = C.yd[0] * C.zd[1] - C.yd[1] * C.zd[0];
-  // R_des columns xd, yd, zd:  R[r][0] = xd[r], R[r][1] = yd[r], R[r][2] = zd[r]
-  const float R00 = C.xd[0], R10 = C.xd[1], R20 = C.xd[2];
-  const float R01 = C.yd[0], R11 = C.yd[1], R21 = C.yd[2];
-  const float R02 = C.zd[0], R12 = C.zd[1], R22 = C.zd[2];
-  // Shepperd: scalar branch if trace > 0, else the largest diagonal
-  const float tr = R00 + R11 + R22;
-  int br = 0;
-  if (!(tr > 0.f)) {
-    br = 1;
-    if (R11 > R00) br = 2;
-    if (R22 > (br == 2 ? R11 : R00)) br = 3;
-  }
-  C.branch = br;
-  float t;
-  if (br == 0) t = 1.f + tr;
-  else if (br == 1) t = 1.f + R00 - R11 - R22;
-  else if (br == 2) t = 1.f - R00 + R11 - R22;
-  else t = 1.f - R00 - R11 + R22;
-  const float rs = rsqrtf(t);  // t >= 1 on the branch taken
-  const float r = t * rs;
-  C.k = 0.5f * rs;
-  if (br == 0) {
-    C.qd[0] = 0.5f * r; C.qd[1] = (R21 - R12) * C.k; C.qd[2] = (R02 - R20) * C.k; C.qd[3] = (R10 - R01) * C.k;
-  } else if (br == 1) {
-    C.qd[1] = 0.5f * r; C.qd[0] = (R21 - R12) * C.k; C.qd[2] = (R01 + R10) * C.k; C.qd[3] = (R02 + R20) * C.k;
-  } else if (br == 2) {
-    C.qd[2] = 0.5f * r; C.qd[0] = (R02 - R20) * C.k; C.qd[1] = (R01 + R10) * C.k; C.qd[3] = (R12 + R21) * C.k;
-  } else {
-    C.qd[3] = 0.5f * r; C.qd[0] = (R10 - R01) * C.k; C.qd[1] = (R02 + R20) * C.k; C.qd[2] = (R12 + R21) * C.k;
-  }
-  // q_e = conj(q) o q_d, shortest way round
   const float w = x[QW], qx = x[QX], qy = x[QY], qz = x[QZ];
-  const float dw = C.qd[0], dx = C.qd[1], dy = C.qd[2], dz = C.qd[3];
-  const float ew = w * dw + qx * dx + qy * dy + qz * dz;
-  const float ex = w * dx - dw * qx - qy * dz + qz * dy;
-  const float ey = w * dy - dw * qy - qz * dx + qx * dz;
-  const float ez = w * dz - dw * qz - qx * dy + qy * dx;
-  C.sgn = ew < 0.f ? -1.f : 1.f;
-  C.qe[0] = C.sgn * ew; C.qe[1] = C.sgn * ex; C.qe[2] = C.sgn * ey; C.qe[3] = C.sgn * ez;
-  // attitude P and normalised rate P, already in Omega^2 units per rotor:
-  // mix_i tau_i = mix_i krate_i taumax_i (2 katt_i qe_i - omega_i)
+  C.b3[0] = 2.f * (qx * qz + w * qy);
+  C.b3[1] = 2.f * (qy * qz - w * qx);
+  C.b3[2] = 1.f - 2.f * (qx * qx + qy * qy);
+  C.fc = C.F[0] * C.b3[0] + C.F[1] * C.b3[1] + C.F[2] * C.b3[2];
+  // R_des = Rz(psi) Rx(phi) Ry(theta): in the heading frame the desired z axis is
+  // (A, B, F_z) / |F| = (sin theta, -sin phi cos theta, cos phi cos theta)
+  C.A = hd.c * C.F[0] + hd.s * C.F[1];
+  C.B = hd.c * C.F[1] - hd.s * C.F[0];
+  const float N2 = C.B * C.B + C.F[2] * C.F[2];
+  C.rN = rsqrtf(N2);
+  C.N = N2 * C.rN;
+  const float M2 = C.A * C.A + N2;
+  C.rM = rsqrtf(M2);
+  C.M = M2 * C.rM;
+  // half angles as unnormalised (cos, sin) pairs: (N + F_z, -B) ~ (1 + cos phi, sin phi),
+  // or (-B, N - F_z) ~ (sin phi, 1 - cos phi) when F_z < 0; (M + N, A) for theta
+  C.up = C.F[2] >= 0.f;
+  C.X[0] = C.up ? C.N + C.F[2] : -C.B;
+  C.X[1] = C.up ? -C.B : C.N - C.F[2];
+  C.Y[0] = C.M + C.N;
+  C.Y[1] = C.A;
+  // q_d ~ q_z(psi) o q_x(phi) o q_y(theta)
+  const float P0 = C.X[0] * C.Y[0], P1 = C.X[1] * C.Y[0], P2 = C.X[0] * C.Y[1], P3 = C.X[1] * C.Y[1];
+  C.Q[0] = hd.c2 * P0 - hd.s2 * P3;
+  C.Q[1] = hd.c2 * P1 - hd.s2 * P2;
+  C.Q[2] = hd.c2 * P2 + hd.s2 * P1;
+  C.Q[3] = hd.c2 * P3 + hd.s2 * P0;
+  // q_e = conj(q) o q_d, shortest way round
+  const float dw = C.Q[0], dx = C.Q[1], dy = C.Q[2], dz = C.Q[3];
+  C.E[0] = w * dw + qx * dx + qy * dy + qz * dz;
+  C.E[1] = w * dx - dw * qx - qy * dz + qz * dy;
+  C.E[2] = w * dy - dw * qy - qz * dx + qx * dz;
+  C.E[3] = w * dz - dw * qz - qx * dy + qy * dx;
+  const float rQ = rsqrtf(dw * dw + dx * dx + dy * dy + dz * dz);
+  C.s = C.E[0] < 0.f ? -rQ : rQ;
+  C.qe[0] = C.s * C.E[0]; C.qe[1] = C.s * C.E[1]; C.qe[2] = C.s * C.E[2]; C.qe[3] = C.s * C.E[3];
   const float f0 = P.f0c * C.fc;
   const float f1 = P.qa[0] * C.qe[1] - P.wa[0] * x[WX];
   const float f2 = P.qa[1] * C.qe[2] - P.wa[1] * x[WX + 1];
   const float f3 = P.qa[2] * C.qe[3] - P.wa[2] * x[WX + 2];
-  // G^-1 by the orthogonal rows of G
   C.S[0] = (f0 + f1) + (f3 - f2);
   C.S[1] = (f0 - f1) - (f2 + f3);
   C.S[2] = (f0 - f1) + (f2 + f3);
@@ -231,10 +230,10 @@ __device__ __forceinline__ void controller_fwd(const DevGroup& P, const float* x
   }
 }
 
-__device__ __forceinline__ void controller(const DevGroup& P, const float* x, const float4 c, float ch, float sh,
+__device__ __forceinline__ void controller(const DevGroup& P, const float* x, const float4 c, const Hd& hd,
                                            float u[4]) {
   Ctl C;
-  controller_fwd(P, x, c, ch, sh, C, u);
+  controller_fwd(P, x, c, hd, C, u);
 }
 
 // ------------------------------------------------------------------ RK4 --
@@ -266,11 +265,11 @@ __device__ __forceinline__ void rk4(const DevGroup& P, St& x, const float u[4], 
 }
 
 template <int MODE>
-__device__ __forceinline__ void step(const DevGroup& P, St& x, const float4 c, float ch, float sh, const StepH& H,
+__device__ __forceinline__ void step(const DevGroup& P, St& x, const float4 c, const Hd& hd, const StepH& H,
                                      const LagCoef& L) {
   float u[4];
   if (MODE == 1) {
-    controller(P, x.a, c, ch, sh, u);
+    controller(P, x.a, c, hd, u);
   } else {
     u[0] = c.x; u[1] = c.y; u[2] = c.z; u[3] = c.w;
   }

@@ -64,15 +64,14 @@ __global__ void __launch_bounds__(256) ckpt_kernel(CkptArgs A, const DevGroup P0
       continue;
     }
     const float4 c = A.cmd[i];
-    float ch = 0.f, sh = 0.f;
-    if (MODE == 1) sincosf(c.w, &sh, &ch);
+    const Hd hd = heading(MODE == 1 ? c.w : 0.f);
     const DevGroup P = HETERO ? sg[A.gid[i]] : P0;
     const LagCoef L = lag_coef(P.inv_tau, A.H);
     float rc = 0.f;
     for (int s = 0; s < A.S; ++s) {
       const int len = (int)min((int64_t)A.C, A.nsteps - (int64_t)s * A.C);
       for (int k = 0; k < len; ++k) {
-        step<MODE>(P, x, c, ch, sh, A.H, L);
+        step<MODE>(P, x, c, hd, A.H, L);
         rc += (x.a[OM] * x.a[OM] + x.a[OM + 1] * x.a[OM + 1]) + (x.a[OM + 2] * x.a[OM + 2] + x.a[OM + 3] * x.a[OM + 3]);
       }
       store_state(A.ckpt + (s + 1) * plane, A.n, i, x);
@@ -137,8 +136,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
       const DevGroup& P = sg[g];  // read from shared memory where used: keeps registers for the adjoint
       const LagCoef L = lag_coef(P.inv_tau, A.H);
       const float4 c = A.cmd[i];
-      float ch = 0.f, sh = 0.f;
-      if (MODE == 1) sincosf(c.w, &sh, &ch);
+      const Hd hd = heading(MODE == 1 ? c.w : 0.f);
       const float w = A.w_run ? A.w_run[i] : 0.f;
       St lam, x;
       load_state(A.dLdxT, A.n, i, lam);
@@ -151,11 +149,11 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
         load_state(A.ckpt + (int64_t)s * plane, A.n, i, x);
         for (int j = 0; j < len; ++j) {
           store_state(scratch + j * sstep, scols, slot, x);
-          if (j + 1 < len) step<MODE>(P, x, c, ch, sh, A.H, L);
+          if (j + 1 < len) step<MODE>(P, x, c, hd, A.H, L);
         }
         for (int j = len - 1; j >= 0; --j) {
           load_state(scratch + j * sstep, scols, slot, x);
-          step_vjp<MODE>(P, x, c, ch, sh, A.H, L, lam, tb);
+          step_vjp<MODE>(P, x, c, hd, A.H, L, lam, tb);
           if (n0 + j >= 1) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) lam.a[OM + q] += 2.f * w * x.a[OM + q];

@@ -53,15 +53,14 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs A, const DevGroup P0
     St x;
     load_state(A.state, A.n, i, x);
     const float4 c = A.cmd[i];
-    float ch = 0.f, sh = 0.f;
-    if (MODE == 1) sincosf(c.w, &sh, &ch);
+    const Hd hd = heading(MODE == 1 ? c.w : 0.f);
     if (HETERO) {
       const DevGroup P = sg[A.gid[i]];
       const LagCoef L = lag_coef(P.inv_tau, A.H);
-      for (int k = 0; k < A.K; ++k) step<MODE>(P, x, c, ch, sh, A.H, L);
+      for (int k = 0; k < A.K; ++k) step<MODE>(P, x, c, hd, A.H, L);
     } else {
       const LagCoef L = lag_coef(P0.inv_tau, A.H);
-      for (int k = 0; k < A.K; ++k) step<MODE>(P0, x, c, ch, sh, A.H, L);
+      for (int k = 0; k < A.K; ++k) step<MODE>(P0, x, c, hd, A.H, L);
     }
     if (all_finite(x)) {
       store_state(A.state, A.n, i, x);

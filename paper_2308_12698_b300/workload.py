@@ -225,6 +225,33 @@ def differentiable(n_per_group: int = 1024, n_groups: int = 4, nsteps: int = 200
                     goal=goal, w_omega=w_omega)
 
 
+def thrust_down(n: int = 4096, nsteps: int = 1, dt: float = 1e-3, seed: int = BASE_SEED + 6) -> Workload:
+    """Demanded force pointing downwards: the reference airframe with its acceleration clamp
+    raised to 25 m/s^2 (above g), climbing at 2-10 m/s towards waypoints 5-20 m below,
+    attitudes uniform over all rotations (half of them inverted), headings uniform in
+    [-pi, pi).  Goal = waypoint, for gradients."""
+    rng = np.random.default_rng(seed)
+    g = dict(base_group())
+    g["a_max"] = 25.0
+    groups = [round_group(g)]
+    wh = hover_speed(groups[0])
+    x = np.zeros((n, STATE_DIM))
+    x[:, 0:3] = rng.uniform(-10.0, 10.0, (n, 3))
+    x[:, 3:5] = rng.normal(0.0, 1.0, (n, 2))
+    x[:, 5] = rng.uniform(2.0, 10.0, n)
+    q = rng.normal(size=(n, 4))
+    x[:, 6:10] = q / np.linalg.norm(q, axis=1, keepdims=True)
+    x[:, 10:13] = rng.normal(0.0, 0.5, (n, 3))
+    x[:, 13:17] = wh * rng.uniform(0.5, 1.5, (n, 4))
+    cmd = np.zeros((n, 4))
+    cmd[:, 0:2] = x[:, 0:2] + rng.uniform(-5.0, 5.0, (n, 2))
+    cmd[:, 2] = x[:, 2] - rng.uniform(5.0, 20.0, n)
+    cmd[:, 3] = rng.uniform(-math.pi, math.pi, n)
+    x, cmd = x.astype(np.float32), cmd.astype(np.float32)
+    return Workload("thrust-down", CLOSED_LOOP, groups, np.zeros(n, np.uint8), x, cmd, dt, nsteps,
+                    goal=cmd[:, 0:3].copy(), w_omega=1e-6)
+
+
 # --- layout helpers (data movement only) -----------------------------------
 
 def to_planes(x: np.ndarray) -> np.ndarray:

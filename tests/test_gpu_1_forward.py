@@ -80,6 +80,28 @@ def test_one_step_from_advanced_states(dev, orc):
     check_one_step(gpu_run(wl, dev, 1, K=1, x0=xs), ref_run(orc, wl, 1, x0=xs))
 
 
+def demand_points_down(wl):
+    """Agents whose first demanded force points downwards: a_z = clamp(kp e_z - kd v_z) < -g."""
+    g = wl.groups[0]
+    az = np.clip(g["kp"][2] * (wl.cmd[:, 2].astype(np.float64) - wl.x0[:, 2]) - g["kd"][2] * wl.x0[:, 5],
+                 -g["a_max"], g["a_max"])
+    return az + g["g"] < 0
+
+
+def test_one_step_thrust_pointing_down(dev, orc):
+    wl = W.thrust_down(4096)
+    down = demand_points_down(wl)
+    assert down.mean() > 0.5
+    m = orc.clamp_margins(wl.groups, wl.gid, wl.x0, wl.cmd, wl.dt, 1)
+    ok = m[:, 0] >= 1e-3  # rotor demand away from the sqrt kink at 0
+    assert (ok & down).sum() > 1000
+    got, ref = gpu_run(wl, dev, 1, K=1), ref_run(orc, wl, 1)
+    check_one_step(got[ok], ref[ok])
+    # near the kink only the rotor speeds leave the bar: check the rigid body there
+    tol = 1e-5 * np.maximum(np.abs(ref[~ok, :13]), FLOOR[:13])
+    assert (np.abs(got[~ok, :13].astype(np.float64) - ref[~ok, :13]) <= tol).all()
+
+
 def test_open_loop_1000_steps(dev, orc):
     wl = W.open_loop(n=64, nsteps=1000)
     check_traj(gpu_run(wl, dev, 1000, K=1), ref_run(orc, wl, 1000))

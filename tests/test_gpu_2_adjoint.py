@@ -316,3 +316,24 @@ def test_adjoint_full_size_bench_configuration(dev, orc):
     np.testing.assert_allclose(dth.cpu().numpy()[0], dtha.double().sum(0).cpu().numpy(), rtol=1e-4,
                                atol=1e-6 * dth.abs().max().item())
     sim.close()
+
+
+def test_adjoint_thrust_pointing_down(dev, orc):
+    """Gradients through the roll half-angle's second formula (demanded force pointing down,
+    inverted and upright bodies, all headings): 5-step rollouts against FP64 reverse mode."""
+    wl = W.thrust_down(2048, nsteps=5)
+    g = wl.groups[0]
+    az = np.clip(g["kp"][2] * (wl.cmd[:, 2].astype(np.float64) - wl.x0[:, 2]) - g["kd"][2] * wl.x0[:, 5],
+                 -g["a_max"], g["a_max"])
+    down = az + g["g"] < 0  # first demanded force points down
+    r = gpu_grad(wl, dev, C=5)
+    dx0, _, dth_a = r["outs"][0]
+    _, rdx0, rdth = orc.grad(wl.groups, wl.gid, wl.x0, wl.cmd, wl.dt, wl.nsteps, wl.mode, wl.goal, wl.w_omega)
+    fl = flagged(orc, wl)
+    strict = ~fl & down
+    assert strict.sum() > 500, strict.sum()
+    for a in np.flatnonzero(~fl):
+        check_block(dth_a[a], rdth[a], f"theta agent {a}")
+        check_block(dx0[a], rdx0[a], f"x0 agent {a}")
+    for a in np.flatnonzero(fl):
+        check_loose(dx0[a], rdx0[a], f"x0 agent {a} (near a kink)")
