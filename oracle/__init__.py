@@ -29,10 +29,16 @@ LIB_PATH = os.environ.get("ORACLE_LIB") or os.path.join(_HERE, "liboracle.so")
 _SOURCES = ("oracle.cpp", "quad_model.hpp", "scalar_types.hpp")
 
 NX = 17
-NPARAM = 25
+NXP = 20  # PID mode: the 17 states and the rate-error integral xi
+NPARAM = 34
 NTHETA = 16
 OPEN_LOOP = 0
 CLOSED_LOOP = 1
+CLOSED_LOOP_PID = 2
+
+
+def state_dim(mode: int) -> int:
+    return NXP if mode == CLOSED_LOOP_PID else NX
 
 
 def build(force: bool = False) -> str:
@@ -63,13 +69,14 @@ def lib():
                                   ctypes.c_int64, ctypes.c_int, P, ctypes.c_double, ctypes.c_int, P, P, P]
         L.oracle_derivative.argtypes = [P, P, P, P]
         L.oracle_controller.argtypes = [P, P, P, P]
+        L.oracle_controller_pid.argtypes = [P, P, P, P, P, P]
         L.oracle_allocation.argtypes = [P, P, P, P]
         L.oracle_shepperd.argtypes = [P, P]
         L.oracle_count_ops.argtypes = [P, P, P, ctypes.c_double, ctypes.c_int, P]
         L.oracle_count_adjoint_edges.argtypes = [P, P, P, ctypes.c_double, ctypes.c_int, P]
         L.oracle_collisions.argtypes = [P, P, P, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int, P]
         L.oracle_clamp_margins.argtypes = [P, ctypes.c_int, P, ctypes.c_int64, P, P, ctypes.c_double, ctypes.c_int64,
-                                           ctypes.c_int, P]
+                                           ctypes.c_int, ctypes.c_int, P]
         _lib = L
     return _lib
 
@@ -79,9 +86,11 @@ def _p(a: np.ndarray):
 
 
 def pack_group(g: dict) -> np.ndarray:
-    """Packed FP64 parameter group: m Jxx Jyy Jzz L alpha kt kq tau_m c_d omega_max g kp kd katt krate a_max."""
+    """Packed FP64 parameter group: m Jxx Jyy Jzz L alpha kt kq tau_m c_d omega_max g kp kd katt krate a_max
+    kI kD xi_max (the PID rate loop's gains and integrator limit; absent keys: 0, 0, 1e30)."""
     v = [g["m"], g["Jxx"], g["Jyy"], g["Jzz"], g["L"], g["alpha"], g["kt"], g["kq"], g["tau_m"], g["c_d"],
-         g["omega_max"], g["g"], *g["kp"], *g["kd"], *g["katt"], *g["krate"], g["a_max"]]
+         g["omega_max"], g["g"], *g["kp"], *g["kd"], *g["katt"], *g["krate"], g["a_max"],
+         *g.get("kI", [0.0] * 3), *g.get("kD", [0.0] * 3), *g.get("xi_max", [1e30] * 3)]
     a = np.asarray(v, dtype=np.float64)
     assert a.size == NPARAM
     return a
@@ -95,10 +104,17 @@ def _threads(nthreads):
     return nthreads if nthreads else (os.cpu_count() or 1)
 
 
+def _states(x0, mode):
+    x = np.ascontiguousarray(np.asarray(x0, dtype=np.float64))
+    if x.ndim != 2 or x.shape[1] != state_dim(mode):
+        raise ValueError(f"states must be (n, {state_dim(mode)}) in mode {mode}")
+    return x
+
+
 def rollout(groups, gid, x0, cmd, h, nsteps, mode, nthreads=None, with_cost=False):
-    """Advance every agent nsteps RK4 steps; returns the (n, 17) FP64 final state
-    (and the per-agent running sum of Omega^2 over step ends when asked)."""
-    x = np.ascontiguousarray(np.asarray(x0, dtype=np.float64)).copy()
+    """Advance every agent nsteps RK4 steps; returns the (n, 17) FP64 final state ((n, 20) in
+    the PID mode) and, when asked, the per-agent running sum of Omega^2 over step ends."""
+    x = _states(x0, mode).copy()
     n = x.shape[0]
     c = np.ascontiguousarray(np.asarray(cmd, dtype=np.float64))
     gi = np.ascontiguousarray(np.asarray(gid, dtype=np.int32))
@@ -112,15 +128,16 @@ def rollout(groups, gid, x0, cmd, h, nsteps, mode, nthreads=None, with_cost=Fals
 
 
 def grad(groups, gid, x0, cmd, h, nsteps, mode, goal, w_omega, nthreads=None):
-    """Per-agent loss, dL/dx0 (n, 17) and dL/dtheta (n, 16) by FP64 reverse mode."""
-    x = np.ascontiguousarray(np.asarray(x0, dtype=np.float64))
+    """Per-agent loss, dL/dx0 (n, 17; (n, 20) in the PID mode) and dL/dtheta (n, 16) by FP64
+    reverse mode."""
+    x = _states(x0, mode)
     n = x.shape[0]
     c = np.ascontiguousarray(np.asarray(cmd, dtype=np.float64))
     gi = np.ascontiguousarray(np.asarray(gid, dtype=np.int32))
     gl = np.ascontiguousarray(np.asarray(goal, dtype=np.float64))
     pg = pack_groups(groups)
     loss = np.zeros(n)
-    dx0 = np.zeros((n, NX))
+    dx0 = np.zeros((n, state_dim(mode)))
     dth = np.zeros((n, NTHETA))
     rcode = lib().oracle_grad(_p(pg), len(groups), _p(gi), n, _p(x), _p(c), float(h), int(nsteps), int(mode),
                               _p(gl), float(w_omega), _threads(nthreads), _p(loss), _p(dx0), _p(dth))
@@ -136,17 +153,17 @@ def loss(groups, gid, x0, cmd, h, nsteps, mode, goal, w_omega, nthreads=None):
     return (d * d).sum(axis=1) + w_omega * rc
 
 
-def clamp_margins(groups, gid, x0, cmd, h, nsteps, nthreads=None):
+def clamp_margins(groups, gid, x0, cmd, h, nsteps, nthreads=None, mode=CLOSED_LOOP):
     """(n, 3) minima over a closed-loop trajectory of: |S|/omega_max^2 (rotor demand near the
     sqrt kink at 0), |S - omega_max^2|/omega_max^2 (rotor ceiling), ||ar| - a_max|/a_max
     (acceleration clamp)."""
-    x = np.ascontiguousarray(np.asarray(x0, dtype=np.float64))
+    x = _states(x0, mode)
     n = x.shape[0]
     c = np.ascontiguousarray(np.asarray(cmd, dtype=np.float64))
     gi = np.ascontiguousarray(np.asarray(gid, dtype=np.int32))
     pg = pack_groups(groups)
     out = np.zeros((n, 3))
-    if lib().oracle_clamp_margins(_p(pg), len(groups), _p(gi), n, _p(x), _p(c), float(h), int(nsteps),
+    if lib().oracle_clamp_margins(_p(pg), len(groups), _p(gi), n, _p(x), _p(c), float(h), int(nsteps), int(mode),
                                   _threads(nthreads), _p(out)) != 0:
         raise ValueError("oracle_clamp_margins rejected its arguments")
     return out
@@ -189,6 +206,17 @@ def controller(group, x, cmd):
     w = np.zeros(4)
     lib().oracle_controller(_p(pg), _p(xx), _p(cc), _p(w))
     return w
+
+
+def controller_pid(group, x, cmd):
+    """PID mode, one agent with its 20-state x: (rotor-speed commands (4), rate error (3),
+    omega' at x (3))."""
+    pg = pack_group(group)
+    xx = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(NXP))
+    cc = np.ascontiguousarray(np.asarray(cmd, dtype=np.float64))
+    w, e, wd = np.zeros(4), np.zeros(3), np.zeros(3)
+    lib().oracle_controller_pid(_p(pg), _p(xx), _p(cc), _p(w), _p(e), _p(wd))
+    return w, e, wd
 
 
 def allocation(group):

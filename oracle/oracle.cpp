@@ -2,9 +2,10 @@
 // oracle/liboracle.so).  Used by tests, the smoke check and the bench's CPU
 // baseline; never by the CUDA library.
 //
-// Layouts: states are agent-major (n x 17 doubles: p v q omega Omega),
-// commands n x 4, parameter groups n_groups x 25 doubles in the packed order
-// of unpack_group(), group ids int32.
+// Layouts: states are agent-major (n x 17 doubles: p v q omega Omega; n x 20
+// in the PID mode, with the rate-error integral xi last), commands n x 4,
+// parameter groups n_groups x 34 doubles in the packed order of
+// unpack_group(), group ids int32.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -91,6 +92,19 @@ int oracle_controller(const double* group, const double* x, const double* cmd, d
   return 0;
 }
 
+// PID mode, one agent with its 20-state x: rotor-speed commands w (4), the
+// rate error e (3) and omega' at x (3), as the step uses them.
+int oracle_controller_pid(const double* group, const double* x, const double* cmd, double* w, double* e,
+                          double* wdot) {
+  const Group<double> P = unpack_group(group);
+  const Fixed F = make_fixed(P);
+  double d0[NX];
+  derivative(P, F, x, x + 13, d0);
+  for (int i = 0; i < 3; ++i) wdot[i] = d0[10 + i];
+  controller(P, F, x, cmd, w, nullptr, nullptr, x + NX, d0 + 10, e);
+  return 0;
+}
+
 // Unit quaternion of a row-major 3x3 rotation matrix (Shepperd).
 int oracle_shepperd(const double* R9, double* q) {
   double R[3][3];
@@ -105,20 +119,21 @@ int oracle_shepperd(const double* R9, double* q) {
 // sum_i Omega_i^2.
 int oracle_rollout(const double* groups, int n_groups, const int32_t* gid, int64_t n, double* x,
                    const double* cmd, double h, int64_t nsteps, int mode, int nthreads, double* run_cost) {
-  if (n < 0 || nsteps < 0 || n_groups < 1) return -1;
+  if (n < 0 || nsteps < 0 || n_groups < 1 || mode < OPEN_LOOP || mode > CLOSED_LOOP_PID) return -1;
   const GroupSet S(groups, n_groups);
+  const int nx = state_dim(mode);
   parallel_for(n, nthreads, [&](int64_t lo, int64_t hi) {
     for (int64_t a = lo; a < hi; ++a) {
       const int g = gid ? gid[a] : 0;
-      double cur[NX], nxt[NX];
-      std::memcpy(cur, x + a * NX, sizeof(cur));
+      double cur[NXP], nxt[NXP];
+      std::memcpy(cur, x + a * nx, nx * sizeof(double));
       double rc = 0.0;
       for (int64_t s = 0; s < nsteps; ++s) {
-        rk4_step(S.P[g], S.F[g], mode, cur, cmd + a * 4, h, nxt);
-        std::memcpy(cur, nxt, sizeof(cur));
+        step_any(S.P[g], S.F[g], mode, cur, cmd + a * 4, h, nxt);
+        std::memcpy(cur, nxt, nx * sizeof(double));
         rc += omega_sq(cur);
       }
-      std::memcpy(x + a * NX, cur, sizeof(cur));
+      std::memcpy(x + a * nx, cur, nx * sizeof(double));
       if (run_cost) run_cost[a] = rc;
     }
   });
@@ -126,34 +141,36 @@ int oracle_rollout(const double* groups, int n_groups, const int32_t* gid, int64
 }
 
 // Per-agent loss L_a = |p_T - goal_a|^2 + w_omega * sum_{n=1..T} sum_i Omega_{n,i}^2
-// and its exact discrete gradient by reverse mode: dL/dx0 (n x 17) and
+// and its exact discrete gradient by reverse mode: dL/dx0 (n x 17; n x 20 in
+// the PID mode) and
 // dL/dtheta (n x 16, order kp kd katt krate m Jxx Jyy Jzz) of the agent's
 // own group parameters.  The forward states are stored; each step is then
 // re-taped on its own and swept backwards with the incoming adjoint.
 int oracle_grad(const double* groups, int n_groups, const int32_t* gid, int64_t n, const double* x0,
                 const double* cmd, double h, int64_t nsteps, int mode, const double* goal, double w_omega,
                 int nthreads, double* loss, double* dx0, double* dtheta) {
-  if (n < 0 || nsteps < 0 || n_groups < 1) return -1;
+  if (n < 0 || nsteps < 0 || n_groups < 1 || mode < OPEN_LOOP || mode > CLOSED_LOOP_PID) return -1;
   const GroupSet S(groups, n_groups);
+  const int NS = state_dim(mode);
   parallel_for(n, nthreads, [&](int64_t lo, int64_t hi) {
     Tape tape;
     g_tape = &tape;
-    std::vector<double> xs((nsteps + 1) * NX);
+    std::vector<double> xs((nsteps + 1) * NS);
     std::vector<double> adj;
     for (int64_t a = lo; a < hi; ++a) {
       const int g = gid ? gid[a] : 0;
       const Group<double>& Pd = S.P[g];
       const Fixed& F = S.F[g];
       const double* c = cmd + a * 4;
-      std::memcpy(xs.data(), x0 + a * NX, NX * sizeof(double));
+      std::memcpy(xs.data(), x0 + a * NS, NS * sizeof(double));
       double rc = 0.0;
       for (int64_t s = 0; s < nsteps; ++s) {
-        rk4_step(Pd, F, mode, xs.data() + s * NX, c, h, xs.data() + (s + 1) * NX);
-        rc += omega_sq(xs.data() + (s + 1) * NX);
+        step_any(Pd, F, mode, xs.data() + s * NS, c, h, xs.data() + (s + 1) * NS);
+        rc += omega_sq(xs.data() + (s + 1) * NS);
       }
-      const double* xT = xs.data() + nsteps * NX;
+      const double* xT = xs.data() + nsteps * NS;
       double L = w_omega * rc;
-      double lam[NX] = {0};
+      double lam[NXP] = {0};
       for (int i = 0; i < 3; ++i) {
         const double d = xT[i] - goal[a * 3 + i];
         L += d * d;
@@ -171,21 +188,21 @@ int oracle_grad(const double* groups, int n_groups, const int32_t* gid, int64_t 
         for (int i = 0; i < 3; ++i) Pv.krate[i] = Var::leaf(Pd.krate[i]);
         Pv.m = Var::leaf(Pd.m);
         for (int i = 0; i < 3; ++i) Pv.J[i] = Var::leaf(Pd.J[i]);
-        Var xv[NX], xn[NX];
-        for (int i = 0; i < NX; ++i) xv[i] = Var::leaf(xs[s * NX + i]);
-        rk4_step(Pv, F, mode, xv, c, h, xn);
+        Var xv[NXP], xn[NXP];
+        for (int i = 0; i < NS; ++i) xv[i] = Var::leaf(xs[s * NS + i]);
+        step_any(Pv, F, mode, xv, c, h, xn);
         adj.assign(tape.nodes.size(), 0.0);
-        for (int i = 0; i < NX; ++i)
+        for (int i = 0; i < NS; ++i)
           if (xn[i].idx >= 0) adj[xn[i].idx] += lam[i];
         tape.backprop(adj);
         // theta leaves were created first, in theta order (indices 0..15)
         for (int k = 0; k < NTHETA; ++k) th[k] += adj[k];
-        for (int i = 0; i < NX; ++i) lam[i] = adj[xv[i].idx];
+        for (int i = 0; i < NS; ++i) lam[i] = adj[xv[i].idx];
         if (s >= 1)
-          for (int i = 0; i < 4; ++i) lam[13 + i] += 2.0 * w_omega * xs[s * NX + 13 + i];
+          for (int i = 0; i < 4; ++i) lam[13 + i] += 2.0 * w_omega * xs[s * NS + 13 + i];
       }
       loss[a] = L;
-      if (dx0) std::memcpy(dx0 + a * NX, lam, sizeof(lam));
+      if (dx0) std::memcpy(dx0 + a * NS, lam, NS * sizeof(double));
       if (dtheta) std::memcpy(dtheta + a * NTHETA, th, sizeof(th));
     }
     g_tape = nullptr;
@@ -202,27 +219,34 @@ int oracle_grad(const double* groups, int n_groups, const int32_t* gid, int64_t 
 // ill-conditioned: a perturbation at rounding level moves them by a finite
 // amount.
 int oracle_clamp_margins(const double* groups, int n_groups, const int32_t* gid, int64_t n, const double* x0,
-                         const double* cmd, double h, int64_t nsteps, int nthreads, double* out) {
-  if (n < 0 || nsteps < 0 || n_groups < 1) return -1;
+                         const double* cmd, double h, int64_t nsteps, int mode, int nthreads, double* out) {
+  if (n < 0 || nsteps < 0 || n_groups < 1 || (mode != CLOSED_LOOP && mode != CLOSED_LOOP_PID)) return -1;
   const GroupSet S(groups, n_groups);
+  const int nx = state_dim(mode);
   parallel_for(n, nthreads, [&](int64_t lo, int64_t hi) {
     for (int64_t a = lo; a < hi; ++a) {
       const int g = gid ? gid[a] : 0;
       const Group<double>& P = S.P[g];
-      double cur[NX], nxt[NX];
-      std::memcpy(cur, x0 + a * NX, sizeof(cur));
+      double cur[NXP], nxt[NXP];
+      std::memcpy(cur, x0 + a * nx, nx * sizeof(double));
       const double om2 = P.omega_max * P.omega_max;
       double m0 = 1e300, m1 = 1e300, m2 = 1e300;
       for (int64_t s = 0; s < nsteps; ++s) {
         double ar[3], Sd[4], w[4];
-        controller(P, S.F[g], cur, cmd + a * 4, w, ar, Sd);
+        if (mode == CLOSED_LOOP_PID) {
+          double d0[NX], e[3];
+          derivative(P, S.F[g], cur, cur + 13, d0);
+          controller(P, S.F[g], cur, cmd + a * 4, w, ar, Sd, cur + NX, d0 + 10, e);
+        } else {
+          controller(P, S.F[g], cur, cmd + a * 4, w, ar, Sd);
+        }
         for (int i = 0; i < 4; ++i) {
           m0 = std::min(m0, std::fabs(Sd[i]) / om2);
           m1 = std::min(m1, std::fabs(Sd[i] - om2) / om2);
         }
         for (int i = 0; i < 3; ++i) m2 = std::min(m2, std::fabs(std::fabs(ar[i]) - P.a_max) / P.a_max);
-        rk4_step(P, S.F[g], CLOSED_LOOP, cur, cmd + a * 4, h, nxt);
-        std::memcpy(cur, nxt, sizeof(cur));
+        step_any(P, S.F[g], mode, cur, cmd + a * 4, h, nxt);
+        std::memcpy(cur, nxt, nx * sizeof(double));
       }
       out[a * 3 + 0] = m0;
       out[a * 3 + 1] = m1;
@@ -273,8 +297,8 @@ int oracle_collisions(const float* p, const float* radius, const uint8_t* alive,
 }
 
 // Reverse-sweep work of one step in the checker's reverse mode: the number of
-// tape edges of a closed- or open-loop step taped with respect to the 17
-// states and the 16 differentiated parameters.  Sweeping backwards costs one
+// tape edges of a step (any mode) taped with respect to its states and the 16
+// differentiated parameters.  Sweeping backwards costs one
 // multiply and one add per edge.
 int oracle_count_adjoint_edges(const double* group, const double* x, const double* cmd, double h, int mode,
                                int64_t* edges) {
@@ -291,9 +315,9 @@ int oracle_count_adjoint_edges(const double* group, const double* x, const doubl
     Pv.J[i] = Var::leaf(Pd.J[i]);
   }
   Pv.m = Var::leaf(Pd.m);
-  Var xv[NX], xn[NX];
-  for (int i = 0; i < NX; ++i) xv[i] = Var::leaf(x[i]);
-  rk4_step(Pv, F, mode, xv, cmd, h, xn);
+  Var xv[NXP], xn[NXP];
+  for (int i = 0; i < state_dim(mode); ++i) xv[i] = Var::leaf(x[i]);
+  step_any(Pv, F, mode, xv, cmd, h, xn);
   int64_t e = 0;
   for (const Node& n : tape.nodes) e += (n.a >= 0) + (n.b >= 0);
   *edges = e;
@@ -308,10 +332,10 @@ int oracle_count_ops(const double* group, const double* x, const double* cmd, do
   const Group<double> Pd = unpack_group(group);
   const Fixed F = make_fixed(Pd);
   const Group<Cnt> P = cast_group<Cnt>(Pd);
-  Cnt xc[NX], xn[NX];
-  for (int i = 0; i < NX; ++i) xc[i] = Cnt(x[i]);
+  Cnt xc[NXP], xn[NXP];
+  for (int i = 0; i < state_dim(mode); ++i) xc[i] = Cnt(x[i]);
   g_count = OpCount();
-  rk4_step(P, F, mode, xc, cmd, h, xn);
+  step_any(P, F, mode, xc, cmd, h, xn);
   counts[0] = g_count.add;
   counts[1] = g_count.mul;
   counts[2] = g_count.div;

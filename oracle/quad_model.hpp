@@ -25,7 +25,15 @@
 //     heading -> attitude P on the error quaternion -> body-rate P scaled by
 //     the maximum torque per axis -> inverse allocation G^-1 -> per-rotor
 //     clamp of Omega^2 to [0, Omega_max^2] -> square root;
-//   * no quaternion renormalisation.
+//   * no quaternion renormalisation;
+//   * PID variant of the body-rate loop (mode CLOSED_LOOP_PID; the paper names
+//     a "PID body rate controller" and gives no gains): per axis
+//     tau_i = taumax_i (krate_i e_i + kI_i xi_i - kD_i omega'_i) with the rate
+//     error e = omega_des - omega, the integral xi of e as three extra states
+//     (20 in all), advanced once per step by xi <- clamp(xi + h e, +-xi_max)
+//     and held over the RK4 stages like the command, and the derivative taken
+//     on the measurement: omega' of Eq. (qd4) at the step start.  kI = kD = 0
+//     gives the P loop exactly.
 #pragma once
 #include <cmath>
 #include "scalar_types.hpp"
@@ -33,9 +41,12 @@
 namespace orc {
 
 constexpr int NX = 17;      // p(3) v(3) q(4: w x y z) omega(3) Omega(4)
-constexpr int NPARAM = 25;  // packed parameter group (see unpack_group)
+constexpr int NXP = 20;     // PID mode: the 17 plus the rate-error integral xi(3)
+constexpr int NPARAM = 34;  // packed parameter group (see unpack_group)
 constexpr int NTHETA = 16;  // kp(3) kd(3) katt(3) krate(3) m Jxx Jyy Jzz
-enum { OPEN_LOOP = 0, CLOSED_LOOP = 1 };
+enum { OPEN_LOOP = 0, CLOSED_LOOP = 1, CLOSED_LOOP_PID = 2 };
+
+inline int state_dim(int mode) { return mode == CLOSED_LOOP_PID ? NXP : NX; }
 
 template <class T>
 struct Group {
@@ -45,10 +56,11 @@ struct Group {
   T tau_m, c_d, omega_max, g;
   T kp[3], kd[3], katt[3], krate[3];
   T a_max;
+  T kI[3], kD[3], xi_max[3];  // PID mode only
 };
 
 // Packed order: m Jxx Jyy Jzz L alpha kt kq tau_m c_d omega_max g kp[3] kd[3]
-// katt[3] krate[3] a_max.
+// katt[3] krate[3] a_max kI[3] kD[3] xi_max[3].
 inline Group<double> unpack_group(const double* p) {
   Group<double> G;
   G.m = p[0];
@@ -59,6 +71,9 @@ inline Group<double> unpack_group(const double* p) {
     G.kp[i] = p[12 + i]; G.kd[i] = p[15 + i]; G.katt[i] = p[18 + i]; G.krate[i] = p[21 + i];
   }
   G.a_max = p[24];
+  for (int i = 0; i < 3; ++i) {
+    G.kI[i] = p[25 + i]; G.kD[i] = p[28 + i]; G.xi_max[i] = p[31 + i];
+  }
   return G;
 }
 
@@ -74,6 +89,9 @@ Group<T> cast_group(const Group<S>& s) {
     G.katt[i] = T(val(s.katt[i])); G.krate[i] = T(val(s.krate[i]));
   }
   G.a_max = T(val(s.a_max));
+  for (int i = 0; i < 3; ++i) {
+    G.kI[i] = T(val(s.kI[i])); G.kD[i] = T(val(s.kD[i])); G.xi_max[i] = T(val(s.xi_max[i]));
+  }
   return G;
 }
 
@@ -272,10 +290,12 @@ void derivative(const Group<T>& P, const Fixed& F, const T x[NX], const T w[4], 
 // Cascaded controller: state and waypoint command -> rotor speed commands.
 // Optional diagnostics (no effect on the result): the unclamped acceleration
 // demand ar[3] and the unclamped rotor demand S[4] = Omega_cmd^2 before the
-// clamp to [0, omega_max^2].
+// clamp to [0, omega_max^2].  PID rate loop when xi (the rate-error integral)
+// and wdot (omega' at this state) are given; e_out receives the rate error.
 template <class T>
 void controller(const Group<T>& P, const Fixed& F, const T x[NX], const double cmd[4], T w[4],
-                double* ar_out = nullptr, double* S_out = nullptr) {
+                double* ar_out = nullptr, double* S_out = nullptr, const T* xi = nullptr,
+                const T* wdot = nullptr, T* e_out = nullptr) {
   const T* p = x;
   const T* v = x + 3;
   const T* q = x + 6;
@@ -322,7 +342,11 @@ void controller(const Group<T>& P, const Fixed& F, const T x[NX], const double c
   u[0] = fc;
   for (int i = 0; i < 3; ++i) {
     const T wdes = T(2.0) * P.katt[i] * qe[1 + i];
-    u[1 + i] = P.krate[i] * T(F.taumax[i]) * (wdes - om[i]);
+    if (e_out) e_out[i] = wdes - om[i];
+    if (xi)
+      u[1 + i] = T(F.taumax[i]) * (P.krate[i] * (wdes - om[i]) + P.kI[i] * xi[i] - P.kD[i] * wdot[i]);
+    else
+      u[1 + i] = P.krate[i] * T(F.taumax[i]) * (wdes - om[i]);
   }
   // inverse allocation, then per-rotor clamp in Omega^2 and square root
   const double om2max = val(P.omega_max) * val(P.omega_max);
@@ -335,17 +359,10 @@ void controller(const Group<T>& P, const Fixed& F, const T x[NX], const double c
   }
 }
 
-// One classical RK4 step of length h with the rotor command held (zero-order
-// hold) over the four stages.  Open loop: cmd holds the rotor speed commands.
+// One classical RK4 step of length h of the 17 states with the rotor command
+// w held (zero-order hold) over the four stages.
 template <class T>
-void rk4_step(const Group<T>& P, const Fixed& F, int mode, const T x[NX], const double cmd[4], double h,
-              T xn[NX]) {
-  T w[4];
-  if (mode == CLOSED_LOOP) {
-    controller(P, F, x, cmd, w);
-  } else {
-    for (int i = 0; i < 4; ++i) w[i] = T(cmd[i]);
-  }
+void rk4_core(const Group<T>& P, const Fixed& F, const T x[NX], const T w[4], double h, T xn[NX]) {
   T k1[NX], k2[NX], k3[NX], k4[NX], y[NX];
   derivative(P, F, x, w, k1);
   for (int i = 0; i < NX; ++i) y[i] = x[i] + T(0.5 * h) * k1[i];
@@ -356,6 +373,45 @@ void rk4_step(const Group<T>& P, const Fixed& F, int mode, const T x[NX], const 
   derivative(P, F, y, w, k4);
   for (int i = 0; i < NX; ++i)
     xn[i] = x[i] + T(h / 6.0) * (k1[i] + T(2.0) * k2[i] + T(2.0) * k3[i] + k4[i]);
+}
+
+// One step, open or closed loop (P rate loop).  Open loop: cmd holds the
+// rotor speed commands.
+template <class T>
+void rk4_step(const Group<T>& P, const Fixed& F, int mode, const T x[NX], const double cmd[4], double h,
+              T xn[NX]) {
+  T w[4];
+  if (mode == CLOSED_LOOP) {
+    controller(P, F, x, cmd, w);
+  } else {
+    for (int i = 0; i < 4; ++i) w[i] = T(cmd[i]);
+  }
+  rk4_core(P, F, x, w, h, xn);
+}
+
+// One step of the PID variant on the 20-state x = (17 states, xi): omega' at
+// the step start from Eq. (qd4) (it does not depend on the rotor command), the
+// controller, RK4 of the 17 states, then xi <- clamp(xi + h e, +-xi_max).
+template <class T>
+void rk4_step_pid(const Group<T>& P, const Fixed& F, const T x[NXP], const double cmd[4], double h, T xn[NXP]) {
+  T d0[NX];
+  derivative(P, F, x, x + 13, d0);
+  T w[4], e[3];
+  controller(P, F, x, cmd, w, nullptr, nullptr, x + NX, d0 + 10, e);
+  rk4_core(P, F, x, w, h, xn);
+  for (int i = 0; i < 3; ++i) {
+    const double lim = val(P.xi_max[i]);
+    xn[NX + i] = clampv(x[NX + i] + T(h) * e[i], -lim, lim);
+  }
+}
+
+// Either step on a state of state_dim(mode) components.
+template <class T>
+void step_any(const Group<T>& P, const Fixed& F, int mode, const T* x, const double cmd[4], double h, T* xn) {
+  if (mode == CLOSED_LOOP_PID)
+    rk4_step_pid(P, F, x, cmd, h, xn);
+  else
+    rk4_step(P, F, mode, x, cmd, h, xn);
 }
 
 }  // namespace orc

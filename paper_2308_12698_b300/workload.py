@@ -37,6 +37,9 @@ THETA_NAMES = ("kp_x", "kp_y", "kp_z", "kd_x", "kd_y", "kd_z",
 
 OPEN_LOOP = 0
 CLOSED_LOOP = 1
+CLOSED_LOOP_PID = 2
+#: state components in the PID mode: the 17 and the rate-error integral xi (3)
+STATE_DIM_PID = 20
 
 #: Fixed group sizes of the uneven heterogeneous swarm (sum 600,000).
 HETERO_SIZES = (100, 900, 5000, 19000, 55000, 130000, 190000, 200000)
@@ -56,6 +59,17 @@ def base_group() -> dict:
              alpha=math.pi / 4, kt=1e-5, kq=1.6e-7, tau_m=0.03, c_d=0.1,
              omega_max=1200.0, g=9.81, kp=[6.0] * 3, kd=[4.5] * 3,
              katt=[8.0] * 3, krate=[0.2] * 3, a_max=4.0)
+    return round_group(g)
+
+
+def pid_group() -> dict:
+    """The reference quadrotor with a PID body-rate loop: the P gain 0.2 of the base group plus
+    integral gain kI = 0.05 and derivative gain kD = 0.005 per axis (normalised by the axis
+    torque limit like the P gain) and integrator limit |xi| <= 2 rad.  At hover the slowest
+    closed-loop pole sits at -0.23 1/s and the fastest rate mode is damped to |Im| = 7.6 rad/s
+    (0.05 < kI < 0.2 is the stable band at kD = 0.005)."""
+    g = dict(base_group())
+    g.update(kI=[0.05] * 3, kD=[0.005] * 3, xi_max=[2.0] * 3)
     return round_group(g)
 
 
@@ -180,6 +194,23 @@ def closed_loop(n: int = 5000, nsteps: int = 10000, dt: float = 1e-3, seed: int 
     cmd[:, 0:3] = rng.uniform(-50.0, 50.0, (n, 3))
     cmd[:, 3] = psi
     return Workload(name, CLOSED_LOOP, groups, gid, x0, cmd.astype(np.float32), dt, nsteps)
+
+
+def closed_loop_pid(n: int = 5000, nsteps: int = 1000, dt: float = 1e-3, seed: int = BASE_SEED + 7,
+                    name: str = "closed-loop-pid") -> Workload:
+    """Reference quadrotors under the cascade with the PID rate loop (pid_group), waypoints
+    ~ U[-50, 50]^3, heading hold; 20-component states with the integral xi starting at 0."""
+    rng = np.random.default_rng(seed)
+    groups = [pid_group()]
+    gid = np.zeros(n, dtype=np.uint8)
+    wh = _hover_per_agent(groups, gid)
+    x17, psi = _initial_states(rng, n, wh)
+    x0 = np.zeros((n, STATE_DIM_PID), dtype=np.float32)
+    x0[:, :STATE_DIM] = x17
+    cmd = np.zeros((n, 4), dtype=np.float64)
+    cmd[:, 0:3] = rng.uniform(-50.0, 50.0, (n, 3))
+    cmd[:, 3] = psi
+    return Workload(name, CLOSED_LOOP_PID, groups, gid, x0, cmd.astype(np.float32), dt, nsteps)
 
 
 def scale_sweep(n: int, nsteps: int = 1000, dt: float = 1e-3) -> Workload:

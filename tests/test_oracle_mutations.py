@@ -32,6 +32,10 @@ MUTATIONS = {
     "no acceleration clamp": ("const T a = clampv(ar, -val(P.a_max), val(P.a_max));", "const T a = ar;"),
     "rate loop sign": ("(wdes - om[i]);", "(om[i] - wdes);"),
     "attitude gain x1": ("const T wdes = T(2.0) * P.katt[i] * qe[1 + i];", "const T wdes = P.katt[i] * qe[1 + i];"),
+    "PID derivative sign": ("+ P.kI[i] * xi[i] - P.kD[i] * wdot[i]);", "+ P.kI[i] * xi[i] + P.kD[i] * wdot[i]);"),
+    "PID integrator sign": ("x[NX + i] + T(h) * e[i]", "x[NX + i] - T(h) * e[i]"),
+    "PID integral index": ("P.kI[i] * xi[i]", "P.kI[i] * xi[(i + 1) % 3]"),
+    "PID no anti-windup": ("xn[NX + i] = clampv(x[NX + i] + T(h) * e[i], -lim, lim);", "xn[NX + i] = x[NX + i] + T(h) * e[i];"),
 }
 
 
@@ -50,6 +54,7 @@ def test_pins_catch_planted_mistake(tmp_path, name):
                     str(work / "oracle.cpp"), "-o", str(lib)], check=True)
     env = dict(os.environ, ORACLE_LIB=str(lib), PYTHONPATH=ROOT)
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")], cwd=ROOT, env=env,
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_pid.py")], cwd=ROOT, env=env,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"no pin caught the mutation {name!r}:\n{r.stdout[-2000:]}"
