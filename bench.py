@@ -50,6 +50,10 @@ FLOPS_PER_AGENT_STEP = 748
 #: forward recomputation that checkpointing adds is not counted.
 ADJ_TAPE_EDGES_PER_AGENT_STEP = 1348
 FWD_ADJ_FLOPS_PER_AGENT_STEP = 2 * FLOPS_PER_AGENT_STEP + 2 * ADJ_TAPE_EDGES_PER_AGENT_STEP
+#: The same count for one step with the PID body-rate loop (minimum over the PID workload's
+#: states, 760..774), less the checker's second evaluation of the time derivative for omega'
+#: (a step takes omega' from its first RK4 stage).
+FLOPS_PER_AGENT_STEP_PID = 760
 #: Bytes one plain step moves per agent: state 68 read + 68 written, command
 #: 16, group id 1, status 1.
 BYTES_PER_AGENT_STEP_PLAIN = 154
@@ -619,6 +623,28 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
                      "block": ht["block"]}
     hg.close()
     hs.close()
+
+    # PID body-rate loop: 1e6 agents with 20-component states, tuned K, one graph
+    pw = W.closed_loop_pid(n=N_AGENTS, nsteps=T_STEPS)
+    ps = Sim(pw.groups, pw.n, pw.mode)
+    px0 = planar(torch.from_numpy(pw.x0)).to(x0.device)
+    pcmd = torch.from_numpy(pw.cmd).reshape(-1).to(x0.device)
+    px = px0.clone()
+    pt = autotune.tune_step(ps, px0, pcmd, DT, T_STEPS)
+    pg = ps.graph(px, pcmd, DT, T_STEPS, K=pt["K"])
+    preset = lambda: px.copy_(px0)  # noqa: E731
+    timed_steps(pg.launch, 2, preset)
+    t = timed_steps(pg.launch, reps, preset)
+    ms = max_over_ranks(sum(t), world) / reps
+    rate = pw.n * T_STEPS / (ms / 1e3)
+    out["pid"] = {"value": world * rate, "unit": UNIT, "ms_per_step": ms, "n_agents": pw.n, "K": pt["K"],
+                  "block": pt["block"],
+                  "roofline": {"bound": "alu", "achieved": FLOPS_PER_AGENT_STEP_PID * rate / 1e12, "peak": peak_tf,
+                               "unit": "TFLOP/s", "frac": FLOPS_PER_AGENT_STEP_PID * rate / 1e12 / peak_tf,
+                               "flops_per_agent_step": FLOPS_PER_AGENT_STEP_PID}}
+    pg.close()
+    ps.close()
+    del px, px0, pcmd
 
     # decision rounds: commands from pinned host memory every M steps, positions back after
     # each round, both overlapped with the physics (1000 steps per bench step)

@@ -18,17 +18,27 @@
  *     quaternion -> body-rate P scaled by the axis torque limit -> G^-1 ->
  *     per-rotor clamp of Omega^2 to [0, omega_max^2] -> sqrt).  The paper
  *     names only the inner body-rate loop (Sec. III-B); the cascade above is
- *     this library's definition of it.
+ *     this library's definition of it;
+ *   - closed loop with a PID body-rate loop (the paper's "PID body rate
+ *     controller", Sec. III-B; it gives no gains): the rate loop's torque
+ *     becomes taumax_i (krate_i e_i + kI_i xi_i - kD_i omega'_i), e = omega_des
+ *     - omega, omega' of Eq. (qd4) at the step start (derivative on the
+ *     measurement), and xi, the integral of e, is three more state components
+ *     advanced once per step: xi <- clamp(xi + dt e, +-xi_max).
  *
  * Conventions
  *   State of one agent, 17 floats: p(3) v(3) q(4: w,x,y,z, Hamilton,
  *   body->inertial) omega(3, body) Omega(4, rad/s).  Frames ENU / FLU.
  *   Rotors: 1 front-left, 2 front-right, 3 rear-right, 4 rear-left.
  *
+ *   SIM_CLOSED_LOOP_PID adds xi(3), the body-rate error integral: 20 floats.
+ *
  *   State buffers are PLANAR ("SoA of float4"): for N agents, 17*N floats,
  *     plane k = 0..3 : N float4 holding components 4k..4k+3 of every agent,
  *                      at float offset 4*k*N;
  *     plane 4        : N floats holding component 16, at float offset 16*N.
+ *   In SIM_CLOSED_LOOP_PID, 20*N floats: plane 4 is N float4 holding
+ *   components 16..19 (Omega_4, xi_x, xi_y, xi_z) at float offset 16*N.
  *   The base pointer must be 16-byte aligned.
  *   Commands: N float4 (16-byte aligned).  Closed loop: waypoint x, y, z and
  *   heading psi (rad).  Open loop: the four rotor speed commands (rad/s).
@@ -70,6 +80,7 @@ extern "C" {
 
 #define SIM_OPEN_LOOP 0
 #define SIM_CLOSED_LOOP 1
+#define SIM_CLOSED_LOOP_PID 2 /* closed loop, PID body-rate loop, 20-float state */
 
 #define SIM_MAX_GROUPS 32 /* parameter groups per handle */
 #define SIM_NTHETA 16     /* differentiable parameters per group */
@@ -82,6 +93,8 @@ typedef struct {
   float tau_m, c_d, omega_max, g;       /* rotor lag s; drag N s/m; rotor clamp rad/s; m/s^2 */
   float kp[3], kd[3], katt[3], krate[3]; /* position PD, attitude P, normalised rate P */
   float a_max;                          /* per-axis acceleration clamp m/s^2 (INFINITY = off) */
+  float kI[3], kD[3];                   /* PID rate loop: integral (1/rad), derivative (s^2/rad), */
+  float xi_max[3];                      /* normalised like krate; integrator limit rad (INFINITY = off) */
 } sim_group_params_t;
 
 typedef struct sim_s* sim_handle_t;
@@ -91,8 +104,10 @@ typedef struct sim_graph_s* sim_graph_t;
  * d_group_id: device array of n_agents uint8 group ids, or NULL when
  * n_groups == 1.  The handle keeps the pointer (the caller keeps the buffer
  * alive and unchanged); sim_create checks every id once (synchronously) and
- * returns SIM_ERR_GROUP if one is out of range.  mode: SIM_OPEN_LOOP or
- * SIM_CLOSED_LOOP.  Runs on the current CUDA device. */
+ * returns SIM_ERR_GROUP if one is out of range.  mode: SIM_OPEN_LOOP,
+ * SIM_CLOSED_LOOP or SIM_CLOSED_LOOP_PID (kI, kD, xi_max are read only in the
+ * last; they must be finite, xi_max >= 0, in every mode).  Runs on the current
+ * CUDA device. */
 int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents, const uint8_t* d_group_id,
                int mode, sim_handle_t* out);
 
@@ -136,12 +151,14 @@ int sim_run_rounds(sim_handle_t h, float* d_state, float* d_cmd2, const float* h
  * S+1 planar states into d_ckpt (S = ceil(nsteps/ckpt_C)): x_0, x_C, ...,
  * x_{(S-1)C}, then x_nsteps last.  d_ckpt holds (S+1)*17*N floats.
  * d_run_cost (N floats, may be NULL) receives, per agent, the sum over step
- * ends n = 1..nsteps of sum_i Omega_{n,i}^2. */
+ * ends n = 1..nsteps of sum_i Omega_{n,i}^2.  Not in SIM_CLOSED_LOOP_PID
+ * (SIM_ERR_ARG): the rollouts and the adjoint cover the 17-state modes. */
 int sim_rollout_forward(sim_handle_t h, const float* d_state0, const float* d_cmd, float dt, int64_t nsteps,
                         int ckpt_C, float* d_ckpt, float* d_run_cost, void* stream);
 
 /* Bytes of workspace sim_rollout_backward needs for this handle, its
- * current launch configuration and checkpoint interval ckpt_C. */
+ * current launch configuration and checkpoint interval ckpt_C (0 in
+ * SIM_CLOSED_LOOP_PID). */
 size_t sim_workspace_bytes(sim_handle_t h, int ckpt_C);
 
 /* Discrete adjoint of the rollout of sim_rollout_forward (same dt, nsteps,
@@ -158,7 +175,7 @@ size_t sim_workspace_bytes(sim_handle_t h, int ckpt_C);
  * interval, sqrt(0) has derivative 0, branch choices are constants.  The
  * per-group sums are deterministic (fixed reduction order, no atomics).
  * d_workspace must hold sim_workspace_bytes(h, ckpt_C) bytes, 256-byte
- * aligned. */
+ * aligned.  Not in SIM_CLOSED_LOOP_PID (SIM_ERR_ARG). */
 int sim_rollout_backward(sim_handle_t h, const float* d_ckpt, const float* d_cmd, float dt, int64_t nsteps,
                          int ckpt_C, const float* d_dL_dxT, const float* d_w_run, float* d_dL_dx0,
                          float* d_dL_dtheta, float* d_dL_dtheta_agent, void* d_workspace, size_t ws_bytes,

@@ -73,6 +73,7 @@ def lib():
         L.oracle_allocation.argtypes = [P, P, P, P]
         L.oracle_shepperd.argtypes = [P, P]
         L.oracle_count_ops.argtypes = [P, P, P, ctypes.c_double, ctypes.c_int, P]
+        L.oracle_count_derivative_ops.argtypes = [P, P, P, P]
         L.oracle_count_adjoint_edges.argtypes = [P, P, P, ctypes.c_double, ctypes.c_int, P]
         L.oracle_collisions.argtypes = [P, P, P, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int, P]
         L.oracle_clamp_margins.argtypes = [P, ctypes.c_int, P, ctypes.c_int64, P, P, ctypes.c_double, ctypes.c_int64,
@@ -252,4 +253,14 @@ def count_ops(group, x, cmd, h, mode):
     cc = np.ascontiguousarray(np.asarray(cmd, dtype=np.float64))
     out = np.zeros(6, dtype=np.int64)
     lib().oracle_count_ops(_p(pg), _p(xx), _p(cc), float(h), int(mode), _p(out))
+    return dict(zip(("add", "mul", "div", "sqrt", "trig", "cmp"), out.tolist()))
+
+
+def count_derivative_ops(group, x, w):
+    """Non-trivial FP64 operations of one time-derivative evaluation: dict(add, mul, div, sqrt, trig, cmp)."""
+    pg = pack_group(group)
+    xx = np.ascontiguousarray(np.asarray(x, dtype=np.float64)[:NX])
+    ww = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    out = np.zeros(6, dtype=np.int64)
+    lib().oracle_count_derivative_ops(_p(pg), _p(xx), _p(ww), _p(out))
     return dict(zip(("add", "mul", "div", "sqrt", "trig", "cmp"), out.tolist()))

@@ -325,6 +325,27 @@ int oracle_count_adjoint_edges(const double* group, const double* x, const doubl
   return 0;
 }
 
+// Non-trivial FP64 operations of one evaluation of the time derivative (the
+// 17 states, rotor commands w): the PID step evaluates it once more for
+// omega', which a step implementation may take from its first RK4 stage.
+int oracle_count_derivative_ops(const double* group, const double* x, const double* w, int64_t* counts) {
+  const Group<double> Pd = unpack_group(group);
+  const Fixed F = make_fixed(Pd);
+  const Group<Cnt> P = cast_group<Cnt>(Pd);
+  Cnt xc[NX], wc[4], dx[NX];
+  for (int i = 0; i < NX; ++i) xc[i] = Cnt(x[i]);
+  for (int i = 0; i < 4; ++i) wc[i] = Cnt(w[i]);
+  g_count = OpCount();
+  derivative(P, F, xc, wc, dx);
+  counts[0] = g_count.add;
+  counts[1] = g_count.mul;
+  counts[2] = g_count.div;
+  counts[3] = g_count.sqrt;
+  counts[4] = g_count.trig;
+  counts[5] = g_count.cmp;
+  return 0;
+}
+
 // Non-trivial FP64 operations of one step for one agent:
 // counts = {add/sub, mul, div, sqrt, sin/cos, comparisons}.
 int oracle_count_ops(const double* group, const double* x, const double* cmd, double h, int mode,

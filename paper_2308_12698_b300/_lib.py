@@ -15,6 +15,7 @@ SIM_ERR_TIMEOUT = -4
 SIM_ERR_GROUP = -5
 SIM_OPEN_LOOP = 0
 SIM_CLOSED_LOOP = 1
+SIM_CLOSED_LOOP_PID = 2
 SIM_MAX_GROUPS = 32
 SIM_NTHETA = 16
 SIM_NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -33,7 +34,12 @@ class GroupParams(ctypes.Structure):
                 ("L", ctypes.c_float), ("alpha", ctypes.c_float), ("kt", ctypes.c_float), ("kq", ctypes.c_float),
                 ("tau_m", ctypes.c_float), ("c_d", ctypes.c_float), ("omega_max", ctypes.c_float),
                 ("g", ctypes.c_float), ("kp", ctypes.c_float * 3), ("kd", ctypes.c_float * 3),
-                ("katt", ctypes.c_float * 3), ("krate", ctypes.c_float * 3), ("a_max", ctypes.c_float)]
+                ("katt", ctypes.c_float * 3), ("krate", ctypes.c_float * 3), ("a_max", ctypes.c_float),
+                ("kI", ctypes.c_float * 3), ("kD", ctypes.c_float * 3), ("xi_max", ctypes.c_float * 3)]
+
+
+#: PID rate-loop fields and the values a group without them gets (P loop, no integrator limit).
+PID_DEFAULTS = {"kI": [0.0] * 3, "kD": [0.0] * 3, "xi_max": [float("inf")] * 3}
 
 
 def group_struct(g: dict) -> GroupParams:
@@ -42,6 +48,8 @@ def group_struct(g: dict) -> GroupParams:
         setattr(s, k, float(g[k]))
     for k in ("kp", "kd", "katt", "krate"):
         getattr(s, k)[:] = [float(v) for v in g[k]]
+    for k, d in PID_DEFAULTS.items():
+        getattr(s, k)[:] = [float(v) for v in g.get(k, d)]
     return s
 
 

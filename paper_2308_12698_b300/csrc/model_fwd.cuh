@@ -15,19 +15,26 @@
 //                   unnormalised half-angle pairs and normalised once -- the
 //                   same rotation as building the matrix and converting it
 //                   (Shepperd), without the matrix or the branch
+//   PID rate loop   MODE 2 (the paper's "PID body rate controller", Sec. III-B):
+//                   adds taumax (kI xi - kD omega') to the rate loop's torque,
+//                   omega' on the measurement (Eq. qd4 at the step start, the
+//                   first RK4 stage's derivative), xi <- clamp(xi + h e) once
+//                   per step
 //   rk4             classical RK4, command held over the stages (Sec. III-B)
 //   (the vector-Jacobian products of the adjoint are in model_adj.cuh)
 //
 // State index map (17 floats): p 0-2, v 3-5, q 6-9 (w x y z), omega 10-12,
-// Omega 13-16.  rb_derivative returns 2 q' for the quaternion (q o [0, w]),
-// and the RK4 coefficients of those four components are halved to match.
+// Omega 13-16; in the PID mode (MODE 2) also xi 17-19, the integral of the
+// body-rate error.  rb_derivative returns 2 q' for the quaternion
+// (q o [0, w]), and the RK4 coefficients of those four components are halved
+// to match.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace qs {
 
-enum { PX = 0, VX = 3, QW = 6, QX = 7, QY = 8, QZ = 9, WX = 10, OM = 13, NX = 17, NRB = 13 };
+enum { PX = 0, VX = 3, QW = 6, QX = 7, QY = 8, QZ = 9, WX = 10, OM = 13, NX = 17, NRB = 13, XI = 17, NXP = 20 };
 enum { TH_KP = 0, TH_KD = 3, TH_KATT = 6, TH_KRATE = 9, TH_M = 12, TH_J = 13, NTH = 16 };
 
 // Per-group constants, derived on the host in double from the public
@@ -48,11 +55,21 @@ struct __align__(16) DevGroup {
   float krate[3], pad2;
   float katt2[3], pad3;         // 2 katt
   float mt[3], pad4;            // mix_i taumax_i  (mix = 1/(4 kt L sin a), 1/(4 kt L cos a), 1/(4 kq))
+  // forward: PID rate loop (MODE 2)
+  float kic[3], pad5;           // mix_i taumax_i kI_i: rate-error integral -> Omega^2
+  float kdc[3], pad6;           // mix_i taumax_i kD_i: angular acceleration -> Omega^2
+  float xim[3], pad7;           // integrator limit |xi_i| <= xim_i
 };
-static_assert(sizeof(DevGroup) == 48 * 4, "DevGroup layout");
+static_assert(sizeof(DevGroup) == 60 * 4, "DevGroup layout");
+
+// Components of an agent's state in a mode: 17, or 20 with the PID integral.
+template <int MODE>
+__host__ __device__ constexpr int state_dim() {
+  return MODE == 2 ? NXP : NX;
+}
 
 struct St {
-  float a[NX];
+  float a[NXP];  // the first state_dim<MODE>() are used
 };
 
 // Commanded heading psi: cos, sin of psi and of psi / 2.
@@ -92,25 +109,36 @@ __device__ __forceinline__ LagCoef lag_coef(float inv_tau, const StepH& H) {
 }
 
 // ------------------------------------------------------------ planar I/O --
-// Plane k (0..3) holds float4 of components 4k..4k+3, plane 4 component 16.
+// Plane k (0..3) holds float4 of components 4k..4k+3; plane 4 holds
+// component 16 (a float per agent), or components 16..19 (a float4 per
+// agent) when the state has 20 components.
+template <int NS = NX>
 __device__ __forceinline__ void load_state(const float* __restrict__ base, int64_t n, int64_t i, St& x) {
   const float4* P = reinterpret_cast<const float4*>(base);
   const float4 a = P[i], b = P[n + i], c = P[2 * n + i], d = P[3 * n + i];
-  const float e = base[16 * n + i];
   x.a[0] = a.x; x.a[1] = a.y; x.a[2] = a.z; x.a[3] = a.w;
   x.a[4] = b.x; x.a[5] = b.y; x.a[6] = b.z; x.a[7] = b.w;
   x.a[8] = c.x; x.a[9] = c.y; x.a[10] = c.z; x.a[11] = c.w;
   x.a[12] = d.x; x.a[13] = d.y; x.a[14] = d.z; x.a[15] = d.w;
-  x.a[16] = e;
+  if (NS == NXP) {
+    const float4 e = P[4 * n + i];
+    x.a[16] = e.x; x.a[17] = e.y; x.a[18] = e.z; x.a[19] = e.w;
+  } else {
+    x.a[16] = base[16 * n + i];
+  }
 }
 
+template <int NS = NX>
 __device__ __forceinline__ void store_state(float* __restrict__ base, int64_t n, int64_t i, const St& x) {
   float4* P = reinterpret_cast<float4*>(base);
   P[i] = make_float4(x.a[0], x.a[1], x.a[2], x.a[3]);
   P[n + i] = make_float4(x.a[4], x.a[5], x.a[6], x.a[7]);
   P[2 * n + i] = make_float4(x.a[8], x.a[9], x.a[10], x.a[11]);
   P[3 * n + i] = make_float4(x.a[12], x.a[13], x.a[14], x.a[15]);
-  base[16 * n + i] = x.a[16];
+  if (NS == NXP)
+    P[4 * n + i] = make_float4(x.a[16], x.a[17], x.a[18], x.a[19]);
+  else
+    base[16 * n + i] = x.a[16];
 }
 
 __device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
@@ -165,8 +193,12 @@ struct Ctl {
   float S[4];    // Omega^2 demanded by the mixer, before the clamp
 };
 
+// PID: also the integral and derivative terms of the rate loop (x holds xi at
+// XI..XI+2, wdot is omega' at x); e receives the rate error omega_des - omega.
+template <bool PID = false>
 __device__ __forceinline__ void controller_fwd(const DevGroup& P, const float* x, const float4 c, const Hd& hd,
-                                               Ctl& C, float u[4]) {
+                                               Ctl& C, float u[4], const float* wdot = nullptr,
+                                               float* e = nullptr) {
   const float cc[3] = {c.x, c.y, c.z};
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -216,9 +248,17 @@ __device__ __forceinline__ void controller_fwd(const DevGroup& P, const float* x
   C.s = C.E[0] < 0.f ? -rQ : rQ;
   C.qe[0] = C.s * C.E[0]; C.qe[1] = C.s * C.E[1]; C.qe[2] = C.s * C.E[2]; C.qe[3] = C.s * C.E[3];
   const float f0 = P.f0c * C.fc;
-  const float f1 = P.qa[0] * C.qe[1] - P.wa[0] * x[WX];
-  const float f2 = P.qa[1] * C.qe[2] - P.wa[1] * x[WX + 1];
-  const float f3 = P.qa[2] * C.qe[3] - P.wa[2] * x[WX + 2];
+  float f1 = P.qa[0] * C.qe[1] - P.wa[0] * x[WX];
+  float f2 = P.qa[1] * C.qe[2] - P.wa[1] * x[WX + 1];
+  float f3 = P.qa[2] * C.qe[3] - P.wa[2] * x[WX + 2];
+  if (PID) {
+    // mix_i taumax_i (kI_i xi_i - kD_i omega'_i), added after the P term
+    f1 = fmaf(-P.kdc[0], wdot[0], fmaf(P.kic[0], x[XI], f1));
+    f2 = fmaf(-P.kdc[1], wdot[1], fmaf(P.kic[1], x[XI + 1], f2));
+    f3 = fmaf(-P.kdc[2], wdot[2], fmaf(P.kic[2], x[XI + 2], f3));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) e[i] = P.katt2[i] * C.qe[1 + i] - x[WX + i];
+  }
   C.S[0] = (f0 + f1) + (f3 - f2);
   C.S[1] = (f0 - f1) - (f2 + f3);
   C.S[2] = (f0 - f1) + (f2 + f3);
@@ -237,12 +277,13 @@ __device__ __forceinline__ void controller(const DevGroup& P, const float* x, co
 }
 
 // ------------------------------------------------------------------ RK4 --
-__device__ __forceinline__ void rk4(const DevGroup& P, St& x, const float u[4], const StepH& H, const LagCoef& L) {
+// RK4 with the first stage's derivative k (rb_derivative at x) already known.
+__device__ __forceinline__ void rk4_k1(const DevGroup& P, St& x, const float u[4], const StepH& H, const LagCoef& L,
+                                       float k[NRB]) {
   float dOm[4], Om[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) dOm[i] = u[i] - x.a[OM + i];
-  float k[NRB], y[NRB], acc[NRB];
-  rb_derivative(P, x.a, x.a + OM, k);
+  float y[NRB], acc[NRB];
 #pragma unroll
   for (int i = 0; i < NRB; ++i) { acc[i] = k[i]; y[i] = x.a[i] + coef(i, H.h2, H.h2q) * k[i]; }
 #pragma unroll
@@ -264,10 +305,28 @@ __device__ __forceinline__ void rk4(const DevGroup& P, St& x, const float u[4], 
   for (int i = 0; i < 4; ++i) x.a[OM + i] = x.a[OM + i] + L.c5 * dOm[i];
 }
 
+__device__ __forceinline__ void rk4(const DevGroup& P, St& x, const float u[4], const StepH& H, const LagCoef& L) {
+  float k[NRB];
+  rb_derivative(P, x.a, x.a + OM, k);
+  rk4_k1(P, x, u, H, L, k);
+}
+
 template <int MODE>
 __device__ __forceinline__ void step(const DevGroup& P, St& x, const float4 c, const Hd& hd, const StepH& H,
                                      const LagCoef& L) {
   float u[4];
+  if (MODE == 2) {
+    // omega' at the step start is the first RK4 stage's; the controller's
+    // derivative term takes it, then RK4 goes on from it
+    float k[NRB], e[3];
+    rb_derivative(P, x.a, x.a + OM, k);
+    Ctl C;
+    controller_fwd<true>(P, x.a, c, hd, C, u, k + WX, e);
+    rk4_k1(P, x, u, H, L, k);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) x.a[XI + i] = clampf(x.a[XI + i] + H.h * e[i], -P.xim[i], P.xim[i]);
+    return;
+  }
   if (MODE == 1) {
     controller(P, x.a, c, hd, u);
   } else {

@@ -327,6 +327,9 @@ DevGroup derive(const sim_group_params_t& p) {
     d.krate[i] = p.krate[i];
     d.katt2[i] = (float)(2.0 * p.katt[i]);
     d.mt[i] = (float)(mix[i] * taumax[i]);
+    d.kic[i] = (float)(mix[i] * taumax[i] * p.kI[i]);
+    d.kdc[i] = (float)(mix[i] * taumax[i] * p.kD[i]);
+    d.xim[i] = p.xi_max[i];
   }
   d.a_max = p.a_max;
   d.f0c = (float)(m / (4.0 * kt));
@@ -345,7 +348,7 @@ bool valid_params(const sim_group_params_t& p) {
   if (!(std::sin((double)p.alpha) > 0.0 && std::cos((double)p.alpha) > 0.0)) return false;
   for (int i = 0; i < 3; ++i)
     if (!std::isfinite(p.kp[i]) || !std::isfinite(p.kd[i]) || !std::isfinite(p.katt[i]) ||
-        !std::isfinite(p.krate[i]))
+        !std::isfinite(p.krate[i]) || !std::isfinite(p.kI[i]) || !std::isfinite(p.kD[i]) || !(p.xi_max[i] >= 0.f))
       return false;
   return p.a_max >= 0.f;  // +inf allowed (no clamp)
 }
@@ -410,7 +413,10 @@ size_t group_smem(const sim_s* h) { return hetero(h) ? sizeof(DevGroup) * h->n_g
 int fwd_grid(const sim_s* h, size_t smem, int64_t count) {
   // one resident wave of blocks, grid-stride over the agents
   int occ;
-  if (h->mode == SIM_CLOSED_LOOP)
+  if (h->mode == SIM_CLOSED_LOOP_PID)
+    occ = hetero(h) ? occupancy(step_kernel<2, true>, h->block_fwd, smem)
+                    : occupancy(step_kernel<2, false>, h->block_fwd, smem);
+  else if (h->mode == SIM_CLOSED_LOOP)
     occ = hetero(h) ? occupancy(step_kernel<1, true>, h->block_fwd, smem)
                     : occupancy(step_kernel<1, false>, h->block_fwd, smem);
   else
@@ -482,7 +488,10 @@ int launch_step(sim_s* h, float* d_state, const float* d_cmd, StepH H, int K, cu
   const size_t smem = group_smem(h);
   const int grid = fwd_grid(h, smem, count);
   const DevGroup& P0 = h->host_group0;
-  if (h->mode == SIM_CLOSED_LOOP) {
+  if (h->mode == SIM_CLOSED_LOOP_PID) {
+    if (hetero(h)) step_kernel<2, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
+    else step_kernel<2, false><<<grid, h->block_fwd, smem, st>>>(A, P0);
+  } else if (h->mode == SIM_CLOSED_LOOP) {
     if (hetero(h)) step_kernel<1, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
     else step_kernel<1, false><<<grid, h->block_fwd, smem, st>>>(A, P0);
   } else {
@@ -558,7 +567,7 @@ int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents,
   if (!out) return SIM_ERR_ARG;
   *out = nullptr;
   if (!groups || n_groups < 1 || n_groups > SIM_MAX_GROUPS || n_agents < 0) return SIM_ERR_ARG;
-  if (mode != SIM_OPEN_LOOP && mode != SIM_CLOSED_LOOP) return SIM_ERR_ARG;
+  if (mode != SIM_OPEN_LOOP && mode != SIM_CLOSED_LOOP && mode != SIM_CLOSED_LOOP_PID) return SIM_ERR_ARG;
   if (n_groups > 1 && !d_group_id && n_agents > 0) return SIM_ERR_ARG;
   for (int g = 0; g < n_groups; ++g)
     if (!valid_params(groups[g])) return SIM_ERR_ARG;
@@ -709,8 +718,9 @@ int sim_step_host(sim_handle_t h, float* h_state, const float* h_cmd, float* d_s
       const size_t off = (size_t)4 * k * n + (size_t)4 * a0;
       if (cudaMemcpyAsync(dst + off, src + off, (size_t)4 * cnt * fs, kind, s2) != cudaSuccess) return false;
     }
-    const size_t off = (size_t)16 * n + (size_t)a0;
-    return cudaMemcpyAsync(dst + off, src + off, (size_t)cnt * fs, kind, s2) == cudaSuccess;
+    const size_t r = h->mode == SIM_CLOSED_LOOP_PID ? 4 : 1;  // components in plane 4
+    const size_t off = (size_t)16 * n + r * (size_t)a0;
+    return cudaMemcpyAsync(dst + off, src + off, r * (size_t)cnt * fs, kind, s2) == cudaSuccess;
   };
   for (int c = 0; c < m; ++c) {
     const int64_t a0 = c * chunk, cnt = std::min<int64_t>(chunk, n - a0);
@@ -799,6 +809,7 @@ int sim_run_rounds(sim_handle_t h, float* d_state, float* d_cmd2, const float* h
 int sim_rollout_forward(sim_handle_t h, const float* d_state0, const float* d_cmd, float dt, int64_t nsteps,
                         int ckpt_C, float* d_ckpt, float* d_run_cost, void* stream) {
   if (!h || nsteps < 1 || ckpt_C < 0 || !(dt > 0.f) || !std::isfinite(dt)) return SIM_ERR_ARG;
+  if (h->mode == SIM_CLOSED_LOOP_PID) return SIM_ERR_ARG;  // no checkpointed rollout in the PID mode
   if (h->n == 0) return SIM_OK;
   if (!d_state0 || !d_cmd || !d_ckpt || !aligned16(d_state0) || !aligned16(d_cmd) || !aligned16(d_ckpt))
     return SIM_ERR_ARG;
@@ -832,7 +843,7 @@ int sim_rollout_forward(sim_handle_t h, const float* d_state0, const float* d_cm
 }
 
 size_t sim_workspace_bytes(sim_handle_t h, int ckpt_C) {
-  if (!h || ckpt_C < 0) return 0;
+  if (!h || ckpt_C < 0 || h->mode == SIM_CLOSED_LOOP_PID) return 0;
   const int C = ckpt_C > 0 ? ckpt_C : h->C;
   const int grid = adj_grid(h, C);
   return scratch_bytes(h, C, grid) + align256((size_t)grid * h->n_groups * NTH * sizeof(float));
@@ -843,7 +854,7 @@ int sim_rollout_backward(sim_handle_t h, const float* d_ckpt, const float* d_cmd
                          float* d_dL_dtheta, float* d_dL_dtheta_agent, void* d_workspace, size_t ws_bytes,
                          void* stream) {
   if (!h || nsteps < 1 || ckpt_C < 0 || !(dt > 0.f) || !std::isfinite(dt)) return SIM_ERR_ARG;
-  if (!d_dL_dtheta) return SIM_ERR_ARG;
+  if (!d_dL_dtheta || h->mode == SIM_CLOSED_LOOP_PID) return SIM_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (h->n == 0) {
     return cudaMemsetAsync(d_dL_dtheta, 0, sizeof(float) * h->n_groups * NTH, st) == cudaSuccess ? SIM_OK
@@ -925,7 +936,7 @@ int sim_rollout_backward_noalloc(sim_handle_t h, const float* d_ckpt, const floa
                                  int ckpt_C, const float* d_dL_dxT, const float* d_w_run, float* d_dL_dx0,
                                  float* d_dL_dtheta, float* d_dL_dtheta_agent, void* stream) {
   if (!h || nsteps < 1 || ckpt_C < 0 || !(dt > 0.f) || !std::isfinite(dt)) return SIM_ERR_ARG;
-  if (!d_dL_dtheta) return SIM_ERR_ARG;
+  if (!d_dL_dtheta || h->mode == SIM_CLOSED_LOOP_PID) return SIM_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (h->n == 0) {
     return cudaMemsetAsync(d_dL_dtheta, 0, sizeof(float) * h->n_groups * NTH, st) == cudaSuccess ? SIM_OK

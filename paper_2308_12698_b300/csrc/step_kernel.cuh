@@ -23,10 +23,11 @@ struct StepArgs {
   const DevGroup* groups;  // device table (several groups)
 };
 
+template <int NS = NX>
 __device__ __forceinline__ bool all_finite(const St& x) {
   float s = 0.f;
 #pragma unroll
-  for (int i = 0; i < NX; ++i) s += x.a[i];
+  for (int i = 0; i < NS; ++i) s += x.a[i];
   return isfinite(s);
 }
 
@@ -51,9 +52,9 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs A, const DevGroup P0
   for (int64_t i = A.first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end; i += stride) {
     if (A.status[i]) continue;  // dead agents are frozen
     St x;
-    load_state(A.state, A.n, i, x);
+    load_state<state_dim<MODE>()>(A.state, A.n, i, x);
     const float4 c = A.cmd[i];
-    const Hd hd = heading(MODE == 1 ? c.w : 0.f);
+    const Hd hd = heading(MODE != 0 ? c.w : 0.f);
     if (HETERO) {
       const DevGroup P = sg[A.gid[i]];
       const LagCoef L = lag_coef(P.inv_tau, A.H);
@@ -62,8 +63,8 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs A, const DevGroup P0
       const LagCoef L = lag_coef(P0.inv_tau, A.H);
       for (int k = 0; k < A.K; ++k) step<MODE>(P0, x, c, hd, A.H, L);
     }
-    if (all_finite(x)) {
-      store_state(A.state, A.n, i, x);
+    if (all_finite<state_dim<MODE>()>(x)) {
+      store_state<state_dim<MODE>()>(A.state, A.n, i, x);
     } else {
       A.status[i] = 1;  // keep the last finite state
     }

@@ -3,7 +3,8 @@ torch.autograd.Function over the hand-written adjoint.
 
 PyTorch only provides device memory and the stream; every step of the
 simulation runs in the library's kernels.  State tensors are flat float32
-CUDA tensors in the planar layout of include/quadsim.h (17 N floats).
+CUDA tensors in the planar layout of include/quadsim.h (17 N floats; 20 N in
+the PID mode).
 """
 from __future__ import annotations
 
@@ -63,6 +64,8 @@ class Sim:
         self.groups = [dict(g) for g in groups]
         self.n = int(n)
         self.mode = int(mode)
+        #: state components per agent: 20 with the PID rate loop's integral, else 17
+        self.nx = 20 if self.mode == _lib.SIM_CLOSED_LOOP_PID else 17
         if gid is not None:
             if not (gid.is_cuda and gid.dtype == torch.uint8 and gid.is_contiguous() and gid.numel() == n):
                 raise SimError("gid: expected a contiguous uint8 CUDA tensor of n elements")
@@ -117,9 +120,13 @@ class Sim:
         check(lib().sim_get_launch(self._h, *[ctypes.byref(x) for x in v]), "sim_get_launch")
         return dict(zip(("block", "block_adj", "K", "C"), (x.value for x in v)))
 
+    def _no_pid(self, what: str):
+        if self.mode == _lib.SIM_CLOSED_LOOP_PID:
+            raise SimError(f"{what}: the rollouts and the adjoint cover the 17-state modes, not the PID mode")
+
     # -- forward --
     def step(self, state: torch.Tensor, cmd: torch.Tensor, dt: float, nsteps: int, K: int = 0, stream=None):
-        _check_f32(state, 17 * self.n, "state")
+        _check_f32(state, self.nx * self.n, "state")
         _check_f32(cmd, 4 * self.n, "cmd")
         check(lib().sim_step(self._h, _ptr(state), _ptr(cmd), float(dt), int(nsteps), int(K), _stream(stream)),
               "sim_step")
@@ -127,10 +134,10 @@ class Sim:
     def step_host(self, h_state: torch.Tensor, h_cmd: torch.Tensor, d_state: torch.Tensor, d_cmd: torch.Tensor,
                   dt: float, nsteps: int, K: int = 0, stream=None):
         """Host-resident state: copy in, step, copy out, wait (pinned host tensors)."""
-        for t, m in ((h_state, 17), (h_cmd, 4)):
+        for t, m in ((h_state, self.nx), (h_cmd, 4)):
             if t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or t.numel() != m * self.n:
                 raise SimError("host buffers: expected contiguous float32 CPU tensors")
-        _check_f32(d_state, 17 * self.n, "d_state")
+        _check_f32(d_state, self.nx * self.n, "d_state")
         _check_f32(d_cmd, 4 * self.n, "d_cmd")
         check(lib().sim_step_host(self._h, _ptr(h_state), _ptr(h_cmd), _ptr(d_state), _ptr(d_cmd), float(dt),
                                   int(nsteps), int(K), _stream(stream)), "sim_step_host")
@@ -140,7 +147,7 @@ class Sim:
                    obs2: torch.Tensor | None = None, stream=None):
         """Decision rounds: h_cmds (rounds, 4 N) pinned host commands, one set per round; the
         positions plane after each round lands in h_obs (rounds, 4 N) pinned host memory."""
-        _check_f32(state, 17 * self.n, "state")
+        _check_f32(state, self.nx * self.n, "state")
         rounds = h_cmds.shape[0]
         if h_cmds.is_cuda or h_cmds.dtype != torch.float32 or not h_cmds.is_contiguous() or \
                 h_cmds.numel() != rounds * 4 * self.n:
@@ -167,6 +174,7 @@ class Sim:
     def rollout_forward(self, x0: torch.Tensor, cmd: torch.Tensor, dt: float, nsteps: int, C: int = 0,
                         ckpt: torch.Tensor | None = None, run_cost: torch.Tensor | None = None, stream=None):
         """Returns (ckpt, run_cost): ckpt is (S+1, 17 N), ckpt[-1] the final state."""
+        self._no_pid("rollout_forward")
         _check_f32(x0, 17 * self.n, "x0")
         _check_f32(cmd, 4 * self.n, "cmd")
         S = self.n_segments(nsteps, C)
@@ -186,6 +194,7 @@ class Sim:
                          w_run: torch.Tensor | None = None, C: int = 0, per_agent: bool = False,
                          workspace: torch.Tensor | None = None, stream=None):
         """Returns (dL/dx0 planar, dL/dtheta (G, 16), per-agent (N, 16) or None)."""
+        self._no_pid("rollout_backward")
         _check_f32(dL_dxT, 17 * self.n, "dL_dxT")
         if w_run is not None:
             _check_f32(w_run, self.n, "w_run")
@@ -208,7 +217,7 @@ class Sim:
     def collide(self, state: torch.Tensor, radius_scale: float = 1.0, workspace: torch.Tensor | None = None,
                 stream=None):
         """Marks agents closer than the sum of their arm lengths (x radius_scale) dead (status 2)."""
-        _check_f32(state, 17 * self.n, "state")
+        _check_f32(state, self.nx * self.n, "state")
         ws = self.collide_workspace_bytes()
         if workspace is None or workspace.numel() < ws:
             workspace = torch.empty(max(ws, 1), dtype=torch.uint8, device=state.device)
@@ -239,7 +248,7 @@ class Graph:
     """ceil(nsteps/K) sim_step launches captured once, replayed by launch()."""
 
     def __init__(self, sim: Sim, state: torch.Tensor, cmd: torch.Tensor, dt: float, nsteps: int, K: int = 0):
-        _check_f32(state, 17 * sim.n, "state")
+        _check_f32(state, sim.nx * sim.n, "state")
         _check_f32(cmd, 4 * sim.n, "cmd")
         self.sim = sim
         self._bufs = (state, cmd)
@@ -299,19 +308,25 @@ class QuadRollout(torch.autograd.Function):
 
 
 def planar(x: torch.Tensor) -> torch.Tensor:
-    """(N, 17) -> flat planar layout (data movement only)."""
-    n = x.shape[0]
-    out = torch.empty(17 * n, dtype=x.dtype, device=x.device)
+    """(N, 17) or (N, 20) -> flat planar layout (data movement only): planes of components
+    0-3, 4-7, 8-11, 12-15, then the rest (16, or 16-19) interleaved per agent."""
+    n, nx = x.shape
+    if nx not in (17, 20):
+        raise SimError("planar: states have 17 or 20 components")
+    out = torch.empty(nx * n, dtype=x.dtype, device=x.device)
     for k in range(4):
         out[4 * k * n: 4 * k * n + 4 * n] = x[:, 4 * k:4 * k + 4].reshape(-1)
-    out[16 * n:] = x[:, 16]
+    out[16 * n:] = x[:, 16:].reshape(-1)
     return out
 
 
 def unplanar(flat: torch.Tensor, n: int) -> torch.Tensor:
-    """flat planar layout -> (N, 17)."""
-    x = torch.empty((n, 17), dtype=flat.dtype, device=flat.device)
+    """flat planar layout -> (N, 17) or (N, 20), from the size."""
+    nx = flat.numel() // n if n else 17
+    if nx not in (17, 20) or nx * n != flat.numel():
+        raise SimError("unplanar: expected 17 N or 20 N floats")
+    x = torch.empty((n, nx), dtype=flat.dtype, device=flat.device)
     for k in range(4):
         x[:, 4 * k:4 * k + 4] = flat[4 * k * n: 4 * k * n + 4 * n].reshape(n, 4)
-    x[:, 16] = flat[16 * n: 17 * n]
+    x[:, 16:] = flat[16 * n: nx * n].reshape(n, nx - 16)
     return x

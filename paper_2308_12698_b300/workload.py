@@ -286,27 +286,28 @@ def thrust_down(n: int = 4096, nsteps: int = 1, dt: float = 1e-3, seed: int = BA
 # --- layout helpers (data movement only) -----------------------------------
 
 def to_planes(x: np.ndarray) -> np.ndarray:
-    """(N, 17) agent-major -> flat planar layout used on the device.
+    """(N, 17) or (N, 20) agent-major -> flat planar layout used on the device.
 
-    Plane 0..3 hold float4 groups of state components (0-3, 4-7, 8-11,
-    12-15) for all agents, plane 4 holds component 16.  Returns a flat
-    float32 array of 17 N values.
+    Planes 0..3 hold float4 groups of state components (0-3, 4-7, 8-11,
+    12-15) for all agents; plane 4 holds the rest (component 16, or 16-19 in
+    the PID mode) interleaved per agent.  Returns a flat float32 array.
     """
-    n = x.shape[0]
-    out = np.empty(17 * n, dtype=np.float32)
+    n, nx = x.shape
+    out = np.empty(nx * n, dtype=np.float32)
     for k in range(4):
         out[4 * k * n: 4 * k * n + 4 * n] = x[:, 4 * k:4 * k + 4].reshape(-1)
-    out[16 * n:] = x[:, 16]
+    out[16 * n:] = x[:, 16:].reshape(-1)
     return out
 
 
 def from_planes(flat: np.ndarray, n: int) -> np.ndarray:
-    """Inverse of :func:`to_planes`."""
+    """Inverse of :func:`to_planes` (17 or 20 components, from the size)."""
     flat = np.asarray(flat)
-    x = np.empty((n, 17), dtype=flat.dtype)
+    nx = flat.size // n
+    x = np.empty((n, nx), dtype=flat.dtype)
     for k in range(4):
         x[:, 4 * k:4 * k + 4] = flat[4 * k * n: 4 * k * n + 4 * n].reshape(n, 4)
-    x[:, 16] = flat[16 * n: 17 * n]
+    x[:, 16:] = flat[16 * n: nx * n].reshape(n, nx - 16)
     return x
 
 

@@ -29,3 +29,17 @@ def test_adjoint_tape_edges_are_the_checkers_count(orc):
     assert bench.ADJ_TAPE_EDGES_PER_AGENT_STEP <= min(edges) <= 1.01 * bench.ADJ_TAPE_EDGES_PER_AGENT_STEP, \
         (min(edges), max(edges))
     assert bench.FWD_ADJ_FLOPS_PER_AGENT_STEP == 2 * bench.FLOPS_PER_AGENT_STEP + 2 * bench.ADJ_TAPE_EDGES_PER_AGENT_STEP
+
+
+def test_pid_flops_per_agent_step_is_the_checkers_count(orc):
+    """PID step: the checker's count less its second evaluation of the time derivative (for
+    omega', which the kernel takes from the first RK4 stage); minimum over the PID workload."""
+    wl = W.closed_loop_pid(n=bench.N_AGENTS)
+    counts = []
+    for a in range(0, wl.n, wl.n // 256):
+        x = wl.x0[a].astype(np.float64)
+        c = orc.count_ops(wl.groups[0], x, wl.cmd[a], wl.dt, W.CLOSED_LOOP_PID)
+        d = orc.count_derivative_ops(wl.groups[0], x, x[13:17])
+        counts.append(sum(c[k] - d[k] for k in ("add", "mul", "div", "sqrt")))
+    assert bench.FLOPS_PER_AGENT_STEP_PID <= min(counts) <= 1.01 * bench.FLOPS_PER_AGENT_STEP_PID, (min(counts),)
+    assert max(counts) <= 1.03 * bench.FLOPS_PER_AGENT_STEP_PID

@@ -281,24 +281,26 @@ def test_shared_and_global_scratch_agree(dev):
     sim.close()
 
 
-def test_adjoint_full_size_bench_configuration(dev, orc):
-    """1e6 agents x 1000 steps in the bench's launch shape (C = 2, shared scratch, 64-thread
-    blocks): 24 sampled agents' gradients against FP64 reverse mode."""
+@pytest.mark.parametrize("C,block_adj", [(1, 128), (2, 64)])
+def test_adjoint_full_size_bench_configuration(dev, orc, C, block_adj):
+    """1e6 agents x 1000 steps in the launch shapes the bench's autotuner picks (C = 1 or 2,
+    shared scratch, 128- or 64-thread blocks): 24 sampled agents' gradients against FP64
+    reverse mode."""
     from paper_2308_12698_b300.sim import Sim, planar, unplanar
     base = W.scale_sweep(1_000_000, nsteps=1000)
     goal = base.cmd[:, 0:3].copy()
     wl = W.Workload("full", base.mode, base.groups, base.gid, base.x0, base.cmd, base.dt, 1000, goal=goal,
                     w_omega=1e-6)
     sim = Sim(wl.groups, wl.n, wl.mode)
-    sim.set_launch(block_adj=64)
+    sim.set_launch(block_adj=block_adj)
     x0 = planar(torch.from_numpy(wl.x0)).to(dev)
     cmd = torch.from_numpy(wl.cmd).reshape(-1).to(dev)
-    ckpt, rc = sim.rollout_forward(x0, cmd, wl.dt, wl.nsteps, C=2)
+    ckpt, rc = sim.rollout_forward(x0, cmd, wl.dt, wl.nsteps, C=C)
     xT = unplanar(ckpt[-1], wl.n)
     g = torch.zeros_like(xT)
     g[:, 0:3] = 2 * (xT[:, 0:3] - torch.from_numpy(goal).to(dev))
     w = torch.full((wl.n,), wl.w_omega, device=dev)
-    dx0, dth, dtha = sim.rollout_backward(ckpt, cmd, wl.dt, wl.nsteps, planar(g), w, C=2, per_agent=True)
+    dx0, dth, dtha = sim.rollout_backward(ckpt, cmd, wl.dt, wl.nsteps, planar(g), w, C=C, per_agent=True)
     torch.cuda.synchronize()
     idx = np.random.default_rng(12).choice(wl.n, 24, replace=False)
     sel = torch.from_numpy(idx).to(dev)

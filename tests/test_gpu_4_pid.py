@@ -1,0 +1,172 @@
+"""PID body-rate loop (SIM_CLOSED_LOOP_PID, 20-component states) on the GPU, through the C ABI,
+against the FP64 checker.
+
+Tolerances as for the P loop: one step 1e-5 relative with floors (xi: floor 1 rad); 1000 steps
+1e-3 m in position, 1e-3 rad in attitude, and 1e-3 rad in xi.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2308_12698_b300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+FLOOR = np.array([1.0] * 3 + [1.0] * 3 + [1.0] * 4 + [1.0] * 3 + [100.0] * 4 + [1.0] * 3)
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch.device("cuda:0")
+
+
+def gpu_run(wl, dev, nsteps, K=0, x0=None, groups=None, block=0, mode=None):
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    groups = wl.groups if groups is None else groups
+    g = torch.from_numpy(wl.gid).to(dev) if len(groups) > 1 else None
+    sim = Sim(groups, wl.n, wl.mode if mode is None else mode, gid=g)
+    if block:
+        sim.set_launch(block=block)
+    x = planar(torch.from_numpy(wl.x0 if x0 is None else x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    sim.step(x, cmd, wl.dt, nsteps, K=K)
+    torch.cuda.synchronize()
+    out = unplanar(x, wl.n).cpu().numpy()
+    sim.close()
+    return out
+
+
+def ref_run(orc, wl, nsteps, x0=None):
+    return orc.rollout(wl.groups, wl.gid, wl.x0 if x0 is None else x0, wl.cmd, wl.dt, nsteps, wl.mode)
+
+
+def check_one_step(got, ref):
+    tol = 1e-5 * np.maximum(np.abs(ref), FLOOR)
+    bad = np.abs(got.astype(np.float64) - ref) > tol
+    assert not bad.any(), (np.argwhere(bad)[:5], (np.abs(got - ref) / tol).max())
+
+
+def attitude_err(qa, qb):
+    qa = qa / np.linalg.norm(qa, axis=1, keepdims=True)
+    qb = qb / np.linalg.norm(qb, axis=1, keepdims=True)
+    return 2.0 * np.arccos(np.clip(np.abs(np.sum(qa * qb, axis=1)), 0.0, 1.0))
+
+
+def check_traj(got, ref, tol=1e-3):
+    perr = np.abs(got[:, 0:3].astype(np.float64) - ref[:, 0:3]).max()
+    aerr = attitude_err(got[:, 6:10].astype(np.float64), ref[:, 6:10]).max()
+    xerr = np.abs(got[:, 17:20].astype(np.float64) - ref[:, 17:20]).max()
+    assert perr <= tol and aerr <= tol and xerr <= tol, (perr, aerr, xerr)
+
+
+@pytest.mark.parametrize("n", [1, 33, 4097])
+def test_pid_one_step(dev, orc, n):
+    wl = W.closed_loop_pid(n=n)
+    check_one_step(gpu_run(wl, dev, 1, K=1), ref_run(orc, wl, 1))
+
+
+def test_pid_one_step_from_advanced_states(dev, orc):
+    """One step from states 1.5 s into the transient: tilted, spinning, xi built up (some clamped)."""
+    wl = W.closed_loop_pid(n=2000)
+    xs = ref_run(orc, wl, 1500).astype(np.float32)
+    assert np.abs(xs[:, 17:20]).max() > 0.05
+    check_one_step(gpu_run(wl, dev, 1, K=1, x0=xs), ref_run(orc, wl, 1, x0=xs))
+
+
+@pytest.mark.parametrize("K", [1, 10, 1000])
+def test_pid_1000_steps(dev, orc, K):
+    wl = W.closed_loop_pid(n=5000)
+    check_traj(gpu_run(wl, dev, 1000, K=K), ref_run(orc, wl, 1000))
+
+
+def test_pid_fused_is_bitwise_plain(dev):
+    wl = W.closed_loop_pid(n=3001)
+    a = gpu_run(wl, dev, 120, K=1)
+    np.testing.assert_array_equal(a, gpu_run(wl, dev, 120, K=120))
+    np.testing.assert_array_equal(a, gpu_run(wl, dev, 120, K=7, block=128))
+
+
+def test_pid_zero_gains_is_bitwise_the_p_loop(dev):
+    """kI = kD = 0: the PID kernel's 17 states are bit for bit the P-loop kernel's, whatever xi is."""
+    wl = W.closed_loop_pid(n=4097)
+    g = dict(wl.groups[0])
+    g.update(kI=[0.0] * 3, kD=[0.0] * 3)
+    x0 = wl.x0.copy()
+    x0[:, 17:20] = np.random.default_rng(3).uniform(-1, 1, (wl.n, 3)).astype(np.float32)
+    a = gpu_run(wl, dev, 200, K=50, x0=x0, groups=[g])
+    wl17 = W.Workload("p", W.CLOSED_LOOP, [g], wl.gid, np.ascontiguousarray(x0[:, :17]), wl.cmd, wl.dt, 200)
+    b = gpu_run(wl17, dev, 200, K=50)
+    np.testing.assert_array_equal(a[:, :17], b)
+
+
+def _hetero_pid(n_per=700):
+    base = W.closed_loop_pid(n=3 * n_per)
+    gs = []
+    for i, (kI, kD, xm) in enumerate([(0.05, 0.005, 2.0), (0.08, 0.0, 0.5), (0.02, 0.01, 2.0)]):
+        g = dict(W.scaled_group(0.5 + i, 500.0 + 150 * i))
+        g.update(kI=[kI] * 3, kD=[kD] * 3, xi_max=[xm] * 3)
+        gs.append(W.round_group(g))
+    gid = np.random.default_rng(4).permutation(np.repeat(np.arange(3, dtype=np.uint8), n_per))
+    x0 = base.x0.copy()
+    x0[:, 13:17] = np.array([W.hover_speed(g) for g in gs], dtype=np.float32)[gid][:, None]
+    return W.Workload("pid-hetero", W.CLOSED_LOOP_PID, gs, gid, x0, base.cmd, base.dt, 1000)
+
+
+def test_pid_heterogeneous_parity(dev, orc):
+    wl = _hetero_pid()
+    check_traj(gpu_run(wl, dev, 1000, K=100), ref_run(orc, wl, 1000))
+
+
+def test_pid_heterogeneous_is_bitwise_each_group_alone(dev):
+    wl = _hetero_pid(300)
+    both = gpu_run(wl, dev, 100, K=100)
+    for gi in range(3):
+        idx = np.flatnonzero(wl.gid == gi)
+        one = W.Workload("one", W.CLOSED_LOOP_PID, [wl.groups[gi]], np.zeros(idx.size, np.uint8),
+                         np.ascontiguousarray(wl.x0[idx]), np.ascontiguousarray(wl.cmd[idx]), wl.dt, 100)
+        np.testing.assert_array_equal(both[idx], gpu_run(one, dev, 100, K=100))
+
+
+def test_pid_graph_and_host_entry_are_bitwise_sim_step(dev):
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    wl = W.closed_loop_pid(n=150_001)
+    direct = gpu_run(wl, dev, 30, K=10)
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    x = planar(torch.from_numpy(wl.x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    gr = sim.graph(x, cmd, wl.dt, 30, K=10)
+    gr.launch()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(unplanar(x, wl.n).cpu().numpy(), direct)
+    gr.close()
+    h_state = planar(torch.from_numpy(wl.x0)).pin_memory()
+    h_cmd = torch.from_numpy(wl.cmd).reshape(-1).contiguous().pin_memory()
+    d_state = torch.empty(20 * wl.n, device=dev)
+    d_cmd = torch.empty(4 * wl.n, device=dev)
+    sim.step_host(h_state, h_cmd, d_state, d_cmd, wl.dt, 30, K=10)
+    np.testing.assert_array_equal(unplanar(h_state, wl.n).numpy(), direct)
+    sim.close()
+
+
+def test_pid_rollouts_are_refused(dev):
+    """The checkpointed rollouts and the adjoint cover the 17-state modes: SIM_ERR_ARG."""
+    from paper_2308_12698_b300 import _lib
+    from paper_2308_12698_b300.sim import Sim
+    wl = W.closed_loop_pid(n=64)
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    x = torch.zeros(20 * wl.n, device=dev)
+    c = torch.zeros(4 * wl.n, device=dev)
+    ck = torch.zeros(2 * 20 * wl.n, device=dev)
+    rc = _lib.lib().sim_rollout_forward(sim.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(c.data_ptr()),
+                                        1e-3, 10, 10, ctypes.c_void_p(ck.data_ptr()), None, None)
+    assert rc == _lib.SIM_ERR_ARG
+    assert _lib.lib().sim_workspace_bytes(sim.handle, 10) == 0
+    with pytest.raises(_lib.SimError):
+        sim.rollout_forward(x, c, 1e-3, 10, C=10)
+    sim.close()
