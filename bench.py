@@ -365,6 +365,9 @@ def main():
                     help="time only the checkpointed forward + adjoint (profiling case)")
     ap.add_argument("--C", type=int, default=0, help="fix the checkpoint interval (with --adjoint-only)")
     ap.add_argument("--block-adj", type=int, default=0, help="fix the adjoint block size (with --adjoint-only)")
+    ap.add_argument("--pid-only", action="store_true",
+                    help="time only the PID-rate-loop swarm at --agents x --physics-steps (profiling case)")
+    ap.add_argument("--block", type=int, default=0, help="fix the forward block size (with --pid-only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -388,6 +391,9 @@ def main():
     dev = torch.device("cuda", local)
     if args.adjoint_only:
         run_adjoint_only(args, world, rank, dev)
+        return
+    if args.pid_only:
+        run_pid_only(args, world, rank, dev)
         return
     stream = torch.cuda.current_stream()
     props = torch.cuda.get_device_properties(dev)
@@ -548,6 +554,48 @@ def run_adjoint_only(args, world, rank, dev):
     if rank == 0:
         print(json.dumps({"leg": "fwd_adjoint", "agents": NA, "physics_steps": TS, "C": C, "ms_per_step": ms,
                           "value": NA * TS / (ms / 1e3), "unit": UNIT, "launch": sim.launch()}), flush=True)
+    sim.close()
+
+
+def run_pid_only(args, world, rank, dev):
+    """The PID-rate-loop swarm on --agents x --physics-steps, --K and --block (or tuned)."""
+    import torch
+
+    from paper_2308_12698_b300 import autotune
+    from paper_2308_12698_b300 import workload as W
+    from paper_2308_12698_b300.sim import Sim, planar
+    NA, TS = args.agents, args.physics_steps
+    wl = W.closed_loop_pid(n=NA, nsteps=TS)
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    x0 = planar(torch.from_numpy(wl.x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).reshape(-1).to(dev)
+    x = x0.clone()
+    if args.K:
+        sim.set_launch(block=args.block, K=args.K)
+    else:
+        autotune.tune_step(sim, x0, cmd, DT, TS)
+        if args.block:
+            sim.set_launch(block=args.block)
+    g = sim.graph(x, cmd, DT, TS)
+    for _ in range(args.warmup):
+        x.copy_(x0)
+        g.launch()
+    torch.cuda.synchronize()
+    ms = 0.0
+    for _ in range(args.steps):
+        x.copy_(x0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.launch()
+        b.record()
+        b.synchronize()
+        ms += a.elapsed_time(b) / args.steps
+    if rank == 0:
+        rate = NA * TS / (ms / 1e3)
+        print(json.dumps({"leg": "pid", "agents": NA, "physics_steps": TS, "ms_per_step": ms, "value": rate,
+                          "unit": UNIT, "flops_per_agent_step": FLOPS_PER_AGENT_STEP_PID,
+                          "tflops": FLOPS_PER_AGENT_STEP_PID * rate / 1e12, "launch": sim.launch()}), flush=True)
+    g.close()
     sim.close()
 
 
