@@ -149,24 +149,23 @@ int sim_run_rounds(sim_handle_t h, float* d_state, float* d_cmd2, const float* h
 
 /* Forward rollout with checkpoints, one launch.  Reads d_state0, writes
  * S+1 planar states into d_ckpt (S = ceil(nsteps/ckpt_C)): x_0, x_C, ...,
- * x_{(S-1)C}, then x_nsteps last.  d_ckpt holds (S+1)*17*N floats.
- * d_run_cost (N floats, may be NULL) receives, per agent, the sum over step
- * ends n = 1..nsteps of sum_i Omega_{n,i}^2.  Not in SIM_CLOSED_LOOP_PID
- * (SIM_ERR_ARG): the rollouts and the adjoint cover the 17-state modes. */
+ * x_{(S-1)C}, then x_nsteps last.  d_ckpt holds (S+1)*17*N floats
+ * ((S+1)*20*N in SIM_CLOSED_LOOP_PID).  d_run_cost (N floats, may be NULL)
+ * receives, per agent, the sum over step ends n = 1..nsteps of
+ * sum_i Omega_{n,i}^2. */
 int sim_rollout_forward(sim_handle_t h, const float* d_state0, const float* d_cmd, float dt, int64_t nsteps,
                         int ckpt_C, float* d_ckpt, float* d_run_cost, void* stream);
 
 /* Bytes of workspace sim_rollout_backward needs for this handle, its
- * current launch configuration and checkpoint interval ckpt_C (0 in
- * SIM_CLOSED_LOOP_PID). */
+ * current launch configuration and checkpoint interval ckpt_C. */
 size_t sim_workspace_bytes(sim_handle_t h, int ckpt_C);
 
 /* Discrete adjoint of the rollout of sim_rollout_forward (same dt, nsteps,
  * ckpt_C, d_cmd).  For the loss L = l(x_T) + sum_a w_a * run_cost_a it takes
- *   d_dL_dxT : planar 17*N, dl/dx_T;
+ *   d_dL_dxT : planar 17*N (20*N in SIM_CLOSED_LOOP_PID), dl/dx_T;
  *   d_w_run  : N floats, w_a (NULL = no running cost);
  * and writes
- *   d_dL_dx0          : planar 17*N, dL/dx_0;
+ *   d_dL_dx0          : planar like d_dL_dxT, dL/dx_0;
  *   d_dL_dtheta       : n_groups*16 floats, dL/dtheta per group, theta =
  *                       (kp[3], kd[3], katt[3], krate[3], m, Jxx, Jyy, Jzz);
  *   d_dL_dtheta_agent : N*16 floats of per-agent contributions, or NULL.
@@ -175,7 +174,8 @@ size_t sim_workspace_bytes(sim_handle_t h, int ckpt_C);
  * interval, sqrt(0) has derivative 0, branch choices are constants.  The
  * per-group sums are deterministic (fixed reduction order, no atomics).
  * d_workspace must hold sim_workspace_bytes(h, ckpt_C) bytes, 256-byte
- * aligned.  Not in SIM_CLOSED_LOOP_PID (SIM_ERR_ARG). */
+ * aligned.  In SIM_CLOSED_LOOP_PID the integrator's clamp passes the gradient
+ * on its closed interval too; kI, kD and xi_max are not differentiated. */
 int sim_rollout_backward(sim_handle_t h, const float* d_ckpt, const float* d_cmd, float dt, int64_t nsteps,
                          int ckpt_C, const float* d_dL_dxT, const float* d_w_run, float* d_dL_dx0,
                          float* d_dL_dtheta, float* d_dL_dtheta_agent, void* d_workspace, size_t ws_bytes,
@@ -196,7 +196,7 @@ int sim_rollout_backward(sim_handle_t h, const float* d_ckpt, const float* d_cmd
  *     equal sim_rollout_backward's (per-agent outputs bit for bit, the group
  *     sums up to the order of the final reduction), possibly slower.
  *   - SIM_ERR_WORKSPACE if even one block does not fit, i.e. when
- *     ckpt_C * 68 B * (adjoint block size) + n_groups * 64 B exceeds
+ *     ckpt_C * (68 B, 80 B in the PID mode) * (adjoint block size) + n_groups * 64 B exceeds
  *     32 MiB (ckpt_C above about 3,800 with the default 128-thread adjoint
  *     block).
  *   - The first call on a device looks up the array's device address for

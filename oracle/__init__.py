@@ -157,7 +157,7 @@ def loss(groups, gid, x0, cmd, h, nsteps, mode, goal, w_omega, nthreads=None):
 def clamp_margins(groups, gid, x0, cmd, h, nsteps, nthreads=None, mode=CLOSED_LOOP):
     """(n, 3) minima over a closed-loop trajectory of: |S|/omega_max^2 (rotor demand near the
     sqrt kink at 0), |S - omega_max^2|/omega_max^2 (rotor ceiling), ||ar| - a_max|/a_max
-    (acceleration clamp)."""
+    (acceleration clamp; in the PID mode also the integrator clamp)."""
     x = _states(x0, mode)
     n = x.shape[0]
     c = np.ascontiguousarray(np.asarray(cmd, dtype=np.float64))

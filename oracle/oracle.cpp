@@ -215,7 +215,8 @@ int oracle_grad(const double* groups, int n_groups, const int32_t* gid, int64_t 
 // rotors of |S_i| / omega_max^2 (S = unclamped Omega_cmd^2; sqrt has an
 // unbounded derivative at 0), out[a*3 + 1] = min |S_i - omega_max^2| /
 // omega_max^2 (rotor ceiling), out[a*3 + 2] = min ||ar_i| - a_max| / a_max
-// (acceleration clamp).  Gradients of agents with a small margin are
+// (acceleration clamp; in the PID mode also the integrator clamp,
+// min ||xi_i + h e_i| - xi_max| / xi_max).  Gradients of agents with a small margin are
 // ill-conditioned: a perturbation at rounding level moves them by a finite
 // amount.
 int oracle_clamp_margins(const double* groups, int n_groups, const int32_t* gid, int64_t n, const double* x0,
@@ -237,6 +238,10 @@ int oracle_clamp_margins(const double* groups, int n_groups, const int32_t* gid,
           double d0[NX], e[3];
           derivative(P, S.F[g], cur, cur + 13, d0);
           controller(P, S.F[g], cur, cmd + a * 4, w, ar, Sd, cur + NX, d0 + 10, e);
+          // the integrator clamp is a kink of the same kind as the acceleration clamp
+          for (int i = 0; i < 3; ++i)
+            if (P.xi_max[i] > 0.0)
+              m2 = std::min(m2, std::fabs(std::fabs(cur[NX + i] + h * e[i]) - P.xi_max[i]) / P.xi_max[i]);
         } else {
           controller(P, S.F[g], cur, cmd + a * 4, w, ar, Sd);
         }

@@ -96,7 +96,7 @@ def tune_adjoint(sim: Sim, x0: torch.Tensor, cmd: torch.Tensor, dt: float, nstep
     if key in cache:
         cfg = cache[key]
     else:
-        g = torch.zeros(17 * sim.n, dtype=torch.float32, device=x0.device)
+        g = torch.zeros(sim.nx * sim.n, dtype=torch.float32, device=x0.device)
         g[: 3 * sim.n] = 1.0
         results = []
         for b in blocks:
@@ -113,7 +113,7 @@ def tune_adjoint(sim: Sim, x0: torch.Tensor, cmd: torch.Tensor, dt: float, nstep
                 # checkpoints cost (T/C + 1) states: skip intervals whose checkpoints would
                 # take more than half of the free device memory
                 free, _ = torch.cuda.mem_get_info()
-                if (nsteps // c + 2) * 17 * 4 * sim.n > free // 2:
+                if (nsteps // c + 2) * sim.nx * 4 * sim.n > free // 2:
                     del ws
                     continue
                 results.append((_time(run, reps=2), b, c))

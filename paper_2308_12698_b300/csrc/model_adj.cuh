@@ -1,6 +1,6 @@
 // Hand-written vector-Jacobian products of the device model (model_fwd.cuh)
 // for the discrete adjoint of the RK4 rollout: rb_derivative_vjp,
-// controller_vjp and step_vjp.  Subgradients: clamps pass the gradient on
+// controller_vjp and step_vjp (P and PID rate loops).  Subgradients: clamps pass the gradient on
 // their closed interval, sqrt has derivative 0 at 0, branch choices (the roll
 // half-angle formula, sign of q_e.w) are constants.
 #pragma once
@@ -65,11 +65,17 @@ __device__ __forceinline__ void rb_derivative_vjp(const DevGroup& P, const float
 }
 
 // Cotangent of the controller: ub (rotor commands) -> xb (state), tb (theta).
+// PID: also eb, the cotangent of the rate error e the integrator consumed;
+// adds the integral term's share to xb[XI..] and writes wdb, the cotangent of
+// omega' (wdot, at x), for the caller to carry through Eq. (qd4).
+template <bool PID = false>
 __device__ __forceinline__ void controller_vjp(const DevGroup& P, const float* x, const float4 c, const Hd& hd,
-                                               const float ub[4], float* xb, float tb[NTH]) {
+                                               const float ub[4], float* xb, float tb[NTH],
+                                               const float* wdot = nullptr, const float* eb = nullptr,
+                                               float* wdb = nullptr) {
   Ctl C;
-  float u[4];
-  controller_fwd(P, x, c, hd, C, u);
+  float u[4], e[3];
+  controller_fwd<PID>(P, x, c, hd, C, u, wdot, e);
   // sqrt(clamp(S)): gradient passes on 0 < S <= om2max (sqrt'(0) taken as 0)
   float Sb[4];
 #pragma unroll
@@ -90,7 +96,16 @@ __device__ __forceinline__ void controller_vjp(const DevGroup& P, const float* x
     tb[TH_KRATE + i] += fb[i] * P.mt[i] * (P.katt2[i] * C.qe[1 + i] - x[WX + i]);
     tb[TH_KATT + i] += fb[i] * P.wa[i] * 2.f * C.qe[1 + i];
     xb[WX + i] -= fb[i] * P.wa[i];
-    const float qeb = fb[i] * P.qa[i];
+    float qeb = fb[i] * P.qa[i];
+    if (PID) {
+      // e_i = 2 katt_i qe_i - omega_i feeds the integrator; f_i also holds
+      // mix_i taumax_i (kI_i xi_i - kD_i omega'_i)
+      qeb += eb[i] * P.katt2[i];
+      tb[TH_KATT + i] += eb[i] * 2.f * C.qe[1 + i];
+      xb[WX + i] -= eb[i];
+      xb[XI + i] += fb[i] * P.kic[i];
+      wdb[i] = -fb[i] * P.kdc[i];
+    }
     kap += qeb * C.qe[1 + i];
     Eb[1 + i] = qeb * C.s;
   }
@@ -157,7 +172,14 @@ template <int MODE>
 __device__ __forceinline__ void step_vjp(const DevGroup& P, const St& x, const float4 c, const Hd& hd,
                                          const StepH& H, const LagCoef& L, St& lam, float tb[NTH]) {
   float u[4];
-  if (MODE == 1) {
+  float wdot[3], e[3];  // PID: omega' at x and the rate error
+  if (MODE == 2) {
+    float k0[NRB];
+    rb_derivative(P, x.a, x.a + OM, k0);
+    wdot[0] = k0[WX]; wdot[1] = k0[WX + 1]; wdot[2] = k0[WX + 2];
+    Ctl C;
+    controller_fwd<true>(P, x.a, c, hd, C, u, wdot, e);
+  } else if (MODE == 1) {
     controller(P, x.a, c, hd, u);
   } else {
     u[0] = c.x; u[1] = c.y; u[2] = c.z; u[3] = c.w;
@@ -185,7 +207,7 @@ __device__ __forceinline__ void step_vjp(const DevGroup& P, const St& x, const f
   for (int i = 0; i < 4; ++i) Om[i] = x.a[OM + i] + L.c4 * dOm[i];
 #pragma unroll
   for (int i = 0; i < NRB; ++i) y4[i] = x.a[i] + coef(i, H.h, H.hq) * k[i];
-  float xb[NX], g[NRB], yb[NRB], Ob[4], ub[4];
+  float xb[NXP], g[NRB], yb[NRB], Ob[4], ub[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     ub[i] = L.c5 * lam.a[OM + i];
@@ -236,9 +258,31 @@ __device__ __forceinline__ void step_vjp(const DevGroup& P, const St& x, const f
   for (int i = 0; i < 4; ++i) xb[OM + i] += Ob[i];
 #pragma unroll
   for (int i = 0; i < NRB; ++i) xb[i] += yb[i];
-  if (MODE == 1) controller_vjp(P, x.a, c, hd, ub, xb, tb);
+  if (MODE == 2) {
+    // xi' = clamp(xi + h e): the gradient passes where the clamp does not bind
+    float eb[3], wdb[3];
 #pragma unroll
-  for (int i = 0; i < NX; ++i) lam.a[i] = xb[i];
+    for (int i = 0; i < 3; ++i) {
+      const float v = x.a[XI + i] + H.h * e[i];
+      const bool pass = (v >= -P.xim[i]) && (v <= P.xim[i]);
+      xb[XI + i] = pass ? lam.a[XI + i] : 0.f;
+      eb[i] = pass ? H.h * lam.a[XI + i] : 0.f;
+    }
+    controller_vjp<true>(P, x.a, c, hd, ub, xb, tb, wdot, eb, wdb);
+    // omega' = rows WX.. of Eq. (qd4) at (x, Omega)
+#pragma unroll
+    for (int i = 0; i < NRB; ++i) { g[i] = 0.f; yb[i] = 0.f; }
+    g[WX] = wdb[0]; g[WX + 1] = wdb[1]; g[WX + 2] = wdb[2];
+    rb_derivative_vjp(P, x.a, x.a + OM, g, yb, Ob, tb);
+#pragma unroll
+    for (int i = 0; i < NRB; ++i) xb[i] += yb[i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) xb[OM + i] += Ob[i];
+  } else if (MODE == 1) {
+    controller_vjp(P, x.a, c, hd, ub, xb, tb);
+  }
+#pragma unroll
+  for (int i = 0; i < state_dim<MODE>(); ++i) lam.a[i] = xb[i];
 }
 
 }  // namespace qs

@@ -52,19 +52,20 @@ __global__ void __launch_bounds__(256) ckpt_kernel(CkptArgs A, const DevGroup P0
   extern __shared__ float4 smem4[];
   DevGroup* sg = reinterpret_cast<DevGroup*>(smem4);
   load_groups<HETERO>(sg, A.groups, A.n_groups);
+  constexpr int NS = state_dim<MODE>();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t plane = (int64_t)NX * A.n;
+  const int64_t plane = (int64_t)NS * A.n;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) {
     St x;
-    load_state(A.x0, A.n, i, x);
-    store_state(A.ckpt, A.n, i, x);
+    load_state<NS>(A.x0, A.n, i, x);
+    store_state<NS>(A.ckpt, A.n, i, x);
     if (A.status[i]) {  // frozen: every checkpoint is the current state
-      for (int s = 1; s <= A.S; ++s) store_state(A.ckpt + s * plane, A.n, i, x);
+      for (int s = 1; s <= A.S; ++s) store_state<NS>(A.ckpt + s * plane, A.n, i, x);
       if (A.run_cost) A.run_cost[i] = 0.f;
       continue;
     }
     const float4 c = A.cmd[i];
-    const Hd hd = heading(MODE == 1 ? c.w : 0.f);
+    const Hd hd = heading(MODE != 0 ? c.w : 0.f);
     const DevGroup P = HETERO ? sg[A.gid[i]] : P0;
     const LagCoef L = lag_coef(P.inv_tau, A.H);
     float rc = 0.f;
@@ -74,10 +75,10 @@ __global__ void __launch_bounds__(256) ckpt_kernel(CkptArgs A, const DevGroup P0
         step<MODE>(P, x, c, hd, A.H, L);
         rc += (x.a[OM] * x.a[OM] + x.a[OM + 1] * x.a[OM + 1]) + (x.a[OM + 2] * x.a[OM + 2] + x.a[OM + 3] * x.a[OM + 3]);
       }
-      store_state(A.ckpt + (s + 1) * plane, A.n, i, x);
+      store_state<NS>(A.ckpt + (s + 1) * plane, A.n, i, x);
     }
     if (A.run_cost) A.run_cost[i] = rc;
-    if (!all_finite(x)) A.status[i] = 1;
+    if (!all_finite<NS>(x)) A.status[i] = 1;
   }
 }
 
@@ -91,7 +92,7 @@ struct AdjArgs {
   float* dLdx0;
   float* th_agent;
   float* partials;  // [gridDim.x][n_groups][16]
-  float* scratch;   // [C][17 planes][grid threads]
+  float* scratch;   // [C][state planes][grid threads]
   int64_t n;
   int64_t nsteps;
   int C;
@@ -123,8 +124,9 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
   // scratch column of this thread: its own slot in the block (shared) or in the grid (global)
   const int64_t scols = SMEMS ? (int64_t)blockDim.x : nthreads;
   const int64_t slot = SMEMS ? (int64_t)threadIdx.x : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t sstep = (int64_t)NX * scols;
-  const int64_t plane = (int64_t)NX * A.n;
+  constexpr int NS = state_dim<MODE>();
+  const int64_t sstep = (int64_t)NS * scols;
+  const int64_t plane = (int64_t)NS * A.n;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < A.n; base += nthreads) {
     const int64_t i = base + threadIdx.x;
     float tb[NTH];
@@ -136,23 +138,23 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
       const DevGroup& P = sg[g];  // read from shared memory where used: keeps registers for the adjoint
       const LagCoef L = lag_coef(P.inv_tau, A.H);
       const float4 c = A.cmd[i];
-      const Hd hd = heading(MODE == 1 ? c.w : 0.f);
+      const Hd hd = heading(MODE != 0 ? c.w : 0.f);
       const float w = A.w_run ? A.w_run[i] : 0.f;
       St lam, x;
-      load_state(A.dLdxT, A.n, i, lam);
-      load_state(A.ckpt + (int64_t)A.S * plane, A.n, i, x);
+      load_state<NS>(A.dLdxT, A.n, i, lam);
+      load_state<NS>(A.ckpt + (int64_t)A.S * plane, A.n, i, x);
 #pragma unroll
       for (int q = 0; q < 4; ++q) lam.a[OM + q] += 2.f * w * x.a[OM + q];
       for (int s = A.S - 1; s >= 0; --s) {
         const int64_t n0 = (int64_t)s * A.C;
         const int len = (int)min((int64_t)A.C, A.nsteps - n0);
-        load_state(A.ckpt + (int64_t)s * plane, A.n, i, x);
+        load_state<NS>(A.ckpt + (int64_t)s * plane, A.n, i, x);
         for (int j = 0; j < len; ++j) {
-          store_state(scratch + j * sstep, scols, slot, x);
+          store_state<NS>(scratch + j * sstep, scols, slot, x);
           if (j + 1 < len) step<MODE>(P, x, c, hd, A.H, L);
         }
         for (int j = len - 1; j >= 0; --j) {
-          load_state(scratch + j * sstep, scols, slot, x);
+          load_state<NS>(scratch + j * sstep, scols, slot, x);
           step_vjp<MODE>(P, x, c, hd, A.H, L, lam, tb);
           if (n0 + j >= 1) {
 #pragma unroll
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
           }
         }
       }
-      store_state(A.dLdx0, A.n, i, lam);
+      store_state<NS>(A.dLdx0, A.n, i, lam);
       if (A.th_agent) {
 #pragma unroll
         for (int q = 0; q < NTH; ++q) A.th_agent[i * NTH + q] = tb[q];
@@ -381,6 +383,7 @@ struct sim_s {
   int n_groups = 1;
   int64_t n = 0;
   int mode = SIM_CLOSED_LOOP;
+  int nx = NX;                   // state floats per agent: 17, or 20 in the PID mode
   const uint8_t* gid = nullptr;  // borrowed
   uint8_t* status = nullptr;     // owned
   DevGroup* d_groups = nullptr;  // owned
@@ -430,12 +433,12 @@ int fwd_grid(const sim_s* h, size_t smem, int64_t count) {
 constexpr size_t kSmemScratchMax = 96 * 1024;
 
 bool adj_smem_scratch(const sim_s* h, int C) {
-  return (size_t)C * NX * sizeof(float) * h->block_adj <= kSmemScratchMax;
+  return (size_t)C * h->nx * sizeof(float) * h->block_adj <= kSmemScratchMax;
 }
 
 size_t adj_smem(const sim_s* h, int C) {
   size_t b = sizeof(DevGroup) * h->n_groups + (size_t)(h->block_adj / 32) * h->n_groups * NTH * sizeof(float);
-  if (adj_smem_scratch(h, C)) b = ((b + 15) & ~(size_t)15) + (size_t)C * NX * sizeof(float) * h->block_adj;
+  if (adj_smem_scratch(h, C)) b = ((b + 15) & ~(size_t)15) + (size_t)C * h->nx * sizeof(float) * h->block_adj;
   return b;
 }
 
@@ -443,7 +446,9 @@ int adj_grid(const sim_s* h, int C) {
   const size_t smem = adj_smem(h, C);
   const bool sm = adj_smem_scratch(h, C);
   int occ;
-  if (h->mode == SIM_CLOSED_LOOP)
+  if (h->mode == SIM_CLOSED_LOOP_PID)
+    occ = sm ? occupancy(adjoint_kernel<2, true>, h->block_adj, smem) : occupancy(adjoint_kernel<2, false>, h->block_adj, smem);
+  else if (h->mode == SIM_CLOSED_LOOP)
     occ = sm ? occupancy(adjoint_kernel<1, true>, h->block_adj, smem) : occupancy(adjoint_kernel<1, false>, h->block_adj, smem);
   else
     occ = sm ? occupancy(adjoint_kernel<0, true>, h->block_adj, smem) : occupancy(adjoint_kernel<0, false>, h->block_adj, smem);
@@ -454,7 +459,10 @@ int adj_grid(const sim_s* h, int C) {
 int launch_adjoint(const sim_s* h, const AdjArgs& A, int C, int grid, cudaStream_t st) {
   const size_t smem = adj_smem(h, C);
   const bool sm = adj_smem_scratch(h, C);
-  if (h->mode == SIM_CLOSED_LOOP) {
+  if (h->mode == SIM_CLOSED_LOOP_PID) {
+    if (sm) adjoint_kernel<2, true><<<grid, h->block_adj, smem, st>>>(A);
+    else adjoint_kernel<2, false><<<grid, h->block_adj, smem, st>>>(A);
+  } else if (h->mode == SIM_CLOSED_LOOP) {
     if (sm) adjoint_kernel<1, true><<<grid, h->block_adj, smem, st>>>(A);
     else adjoint_kernel<1, false><<<grid, h->block_adj, smem, st>>>(A);
   } else {
@@ -468,7 +476,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t scratch_bytes(const sim_s* h, int C, int grid) {
   if (adj_smem_scratch(h, C)) return 0;
-  return align256((size_t)C * NX * sizeof(float) * (size_t)grid * h->block_adj);
+  return align256((size_t)C * h->nx * sizeof(float) * (size_t)grid * h->block_adj);
 }
 
 int launch_step(sim_s* h, float* d_state, const float* d_cmd, StepH H, int K, cudaStream_t st, int64_t first,
@@ -576,6 +584,7 @@ int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents,
   h->n_groups = n_groups;
   h->n = n_agents;
   h->mode = mode;
+  h->nx = mode == SIM_CLOSED_LOOP_PID ? NXP : NX;
   h->gid = d_group_id;
   h->host_group0 = derive(groups[0]);
   int rc = SIM_OK;
@@ -616,7 +625,8 @@ int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents,
   if (rc == SIM_OK) {
     // allow the shared-memory scratch variant of the adjoint its full size
     const int big = (int)(kSmemScratchMax + 64 * 1024);
-    if (cudaFuncSetAttribute(adjoint_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) != cudaSuccess ||
+    if (cudaFuncSetAttribute(adjoint_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) != cudaSuccess ||
+        cudaFuncSetAttribute(adjoint_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) != cudaSuccess ||
         cudaFuncSetAttribute(adjoint_kernel<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) != cudaSuccess)
       rc = SIM_ERR_CUDA;
   }
@@ -809,7 +819,6 @@ int sim_run_rounds(sim_handle_t h, float* d_state, float* d_cmd2, const float* h
 int sim_rollout_forward(sim_handle_t h, const float* d_state0, const float* d_cmd, float dt, int64_t nsteps,
                         int ckpt_C, float* d_ckpt, float* d_run_cost, void* stream) {
   if (!h || nsteps < 1 || ckpt_C < 0 || !(dt > 0.f) || !std::isfinite(dt)) return SIM_ERR_ARG;
-  if (h->mode == SIM_CLOSED_LOOP_PID) return SIM_ERR_ARG;  // no checkpointed rollout in the PID mode
   if (h->n == 0) return SIM_OK;
   if (!d_state0 || !d_cmd || !d_ckpt || !aligned16(d_state0) || !aligned16(d_cmd) || !aligned16(d_ckpt))
     return SIM_ERR_ARG;
@@ -832,7 +841,10 @@ int sim_rollout_forward(sim_handle_t h, const float* d_state0, const float* d_cm
   const int grid = fwd_grid(h, smem, h->n);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const DevGroup& P0 = h->host_group0;
-  if (h->mode == SIM_CLOSED_LOOP) {
+  if (h->mode == SIM_CLOSED_LOOP_PID) {
+    if (hetero(h)) ckpt_kernel<2, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
+    else ckpt_kernel<2, false><<<grid, h->block_fwd, smem, st>>>(A, P0);
+  } else if (h->mode == SIM_CLOSED_LOOP) {
     if (hetero(h)) ckpt_kernel<1, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
     else ckpt_kernel<1, false><<<grid, h->block_fwd, smem, st>>>(A, P0);
   } else {
@@ -843,7 +855,7 @@ int sim_rollout_forward(sim_handle_t h, const float* d_state0, const float* d_cm
 }
 
 size_t sim_workspace_bytes(sim_handle_t h, int ckpt_C) {
-  if (!h || ckpt_C < 0 || h->mode == SIM_CLOSED_LOOP_PID) return 0;
+  if (!h || ckpt_C < 0) return 0;
   const int C = ckpt_C > 0 ? ckpt_C : h->C;
   const int grid = adj_grid(h, C);
   return scratch_bytes(h, C, grid) + align256((size_t)grid * h->n_groups * NTH * sizeof(float));
@@ -854,7 +866,7 @@ int sim_rollout_backward(sim_handle_t h, const float* d_ckpt, const float* d_cmd
                          float* d_dL_dtheta, float* d_dL_dtheta_agent, void* d_workspace, size_t ws_bytes,
                          void* stream) {
   if (!h || nsteps < 1 || ckpt_C < 0 || !(dt > 0.f) || !std::isfinite(dt)) return SIM_ERR_ARG;
-  if (!d_dL_dtheta || h->mode == SIM_CLOSED_LOOP_PID) return SIM_ERR_ARG;
+  if (!d_dL_dtheta) return SIM_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (h->n == 0) {
     return cudaMemsetAsync(d_dL_dtheta, 0, sizeof(float) * h->n_groups * NTH, st) == cudaSuccess ? SIM_OK
@@ -936,7 +948,7 @@ int sim_rollout_backward_noalloc(sim_handle_t h, const float* d_ckpt, const floa
                                  int ckpt_C, const float* d_dL_dxT, const float* d_w_run, float* d_dL_dx0,
                                  float* d_dL_dtheta, float* d_dL_dtheta_agent, void* stream) {
   if (!h || nsteps < 1 || ckpt_C < 0 || !(dt > 0.f) || !std::isfinite(dt)) return SIM_ERR_ARG;
-  if (!d_dL_dtheta || h->mode == SIM_CLOSED_LOOP_PID) return SIM_ERR_ARG;
+  if (!d_dL_dtheta) return SIM_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (h->n == 0) {
     return cudaMemsetAsync(d_dL_dtheta, 0, sizeof(float) * h->n_groups * NTH, st) == cudaSuccess ? SIM_OK
@@ -947,7 +959,7 @@ int sim_rollout_backward_noalloc(sim_handle_t h, const float* d_ckpt, const floa
   const int C = ckpt_C > 0 ? ckpt_C : h->C;
   // as many resident blocks as the usual grid, but no more than the fixed
   // scratch holds: per block, C step-start states per thread plus one partial
-  const size_t per_block = (adj_smem_scratch(h, C) ? 0 : (size_t)C * NX * sizeof(float) * h->block_adj) +
+  const size_t per_block = (adj_smem_scratch(h, C) ? 0 : (size_t)C * h->nx * sizeof(float) * h->block_adj) +
                            (size_t)h->n_groups * NTH * sizeof(float);
   const size_t fit = (SIM_NOALLOC_SCRATCH_BYTES - 512) / per_block;
   if (fit < 1) return SIM_ERR_WORKSPACE;

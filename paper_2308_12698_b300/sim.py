@@ -120,10 +120,6 @@ class Sim:
         check(lib().sim_get_launch(self._h, *[ctypes.byref(x) for x in v]), "sim_get_launch")
         return dict(zip(("block", "block_adj", "K", "C"), (x.value for x in v)))
 
-    def _no_pid(self, what: str):
-        if self.mode == _lib.SIM_CLOSED_LOOP_PID:
-            raise SimError(f"{what}: the rollouts and the adjoint cover the 17-state modes, not the PID mode")
-
     # -- forward --
     def step(self, state: torch.Tensor, cmd: torch.Tensor, dt: float, nsteps: int, K: int = 0, stream=None):
         _check_f32(state, self.nx * self.n, "state")
@@ -173,13 +169,12 @@ class Sim:
 
     def rollout_forward(self, x0: torch.Tensor, cmd: torch.Tensor, dt: float, nsteps: int, C: int = 0,
                         ckpt: torch.Tensor | None = None, run_cost: torch.Tensor | None = None, stream=None):
-        """Returns (ckpt, run_cost): ckpt is (S+1, 17 N), ckpt[-1] the final state."""
-        self._no_pid("rollout_forward")
-        _check_f32(x0, 17 * self.n, "x0")
+        """Returns (ckpt, run_cost): ckpt is (S+1, nx N), ckpt[-1] the final state."""
+        _check_f32(x0, self.nx * self.n, "x0")
         _check_f32(cmd, 4 * self.n, "cmd")
         S = self.n_segments(nsteps, C)
         if ckpt is None:
-            ckpt = torch.empty((S + 1, 17 * self.n), dtype=torch.float32, device=x0.device)
+            ckpt = torch.empty((S + 1, self.nx * self.n), dtype=torch.float32, device=x0.device)
         if run_cost is None:
             run_cost = torch.empty(self.n, dtype=torch.float32, device=x0.device)
         check(lib().sim_rollout_forward(self._h, _ptr(x0), _ptr(cmd), float(dt), int(nsteps), int(C), _ptr(ckpt),
@@ -194,15 +189,14 @@ class Sim:
                          w_run: torch.Tensor | None = None, C: int = 0, per_agent: bool = False,
                          workspace: torch.Tensor | None = None, stream=None):
         """Returns (dL/dx0 planar, dL/dtheta (G, 16), per-agent (N, 16) or None)."""
-        self._no_pid("rollout_backward")
-        _check_f32(dL_dxT, 17 * self.n, "dL_dxT")
+        _check_f32(dL_dxT, self.nx * self.n, "dL_dxT")
         if w_run is not None:
             _check_f32(w_run, self.n, "w_run")
         dev = ckpt.device
         ws = self.workspace_bytes(C)
         if workspace is None or workspace.numel() < ws:
             workspace = torch.empty(max(ws, 1), dtype=torch.uint8, device=dev)
-        dx0 = torch.empty(17 * self.n, dtype=torch.float32, device=dev)
+        dx0 = torch.empty(self.nx * self.n, dtype=torch.float32, device=dev)
         dth = torch.empty((self.n_groups, 16), dtype=torch.float32, device=dev)
         dth_a = torch.empty((self.n, 16), dtype=torch.float32, device=dev) if per_agent else None
         check(lib().sim_rollout_backward(self._h, _ptr(ckpt), _ptr(cmd), float(dt), int(nsteps), int(C),
@@ -301,7 +295,7 @@ class QuadRollout(torch.autograd.Function):
         (ckpt,) = ctx.saved_tensors
         sim = ctx.sim
         if g_xT is None:
-            g_xT = torch.zeros(17 * sim.n, dtype=torch.float32, device=ckpt.device)
+            g_xT = torch.zeros(sim.nx * sim.n, dtype=torch.float32, device=ckpt.device)
         w = None if g_rc is None else g_rc.contiguous().float()
         dx0, dth, _ = sim.rollout_backward(ckpt, ctx.cmd, ctx.dt, ctx.nsteps, g_xT.contiguous().float(), w, ctx.C)
         return dth.to(ctx.theta_device), dx0, None, None, None, None, None

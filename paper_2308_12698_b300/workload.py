@@ -256,6 +256,23 @@ def differentiable(n_per_group: int = 1024, n_groups: int = 4, nsteps: int = 200
                     goal=goal, w_omega=w_omega)
 
 
+def differentiable_pid(n_per_group: int = 1024, n_groups: int = 4, nsteps: int = 2000, dt: float = 1e-3,
+                       seed: int = BASE_SEED + 8, w_omega: float = 1e-6) -> Workload:
+    """The goal-reaching rollout of :func:`differentiable` with the PID body-rate loop: each
+    drawn airframe gets pid_group's kI, kD and xi_max; 20-component states, xi starting at 0."""
+    base = differentiable(n_per_group, n_groups, nsteps, dt, seed, w_omega)
+    pid = pid_group()
+    groups = []
+    for g in base.groups:
+        g = dict(g)
+        g.update(kI=pid["kI"], kD=pid["kD"], xi_max=pid["xi_max"])
+        groups.append(round_group(g))
+    x0 = np.zeros((base.n, STATE_DIM_PID), dtype=np.float32)
+    x0[:, :STATE_DIM] = base.x0
+    return Workload("differentiable-pid", CLOSED_LOOP_PID, groups, base.gid, x0, base.cmd, dt, nsteps,
+                    goal=base.goal, w_omega=w_omega)
+
+
 def thrust_down(n: int = 4096, nsteps: int = 1, dt: float = 1e-3, seed: int = BASE_SEED + 6) -> Workload:
     """Demanded force pointing downwards: the reference airframe with its acceleration clamp
     raised to 25 m/s^2 (above g), climbing at 2-10 m/s towards waypoints 5-20 m below,

@@ -154,19 +154,79 @@ def test_pid_graph_and_host_entry_are_bitwise_sim_step(dev):
     sim.close()
 
 
-def test_pid_rollouts_are_refused(dev):
-    """The checkpointed rollouts and the adjoint cover the 17-state modes: SIM_ERR_ARG."""
-    from paper_2308_12698_b300 import _lib
-    from paper_2308_12698_b300.sim import Sim
-    wl = W.closed_loop_pid(n=64)
-    sim = Sim(wl.groups, wl.n, wl.mode)
-    x = torch.zeros(20 * wl.n, device=dev)
-    c = torch.zeros(4 * wl.n, device=dev)
-    ck = torch.zeros(2 * 20 * wl.n, device=dev)
-    rc = _lib.lib().sim_rollout_forward(sim.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(c.data_ptr()),
-                                        1e-3, 10, 10, ctypes.c_void_p(ck.data_ptr()), None, None)
-    assert rc == _lib.SIM_ERR_ARG
-    assert _lib.lib().sim_workspace_bytes(sim.handle, 10) == 0
-    with pytest.raises(_lib.SimError):
-        sim.rollout_forward(x, c, 1e-3, 10, C=10)
+SQRT_MARGIN, CLAMP_MARGIN = 1e-3, 1e-5
+
+
+def check_grad(got, ref, what, loose=False):
+    """The gradient bars of the P loop: strict 1e-3 |r| + 1e-4 max|r|, cosine >= 0.9999; near a
+    kink 2e-2 |r| + 2e-3 max|r|, cosine >= 0.999."""
+    got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
+    cos = got @ ref / (np.linalg.norm(got) * np.linalg.norm(ref) + 1e-300)
+    a, b, c = (2e-2, 2e-3, 0.999) if loose else (1e-3, 1e-4, 0.9999)
+    tol = a * np.abs(ref) + b * np.abs(ref).max()
+    err = np.abs(got - ref)
+    assert cos >= c and np.all(err <= tol), (what, cos, (err / tol).max())
+
+
+def pid_grads(wl, dev, C, block_adj=0):
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    gid = torch.from_numpy(wl.gid).to(dev)
+    sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
+    if block_adj:
+        sim.set_launch(block_adj=block_adj)
+    x0 = planar(torch.from_numpy(wl.x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    ckpt, rc = sim.rollout_forward(x0, cmd, wl.dt, wl.nsteps, C=C)
+    xT = unplanar(ckpt[-1], wl.n)
+    g = torch.zeros_like(xT)
+    g[:, 0:3] = 2 * (xT[:, 0:3] - torch.from_numpy(wl.goal).to(dev))
+    w = torch.full((wl.n,), wl.w_omega, device=dev)
+    dx0, dth, dtha = sim.rollout_backward(ckpt, cmd, wl.dt, wl.nsteps, planar(g), w, C=C, per_agent=True)
+    torch.cuda.synchronize()
+    out = (unplanar(dx0, wl.n).cpu().numpy(), dth.cpu().numpy(), dtha.cpu().numpy(), xT.cpu().numpy(),
+           rc.cpu().numpy())
     sim.close()
+    return out
+
+
+def test_pid_rollout_forward_is_bitwise_sim_step(dev, orc):
+    """The checkpointed forward runs the same PID step: its last checkpoint equals sim_step's
+    state bit for bit, and its running cost matches the checker's."""
+    wl = W.differentiable_pid(n_per_group=300, n_groups=3, nsteps=400)
+    _, _, _, xT, rc = pid_grads(wl, dev, C=50)
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    sim = Sim(wl.groups, wl.n, wl.mode, gid=torch.from_numpy(wl.gid).to(dev))
+    x = planar(torch.from_numpy(wl.x0)).to(dev)
+    sim.step(x, torch.from_numpy(wl.cmd).to(dev).reshape(-1), wl.dt, wl.nsteps, K=37)
+    np.testing.assert_array_equal(unplanar(x, wl.n).cpu().numpy(), xT)
+    sim.close()
+    _, rref = orc.rollout(wl.groups, wl.gid, wl.x0, wl.cmd, wl.dt, wl.nsteps, wl.mode, with_cost=True)
+    np.testing.assert_allclose(rc, rref, rtol=2e-4)
+
+
+def test_pid_adjoint_matches_fp64_reverse_mode(dev, orc):
+    """Per-agent dL/dtheta and dL/dx0 (20 components, the integral included) against the
+    checker's reverse mode on the PID step; agents whose FP64 trajectory comes near a kink (rotor
+    demand near 0 or the ceiling, acceleration or integrator clamp) take the looser bar."""
+    wl = W.differentiable_pid(n_per_group=16, n_groups=4, nsteps=2000)
+    dx0, dth, dtha, _, _ = pid_grads(wl, dev, C=100)
+    _, rdx0, rdth = orc.grad(wl.groups, wl.gid, wl.x0, wl.cmd, wl.dt, wl.nsteps, wl.mode, wl.goal, wl.w_omega)
+    m = orc.clamp_margins(wl.groups, wl.gid, wl.x0, wl.cmd, wl.dt, wl.nsteps, mode=wl.mode)
+    fl = (m[:, 0] < SQRT_MARGIN) | (m[:, 1] < CLAMP_MARGIN) | (m[:, 2] < CLAMP_MARGIN)
+    assert (~fl).sum() >= 16, fl.sum()
+    assert np.abs(rdx0[:, 17:20]).max() > 0
+    for a in range(wl.n):
+        check_grad(dtha[a], rdth[a], f"theta agent {a}", loose=fl[a])
+        check_grad(dx0[a], rdx0[a], f"x0 agent {a}", loose=fl[a])
+    for gi in range(len(wl.groups)):
+        check_grad(dth[gi], rdth[wl.gid == gi].sum(axis=0), f"theta group {gi}", loose=True)
+
+
+def test_pid_adjoint_shared_and_global_scratch_agree(dev):
+    """C = 2 keeps the segment in shared memory, C = 40 in the global workspace: same
+    checkpointed states and per-step arithmetic, so per-agent gradients agree bit for bit."""
+    wl = W.differentiable_pid(n_per_group=500, n_groups=2, nsteps=200)
+    a = pid_grads(wl, dev, C=2)
+    b = pid_grads(wl, dev, C=40)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[2], b[2])

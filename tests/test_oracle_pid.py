@@ -179,3 +179,50 @@ def test_pid_spectrum_at_hover(orc, kI, kD, stable):
     lam = _spectrum_pid(orc, g)
     _match(lam, _linear_spectrum_pid(g, taumax), 0.03)
     assert (lam.real.max() < 1e-6) == stable
+
+
+def test_pid_reverse_mode_matches_central_differences(orc):
+    """The checker's reverse mode on the 20-state PID step vs FP64 central differences (step 1e-5
+    relative per parameter, 1e-5 max(1, |x|) per state), within 1e-5 relative per component.
+    The step is 10x the P loop's: through omega' the inertias enter the loss more steeply, and
+    at 1e-6 the difference quotient of J (about 3e-8 kg m^2 per step) loses 1e-5 to rounding;
+    at 1e-4 and 1e-5 it converges on the reverse-mode value to 1e-7."""
+    wl = W.differentiable_pid(n_per_group=2, n_groups=2, nsteps=300)
+    x0 = wl.x0.astype(np.float64)
+    x0[:, 17:20] = np.random.default_rng(9).uniform(-0.3, 0.3, (wl.n, 3))  # a nonzero integral to start
+    loss, dx0, dth = orc.grad(wl.groups, wl.gid, x0, wl.cmd, wl.dt, wl.nsteps, PID, wl.goal, wl.w_omega)
+    keys = [("kp", 0), ("kp", 1), ("kp", 2), ("kd", 0), ("kd", 1), ("kd", 2), ("katt", 0), ("katt", 1), ("katt", 2),
+            ("krate", 0), ("krate", 1), ("krate", 2), ("m", None), ("Jxx", None), ("Jyy", None), ("Jzz", None)]
+    h = 1e-5
+
+    def L(a, g, x):
+        return orc.loss([g], [0], x[None], wl.cmd[a:a + 1], wl.dt, wl.nsteps, PID, wl.goal[a:a + 1], wl.w_omega,
+                        nthreads=1)[0]
+
+    for a in range(wl.n):
+        g0 = {k: (list(v) if isinstance(v, list) else v) for k, v in wl.groups[wl.gid[a]].items()}
+        fd = []
+        for k, i in keys:
+            vals = []
+            for s in (+1, -1):
+                gg = {kk: (list(v) if isinstance(v, list) else v) for kk, v in g0.items()}
+                base = gg[k][i] if i is not None else gg[k]
+                step = h * abs(base)
+                if i is None:
+                    gg[k] = base + s * step
+                else:
+                    gg[k][i] = base + s * step
+                vals.append(L(a, gg, x0[a]))
+            fd.append((vals[0] - vals[1]) / (2 * step))
+        for j in range(20):
+            step = h * max(1.0, abs(x0[a, j]))
+            xp, xm = x0[a].copy(), x0[a].copy()
+            xp[j] += step
+            xm[j] -= step
+            fd.append((L(a, g0, xp) - L(a, g0, xm)) / (2 * step))
+        fd = np.array(fd)
+        ad = np.concatenate([dth[a], dx0[a]])
+        scale = np.abs(ad).max()
+        err = np.abs(fd - ad)
+        assert np.all(err <= 1e-5 * np.maximum(np.abs(ad), 1e-3 * scale)), (a, err / np.maximum(np.abs(ad), 1e-3 * scale))
+        assert np.abs(dx0[a, 17:20]).max() > 0  # the integral does reach the loss
