@@ -377,6 +377,11 @@ int occupancy(F kernel, int block, size_t smem) {
 
 }  // namespace
 
+// sim_step_host: at most kHostChunks chunks of at least kHostChunkMin agents.
+// Only the first chunk's copy in and the last chunk's copy out are exposed.
+constexpr int kHostChunks = 16;
+constexpr int64_t kHostChunkMin = 32768;
+
 struct sim_s {
   int device = 0;
   int sms = 1;
@@ -393,7 +398,7 @@ struct sim_s {
   DevGroup host_group0;
   // host-buffer pipeline (sim_step_host): created on first use
   cudaStream_t s_h2d = nullptr, s_d2h = nullptr, s_comp[2] = {nullptr, nullptr};
-  cudaEvent_t ev_start = nullptr, ev_end = nullptr, ev_in[8] = {}, ev_done[8] = {};
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr, ev_in[kHostChunks] = {}, ev_done[kHostChunks] = {};
   // decision rounds (sim_run_rounds): per command plane and observation plane
   cudaEvent_t ev_cmd[2] = {}, ev_cmd_free[2] = {}, ev_obs[2] = {}, ev_obs_free[2] = {};
   int block_fwd = kDefaultBlockFwd;
@@ -516,7 +521,7 @@ int pipeline_streams(sim_s* h) {
     if (cudaStreamCreateWithFlags(p, cudaStreamNonBlocking) != cudaSuccess) return SIM_ERR_CUDA;
   for (cudaEvent_t* e : {&h->ev_start, &h->ev_end})
     if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return SIM_ERR_CUDA;
-  for (int c = 0; c < 8; ++c)
+  for (int c = 0; c < kHostChunks; ++c)
     if (cudaEventCreateWithFlags(&h->ev_in[c], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_done[c], cudaEventDisableTiming) != cudaSuccess)
       return SIM_ERR_CUDA;
@@ -714,7 +719,7 @@ int sim_step_host(sim_handle_t h, float* h_state, const float* h_cmd, float* d_s
   // Chunks of agents flow through H2D copy -> steps -> D2H copy on separate
   // streams, so the copies of one chunk overlap the steps of the others and
   // two compute streams let one chunk's last wave overlap the next chunk.
-  const int m = (int)std::max<int64_t>(1, std::min<int64_t>(8, n / 65536));
+  const int m = (int)std::max<int64_t>(1, std::min<int64_t>(kHostChunks, n / kHostChunkMin));
   const int64_t chunk = (n + m - 1) / m;
   const int K = substeps_K > 0 ? substeps_K : h->K;
   const StepH H = make_h(dt);
@@ -1125,7 +1130,7 @@ void sim_destroy(sim_handle_t h) {
     if (st) cudaStreamDestroy(st);
   for (cudaEvent_t e : {h->ev_start, h->ev_end})
     if (e) cudaEventDestroy(e);
-  for (int c = 0; c < 8; ++c) {
+  for (int c = 0; c < kHostChunks; ++c) {
     if (h->ev_in[c]) cudaEventDestroy(h->ev_in[c]);
     if (h->ev_done[c]) cudaEventDestroy(h->ev_done[c]);
   }
