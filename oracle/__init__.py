@@ -26,15 +26,16 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 #: ORACLE_LIB points the wrapper at another build of the same source (the
 #: mutation test loads deliberately broken copies this way).
 LIB_PATH = os.environ.get("ORACLE_LIB") or os.path.join(_HERE, "liboracle.so")
-_SOURCES = ("oracle.cpp", "quad_model.hpp", "scalar_types.hpp")
+_SOURCES = ("oracle.cpp", "quad_model.hpp", "scalar_types.hpp", "vehicles.hpp")
 
 NX = 17
 NXP = 20  # PID mode: the 17 states and the rate-error integral xi
-NPARAM = 34
+NPARAM = 43
 NTHETA = 16
 OPEN_LOOP = 0
 CLOSED_LOOP = 1
 CLOSED_LOOP_PID = 2
+TYPE_QUAD, TYPE_CAR, TYPE_FIXED_WING = 0, 1, 2
 
 
 def state_dim(mode: int) -> int:
@@ -70,6 +71,8 @@ def lib():
         L.oracle_derivative.argtypes = [P, P, P, P]
         L.oracle_controller.argtypes = [P, P, P, P]
         L.oracle_controller_pid.argtypes = [P, P, P, P, P, P]
+        L.oracle_vehicle_controller.argtypes = [P, P, P, P]
+        L.oracle_vehicle_derivative.argtypes = [P, P, P, P]
         L.oracle_allocation.argtypes = [P, P, P, P]
         L.oracle_shepperd.argtypes = [P, P]
         L.oracle_count_ops.argtypes = [P, P, P, ctypes.c_double, ctypes.c_int, P]
@@ -88,10 +91,12 @@ def _p(a: np.ndarray):
 
 def pack_group(g: dict) -> np.ndarray:
     """Packed FP64 parameter group: m Jxx Jyy Jzz L alpha kt kq tau_m c_d omega_max g kp kd katt krate a_max
-    kI kD xi_max (the PID rate loop's gains and integrator limit; absent keys: 0, 0, 1e30)."""
+    kI kD xi_max (the PID rate loop's gains and integrator limit; absent keys: 0, 0, 1e30), type and
+    veh[8] (agent type 0 quadrotor, 1 car, 2 fixed-wing and its model's parameters; absent: 0)."""
     v = [g["m"], g["Jxx"], g["Jyy"], g["Jzz"], g["L"], g["alpha"], g["kt"], g["kq"], g["tau_m"], g["c_d"],
          g["omega_max"], g["g"], *g["kp"], *g["kd"], *g["katt"], *g["krate"], g["a_max"],
-         *g.get("kI", [0.0] * 3), *g.get("kD", [0.0] * 3), *g.get("xi_max", [1e30] * 3)]
+         *g.get("kI", [0.0] * 3), *g.get("kD", [0.0] * 3), *g.get("xi_max", [1e30] * 3),
+         g.get("type", TYPE_QUAD), *(list(g.get("veh", [])) + [0.0] * 8)[:8]]
     a = np.asarray(v, dtype=np.float64)
     assert a.size == NPARAM
     return a
@@ -264,3 +269,25 @@ def count_derivative_ops(group, x, w):
     out = np.zeros(6, dtype=np.int64)
     lib().oracle_count_derivative_ops(_p(pg), _p(xx), _p(ww), _p(out))
     return dict(zip(("add", "mul", "div", "sqrt", "trig", "cmp"), out.tolist()))
+
+
+def vehicle_controller(group, x, cmd):
+    """Car or fixed-wing agent: its controller's inputs (3) at the 17-state x."""
+    pg = pack_group(group)
+    xx = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(NX))
+    cc = np.ascontiguousarray(np.asarray(cmd, dtype=np.float64))
+    u = np.zeros(3)
+    if lib().oracle_vehicle_controller(_p(pg), _p(xx), _p(cc), _p(u)) != 0:
+        raise ValueError("not a car or fixed-wing group")
+    return u
+
+
+def vehicle_derivative(group, x, u):
+    """Car or fixed-wing agent: time derivative (17) at state x for held inputs u (3)."""
+    pg = pack_group(group)
+    xx = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(NX))
+    uu = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(3))
+    dx = np.zeros(NX)
+    if lib().oracle_vehicle_derivative(_p(pg), _p(xx), _p(uu), _p(dx)) != 0:
+        raise ValueError("not a car or fixed-wing group")
+    return dx

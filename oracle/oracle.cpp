@@ -4,8 +4,9 @@
 //
 // Layouts: states are agent-major (n x 17 doubles: p v q omega Omega; n x 20
 // in the PID mode, with the rate-error integral xi last), commands n x 4,
-// parameter groups n_groups x 34 doubles in the packed order of
-// unpack_group(), group ids int32.
+// parameter groups n_groups x 43 doubles in the packed order of
+// unpack_group(), group ids int32.  Groups of car or fixed-wing type
+// (vehicles.hpp) run their own model in the closed-loop mode.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -14,6 +15,7 @@
 #include <vector>
 
 #include "quad_model.hpp"
+#include "vehicles.hpp"
 
 namespace orc {
 thread_local Tape* g_tape = nullptr;
@@ -92,6 +94,22 @@ int oracle_controller(const double* group, const double* x, const double* cmd, d
   return 0;
 }
 
+// Car or fixed-wing agent: inputs u (3) of its controller at state x (17).
+int oracle_vehicle_controller(const double* group, const double* x, const double* cmd, double* u) {
+  const Group<double> P = unpack_group(group);
+  if (P.type != TYPE_CAR && P.type != TYPE_FIXED_WING) return -1;
+  vehicle_controller(P, x, cmd, u);
+  return 0;
+}
+
+// Car or fixed-wing agent: time derivative (17) at state x for inputs u.
+int oracle_vehicle_derivative(const double* group, const double* x, const double* u, double* dx) {
+  const Group<double> P = unpack_group(group);
+  if (P.type != TYPE_CAR && P.type != TYPE_FIXED_WING) return -1;
+  vehicle_derivative(P, x, u, dx);
+  return 0;
+}
+
 // PID mode, one agent with its 20-state x: rotor-speed commands w (4), the
 // rate error e (3) and omega' at x (3), as the step uses them.
 int oracle_controller_pid(const double* group, const double* x, const double* cmd, double* w, double* e,
@@ -121,6 +139,8 @@ int oracle_rollout(const double* groups, int n_groups, const int32_t* gid, int64
                    const double* cmd, double h, int64_t nsteps, int mode, int nthreads, double* run_cost) {
   if (n < 0 || nsteps < 0 || n_groups < 1 || mode < OPEN_LOOP || mode > CLOSED_LOOP_PID) return -1;
   const GroupSet S(groups, n_groups);
+  for (int g = 0; g < n_groups; ++g)
+    if (S.P[g].type != TYPE_QUAD && (S.P[g].type > TYPE_FIXED_WING || mode != CLOSED_LOOP)) return -1;
   const int nx = state_dim(mode);
   parallel_for(n, nthreads, [&](int64_t lo, int64_t hi) {
     for (int64_t a = lo; a < hi; ++a) {
@@ -129,7 +149,7 @@ int oracle_rollout(const double* groups, int n_groups, const int32_t* gid, int64
       std::memcpy(cur, x + a * nx, nx * sizeof(double));
       double rc = 0.0;
       for (int64_t s = 0; s < nsteps; ++s) {
-        step_any(S.P[g], S.F[g], mode, cur, cmd + a * 4, h, nxt);
+        agent_step(S.P[g], S.F[g], mode, cur, cmd + a * 4, h, nxt);
         std::memcpy(cur, nxt, nx * sizeof(double));
         rc += omega_sq(cur);
       }
@@ -151,6 +171,8 @@ int oracle_grad(const double* groups, int n_groups, const int32_t* gid, int64_t 
                 int nthreads, double* loss, double* dx0, double* dtheta) {
   if (n < 0 || nsteps < 0 || n_groups < 1 || mode < OPEN_LOOP || mode > CLOSED_LOOP_PID) return -1;
   const GroupSet S(groups, n_groups);
+  for (int g = 0; g < n_groups; ++g)
+    if (S.P[g].type != TYPE_QUAD) return -1;  // quadrotor gradients only
   const int NS = state_dim(mode);
   parallel_for(n, nthreads, [&](int64_t lo, int64_t hi) {
     Tape tape;
@@ -223,6 +245,8 @@ int oracle_clamp_margins(const double* groups, int n_groups, const int32_t* gid,
                          const double* cmd, double h, int64_t nsteps, int mode, int nthreads, double* out) {
   if (n < 0 || nsteps < 0 || n_groups < 1 || (mode != CLOSED_LOOP && mode != CLOSED_LOOP_PID)) return -1;
   const GroupSet S(groups, n_groups);
+  for (int g = 0; g < n_groups; ++g)
+    if (S.P[g].type != TYPE_QUAD) return -1;
   const int nx = state_dim(mode);
   parallel_for(n, nthreads, [&](int64_t lo, int64_t hi) {
     for (int64_t a = lo; a < hi; ++a) {
@@ -361,7 +385,7 @@ int oracle_count_ops(const double* group, const double* x, const double* cmd, do
   Cnt xc[NXP], xn[NXP];
   for (int i = 0; i < state_dim(mode); ++i) xc[i] = Cnt(x[i]);
   g_count = OpCount();
-  step_any(P, F, mode, xc, cmd, h, xn);
+  agent_step(P, F, mode, xc, cmd, h, xn);
   counts[0] = g_count.add;
   counts[1] = g_count.mul;
   counts[2] = g_count.div;

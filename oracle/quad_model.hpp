@@ -42,7 +42,7 @@ namespace orc {
 
 constexpr int NX = 17;      // p(3) v(3) q(4: w x y z) omega(3) Omega(4)
 constexpr int NXP = 20;     // PID mode: the 17 plus the rate-error integral xi(3)
-constexpr int NPARAM = 34;  // packed parameter group (see unpack_group)
+constexpr int NPARAM = 43;  // packed parameter group (see unpack_group)
 constexpr int NTHETA = 16;  // kp(3) kd(3) katt(3) krate(3) m Jxx Jyy Jzz
 enum { OPEN_LOOP = 0, CLOSED_LOOP = 1, CLOSED_LOOP_PID = 2 };
 
@@ -57,10 +57,12 @@ struct Group {
   T kp[3], kd[3], katt[3], krate[3];
   T a_max;
   T kI[3], kD[3], xi_max[3];  // PID mode only
+  int type = 0;                // agent type: 0 quadrotor, 1 car, 2 fixed-wing (vehicles.hpp)
+  double veh[8] = {};          // parameters of the car or fixed-wing model
 };
 
 // Packed order: m Jxx Jyy Jzz L alpha kt kq tau_m c_d omega_max g kp[3] kd[3]
-// katt[3] krate[3] a_max kI[3] kD[3] xi_max[3].
+// katt[3] krate[3] a_max kI[3] kD[3] xi_max[3] type veh[8].
 inline Group<double> unpack_group(const double* p) {
   Group<double> G;
   G.m = p[0];
@@ -74,6 +76,8 @@ inline Group<double> unpack_group(const double* p) {
   for (int i = 0; i < 3; ++i) {
     G.kI[i] = p[25 + i]; G.kD[i] = p[28 + i]; G.xi_max[i] = p[31 + i];
   }
+  G.type = (int)p[34];
+  for (int i = 0; i < 8; ++i) G.veh[i] = p[35 + i];
   return G;
 }
 
@@ -92,6 +96,8 @@ Group<T> cast_group(const Group<S>& s) {
   for (int i = 0; i < 3; ++i) {
     G.kI[i] = T(val(s.kI[i])); G.kD[i] = T(val(s.kD[i])); G.xi_max[i] = T(val(s.xi_max[i]));
   }
+  G.type = s.type;
+  for (int i = 0; i < 8; ++i) G.veh[i] = s.veh[i];
   return G;
 }
 

@@ -126,9 +126,13 @@ inline Cnt& operator*=(Cnt& x, Cnt y) { x = x * y; return x; }
 inline Cnt sqrt(Cnt x) { g_count.sqrt++; return Cnt(std::sqrt(x.v)); }
 inline Cnt cos(Cnt x) { g_count.trig++; return Cnt(std::cos(x.v)); }
 inline Cnt sin(Cnt x) { g_count.trig++; return Cnt(std::sin(x.v)); }
+inline Cnt tan(Cnt x) { g_count.trig++; return Cnt(std::tan(x.v)); }
+inline Cnt atan2(Cnt y, Cnt x) { g_count.trig++; return Cnt(std::atan2(y.v, x.v)); }
 inline double val(Cnt x) { g_count.cmp++; return x.v; }
 
 inline double val(double x) { return x; }
 inline double sqrt(double x) { return std::sqrt(x); }
+inline double tan(double x) { return std::tan(x); }
+inline double atan2(double y, double x) { return std::atan2(y, x); }
 
 }  // namespace orc

@@ -40,6 +40,8 @@ CLOSED_LOOP = 1
 CLOSED_LOOP_PID = 2
 #: state components in the PID mode: the 17 and the rate-error integral xi (3)
 STATE_DIM_PID = 20
+#: agent types of a parameter group
+TYPE_QUAD, TYPE_CAR, TYPE_FIXED_WING = 0, 1, 2
 
 #: Fixed group sizes of the uneven heterogeneous swarm (sum 600,000).
 HETERO_SIZES = (100, 900, 5000, 19000, 55000, 130000, 190000, 200000)
@@ -70,6 +72,24 @@ def pid_group() -> dict:
     (0.05 < kI < 0.2 is the stable band at kD = 0.005)."""
     g = dict(base_group())
     g.update(kI=[0.05] * 3, kD=[0.005] * 3, xi_max=[2.0] * 3)
+    return round_group(g)
+
+
+def car_group() -> dict:
+    """A road car under pure pursuit (kinematic bicycle): wheelbase 2.7 m, steering lock 35 deg
+    (tan = 0.7), acceleration clamp 3 m/s^2, speed gain 1 /s, minimum look-ahead 5 m.  The
+    quadrotor fields are those of base_group and unused."""
+    g = dict(base_group())
+    g.update(type=TYPE_CAR, veh=[2.7, 0.7, 3.0, 1.0, 5.0, 0.0, 0.0, 0.0])
+    return round_group(g)
+
+
+def fixed_wing_group() -> dict:
+    """A small fixed-wing drone (coordinated-turn guidance model): bank response 3 /s, bank
+    limit 35 deg (0.61 rad), course gain 1.5 rad of bank per rad of course error, altitude loop
+    b_hd = 2 /s, b_h = 1 /s^2 (critically damped), airspeed response 0.5 /s."""
+    g = dict(base_group())
+    g.update(type=TYPE_FIXED_WING, veh=[3.0, 0.61, 1.5, 2.0, 1.0, 0.5, 0.0, 0.0])
     return round_group(g)
 
 
@@ -271,6 +291,62 @@ def differentiable_pid(n_per_group: int = 1024, n_groups: int = 4, nsteps: int =
     x0[:, :STATE_DIM] = base.x0
     return Workload("differentiable-pid", CLOSED_LOOP_PID, groups, base.gid, x0, base.cmd, dt, nsteps,
                     goal=base.goal, w_omega=w_omega)
+
+
+def _vehicle_states(rng: np.random.Generator, kind: int, n: int):
+    """Initial 17-states and commands of n cars or fixed-wing drones (the unused components 0)."""
+    x = np.zeros((n, STATE_DIM))
+    cmd = np.zeros((n, 4))
+    psi = rng.uniform(-math.pi, math.pi, n)
+    x[:, 6], x[:, 7] = np.cos(psi), np.sin(psi)
+    if kind == TYPE_CAR:
+        x[:, 0:2] = rng.uniform(-50.0, 50.0, (n, 2))
+        x[:, 3] = rng.uniform(0.0, 15.0, n)
+        cmd[:, 0:2] = rng.uniform(-100.0, 100.0, (n, 2))
+        cmd[:, 3] = rng.uniform(5.0, 20.0, n)
+    else:
+        x[:, 0:2] = rng.uniform(-500.0, 500.0, (n, 2))
+        x[:, 2] = rng.uniform(50.0, 150.0, n)
+        x[:, 3] = rng.uniform(15.0, 25.0, n)
+        x[:, 10] = rng.uniform(-0.2, 0.2, n)
+        cmd[:, 0:2] = rng.uniform(-1000.0, 1000.0, (n, 2))
+        cmd[:, 2] = rng.uniform(50.0, 150.0, n)
+        cmd[:, 3] = rng.uniform(15.0, 25.0, n)
+    return x, cmd
+
+
+#: Agents per type of the mixed swarm: quadrotors, cars, fixed-wing drones (sum 600,000).
+MULTI_TYPE_SIZES = (200000, 200000, 200000)
+
+
+def multi_type(sizes=MULTI_TYPE_SIZES, nsteps: int = 1000, dt: float = 1e-3, seed: int = BASE_SEED + 9,
+               shuffle: bool = False) -> Workload:
+    """Quadrotors, cars and fixed-wing drones in one closed-loop swarm (three groups, one type
+    each): the quadrotors as in closed_loop, cars with waypoints ~ U[-100, 100]^2 and target
+    speeds U[5, 20] m/s, drones with waypoints ~ U[-1000, 1000]^2, altitudes U[50, 150] m and
+    airspeeds U[15, 25] m/s.  Group ids sorted by type, or shuffled."""
+    rng = np.random.default_rng(seed)
+    groups = [base_group(), car_group(), fixed_wing_group()]
+    xs, cs = [], []
+    wh = hover_speed(groups[0])
+    xq, psi = _initial_states(rng, sizes[0], np.full(sizes[0], wh))
+    cq = np.zeros((sizes[0], 4))
+    cq[:, 0:3] = rng.uniform(-50.0, 50.0, (sizes[0], 3))
+    cq[:, 3] = psi
+    xs.append(xq.astype(np.float64))
+    cs.append(cq)
+    for kind, m in ((TYPE_CAR, sizes[1]), (TYPE_FIXED_WING, sizes[2])):
+        x, c = _vehicle_states(rng, kind, m)
+        xs.append(x)
+        cs.append(c)
+    gid = np.concatenate([np.full(m, i, dtype=np.uint8) for i, m in enumerate(sizes)])
+    x0 = np.concatenate(xs).astype(np.float32)
+    cmd = np.concatenate(cs).astype(np.float32)
+    if shuffle:
+        perm = rng.permutation(gid.size)
+        gid, x0, cmd = gid[perm], x0[perm], cmd[perm]
+    return Workload("multi-type", CLOSED_LOOP, groups, gid, np.ascontiguousarray(x0), np.ascontiguousarray(cmd),
+                    dt, nsteps, extra=dict(sizes=list(sizes), shuffled=shuffle))
 
 
 def thrust_down(n: int = 4096, nsteps: int = 1, dt: float = 1e-3, seed: int = BASE_SEED + 6) -> Workload:

@@ -36,16 +36,24 @@ MUTATIONS = {
     "PID integrator sign": ("x[NX + i] + T(h) * e[i]", "x[NX + i] - T(h) * e[i]"),
     "PID integral index": ("P.kI[i] * xi[i]", "P.kI[i] * xi[(i + 1) % 3]"),
     "PID no anti-windup": ("xn[NX + i] = clampv(x[NX + i] + T(h) * e[i], -lim, lim);", "xn[NX + i] = x[NX + i] + T(h) * e[i];"),
+    # car and fixed-wing models (vehicles.hpp)
+    "car curvature factor": ("vehicles.hpp", "T(2.0) * cross / (dist * ld)", "cross / (dist * ld)"),
+    "car no look-ahead floor": ("vehicles.hpp", "val(dist) > P.veh[4] ? dist : T(P.veh[4])", "dist"),
+    "heading rotation sign": ("vehicles.hpp", "dx[6] = -s * turn;", "dx[6] = s * turn;"),
+    "fixed-wing turn rate": ("vehicles.hpp", "P.g * tan(x[10]) / v", "P.g * x[10] / v"),
+    "fixed-wing altitude loop": ("vehicles.hpp", "T(P.veh[4]) * (u[1] - x[2])", "T(P.veh[4]) * (x[2] - u[1])"),
+    "fixed-wing course error": ("vehicles.hpp", "atan2(cross, dot)", "atan2(dot, cross)"),
 }
 
 
 @pytest.mark.slow
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_pins_catch_planted_mistake(tmp_path, name):
-    old, new = MUTATIONS[name]
+    entry = MUTATIONS[name]
+    fname, old, new = entry if len(entry) == 3 else ("quad_model.hpp", *entry)
     work = tmp_path / "oracle"
     shutil.copytree(SRC, work, ignore=shutil.ignore_patterns("*.so", "__pycache__"))
-    model = work / "quad_model.hpp"
+    model = work / fname
     text = model.read_text()
     assert text.count(old) == 1, f"mutation anchor not unique for {name!r}"
     model.write_text(text.replace(old, new))
@@ -55,6 +63,7 @@ def test_pins_catch_planted_mistake(tmp_path, name):
     env = dict(os.environ, ORACLE_LIB=str(lib), PYTHONPATH=ROOT)
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_pid.py")], cwd=ROOT, env=env,
+                        os.path.join(ROOT, "tests", "test_oracle_pid.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_vehicles.py")], cwd=ROOT, env=env,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"no pin caught the mutation {name!r}:\n{r.stdout[-2000:]}"
