@@ -54,6 +54,11 @@ FWD_ADJ_FLOPS_PER_AGENT_STEP = 2 * FLOPS_PER_AGENT_STEP + 2 * ADJ_TAPE_EDGES_PER
 #: states, 760..774), less the checker's second evaluation of the time derivative for omega'
 #: (a step takes omega' from its first RK4 stage).
 FLOPS_PER_AGENT_STEP_PID = 760
+#: The checker's count for one step of a car (98..101) and of a fixed-wing drone (156, plus
+#: five transcendental functions: four tan and one atan2, not counted), minimum over the mixed
+#: swarm's states.
+FLOPS_PER_AGENT_STEP_CAR = 98
+FLOPS_PER_AGENT_STEP_FIXED_WING = 156
 #: Bytes one plain step moves per agent: state 68 read + 68 written, command
 #: 16, group id 1, status 1.
 BYTES_PER_AGENT_STEP_PLAIN = 154
@@ -63,7 +68,8 @@ SM_MAX_MHZ = 2032.0
 L2_FLUSH_BYTES = 256 << 20
 #: The sources that define the step kernel: a committed ncu figure is used
 #: only while their fingerprint is the one it was taken on.
-KERNEL_SOURCES = ("paper_2308_12698_b300/csrc/model_fwd.cuh", "paper_2308_12698_b300/csrc/step_kernel.cuh")
+KERNEL_SOURCES = ("paper_2308_12698_b300/csrc/model_fwd.cuh", "paper_2308_12698_b300/csrc/step_kernel.cuh",
+                  "paper_2308_12698_b300/csrc/vehicles.cuh")
 
 
 def kernel_sha() -> str:
@@ -693,6 +699,31 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     pg.close()
     ps.close()
     del px, px0, pcmd
+
+    # quadrotors, cars and fixed-wing drones (200,000 each) in one persistent launch
+    mw = W.multi_type(nsteps=T_STEPS)
+    ms_ = Sim(mw.groups, mw.n, mw.mode, gid=torch.from_numpy(mw.gid).to(x0.device))
+    mx0 = planar(torch.from_numpy(mw.x0)).to(x0.device)
+    mcmd = torch.from_numpy(mw.cmd).reshape(-1).to(x0.device)
+    mx = mx0.clone()
+    mt = autotune.tune_step(ms_, mx0, mcmd, DT, T_STEPS)
+    mg = ms_.graph(mx, mcmd, DT, T_STEPS, K=mt["K"])
+    mreset = lambda: mx.copy_(mx0)  # noqa: E731
+    timed_steps(mg.launch, 2, mreset)
+    t = timed_steps(mg.launch, reps, mreset)
+    ms = max_over_ranks(sum(t), world) / reps
+    sizes = W.MULTI_TYPE_SIZES
+    flops = (sizes[0] * FLOPS_PER_AGENT_STEP + sizes[1] * FLOPS_PER_AGENT_STEP_CAR +
+             sizes[2] * FLOPS_PER_AGENT_STEP_FIXED_WING) * T_STEPS / (ms / 1e3)
+    out["multi_type"] = {"value": world * mw.n * T_STEPS / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                         "n_agents": mw.n, "sizes": {"quadrotor": sizes[0], "car": sizes[1], "fixed_wing": sizes[2]},
+                         "K": mt["K"], "block": mt["block"],
+                         "roofline": {"bound": "alu", "achieved": flops / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
+                                      "frac": flops / 1e12 / peak_tf,
+                                      "note": "flops weighted by type; the drones' tan/atan2 are not counted"}}
+    mg.close()
+    ms_.close()
+    del mx, mx0, mcmd
 
     # decision rounds: commands from pinned host memory every M steps, positions back after
     # each round, both overlapped with the physics (1000 steps per bench step)

@@ -24,7 +24,19 @@
  *     becomes taumax_i (krate_i e_i + kI_i xi_i - kD_i omega'_i), e = omega_des
  *     - omega, omega' of Eq. (qd4) at the step start (derivative on the
  *     measurement), and xi, the integral of e, is three more state components
- *     advanced once per step: xi <- clamp(xi + dt e, +-xi_max).
+ *     advanced once per step: xi <- clamp(xi + dt e, +-xi_max);
+ *   - two more agent types in the same launch (the paper's simulator runs
+ *     fixed-wing drones, quadrotors and cars, Sec. III-B, and cites their
+ *     models without equations), chosen per parameter group, closed loop:
+ *       car: kinematic bicycle on the rear axle, p' = v (cos psi, sin psi),
+ *         v' = a, psi' = v kappa, steered by pure pursuit towards the
+ *         waypoint (kappa = 2 sin(alpha) / max(distance, l_min) for any
+ *         bearing alpha, |kappa| <= tan(delta_max) / L_w) and
+ *         a = clamp(k_v (v_c - v), +-a_max);
+ *       fixed-wing: coordinated-turn guidance model without wind,
+ *         p' = V (cos chi, sin chi), chi' = g tan(phi) / V,
+ *         phi' = b_phi (phi_c - phi), h'' = -b_hd h' + b_h (h_c - h),
+ *         V' = b_V (V_c - V), phi_c = clamp(k_chi * course error, +-phi_max).
  *
  * Conventions
  *   State of one agent, 17 floats: p(3) v(3) q(4: w,x,y,z, Hamilton,
@@ -32,6 +44,11 @@
  *   Rotors: 1 front-left, 2 front-right, 3 rear-right, 4 rear-left.
  *
  *   SIM_CLOSED_LOOP_PID adds xi(3), the body-rate error integral: 20 floats.
+ *   Cars and fixed-wing drones use components of the same 17: position
+ *   0-2 (a car's height is held), speed 3 (v or airspeed V), climb rate 5
+ *   (fixed-wing), heading or course as a unit vector (cos, sin) 6-7, bank 10
+ *   (fixed-wing); the other components are left unchanged.  Their commands:
+ *   car (x_c, y_c, unused, v_c), fixed-wing (x_c, y_c, h_c, V_c).
  *
  *   State buffers are PLANAR ("SoA of float4"): for N agents, 17*N floats,
  *     plane k = 0..3 : N float4 holding components 4k..4k+3 of every agent,
@@ -82,6 +99,10 @@ extern "C" {
 #define SIM_CLOSED_LOOP 1
 #define SIM_CLOSED_LOOP_PID 2 /* closed loop, PID body-rate loop, 20-float state */
 
+#define SIM_TYPE_QUADROTOR 0  /* agent types of a parameter group */
+#define SIM_TYPE_CAR 1
+#define SIM_TYPE_FIXED_WING 2
+
 #define SIM_MAX_GROUPS 32 /* parameter groups per handle */
 #define SIM_NTHETA 16     /* differentiable parameters per group */
 
@@ -95,6 +116,11 @@ typedef struct {
   float a_max;                          /* per-axis acceleration clamp m/s^2 (INFINITY = off) */
   float kI[3], kD[3];                   /* PID rate loop: integral (1/rad), derivative (s^2/rad), */
   float xi_max[3];                      /* normalised like krate; integrator limit rad (INFINITY = off) */
+  int32_t type;                         /* SIM_TYPE_*; a car or fixed-wing group reads only g, L (its */
+                                        /* collision radius) and veh */
+  float veh[8];                         /* car: L_w m, tan(delta_max), a_max m/s^2, k_v 1/s, l_min m; */
+                                        /* fixed-wing: b_phi 1/s, phi_max rad, k_chi, b_hd 1/s, */
+                                        /* b_h 1/s^2, b_V 1/s */
 } sim_group_params_t;
 
 typedef struct sim_s* sim_handle_t;
@@ -106,8 +132,10 @@ typedef struct sim_graph_s* sim_graph_t;
  * alive and unchanged); sim_create checks every id once (synchronously) and
  * returns SIM_ERR_GROUP if one is out of range.  mode: SIM_OPEN_LOOP,
  * SIM_CLOSED_LOOP or SIM_CLOSED_LOOP_PID (kI, kD, xi_max are read only in the
- * last; they must be finite, xi_max >= 0, in every mode).  Runs on the current
- * CUDA device. */
+ * last; they must be finite, xi_max >= 0, in every mode).  Groups of car or
+ * fixed-wing type need SIM_CLOSED_LOOP; such a handle steps (sim_step and
+ * the calls built on it, collisions) but has no checkpointed rollout or
+ * adjoint (SIM_ERR_ARG).  Runs on the current CUDA device. */
 int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents, const uint8_t* d_group_id,
                int mode, sim_handle_t* out);
 

@@ -73,6 +73,8 @@ def lib():
         L.oracle_controller_pid.argtypes = [P, P, P, P, P, P]
         L.oracle_vehicle_controller.argtypes = [P, P, P, P]
         L.oracle_vehicle_derivative.argtypes = [P, P, P, P]
+        L.oracle_vehicle_margins.argtypes = [P, ctypes.c_int, P, ctypes.c_int64, P, P, ctypes.c_double,
+                                             ctypes.c_int64, ctypes.c_int, P]
         L.oracle_allocation.argtypes = [P, P, P, P]
         L.oracle_shepperd.argtypes = [P, P]
         L.oracle_count_ops.argtypes = [P, P, P, ctypes.c_double, ctypes.c_int, P]
@@ -291,3 +293,18 @@ def vehicle_derivative(group, x, u):
     if lib().oracle_vehicle_derivative(_p(pg), _p(xx), _p(uu), _p(dx)) != 0:
         raise ValueError("not a car or fixed-wing group")
     return dx
+
+
+def vehicle_margins(groups, gid, x0, cmd, h, nsteps, nthreads=None):
+    """(n,) minimum over the trajectory of pi - |course error| for fixed-wing agents (the atan2
+    jump when the waypoint passes straight behind); inf for cars and quadrotors."""
+    x = _states(x0, CLOSED_LOOP)
+    n = x.shape[0]
+    c = np.ascontiguousarray(np.asarray(cmd, dtype=np.float64))
+    gi = np.ascontiguousarray(np.asarray(gid, dtype=np.int32))
+    pg = pack_groups(groups)
+    out = np.zeros(n)
+    if lib().oracle_vehicle_margins(_p(pg), len(groups), _p(gi), n, _p(x), _p(c), float(h), int(nsteps),
+                                    _threads(nthreads), _p(out)) != 0:
+        raise ValueError("oracle_vehicle_margins rejected its arguments")
+    return out

@@ -94,6 +94,39 @@ int oracle_controller(const double* group, const double* x, const double* cmd, d
   return 0;
 }
 
+// Distance of each car or fixed-wing agent's trajectory from its controller's
+// one discontinuity, minimised over the nsteps step starts: for a fixed-wing
+// drone pi - |course error| (atan2 jumps from +pi to -pi when the waypoint
+// passes straight behind); for a car and a quadrotor +inf (pure pursuit is
+// continuous in the state).  Trajectories that pass within rounding of the
+// jump may take the other branch in another precision.
+int oracle_vehicle_margins(const double* groups, int n_groups, const int32_t* gid, int64_t n, const double* x0,
+                           const double* cmd, double h, int64_t nsteps, int nthreads, double* out) {
+  if (n < 0 || nsteps < 0 || n_groups < 1) return -1;
+  const GroupSet S(groups, n_groups);
+  parallel_for(n, nthreads, [&](int64_t lo, int64_t hi) {
+    for (int64_t a = lo; a < hi; ++a) {
+      const int g = gid ? gid[a] : 0;
+      const Group<double>& P = S.P[g];
+      double m = 1e300;
+      if (P.type == TYPE_FIXED_WING) {
+        double cur[NX], nxt[NX];
+        std::memcpy(cur, x0 + a * NX, sizeof(cur));
+        const double* c = cmd + a * 4;
+        for (int64_t s = 0; s < nsteps; ++s) {
+          const double dx = c[0] - cur[0], dy = c[1] - cur[1];
+          const double cross = cur[6] * dy - cur[7] * dx, dot = cur[6] * dx + cur[7] * dy;
+          m = std::min(m, M_PI - std::fabs(std::atan2(cross, dot)));
+          vehicle_step(P, cur, c, h, nxt);
+          std::memcpy(cur, nxt, sizeof(cur));
+        }
+      }
+      out[a] = m;
+    }
+  });
+  return 0;
+}
+
 // Car or fixed-wing agent: inputs u (3) of its controller at state x (17).
 int oracle_vehicle_controller(const double* group, const double* x, const double* cmd, double* u) {
   const Group<double> P = unpack_group(group);

@@ -15,10 +15,10 @@
 //   acceleration:
 //       p_x' = v c,  p_y' = v s,  v' = a,  (c, s)' = v kappa (-s, c).
 //   Controller (once per step, held over the RK4 stages), command =
-//   (x_c, y_c, -, v_c): d = (x_c - p_x, y_c - p_y); target ahead: kappa =
-//   2 sin(alpha) / max(|d|, l_min) with sin(alpha) = (c d_y - s d_x) / |d|
-//   (pure pursuit aimed at the waypoint); target behind: full lock towards
-//   its side; |kappa| <= tan(delta_max) / L_w; a = clamp(k_v (v_c - v)).
+//   (x_c, y_c, -, v_c): d = (x_c - p_x, y_c - p_y), kappa = 2 sin(alpha) /
+//   max(|d|, l_min) with sin(alpha) = (c d_y - s d_x) / |d| (pure pursuit
+//   aimed at the waypoint, for any bearing: continuous in the state),
+//   |kappa| <= tan(delta_max) / L_w; a = clamp(k_v (v_c - v)).
 //   veh = [L_w, tan(delta_max), a_max, k_v, l_min].
 //
 //   Fixed-wing (type 2): the point-mass guidance model of a fixed-wing drone
@@ -59,12 +59,8 @@ void vehicle_controller(const Group<T>& P, const T x[NX], const double cmd[4], T
     const T dist = sqrt(dx * dx + dy * dy);
     T kappa = T(0.0);
     if (val(dist) > 0.0) {
-      if (val(dot) < 0.0) {
-        kappa = T(val(cross) >= 0.0 ? kmax : -kmax);
-      } else {
-        const T ld = val(dist) > P.veh[4] ? dist : T(P.veh[4]);
-        kappa = clamp_sym(T(2.0) * cross / (dist * ld), kmax);
-      }
+      const T ld = val(dist) > P.veh[4] ? dist : T(P.veh[4]);
+      kappa = clamp_sym(T(2.0) * cross / (dist * ld), kmax);
     }
     u[0] = kappa;
     u[1] = clamp_sym(T(P.veh[3]) * (T(cmd[3]) - x[3]), P.veh[2]);

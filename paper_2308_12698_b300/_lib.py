@@ -16,6 +16,7 @@ SIM_ERR_GROUP = -5
 SIM_OPEN_LOOP = 0
 SIM_CLOSED_LOOP = 1
 SIM_CLOSED_LOOP_PID = 2
+SIM_TYPE_QUADROTOR, SIM_TYPE_CAR, SIM_TYPE_FIXED_WING = 0, 1, 2
 SIM_MAX_GROUPS = 32
 SIM_NTHETA = 16
 SIM_NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -35,7 +36,8 @@ class GroupParams(ctypes.Structure):
                 ("tau_m", ctypes.c_float), ("c_d", ctypes.c_float), ("omega_max", ctypes.c_float),
                 ("g", ctypes.c_float), ("kp", ctypes.c_float * 3), ("kd", ctypes.c_float * 3),
                 ("katt", ctypes.c_float * 3), ("krate", ctypes.c_float * 3), ("a_max", ctypes.c_float),
-                ("kI", ctypes.c_float * 3), ("kD", ctypes.c_float * 3), ("xi_max", ctypes.c_float * 3)]
+                ("kI", ctypes.c_float * 3), ("kD", ctypes.c_float * 3), ("xi_max", ctypes.c_float * 3),
+                ("type", ctypes.c_int32), ("veh", ctypes.c_float * 8)]
 
 
 #: PID rate-loop fields and the values a group without them gets (P loop, no integrator limit).
@@ -50,6 +52,8 @@ def group_struct(g: dict) -> GroupParams:
         getattr(s, k)[:] = [float(v) for v in g[k]]
     for k, d in PID_DEFAULTS.items():
         getattr(s, k)[:] = [float(v) for v in g.get(k, d)]
+    s.type = int(g.get("type", SIM_TYPE_QUADROTOR))
+    s.veh[:] = [float(v) for v in (list(g.get("veh", [])) + [0.0] * 8)[:8]]
     return s
 
 

@@ -59,8 +59,11 @@ struct __align__(16) DevGroup {
   float kic[3], pad5;           // mix_i taumax_i kI_i: rate-error integral -> Omega^2
   float kdc[3], pad6;           // mix_i taumax_i kD_i: angular acceleration -> Omega^2
   float xim[3], pad7;           // integrator limit |xi_i| <= xim_i
+  // agent type (0 quadrotor, 1 car, 2 fixed-wing) and the vehicle model's constants:
+  // car (tan(delta_max)/L_w, a_max, k_v, l_min), fixed-wing (b_phi, phi_max, k_chi, b_hd, b_h, b_V)
+  float vt, vk[6], pad8;
 };
-static_assert(sizeof(DevGroup) == 60 * 4, "DevGroup layout");
+static_assert(sizeof(DevGroup) == 68 * 4, "DevGroup layout");
 
 // Components of an agent's state in a mode: 17, or 20 with the PID integral.
 template <int MODE>

@@ -333,6 +333,15 @@ DevGroup derive(const sim_group_params_t& p) {
     d.kdc[i] = (float)(mix[i] * taumax[i] * p.kD[i]);
     d.xim[i] = p.xi_max[i];
   }
+  d.vt = (float)p.type;
+  if (p.type == SIM_TYPE_CAR) {
+    d.vk[0] = (float)((double)p.veh[1] / p.veh[0]);  // largest curvature tan(delta_max) / L_w
+    d.vk[1] = p.veh[2];
+    d.vk[2] = p.veh[3];
+    d.vk[3] = p.veh[4];
+  } else if (p.type == SIM_TYPE_FIXED_WING) {
+    for (int i = 0; i < 6; ++i) d.vk[i] = p.veh[i];
+  }
   d.a_max = p.a_max;
   d.f0c = (float)(m / (4.0 * kt));
   d.inv_m = (float)(1.0 / m);
@@ -342,7 +351,21 @@ DevGroup derive(const sim_group_params_t& p) {
   return d;
 }
 
+bool valid_vehicle(const sim_group_params_t& p) {
+  if (!std::isfinite(p.g) || !(std::isfinite(p.L) && p.L > 0.f)) return false;
+  const float* v = p.veh;
+  if (p.type == SIM_TYPE_CAR)  // L_w > 0, tan(delta_max), a_max, k_v >= 0, l_min > 0
+    return v[0] > 0.f && std::isfinite(v[0]) && v[1] >= 0.f && std::isfinite(v[1]) && v[2] >= 0.f &&
+           std::isfinite(v[2]) && v[3] >= 0.f && std::isfinite(v[3]) && v[4] > 0.f && std::isfinite(v[4]);
+  // fixed-wing: b_phi > 0, 0 < phi_max < pi/2, k_chi finite, b_hd, b_h, b_V >= 0
+  return v[0] > 0.f && std::isfinite(v[0]) && v[1] > 0.f && v[1] < 1.5707f && std::isfinite(v[2]) &&
+         v[3] >= 0.f && std::isfinite(v[3]) && v[4] >= 0.f && std::isfinite(v[4]) && v[5] >= 0.f &&
+         std::isfinite(v[5]);
+}
+
 bool valid_params(const sim_group_params_t& p) {
+  if (p.type == SIM_TYPE_CAR || p.type == SIM_TYPE_FIXED_WING) return valid_vehicle(p);
+  if (p.type != SIM_TYPE_QUADROTOR) return false;
   const float pos[] = {p.m, p.Jxx, p.Jyy, p.Jzz, p.L, p.kt, p.kq, p.tau_m, p.omega_max};
   for (float v : pos)
     if (!(std::isfinite(v) && v > 0.f)) return false;
@@ -389,6 +412,7 @@ struct sim_s {
   int64_t n = 0;
   int mode = SIM_CLOSED_LOOP;
   int nx = NX;                   // state floats per agent: 17, or 20 in the PID mode
+  bool multi = false;            // some groups are cars or fixed-wing drones
   const uint8_t* gid = nullptr;  // borrowed
   uint8_t* status = nullptr;     // owned
   DevGroup* d_groups = nullptr;  // owned
@@ -421,7 +445,10 @@ size_t group_smem(const sim_s* h) { return hetero(h) ? sizeof(DevGroup) * h->n_g
 int fwd_grid(const sim_s* h, size_t smem, int64_t count) {
   // one resident wave of blocks, grid-stride over the agents
   int occ;
-  if (h->mode == SIM_CLOSED_LOOP_PID)
+  if (h->multi)
+    occ = hetero(h) ? occupancy(step_kernel<1, true, true>, h->block_fwd, smem)
+                    : occupancy(step_kernel<1, false, true>, h->block_fwd, smem);
+  else if (h->mode == SIM_CLOSED_LOOP_PID)
     occ = hetero(h) ? occupancy(step_kernel<2, true>, h->block_fwd, smem)
                     : occupancy(step_kernel<2, false>, h->block_fwd, smem);
   else if (h->mode == SIM_CLOSED_LOOP)
@@ -501,7 +528,10 @@ int launch_step(sim_s* h, float* d_state, const float* d_cmd, StepH H, int K, cu
   const size_t smem = group_smem(h);
   const int grid = fwd_grid(h, smem, count);
   const DevGroup& P0 = h->host_group0;
-  if (h->mode == SIM_CLOSED_LOOP_PID) {
+  if (h->multi) {
+    if (hetero(h)) step_kernel<1, true, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
+    else step_kernel<1, false, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
+  } else if (h->mode == SIM_CLOSED_LOOP_PID) {
     if (hetero(h)) step_kernel<2, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
     else step_kernel<2, false><<<grid, h->block_fwd, smem, st>>>(A, P0);
   } else if (h->mode == SIM_CLOSED_LOOP) {
@@ -582,14 +612,19 @@ int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents,
   if (!groups || n_groups < 1 || n_groups > SIM_MAX_GROUPS || n_agents < 0) return SIM_ERR_ARG;
   if (mode != SIM_OPEN_LOOP && mode != SIM_CLOSED_LOOP && mode != SIM_CLOSED_LOOP_PID) return SIM_ERR_ARG;
   if (n_groups > 1 && !d_group_id && n_agents > 0) return SIM_ERR_ARG;
-  for (int g = 0; g < n_groups; ++g)
+  bool multi = false;
+  for (int g = 0; g < n_groups; ++g) {
     if (!valid_params(groups[g])) return SIM_ERR_ARG;
+    multi = multi || groups[g].type != SIM_TYPE_QUADROTOR;
+  }
+  if (multi && mode != SIM_CLOSED_LOOP) return SIM_ERR_ARG;  // vehicles run closed loop only
   sim_s* h = new (std::nothrow) sim_s();
   if (!h) return SIM_ERR_ARG;
   h->n_groups = n_groups;
   h->n = n_agents;
   h->mode = mode;
   h->nx = mode == SIM_CLOSED_LOOP_PID ? NXP : NX;
+  h->multi = multi;
   h->gid = d_group_id;
   h->host_group0 = derive(groups[0]);
   int rc = SIM_OK;
@@ -648,8 +683,13 @@ int sim_set_params(sim_handle_t h, const sim_group_params_t* groups, int n_group
   DevGroup tbl[SIM_MAX_GROUPS];
   float arm[SIM_MAX_GROUPS];
   float max_arm = 0.f;
+  bool multi = false;
   for (int g = 0; g < n_groups; ++g) {
     if (!valid_params(groups[g])) return SIM_ERR_ARG;
+    multi = multi || groups[g].type != SIM_TYPE_QUADROTOR;
+  }
+  if (multi && h->mode != SIM_CLOSED_LOOP) return SIM_ERR_ARG;
+  for (int g = 0; g < n_groups; ++g) {
     tbl[g] = derive(groups[g]);
     arm[g] = groups[g].L;
     max_arm = std::max(max_arm, arm[g]);
@@ -659,6 +699,7 @@ int sim_set_params(sim_handle_t h, const sim_group_params_t* groups, int n_group
     return SIM_ERR_CUDA;
   h->max_arm = max_arm;
   h->host_group0 = tbl[0];
+  h->multi = multi;
   return SIM_OK;
 }
 
@@ -824,6 +865,7 @@ int sim_run_rounds(sim_handle_t h, float* d_state, float* d_cmd2, const float* h
 int sim_rollout_forward(sim_handle_t h, const float* d_state0, const float* d_cmd, float dt, int64_t nsteps,
                         int ckpt_C, float* d_ckpt, float* d_run_cost, void* stream) {
   if (!h || nsteps < 1 || ckpt_C < 0 || !(dt > 0.f) || !std::isfinite(dt)) return SIM_ERR_ARG;
+  if (h->multi) return SIM_ERR_ARG;  // rollouts and the adjoint cover quadrotor groups
   if (h->n == 0) return SIM_OK;
   if (!d_state0 || !d_cmd || !d_ckpt || !aligned16(d_state0) || !aligned16(d_cmd) || !aligned16(d_ckpt))
     return SIM_ERR_ARG;
@@ -871,7 +913,7 @@ int sim_rollout_backward(sim_handle_t h, const float* d_ckpt, const float* d_cmd
                          float* d_dL_dtheta, float* d_dL_dtheta_agent, void* d_workspace, size_t ws_bytes,
                          void* stream) {
   if (!h || nsteps < 1 || ckpt_C < 0 || !(dt > 0.f) || !std::isfinite(dt)) return SIM_ERR_ARG;
-  if (!d_dL_dtheta) return SIM_ERR_ARG;
+  if (!d_dL_dtheta || h->multi) return SIM_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (h->n == 0) {
     return cudaMemsetAsync(d_dL_dtheta, 0, sizeof(float) * h->n_groups * NTH, st) == cudaSuccess ? SIM_OK
@@ -953,7 +995,7 @@ int sim_rollout_backward_noalloc(sim_handle_t h, const float* d_ckpt, const floa
                                  int ckpt_C, const float* d_dL_dxT, const float* d_w_run, float* d_dL_dx0,
                                  float* d_dL_dtheta, float* d_dL_dtheta_agent, void* stream) {
   if (!h || nsteps < 1 || ckpt_C < 0 || !(dt > 0.f) || !std::isfinite(dt)) return SIM_ERR_ARG;
-  if (!d_dL_dtheta) return SIM_ERR_ARG;
+  if (!d_dL_dtheta || h->multi) return SIM_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (h->n == 0) {
     return cudaMemsetAsync(d_dL_dtheta, 0, sizeof(float) * h->n_groups * NTH, st) == cudaSuccess ? SIM_OK

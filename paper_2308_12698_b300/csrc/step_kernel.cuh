@@ -6,6 +6,7 @@
 // non-finite keeps its last finite state and is marked (status 1).
 #pragma once
 #include "model_fwd.cuh"
+#include "vehicles.cuh"
 
 namespace qs {
 
@@ -42,7 +43,9 @@ __device__ __forceinline__ void load_groups(DevGroup* sg, const DevGroup* src, i
 }
 
 // K fused RK4 steps per launch; the state touches HBM once per launch.
-template <int MODE, bool HETERO>
+// MULTI: some groups are cars or fixed-wing drones (closed loop only); each
+// agent runs its group's model.
+template <int MODE, bool HETERO, bool MULTI = false>
 __global__ void __launch_bounds__(256) step_kernel(StepArgs A, const DevGroup P0) {
   extern __shared__ float4 smem4[];
   DevGroup* sg = reinterpret_cast<DevGroup*>(smem4);
@@ -55,7 +58,10 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs A, const DevGroup P0
     load_state<state_dim<MODE>()>(A.state, A.n, i, x);
     const float4 c = A.cmd[i];
     const Hd hd = heading(MODE != 0 ? c.w : 0.f);
-    if (HETERO) {
+    if (MULTI && (HETERO ? sg[A.gid[i]].vt : P0.vt) != (float)TYPE_QUAD) {
+      const DevGroup& P = HETERO ? sg[A.gid[i]] : P0;
+      for (int k = 0; k < A.K; ++k) vehicle_step(P, x, c, A.H);
+    } else if (HETERO) {
       const DevGroup P = sg[A.gid[i]];
       const LagCoef L = lag_coef(P.inv_tau, A.H);
       for (int k = 0; k < A.K; ++k) step<MODE>(P, x, c, hd, A.H, L);

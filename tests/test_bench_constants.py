@@ -43,3 +43,15 @@ def test_pid_flops_per_agent_step_is_the_checkers_count(orc):
         counts.append(sum(c[k] - d[k] for k in ("add", "mul", "div", "sqrt")))
     assert bench.FLOPS_PER_AGENT_STEP_PID <= min(counts) <= 1.01 * bench.FLOPS_PER_AGENT_STEP_PID, (min(counts),)
     assert max(counts) <= 1.03 * bench.FLOPS_PER_AGENT_STEP_PID
+
+
+def test_vehicle_flops_per_agent_step_are_the_checkers_count(orc):
+    wl = W.multi_type(sizes=(0, 2000, 2000))
+    for kind, const in ((W.TYPE_CAR, bench.FLOPS_PER_AGENT_STEP_CAR),
+                        (W.TYPE_FIXED_WING, bench.FLOPS_PER_AGENT_STEP_FIXED_WING)):
+        counts = []
+        for a in np.flatnonzero(wl.gid == kind)[::16]:
+            c = orc.count_ops(wl.groups[kind], wl.x0[a].astype(np.float64), wl.cmd[a], wl.dt, W.CLOSED_LOOP)
+            counts.append(c["add"] + c["mul"] + c["div"] + c["sqrt"])
+        assert const <= min(counts) <= 1.01 * const, (kind, min(counts))
+        assert max(counts) <= 1.05 * const

@@ -1,0 +1,128 @@
+"""Cars and fixed-wing drones beside quadrotors in one launch, on the GPU through the C ABI,
+against the FP64 checker.
+
+Tolerances: one step, 1e-5 relative with floor 1 per component.  n steps: position 1e-3 m plus
+n half-ulps of FP32 at its magnitude, n 2^-24 |p| (a drone 300 m out adds its 2 cm per step to
+a position whose ulp is 3e-5 m, and the roundings can pile up over the steps), heading angle
+1e-4 rad, speed 1e-4 relative, climb rate 1e-3 m/s, bank 1e-4 rad.  Quadrotors in the same
+launch keep their own bars.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2308_12698_b300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch.device("cuda:0")
+
+
+def gpu_run(wl, dev, nsteps, K=0, x0=None, groups=None, block=0):
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    groups = wl.groups if groups is None else groups
+    g = torch.from_numpy(wl.gid).to(dev) if len(groups) > 1 else None
+    sim = Sim(groups, wl.n, wl.mode, gid=g)
+    if block:
+        sim.set_launch(block=block)
+    x = planar(torch.from_numpy(wl.x0 if x0 is None else x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    sim.step(x, cmd, wl.dt, nsteps, K=K)
+    torch.cuda.synchronize()
+    out = unplanar(x, wl.n).cpu().numpy()
+    sim.close()
+    return out
+
+
+def ref_run(orc, wl, nsteps, x0=None):
+    return orc.rollout(wl.groups, wl.gid, wl.x0 if x0 is None else x0, wl.cmd, wl.dt, nsteps, wl.mode)
+
+
+def check_vehicles(got, ref, nsteps):
+    got = got.astype(np.float64)
+    dp = np.abs(got[:, 0:3] - ref[:, 0:3]).max(axis=1)
+    tol = 1e-3 + nsteps * 2.0 ** -24 * np.abs(ref[:, 0:3]).max(axis=1)
+    assert (dp <= tol).all(), (dp.max(), (dp / tol).max())
+    ang = np.abs(np.arctan2(got[:, 7] * ref[:, 6] - got[:, 6] * ref[:, 7], got[:, 6] * ref[:, 6] + got[:, 7] * ref[:, 7]))
+    assert ang.max() <= 1e-4, ang.max()
+    assert (np.abs(got[:, 3] - ref[:, 3]) <= 1e-4 * np.maximum(np.abs(ref[:, 3]), 1.0)).all()
+    assert np.abs(got[:, 10] - ref[:, 10]).max() <= 1e-4
+    assert np.abs(got[:, 5] - ref[:, 5]).max() <= 1e-3
+
+
+def check_quads(got, ref):
+    perr = np.abs(got[:, 0:3].astype(np.float64) - ref[:, 0:3]).max()
+    qa = got[:, 6:10] / np.linalg.norm(got[:, 6:10], axis=1, keepdims=True)
+    qb = ref[:, 6:10] / np.linalg.norm(ref[:, 6:10], axis=1, keepdims=True)
+    aerr = (2 * np.arccos(np.clip(np.abs((qa * qb).sum(axis=1)), 0, 1))).max()
+    assert perr <= 1e-3 and aerr <= 1e-3, (perr, aerr)
+
+
+@pytest.mark.parametrize("kind", [W.TYPE_CAR, W.TYPE_FIXED_WING])
+def test_vehicle_one_step(dev, orc, kind):
+    sizes = (0, 4097, 0) if kind == W.TYPE_CAR else (0, 0, 4097)
+    wl = W.multi_type(sizes=sizes)
+    g = wl.groups[kind]
+    one = W.Workload("one", W.CLOSED_LOOP, [g], np.zeros(wl.n, np.uint8), wl.x0, wl.cmd, wl.dt, 1)
+    got, ref = gpu_run(one, dev, 1, K=1), ref_run(orc, one, 1)
+    tol = 1e-5 * np.maximum(np.abs(ref), 1.0)
+    assert (np.abs(got.astype(np.float64) - ref) <= tol).all(), (np.abs(got - ref) / tol).max()
+
+
+@pytest.mark.parametrize("shuffle", [False, True])
+def test_mixed_swarm_1000_steps(dev, orc, shuffle):
+    """Every car, every quadrotor and every drone whose course error stays 1e-3 rad away from
+    the atan2 jump at +-pi (waypoint straight behind) meets the bars."""
+    wl = W.multi_type(sizes=(3000, 3000, 3000), shuffle=shuffle)
+    got, ref = gpu_run(wl, dev, 1000, K=100), ref_run(orc, wl, 1000)
+    q = wl.gid == W.TYPE_QUAD
+    check_quads(got[q], ref[q])
+    m = orc.vehicle_margins(wl.groups, wl.gid, wl.x0, wl.cmd, wl.dt, 1000)
+    ok = ~q & (m > 1e-3)
+    assert ok.sum() >= 5900, ok.sum()
+    check_vehicles(got[ok], ref[ok], 1000)
+
+
+def test_mixed_launch_is_bitwise_each_group_alone(dev):
+    wl = W.multi_type(sizes=(700, 900, 1100), shuffle=True)
+    both = gpu_run(wl, dev, 200, K=200)
+    for gi in range(3):
+        idx = np.flatnonzero(wl.gid == gi)
+        one = W.Workload("one", W.CLOSED_LOOP, [wl.groups[gi]], np.zeros(idx.size, np.uint8),
+                         np.ascontiguousarray(wl.x0[idx]), np.ascontiguousarray(wl.cmd[idx]), wl.dt, 200)
+        np.testing.assert_array_equal(both[idx], gpu_run(one, dev, 200, K=200))
+
+
+def test_mixed_fused_is_bitwise_plain(dev):
+    wl = W.multi_type(sizes=(500, 500, 501), shuffle=True)
+    a = gpu_run(wl, dev, 60, K=1)
+    np.testing.assert_array_equal(a, gpu_run(wl, dev, 60, K=60))
+    np.testing.assert_array_equal(a, gpu_run(wl, dev, 60, K=7, block=64))
+
+
+def test_vehicle_handles_refuse_rollouts_and_open_loop(dev):
+    from paper_2308_12698_b300 import _lib
+    from paper_2308_12698_b300.sim import Sim
+    wl = W.multi_type(sizes=(10, 10, 10))
+    gid = torch.from_numpy(wl.gid).to(dev)
+    with pytest.raises(_lib.SimError):
+        Sim(wl.groups, wl.n, W.OPEN_LOOP, gid=gid)
+    with pytest.raises(_lib.SimError):
+        Sim(wl.groups, wl.n, W.CLOSED_LOOP_PID, gid=gid)
+    sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
+    x = torch.zeros(17 * wl.n, device=dev)
+    c = torch.zeros(4 * wl.n, device=dev)
+    ck = torch.zeros(2 * 17 * wl.n, device=dev)
+    rc = _lib.lib().sim_rollout_forward(sim.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(c.data_ptr()),
+                                        1e-3, 10, 10, ctypes.c_void_p(ck.data_ptr()), None, None)
+    assert rc == _lib.SIM_ERR_ARG
+    sim.close()

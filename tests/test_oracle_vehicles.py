@@ -65,26 +65,28 @@ def test_car_speed_response(orc):
 
 
 def test_car_full_lock_circle(orc):
-    """Waypoint far behind: full lock towards its side, kappa = tan(delta_max)/L_w, so at
-    constant speed the car runs on a circle of radius 1/kappa and turns by v kappa t."""
+    """Waypoint 3 m to the left: the pursuit curvature 2 sin(alpha) / l_min exceeds the steering
+    limit all the way round, so kappa = tan(delta_max)/L_w and at constant speed the car runs on
+    a circle of radius 1/kappa, turning by v kappa t."""
     g = W.car_group()
     Lw, tmax = g["veh"][0], g["veh"][1]
     kappa = tmax / Lw
     v = 6.0
     x0 = _car_state(v=v)
-    cmd = (-1e5, 10.0, 0.0, v)  # behind, slightly to the left
-    t = 0.5 * (math.pi / 2) / (v * kappa)  # turn by pi/4: the waypoint stays behind
-    n = int(round(t / 1e-3))
+    cmd = (0.0, 3.0, 0.0, v)
+    n = 3000
     x = _run(orc, g, x0, cmd, 1e-3, n)
-    ang = v * kappa * n * 1e-3
+    ang = v * kappa * n * 1e-3  # about 4.7 rad: most of a lap
     np.testing.assert_allclose(x[0:2], [math.sin(ang) / kappa, (1 - math.cos(ang)) / kappa], rtol=0, atol=1e-10)
     np.testing.assert_allclose(x[6:8], [math.cos(ang), math.sin(ang)], rtol=0, atol=1e-12)
+    assert orc.vehicle_controller(g, x, cmd)[0] == pytest.approx(kappa, rel=1e-15)  # still saturated
 
 
-@pytest.mark.parametrize("bearing,dist", [(0.3, 40.0), (-0.7, 12.0), (1.2, 3.0), (0.2, 3.0)])
+@pytest.mark.parametrize("bearing,dist", [(0.3, 40.0), (-0.7, 12.0), (1.2, 3.0), (0.2, 3.0), (2.8, 60.0),
+                                          (-3.0, 25.0)])
 def test_car_pure_pursuit_by_hand(orc, bearing, dist):
-    """Target ahead at bearing alpha and distance d: kappa = 2 sin(alpha) / max(d, l_min),
-    clamped to tan(delta_max)/L_w; a = clamp(k_v (v_c - v), +-a_max)."""
+    """Target at bearing alpha (ahead or behind) and distance d: kappa = 2 sin(alpha) /
+    max(d, l_min), clamped to tan(delta_max)/L_w; a = clamp(k_v (v_c - v), +-a_max)."""
     g = W.car_group()
     Lw, tmax, amax, kv, lmin = g["veh"][:5]
     psi = 0.4
@@ -190,3 +192,20 @@ def test_vehicle_types_only_in_the_closed_loop(orc):
         orc.rollout([g], [0], np.zeros((1, 17)), np.zeros((1, 4)), 1e-3, 1, W.OPEN_LOOP)
     with pytest.raises(ValueError):
         orc.grad([g], [0], np.zeros((1, 17)), np.zeros((1, 4)), 1e-3, 1, CL, np.zeros((1, 3)), 0.0)
+
+
+def test_vehicle_margins(orc):
+    """The course-error jump margin over one step start: 0 for a drone whose waypoint is
+    straight behind, pi - |bearing| otherwise, and inf for cars and quadrotors; over more steps
+    the minimum along the trajectory."""
+    gq, gc, gf = W.base_group(), W.car_group(), W.fixed_wing_group()
+    x = np.stack([_fw_state(), _fw_state(), _car_state(v=5.0), np.zeros(17)])
+    x[3, 6] = 1.0
+    cmd = np.array([[-500.0, 0.0, 100.0, 20.0], [100.0, 300.0, 100.0, 20.0], [-50.0, 1e-9, 0.0, 5.0],
+                    [1.0, 1.0, 1.0, 0.0]])
+    m = orc.vehicle_margins([gq, gc, gf], [2, 2, 1, 0], x, cmd, 1e-3, 1)
+    assert m[0] == 0.0
+    np.testing.assert_allclose(m[1], math.pi - math.atan2(300.0, 100.0), rtol=1e-12)
+    assert m[2] > 1e299 and m[3] > 1e299
+    m50 = orc.vehicle_margins([gq, gc, gf], [2, 2, 1, 0], x, cmd, 1e-3, 50)
+    assert m50[0] == 0.0 and m50[1] <= m[1]
