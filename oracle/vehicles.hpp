@@ -53,7 +53,7 @@ template <class T>
 void vehicle_controller(const Group<T>& P, const T x[NX], const double cmd[4], T u[3]) {
   const T dx = T(cmd[0]) - x[0], dy = T(cmd[1]) - x[1];
   const T c = x[6], s = x[7];
-  const T cross = c * dy - s * dx, dot = c * dx + s * dy;
+  const T cross = c * dy - s * dx;
   if (P.type == TYPE_CAR) {
     const double Lw = P.veh[0], kmax = P.veh[1] / Lw;
     const T dist = sqrt(dx * dx + dy * dy);
@@ -66,6 +66,7 @@ void vehicle_controller(const Group<T>& P, const T x[NX], const double cmd[4], T
     u[1] = clamp_sym(T(P.veh[3]) * (T(cmd[3]) - x[3]), P.veh[2]);
     u[2] = T(0.0);
   } else {
+    const T dot = c * dx + s * dy;
     const T err = (val(cross) == 0.0 && val(dot) == 0.0) ? T(0.0) : atan2(cross, dot);
     u[0] = clamp_sym(T(P.veh[2]) * err, P.veh[1]);
     u[1] = T(cmd[2]);
