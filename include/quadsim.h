@@ -139,7 +139,10 @@ typedef struct sim_graph_s* sim_graph_t;
 int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents, const uint8_t* d_group_id,
                int mode, sim_handle_t* out);
 
-/* Replace the parameter groups (same count).  Synchronous. */
+/* Replace the parameter groups (same count; vehicle types need the handle's
+ * mode to be SIM_CLOSED_LOOP).  Synchronous.  CUDA graphs captured before
+ * keep the kernels and the single-group parameters they captured: capture
+ * them again after this call. */
 int sim_set_params(sim_handle_t h, const sim_group_params_t* groups, int n_groups);
 
 /* Advance every live agent nsteps RK4 steps of length dt, in place.
