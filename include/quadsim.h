@@ -159,7 +159,8 @@ int sim_step(sim_handle_t h, float* d_state, const float* d_cmd, float dt, int64
  * device-to-host copies run on library-owned streams, so copies overlap
  * compute; the call is ordered after earlier work on `stream`.  Host buffers
  * should be pinned for the copies to be asynchronous.  Not capturable in a
- * CUDA graph (it waits). */
+ * CUDA graph (it waits).  On SIM_ERR_TIMEOUT the copies may still be running:
+ * keep every buffer alive until `stream` is idle. */
 int sim_step_host(sim_handle_t h, float* h_state, const float* h_cmd, float* d_state, float* d_cmd, float dt,
                   int64_t nsteps, int substeps_K, void* stream);
 
@@ -174,7 +175,9 @@ int sim_step_host(sim_handle_t h, float* h_state, const float* h_cmd, float* d_s
  * NULL with h_obs NULL) and copied to h_obs + r * 4 N on another copy stream
  * while round r + 1 runs.  d_state is updated in place.  The call is ordered
  * after earlier work on `stream` and returns when the last round and its
- * observations are done (bounded wait).  Not capturable (it waits). */
+ * observations are done (bounded wait).  Not capturable (it waits).  On
+ * SIM_ERR_TIMEOUT the copies may still be running: keep every buffer alive
+ * until `stream` is idle. */
 int sim_run_rounds(sim_handle_t h, float* d_state, float* d_cmd2, const float* h_cmds, float* d_obs2, float* h_obs,
                    float dt, int64_t steps_per_round, int64_t rounds, int substeps_K, void* stream);
 

@@ -418,6 +418,7 @@ struct sim_s {
   DevGroup* d_groups = nullptr;  // owned
   float* d_arm = nullptr;        // owned: arm length per group (collision radius)
   unsigned long long* d_count = nullptr;  // owned: counter for sim_status
+  unsigned long long* h_count = nullptr;  // owned, pinned: its host copy (outlives a timed-out wait)
   float max_arm = 0.f;
   DevGroup host_group0;
   // host-buffer pipeline (sim_step_host): created on first use
@@ -457,7 +458,7 @@ int fwd_grid(const sim_s* h, size_t smem, int64_t count) {
   else
     occ = hetero(h) ? occupancy(step_kernel<0, true>, h->block_fwd, smem)
                     : occupancy(step_kernel<0, false>, h->block_fwd, smem);
-  const int64_t need = (h->n + h->block_fwd - 1) / h->block_fwd;
+  const int64_t need = (count + h->block_fwd - 1) / h->block_fwd;
   return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)occ * h->sms));
 }
 
@@ -641,6 +642,7 @@ int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents,
       cudaMemcpy(h->d_groups, tbl, sizeof(DevGroup) * n_groups, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMalloc(&h->d_arm, sizeof(float) * n_groups) != cudaSuccess ||
       cudaMalloc(&h->d_count, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMallocHost(&h->h_count, sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemcpy(h->d_arm, arm, sizeof(float) * n_groups, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMalloc(&h->status, std::max<int64_t>(n_agents, 1)) != cudaSuccess ||
       cudaMemset(h->status, 0, std::max<int64_t>(n_agents, 1)) != cudaSuccess) {
@@ -1109,14 +1111,15 @@ int sim_status(sim_handle_t h, int64_t* n_dead, int timeout_ms, void* stream) {
   *n_dead = 0;
   if (h->n == 0) return SIM_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  unsigned long long v = 0;
-  if (cudaMemsetAsync(h->d_count, 0, sizeof(v), st) != cudaSuccess) return SIM_ERR_CUDA;
+  // the count lands in the handle's pinned word: a copy still in flight after
+  // a timed-out wait writes there, not into a dead stack frame
+  if (cudaMemsetAsync(h->d_count, 0, sizeof(unsigned long long), st) != cudaSuccess) return SIM_ERR_CUDA;
   count_dead_kernel<<<std::min<int64_t>((h->n + 255) / 256, 4096), 256, 0, st>>>(h->status, h->n, h->d_count);
   if (cudaGetLastError() != cudaSuccess ||
-      cudaMemcpyAsync(&v, h->d_count, sizeof(v), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      cudaMemcpyAsync(h->h_count, h->d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return SIM_ERR_CUDA;
   const int rc = wait_stream(st, timeout_ms);
-  if (rc == SIM_OK) *n_dead = (int64_t)v;
+  if (rc == SIM_OK) *n_dead = (int64_t)*h->h_count;
   return rc;
 }
 
@@ -1183,6 +1186,7 @@ void sim_destroy(sim_handle_t h) {
   if (h->d_groups) cudaFree(h->d_groups);
   if (h->d_arm) cudaFree(h->d_arm);
   if (h->d_count) cudaFree(h->d_count);
+  if (h->h_count) cudaFreeHost(h->h_count);
   delete h;
 }
 
