@@ -230,3 +230,12 @@ def test_pid_adjoint_shared_and_global_scratch_agree(dev):
     b = pid_grads(wl, dev, C=40)
     np.testing.assert_array_equal(a[0], b[0])
     np.testing.assert_array_equal(a[2], b[2])
+
+
+def test_pid_empty_swarm(dev):
+    from paper_2308_12698_b300.sim import Sim
+    sim = Sim([W.pid_group()], 0, W.CLOSED_LOOP_PID)
+    x = torch.zeros(0, device=dev)
+    sim.step(x, torch.zeros(0, device=dev), 1e-3, 10)
+    assert sim.n_dead() == 0
+    sim.close()

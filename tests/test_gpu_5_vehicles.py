@@ -126,3 +126,52 @@ def test_vehicle_handles_refuse_rollouts_and_open_loop(dev):
                                         1e-3, 10, 10, ctypes.c_void_p(ck.data_ptr()), None, None)
     assert rc == _lib.SIM_ERR_ARG
     sim.close()
+
+
+def test_vehicle_parameter_checks(dev):
+    from paper_2308_12698_b300 import _lib
+    from paper_2308_12698_b300.sim import Sim
+    for bad in (dict(W.car_group(), veh=[0.0, 0.7, 3.0, 1.0, 5.0, 0, 0, 0]),        # wheelbase 0
+                dict(W.fixed_wing_group(), veh=[3.0, 1.6, 1.5, 2.0, 1.0, 0.5, 0, 0]),  # bank limit >= pi/2
+                dict(W.car_group(), type=7)):                                        # unknown type
+        with pytest.raises(_lib.SimError):
+            Sim([bad], 4, W.CLOSED_LOOP)
+
+
+def test_stalled_drone_is_frozen_and_counted(dev):
+    """A drone at zero airspeed divides by zero in g tan(phi) / V: it is marked dead and kept at
+    its last finite state; the cars and quadrotors of the launch step on."""
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    wl = W.multi_type(sizes=(64, 64, 64))
+    x0 = wl.x0.copy()
+    bad = int(np.flatnonzero(wl.gid == W.TYPE_FIXED_WING)[5])
+    x0[bad, 3] = 0.0
+    x0[bad, 10] = 0.3
+    sim = Sim(wl.groups, wl.n, wl.mode, gid=torch.from_numpy(wl.gid).to(dev))
+    x = planar(torch.from_numpy(x0)).to(dev)
+    sim.step(x, torch.from_numpy(wl.cmd).to(dev).reshape(-1), wl.dt, 50, K=10)
+    assert sim.n_dead() == 1
+    st = sim.status().cpu().numpy()
+    assert st[bad] == 1 and (np.delete(st, bad) == 0).all()
+    got = unplanar(x, wl.n).cpu().numpy()
+    np.testing.assert_array_equal(got[bad], x0[bad])
+    assert np.isfinite(got).all()
+    sim.close()
+
+
+def test_mixed_swarm_collisions(dev, orc):
+    """Collision detection over quadrotors, cars and drones: each group's L is its radius."""
+    from paper_2308_12698_b300.sim import Sim, planar
+    wl = W.multi_type(sizes=(300, 300, 300), shuffle=True)
+    x0 = wl.x0.copy()
+    x0[:, 0:3] = np.random.default_rng(11).uniform(-6.0, 6.0, (wl.n, 3)).astype(np.float32)
+    groups = [dict(g, L=r) for g, r in zip(wl.groups, (0.225, 1.5, 0.9))]
+    sim = Sim(groups, wl.n, wl.mode, gid=torch.from_numpy(wl.gid).to(dev))
+    x = planar(torch.from_numpy(x0)).to(dev)
+    sim.collide(x, radius_scale=1.0)
+    got = (sim.status().cpu().numpy() == 2).astype(np.uint8)
+    radius = np.array([0.225, 1.5, 0.9], np.float32)[wl.gid]
+    ref = orc.collisions(x0[:, 0:3], radius, np.ones(wl.n, np.uint8))
+    np.testing.assert_array_equal(got, ref)
+    assert 0 < ref.sum() < wl.n
+    sim.close()
