@@ -256,8 +256,9 @@ def test_autograd_function(dev):
 
 
 def test_shared_and_global_scratch_agree(dev):
-    """C = 8 keeps the segment in shared memory, C = 40 in the global workspace: the same
-    checkpointed states and per-step arithmetic, so per-agent gradients are bitwise equal."""
+    """C = 8 keeps the segment in shared memory, C = 40 in the global workspace, C = 1 needs no
+    scratch at all: the same checkpointed or recomputed states and per-step arithmetic, so
+    per-agent gradients are bitwise equal."""
     from paper_2308_12698_b300.sim import Sim, planar
     wl = W.differentiable(n_per_group=500, n_groups=3, nsteps=240)
     gid = torch.from_numpy(wl.gid).to(dev)
@@ -268,14 +269,14 @@ def test_shared_and_global_scratch_agree(dev):
     gT[: 3 * wl.n] = 1.0
     w = torch.full((wl.n,), wl.w_omega, device=dev)
     out = {}
-    for C in (8, 40):
+    for C in (1, 8, 40):
         ckpt, _ = sim.rollout_forward(x0, cmd, wl.dt, wl.nsteps, C=C)
         assert sim.workspace_bytes(C) > 0
         out[C] = sim.rollout_backward(ckpt, cmd, wl.dt, wl.nsteps, gT, w, C=C, per_agent=True)
     torch.cuda.synchronize()
     assert sim.workspace_bytes(8) < sim.workspace_bytes(40)  # no global scratch for C = 8
-    assert torch.equal(out[8][0], out[40][0])
-    assert torch.equal(out[8][2], out[40][2])
+    assert torch.equal(out[8][0], out[40][0]) and torch.equal(out[1][0], out[40][0])
+    assert torch.equal(out[8][2], out[40][2]) and torch.equal(out[1][2], out[40][2])
     np.testing.assert_allclose(out[8][1].cpu().numpy(), out[40][1].cpu().numpy(), rtol=1e-5,
                                atol=1e-6 * out[40][1].abs().max().item())
     sim.close()
