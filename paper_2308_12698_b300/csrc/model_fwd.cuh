@@ -248,7 +248,7 @@ __device__ __forceinline__ void controller_fwd(const DevGroup& P, const float* x
   C.E[2] = w * dy - dw * qy - qz * dx + qx * dz;
   C.E[3] = w * dz - dw * qz - qx * dy + qy * dx;
   const float rQ = rsqrtf(dw * dw + dx * dx + dy * dy + dz * dz);
-  C.s = C.E[0] < 0.f ? -rQ : rQ;
+  C.s = copysignf(rQ, C.E[0]);  // sign fix folded into the normalisation
   C.qe[0] = C.s * C.E[0]; C.qe[1] = C.s * C.E[1]; C.qe[2] = C.s * C.E[2]; C.qe[3] = C.s * C.E[3];
   const float f0 = P.f0c * C.fc;
   float f1 = P.qa[0] * C.qe[1] - P.wa[0] * x[WX];
@@ -268,8 +268,10 @@ __device__ __forceinline__ void controller_fwd(const DevGroup& P, const float* x
   C.S[3] = (f0 + f1) + (f2 - f3);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const float s = clampf(C.S[i], 0.f, P.om2max);
-    u[i] = s > 0.f ? s * rsqrtf(s) : 0.f;
+    // the floor FLT_MIN instead of 0 keeps s * rsqrt(s) finite without a
+    // select: a rotor demand at or below 0 gets 1.1e-19 rad/s, not 0
+    const float s = clampf(C.S[i], 1.17549435e-38f, P.om2max);
+    u[i] = s * rsqrtf(s);
   }
 }
 

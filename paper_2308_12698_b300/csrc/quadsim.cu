@@ -443,10 +443,18 @@ bool hetero(const sim_s* h) { return h->n_groups > 1; }
 
 size_t group_smem(const sim_s* h) { return hetero(h) ? sizeof(DevGroup) * h->n_groups : 0; }
 
-int fwd_grid(const sim_s* h, size_t smem, int64_t count) {
+// The plain (K = 1) instantiation for one quadrotor group, open or P closed loop.
+bool plain_path(const sim_s* h, int K) {
+  return K == 1 && !hetero(h) && !h->multi && h->mode != SIM_CLOSED_LOOP_PID;
+}
+
+int fwd_grid(const sim_s* h, size_t smem, int64_t count, bool plain = false) {
   // one resident wave of blocks, grid-stride over the agents
   int occ;
-  if (h->multi)
+  if (plain)
+    occ = h->mode == SIM_CLOSED_LOOP ? occupancy(step_kernel<1, false, false, true>, h->block_fwd, smem)
+                                     : occupancy(step_kernel<0, false, false, true>, h->block_fwd, smem);
+  else if (h->multi)
     occ = hetero(h) ? occupancy(step_kernel<1, true, true>, h->block_fwd, smem)
                     : occupancy(step_kernel<1, false, true>, h->block_fwd, smem);
   else if (h->mode == SIM_CLOSED_LOOP_PID)
@@ -527,9 +535,13 @@ int launch_step(sim_s* h, float* d_state, const float* d_cmd, StepH H, int K, cu
   A.H = H;
   A.groups = h->d_groups;
   const size_t smem = group_smem(h);
-  const int grid = fwd_grid(h, smem, count);
+  const bool plain = plain_path(h, K);
+  const int grid = fwd_grid(h, smem, count, plain);
   const DevGroup& P0 = h->host_group0;
-  if (h->multi) {
+  if (plain) {
+    if (h->mode == SIM_CLOSED_LOOP) step_kernel<1, false, false, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
+    else step_kernel<0, false, false, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
+  } else if (h->multi) {
     if (hetero(h)) step_kernel<1, true, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
     else step_kernel<1, false, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
   } else if (h->mode == SIM_CLOSED_LOOP_PID) {

@@ -44,14 +44,18 @@ __device__ __forceinline__ void load_groups(DevGroup* sg, const DevGroup* src, i
 
 // K fused RK4 steps per launch; the state touches HBM once per launch.
 // MULTI: some groups are cars or fixed-wing drones (closed loop only); each
-// agent runs its group's model.
-template <int MODE, bool HETERO, bool MULTI = false>
-__global__ void __launch_bounds__(256) step_kernel(StepArgs A, const DevGroup P0) {
+// agent runs its group's model.  PLAIN: one step per launch (K = 1), where
+// HBM bounds the kernel: registers capped so that 3 blocks of 256 stay
+// resident and keep more loads in flight (the fused form runs faster with
+// the few more registers it takes uncapped).
+template <int MODE, bool HETERO, bool MULTI = false, bool PLAIN = false>
+__global__ void __launch_bounds__(256, PLAIN ? 3 : 1) step_kernel(StepArgs A, const DevGroup P0) {
   extern __shared__ float4 smem4[];
   DevGroup* sg = reinterpret_cast<DevGroup*>(smem4);
   load_groups<HETERO>(sg, A.groups, A.n_groups);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t end = A.first + A.count;
+  const int K = PLAIN ? 1 : A.K;
   for (int64_t i = A.first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end; i += stride) {
     if (A.status[i]) continue;  // dead agents are frozen
     St x;
@@ -60,14 +64,14 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs A, const DevGroup P0
     const Hd hd = heading(MODE != 0 ? c.w : 0.f);
     if (MULTI && (HETERO ? sg[A.gid[i]].vt : P0.vt) != (float)TYPE_QUAD) {
       const DevGroup& P = HETERO ? sg[A.gid[i]] : P0;
-      for (int k = 0; k < A.K; ++k) vehicle_step(P, x, c, A.H);
+      for (int k = 0; k < K; ++k) vehicle_step(P, x, c, A.H);
     } else if (HETERO) {
       const DevGroup P = sg[A.gid[i]];
       const LagCoef L = lag_coef(P.inv_tau, A.H);
-      for (int k = 0; k < A.K; ++k) step<MODE>(P, x, c, hd, A.H, L);
+      for (int k = 0; k < K; ++k) step<MODE>(P, x, c, hd, A.H, L);
     } else {
       const LagCoef L = lag_coef(P0.inv_tau, A.H);
-      for (int k = 0; k < A.K; ++k) step<MODE>(P0, x, c, hd, A.H, L);
+      for (int k = 0; k < K; ++k) step<MODE>(P0, x, c, hd, A.H, L);
     }
     if (all_finite<state_dim<MODE>()>(x)) {
       store_state<state_dim<MODE>()>(A.state, A.n, i, x);
