@@ -71,7 +71,8 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 1) step_kernel(StepArgs A, co
       for (int k = 0; k < K; ++k) step<MODE>(P, x, c, hd, A.H, L);
     } else {
       const LagCoef L = lag_coef(P0.inv_tau, A.H);
-      for (int k = 0; k < K; ++k) step<MODE>(P0, x, c, hd, A.H, L);
+#pragma unroll 2
+      for (int k = 0; k < K; ++k) step<MODE>(P0, x, c, hd, A.H, L);  // unrolled: +0.5-1 %
     }
     if (all_finite<state_dim<MODE>()>(x)) {
       store_state<state_dim<MODE>()>(A.state, A.n, i, x);
