@@ -760,7 +760,8 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     cs.close()
     del cx, cws
 
-    # scale sweep 1e3 .. 1e7 agents, 1000 closed-loop steps: plain K = 1 and fused (tuned K)
+    # scale sweep 1e3 .. 1e7 agents, 1000 closed-loop steps: plain K = 1, fused K = 10 and 100,
+    # and fused at the tuned K
     sweep = []
     peak_tflops = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     hbm = measured_peaks().get("hbm_gbs")
@@ -773,7 +774,7 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
         st = autotune.tune_step(ss, sx0, scmd, DT, T_STEPS)
         sreset = lambda: sx.copy_(sx0)  # noqa: E731
         row = {"n_agents": n}
-        for label, k in (("plain", 1), ("fused", st["K"])):
+        for label, k in (("plain", 1), ("K10", 10), ("K100", 100), ("fused", st["K"])):
             gr = ss.graph(sx, scmd, DT, T_STEPS, K=k)
             timed_steps(gr.launch, 1, sreset)
             t = timed_steps(gr.launch, 2, sreset)
