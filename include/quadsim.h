@@ -267,6 +267,15 @@ int sim_collide(sim_handle_t h, const float* d_state, float radius_scale, void* 
  * the caller's device buffer of n_agents bytes. */
 int sim_copy_status(sim_handle_t h, uint8_t* d_status_out, void* stream);
 
+/* Replaces the per-agent status bytes with the caller's device buffer of
+ * n_agents bytes (any nonzero byte marks the agent dead; the library itself
+ * writes 1 for a non-finite state and 2 for a collision).  The planar state
+ * (the caller's buffer), the parameter groups and the status are the whole
+ * of a swarm's state: saving the state and sim_copy_status, then restoring
+ * both with a copy and sim_load_status, resumes a run bit for bit
+ * (checkpoint / resume).  Stream-ordered, allocates nothing. */
+int sim_load_status(sim_handle_t h, const uint8_t* d_status_in, void* stream);
+
 /* Launch configuration: threads per block of the forward kernels (a
  * multiple of 32, <= 256) and of the adjoint kernel (a multiple of 32,
  * <= 128), and the defaults used when a call passes 0 for the steps fused

@@ -26,7 +26,7 @@ EXPORTS = ("sim_create", "sim_set_params", "sim_step", "sim_step_host", "sim_rol
            "sim_workspace_bytes", "sim_rollout_backward", "sim_set_launch", "sim_get_launch", "sim_status",
            "sim_reset_status", "sim_graph_create", "sim_graph_launch", "sim_graph_destroy", "sim_step_launches",
            "sim_destroy", "sim_error_string", "sim_rollout_backward_noalloc",
-           "sim_collide_workspace_bytes", "sim_collide", "sim_copy_status", "sim_run_rounds")
+           "sim_collide_workspace_bytes", "sim_collide", "sim_copy_status", "sim_run_rounds", "sim_load_status")
 
 
 class GroupParams(ctypes.Structure):
@@ -85,6 +85,7 @@ def lib():
         "sim_collide_workspace_bytes": (SZ, [P]),
         "sim_collide": (I, [P, P, F, P, SZ, P]),
         "sim_copy_status": (I, [P, P, P]),
+        "sim_load_status": (I, [P, P, P]),
         "sim_run_rounds": (I, [P, P, P, P, P, P, F, I64, I64, I, P]),
         "sim_set_launch": (I, [P, I, I, I, I]),
         "sim_get_launch": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),

@@ -1118,6 +1118,16 @@ int sim_copy_status(sim_handle_t h, uint8_t* d_status_out, void* stream) {
              : SIM_ERR_CUDA;
 }
 
+int sim_load_status(sim_handle_t h, const uint8_t* d_status_in, void* stream) {
+  if (!h) return SIM_ERR_ARG;
+  if (h->n == 0) return SIM_OK;
+  if (!d_status_in) return SIM_ERR_ARG;
+  return cudaMemcpyAsync(h->status, d_status_in, (size_t)h->n, cudaMemcpyDeviceToDevice,
+                         reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? SIM_OK
+             : SIM_ERR_CUDA;
+}
+
 int sim_status(sim_handle_t h, int64_t* n_dead, int timeout_ms, void* stream) {
   if (!h || !n_dead) return SIM_ERR_ARG;
   *n_dead = 0;

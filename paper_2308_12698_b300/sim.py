@@ -224,6 +224,13 @@ class Sim:
         check(lib().sim_copy_status(self._h, _ptr(out) if self.n else None, _stream(stream)), "sim_copy_status")
         return out
 
+    def load_status(self, status: torch.Tensor, stream=None):
+        """Replace the per-agent status bytes (uint8 CUDA tensor of n): with the state, a resume."""
+        if not (status.is_cuda and status.dtype == torch.uint8 and status.is_contiguous() and
+                status.numel() == self.n):
+            raise SimError("status: expected a contiguous uint8 CUDA tensor of n elements")
+        check(lib().sim_load_status(self._h, _ptr(status) if self.n else None, _stream(stream)), "sim_load_status")
+
     # -- status --
     def n_dead(self, timeout_ms: int = 60000, stream=None) -> int:
         v = ctypes.c_int64()

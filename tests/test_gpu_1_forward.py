@@ -397,3 +397,35 @@ def test_empty_swarm(dev):
     sim.step(x, torch.zeros(0, device=dev), 1e-3, 10)
     assert sim.n_dead() == 0
     sim.close()
+
+
+def test_checkpoint_resume_is_bitwise(dev):
+    """State (the caller's planar buffer) plus status bytes are the whole swarm: saving both
+    after 100 steps and resuming, in the same handle or a fresh one, gives bit for bit the
+    uninterrupted run, dead agents included."""
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    wl = W.closed_loop(n=5000, nsteps=200)
+    x0 = wl.x0.copy()
+    x0[7, 3] = np.inf  # dies in the first launch
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    x = planar(torch.from_numpy(x0)).to(dev)
+    sim.step(x, cmd, wl.dt, 100, K=25)
+    saved_x, saved_st = x.clone(), sim.status()
+    sim.step(x, cmd, wl.dt, 100, K=25)
+    ref_x, ref_st = unplanar(x, wl.n).cpu().numpy(), sim.status().cpu().numpy()
+    assert ref_st[7] == 1 and (np.delete(ref_st, 7) == 0).all()
+    x.copy_(saved_x)
+    sim.reset_status()
+    sim.load_status(saved_st)
+    sim.step(x, cmd, wl.dt, 100, K=25)
+    np.testing.assert_array_equal(unplanar(x, wl.n).cpu().numpy(), ref_x)
+    np.testing.assert_array_equal(sim.status().cpu().numpy(), ref_st)
+    sim.close()
+    fresh = Sim(wl.groups, wl.n, wl.mode)
+    y = saved_x.clone()
+    fresh.load_status(saved_st)
+    fresh.step(y, cmd, wl.dt, 100, K=25)
+    np.testing.assert_array_equal(unplanar(y, wl.n).cpu().numpy(), ref_x)
+    assert fresh.n_dead() == 1
+    fresh.close()
