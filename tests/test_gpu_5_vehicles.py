@@ -175,3 +175,23 @@ def test_mixed_swarm_collisions(dev, orc):
     np.testing.assert_array_equal(got, ref)
     assert 0 < ref.sum() < wl.n
     sim.close()
+
+
+def test_mixed_swarm_host_entry_and_rounds_are_bitwise_sim_step(dev):
+    """The host-buffer pipeline and the decision rounds run the mixed launch like sim_step."""
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    wl = W.multi_type(sizes=(70_000, 40_000, 50_001), shuffle=True)
+    direct = gpu_run(wl, dev, 40, K=20)
+    sim = Sim(wl.groups, wl.n, wl.mode, gid=torch.from_numpy(wl.gid).to(dev))
+    h_state = planar(torch.from_numpy(wl.x0)).pin_memory()
+    h_cmd = torch.from_numpy(wl.cmd).reshape(-1).contiguous().pin_memory()
+    d_state = torch.empty(17 * wl.n, device=dev)
+    d_cmd = torch.empty(4 * wl.n, device=dev)
+    sim.step_host(h_state, h_cmd, d_state, d_cmd, wl.dt, 40, K=20)
+    np.testing.assert_array_equal(unplanar(h_state, wl.n).numpy(), direct)
+    x = planar(torch.from_numpy(wl.x0)).to(dev)
+    h_cmds = torch.from_numpy(wl.cmd).reshape(1, -1).repeat(4, 1).contiguous().pin_memory()
+    sim.run_rounds(x, h_cmds, 10, wl.dt, K=10)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(unplanar(x, wl.n).cpu().numpy(), direct)
+    sim.close()
