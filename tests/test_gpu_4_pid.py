@@ -239,3 +239,18 @@ def test_pid_empty_swarm(dev):
     sim.step(x, torch.zeros(0, device=dev), 1e-3, 10)
     assert sim.n_dead() == 0
     sim.close()
+
+
+def test_pid_full_size_sampled(dev, orc):
+    """The bench's PID leg (1e6 agents, one launch of K = 1000): 2048 sampled agents."""
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    wl = W.closed_loop_pid(n=1_000_000, nsteps=1000)
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    x = planar(torch.from_numpy(wl.x0)).to(dev)
+    sim.step(x, torch.from_numpy(wl.cmd).to(dev).reshape(-1), wl.dt, 1000, K=1000)
+    idx = np.random.default_rng(21).choice(wl.n, 2048, replace=False)
+    got = unplanar(x, wl.n)[torch.from_numpy(idx).to(dev)].cpu().numpy()
+    ref = orc.rollout(wl.groups, wl.gid[idx], wl.x0[idx], wl.cmd[idx], wl.dt, 1000, wl.mode)
+    check_traj(got, ref)
+    assert sim.n_dead() == 0
+    sim.close()

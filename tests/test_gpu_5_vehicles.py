@@ -195,3 +195,26 @@ def test_mixed_swarm_host_entry_and_rounds_are_bitwise_sim_step(dev):
     torch.cuda.synchronize()
     np.testing.assert_array_equal(unplanar(x, wl.n).cpu().numpy(), direct)
     sim.close()
+
+
+def test_mixed_swarm_full_size_sampled(dev, orc):
+    """The bench's mixed-type leg (600,000 agents, one launch of K = 1000): 1000 sampled agents
+    of each type against the checker."""
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    wl = W.multi_type(nsteps=1000)
+    sim = Sim(wl.groups, wl.n, wl.mode, gid=torch.from_numpy(wl.gid).to(dev))
+    x = planar(torch.from_numpy(wl.x0)).to(dev)
+    sim.step(x, torch.from_numpy(wl.cmd).to(dev).reshape(-1), wl.dt, 1000, K=1000)
+    rng = np.random.default_rng(22)
+    idx = np.concatenate([rng.choice(np.flatnonzero(wl.gid == t), 1000, replace=False) for t in range(3)])
+    got = unplanar(x, wl.n)[torch.from_numpy(idx).to(dev)].cpu().numpy()
+    sub = dict(gid=wl.gid[idx], x0=wl.x0[idx], cmd=wl.cmd[idx])
+    ref = orc.rollout(wl.groups, sub["gid"], sub["x0"], sub["cmd"], wl.dt, 1000, wl.mode)
+    q = sub["gid"] == W.TYPE_QUAD
+    check_quads(got[q], ref[q])
+    m = orc.vehicle_margins(wl.groups, sub["gid"], sub["x0"], sub["cmd"], wl.dt, 1000)
+    ok = ~q & (m > 1e-3)
+    assert ok.sum() >= 1990
+    check_vehicles(got[ok], ref[ok], 1000)
+    assert sim.n_dead() == 0
+    sim.close()
