@@ -429,3 +429,25 @@ def test_checkpoint_resume_is_bitwise(dev):
     np.testing.assert_array_equal(unplanar(y, wl.n).cpu().numpy(), ref_x)
     assert fresh.n_dead() == 1
     fresh.close()
+
+
+def test_size_beyond_int32_plane_offsets(dev, orc):
+    """130 million agents: the state holds 17 N = 2.2e9 floats, past 2^31, so every plane offset
+    needs 64-bit indexing.  The swarm repeats a 1e6-agent workload; agents sampled at the start,
+    across the middle and at the very end match the checker's run of their originals."""
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    base = W.scale_sweep(1_000_000, nsteps=10)
+    reps = 130
+    n = reps * base.n
+    assert 17 * n > 2 ** 31
+    x = planar(torch.from_numpy(base.x0).to(dev).repeat(reps, 1))
+    cmd = torch.from_numpy(base.cmd).to(dev).repeat(reps, 1).reshape(-1)
+    sim = Sim(base.groups, n, base.mode)
+    sim.step(x, cmd, base.dt, 10, K=10)
+    idx = np.concatenate([np.arange(64), np.random.default_rng(23).choice(n, 256, replace=False), np.arange(n - 64, n)])
+    got = unplanar(x, n)[torch.from_numpy(idx).to(dev)].cpu().numpy()
+    orig = idx % base.n
+    ref = orc.rollout(base.groups, base.gid[orig], base.x0[orig], base.cmd[orig], base.dt, 10, base.mode)
+    check_traj(got, ref, tol=1e-4)
+    assert sim.n_dead() == 0
+    sim.close()
