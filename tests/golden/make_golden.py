@@ -1,7 +1,8 @@
 """Writes tests/golden/oracle_regression.json from the FP64 checker alone.
 
 The fixture freezes a few short rollouts of the checker (closed loop, open
-loop, heterogeneous groups) so that an accidental change of its arithmetic
+loop, heterogeneous groups, the PID rate loop, a swarm of quadrotors, cars and
+fixed-wing drones) so that an accidental change of its arithmetic
 shows up as a failing test.  A deliberate change must regenerate it and name,
 in the commit message, the equation or reading that justifies the change.
 
@@ -26,6 +27,8 @@ def cases():
     yield "closed_loop", W.closed_loop(n=6, nsteps=250)
     yield "open_loop", W.open_loop(n=4, nsteps=250)
     yield "heterogeneous", W.heterogeneous(sizes=(2, 1, 3), nsteps=250, shuffle=True)
+    yield "pid", W.closed_loop_pid(n=4, nsteps=250)
+    yield "multi_type", W.multi_type(sizes=(2, 2, 2), nsteps=250, shuffle=True)
 
 
 def main():
