@@ -254,3 +254,22 @@ def test_pid_full_size_sampled(dev, orc):
     check_traj(got, ref)
     assert sim.n_dead() == 0
     sim.close()
+
+
+def test_pid_autograd_function(dev):
+    """torch.autograd through QuadRollout in the PID mode equals the direct adjoint call."""
+    from paper_2308_12698_b300.sim import QuadRollout, Sim, planar, unplanar
+    wl = W.differentiable_pid(n_per_group=64, n_groups=2, nsteps=300)
+    sim = Sim(wl.groups, wl.n, wl.mode, gid=torch.from_numpy(wl.gid).to(dev))
+    theta = torch.tensor(sim.theta(), requires_grad=True)
+    x0 = planar(torch.from_numpy(wl.x0)).to(dev).requires_grad_(True)
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    goal = torch.from_numpy(wl.goal).to(dev)
+    xT, rc = QuadRollout.apply(theta, x0, sim, cmd, wl.dt, wl.nsteps, 30)
+    loss = ((unplanar(xT, wl.n)[:, 0:3] - goal) ** 2).sum() + wl.w_omega * rc.sum()
+    loss.backward()
+    sim.close()
+    dx0, dth, _, _, _ = pid_grads(wl, dev, C=30)
+    np.testing.assert_allclose(theta.grad.cpu().numpy(), dth, rtol=1e-5, atol=1e-6 * np.abs(dth).max())
+    np.testing.assert_allclose(unplanar(x0.grad, wl.n).cpu().numpy(), dx0, rtol=1e-5, atol=1e-7)
+    assert x0.grad.shape[0] == 20 * wl.n
