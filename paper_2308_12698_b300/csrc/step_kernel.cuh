@@ -32,6 +32,20 @@ __device__ __forceinline__ bool all_finite(const St& x) {
   return isfinite(s);
 }
 
+// The grid's warps take 32-agent chunks: warp r takes chunks r, r + W, r + 2W,
+// ... (W warps in the grid; a round of W chunks is one resident wave).  r
+// numbers the warps scheduler-first: warp j of a block runs on scheduler
+// j % 4 of its SM and consecutive blocks start on different SMs, so the
+// first chunks of each round go one per scheduler.  A last round that the
+// agents fill only partly is then spread over all schedulers instead of
+// doubling the load of the first blocks' SMs.
+__device__ __forceinline__ int64_t first_agent() {
+  const int wpb = blockDim.x >> 5, j = threadIdx.x >> 5;
+  const int q = (wpb & 3) == 0 ? 4 : (wpb & 1) == 0 ? 2 : 1;
+  const int64_t r = ((int64_t)(j / q) * gridDim.x + blockIdx.x) * q + (j % q);
+  return r * 32 + (threadIdx.x & 31);
+}
+
 template <bool HETERO>
 __device__ __forceinline__ void load_groups(DevGroup* sg, const DevGroup* src, int n_groups) {
   if (HETERO) {
@@ -56,7 +70,7 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 1) step_kernel(StepArgs A, co
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t end = A.first + A.count;
   const int K = PLAIN ? 1 : A.K;
-  for (int64_t i = A.first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end; i += stride) {
+  for (int64_t i = A.first + first_agent(); i < end; i += stride) {
     if (A.status[i]) continue;  // dead agents are frozen
     St x;
     load_state<state_dim<MODE>()>(A.state, A.n, i, x);
