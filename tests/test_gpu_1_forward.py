@@ -173,6 +173,36 @@ def test_block_sizes_agree(dev, block):
     np.testing.assert_array_equal(gpu_run(wl, dev, 30, K=10, block=block), ref)
 
 
+ROUNDS_N = 300_001  # several resident waves at every block size, ragged last round
+
+
+@pytest.fixture(scope="module")
+def rounds_ref(dev):
+    wl = W.closed_loop(n=ROUNDS_N, nsteps=30)
+    return wl, gpu_run(wl, dev, 30, K=10, block=256)
+
+
+@pytest.mark.parametrize("block", [32, 96, 160, 224])
+def test_block_sizes_agree_over_several_rounds(dev, rounds_ref, block):
+    """1, 3, 5 and 7 warps per block (the odd counts take the chunk order's other interleaves)
+    over several grid-stride rounds give the block-256 bits for every agent."""
+    wl, ref = rounds_ref
+    np.testing.assert_array_equal(gpu_run(wl, dev, 30, K=10, block=block), ref)
+
+
+def test_several_rounds_every_agent_stepped(dev, orc, rounds_ref):
+    """The block-256 run of the round test against the checker at the first and last agents, both
+    sides of every resident-wave boundary, the last chunk, and a random sample."""
+    wl, got = rounds_ref
+    wave = 148 * 2 * 256  # resident agents per round at 256-thread blocks, 2 per SM
+    edges = [k * wave + d for k in range(1, ROUNDS_N // wave + 1) for d in (-1, 0)]
+    idx = np.unique(np.concatenate([[0, 1, 31, 32, ROUNDS_N - 33, ROUNDS_N - 2, ROUNDS_N - 1], edges,
+                                    np.random.default_rng(3).choice(ROUNDS_N, 512, replace=False)]))
+    ref = orc.rollout(wl.groups, wl.gid[idx], wl.x0[idx], wl.cmd[idx], wl.dt, 30, wl.mode)
+    check_traj(got[idx], ref, tol=1e-4)
+    assert np.all(np.any(got[idx] != wl.x0[idx], axis=1))
+
+
 def test_graph_replay_matches_direct(dev):
     from paper_2308_12698_b300.sim import Sim, planar, unplanar
     wl = W.closed_loop(n=2048, nsteps=100)
