@@ -37,6 +37,11 @@ UNIT = "agent-steps/s"
 N_AGENTS = 1_000_000
 T_STEPS = 1000
 DT = 1e-3
+# The paper's own timing of this workload size (Table I), quoted for context only: another GPU,
+# PyTorch/TorchScript, and a "round" that may include more than the step
+PAPER_1000 = {"ms_per_round": 0.8452, "agent_steps_per_s": 1000 / 0.8452e-3, "n_agents": 1000,
+              "hardware": "NVIDIA GTX 1660 SUPER + Intel i7-10700", "software": "Python 3.8, PyTorch 1.10.0+cu102",
+              "source": "arXiv 2308.12698, Table I"}
 
 #: Non-trivial floating operations (add/sub, mul, div, sqrt) of one
 #: closed-loop agent-step in the checker's definition, the minimum over the
@@ -805,7 +810,8 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     t = timed_steps(pg.launch, reps, preset)
     ms = sum(t) / reps
     out["n1000"] = {"value": 1000 * T_STEPS / (ms / 1e3), "unit": UNIT, "us_per_physics_step": ms,
-                    "K": pt["K"], "note": "latency bound: 1000 agents fill 4 of the SMs"}
+                    "K": pt["K"], "note": "latency bound: 1000 agents fill 4 of the SMs",
+                    "paper_context": PAPER_1000}
     pg.close()
     ps.close()
     return out
