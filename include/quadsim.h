@@ -70,6 +70,13 @@
  *   CUDA graph.  A stream argument is a cudaStream_t passed as void*
  *   (NULL = the legacy default stream).
  *
+ * Threads
+ *   Calls on one handle must not overlap in time from several host threads:
+ *   the handle holds the launch settings, the host pipeline's streams and
+ *   events and a pinned status word.  Different handles may be used from
+ *   different threads at once, except by sim_rollout_backward_noalloc, whose
+ *   scratch is one per device.
+ *
  * Errors
  *   Every int-returning call returns SIM_OK (0) or a negative SIM_ERR_*.
  *   Arguments are checked on the host before anything is enqueued.  No call
