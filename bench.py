@@ -64,9 +64,9 @@ FLOPS_PER_AGENT_STEP_PID = 760
 #: swarm's states.
 FLOPS_PER_AGENT_STEP_CAR = 98
 FLOPS_PER_AGENT_STEP_FIXED_WING = 156
-#: Bytes one plain step moves per agent: state 68 read + 68 written, command
-#: 16, group id 1, status 1.
-BYTES_PER_AGENT_STEP_PLAIN = 154
+#: Bytes one plain step of a one-group swarm moves per agent: state 68 read +
+#: 68 written, command 16, status 1 (with one group the group id is not read).
+BYTES_PER_AGENT_STEP_PLAIN = 153
 #: FP32 lanes per SM (Blackwell) and the largest SM clock of the part.
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2032.0

@@ -18,8 +18,9 @@ def test_flops_per_agent_step_is_the_checkers_count(orc):
 
 
 def test_plain_bytes_per_agent_step():
-    # state 17 floats in + out, one float4 command, one uint8 group id, one uint8 status
-    assert bench.BYTES_PER_AGENT_STEP_PLAIN == 17 * 4 * 2 + 16 + 1 + 1
+    # state 17 floats in + out, one float4 command, one uint8 status (the bench's swarm is one
+    # group: the kernel takes its parameters from the launch and reads no group id)
+    assert bench.BYTES_PER_AGENT_STEP_PLAIN == 17 * 4 * 2 + 16 + 1
 
 
 def test_adjoint_tape_edges_are_the_checkers_count(orc):
