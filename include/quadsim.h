@@ -147,9 +147,13 @@ int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents,
                int mode, sim_handle_t* out);
 
 /* Replace the parameter groups (same count; vehicle types need the handle's
- * mode to be SIM_CLOSED_LOOP).  Synchronous.  CUDA graphs captured before
- * keep the kernels and the single-group parameters they captured: capture
- * them again after this call. */
+ * mode to be SIM_CLOSED_LOOP).  Every group is checked first; on
+ * SIM_ERR_ARG nothing changes.  Synchronous on the host, but it does not wait for work
+ * of this handle already enqueued on other streams: synchronise those first,
+ * or a launch in flight may see some blocks with the old groups and some
+ * with the new.  CUDA graphs captured before keep the kernels and the
+ * single-group parameters they captured: capture them again after this
+ * call. */
 int sim_set_params(sim_handle_t h, const sim_group_params_t* groups, int n_groups);
 
 /* Advance every live agent nsteps RK4 steps of length dt, in place.

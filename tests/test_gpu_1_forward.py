@@ -440,6 +440,93 @@ def test_device_argument_errors(dev):
     sim.close()
 
 
+def _changed_groups(groups):
+    """The same groups with the 12 gains, the mass and the inertias scaled (rounded to float32)."""
+    from paper_2308_12698_b300.sim import theta_of, with_theta
+    scale = np.array([1.2] * 3 + [0.9] * 3 + [1.1] * 3 + [0.8] * 3 + [1.15, 1.1, 1.05, 1.2])
+    return [W.round_group(with_theta(g, np.array(theta_of(g)) * scale)) for g in groups]
+
+
+@pytest.mark.parametrize("hetero", [False, True])
+def test_set_params_mid_run(dev, orc, hetero):
+    """sim_set_params between two runs of steps: the second run uses the new groups, bit for bit as a
+    handle created with them, and the whole trajectory agrees with the checker run with the old
+    groups and then the new ones."""
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    wl = W.heterogeneous(sizes=(700, 1301), nsteps=300) if hetero else W.closed_loop(n=2001, nsteps=300)
+    new = _changed_groups(wl.groups)
+    gid = torch.from_numpy(wl.gid).to(dev) if hetero else None
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
+    x = planar(torch.from_numpy(wl.x0)).to(dev)
+    sim.step(x, cmd, wl.dt, 150, K=50)
+    mid = x.clone()
+    sim.set_params(new)
+    sim.step(x, cmd, wl.dt, 150, K=50)
+    torch.cuda.synchronize()
+    fresh = Sim(new, wl.n, wl.mode, gid=gid)
+    fresh.step(mid, cmd, wl.dt, 150, K=50)
+    torch.cuda.synchronize()
+    assert torch.equal(x, mid)
+    ref = orc.rollout(wl.groups, wl.gid, wl.x0, wl.cmd, wl.dt, 150, wl.mode)
+    ref = orc.rollout(new, wl.gid, ref, wl.cmd, wl.dt, 150, wl.mode)
+    check_traj(unplanar(x, wl.n).cpu().numpy(), ref)
+    # and the new parameters really differ: the old ones give another attitude (0.06-0.1 apart)
+    old = orc.rollout(wl.groups, wl.gid, wl.x0, wl.cmd, wl.dt, 300, wl.mode)
+    assert np.abs(old[:, 6:10] - ref[:, 6:10]).max() > 1e-2
+    sim.close()
+    fresh.close()
+
+
+def test_set_params_rejections_keep_the_old_groups(dev):
+    """A wrong group count or an invalid group is refused before anything changes."""
+    from paper_2308_12698_b300 import _lib
+    from paper_2308_12698_b300.sim import Sim, SimError, planar
+    wl = W.closed_loop(n=513, nsteps=40)
+    a = gpu_run(wl, dev, 40, K=20)
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    with pytest.raises(SimError):
+        sim.set_params(wl.groups * 2)
+    bad = dict(wl.groups[0])
+    bad["m"] = -1.0
+    with pytest.raises(SimError):
+        sim.set_params([bad])
+    bad = dict(wl.groups[0])
+    bad["type"] = _lib.SIM_TYPE_CAR  # vehicles need the closed loop, this handle has it; a car's constants
+    bad["veh"] = [float("nan")] * 8  # are checked: NaN is refused
+    with pytest.raises(SimError):
+        sim.set_params([bad])
+    x = planar(torch.from_numpy(wl.x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    sim.step(x, cmd, wl.dt, 40, K=20)
+    torch.cuda.synchronize()
+    from paper_2308_12698_b300.sim import unplanar
+    np.testing.assert_array_equal(unplanar(x, wl.n).cpu().numpy(), a)
+    sim.close()
+
+
+def test_graph_captured_after_set_params_uses_the_new_groups(dev):
+    from paper_2308_12698_b300.sim import Sim, planar
+    wl = W.closed_loop(n=1000, nsteps=100)
+    new = _changed_groups(wl.groups)
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    x0 = planar(torch.from_numpy(wl.x0)).to(dev)
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    sim.set_params(new)
+    x = x0.clone()
+    g = sim.graph(x, cmd, wl.dt, 100, K=10)
+    g.launch()
+    torch.cuda.synchronize()
+    fresh = Sim(new, wl.n, wl.mode)
+    y = x0.clone()
+    fresh.step(y, cmd, wl.dt, 100, K=10)
+    torch.cuda.synchronize()
+    assert torch.equal(x, y)
+    g.close()
+    sim.close()
+    fresh.close()
+
+
 def test_empty_swarm(dev):
     from paper_2308_12698_b300.sim import Sim
     sim = Sim([W.base_group()], 0, 1)
