@@ -159,7 +159,9 @@ int sim_set_params(sim_handle_t h, const sim_group_params_t* groups, int n_group
 /* Advance every live agent nsteps RK4 steps of length dt, in place.
  * substeps_K: steps fused per launch (state stays in registers between
  * them and touches HBM once per launch); 0 = the handle's tuned value.
- * nsteps % K remainder steps run as one shorter launch. */
+ * nsteps % K remainder steps run as one shorter launch.  nsteps >= 0 (0
+ * enqueues nothing), dt > 0 and finite, d_state and d_cmd 16-byte aligned;
+ * otherwise SIM_ERR_ARG. */
 int sim_step(sim_handle_t h, float* d_state, const float* d_cmd, float dt, int64_t nsteps, int substeps_K,
              void* stream);
 
@@ -192,7 +194,8 @@ int sim_step_host(sim_handle_t h, float* h_state, const float* h_cmd, float* d_s
 int sim_run_rounds(sim_handle_t h, float* d_state, float* d_cmd2, const float* h_cmds, float* d_obs2, float* h_obs,
                    float dt, int64_t steps_per_round, int64_t rounds, int substeps_K, void* stream);
 
-/* Forward rollout with checkpoints, one launch.  Reads d_state0, writes
+/* Forward rollout with checkpoints, one launch (nsteps >= 1; ckpt_C >= 0,
+ * 0 = the handle's tuned interval).  Reads d_state0, writes
  * S+1 planar states into d_ckpt (S = ceil(nsteps/ckpt_C)): x_0, x_C, ...,
  * x_{(S-1)C}, then x_nsteps last.  d_ckpt holds (S+1)*17*N floats
  * ((S+1)*20*N in SIM_CLOSED_LOOP_PID).  d_run_cost (N floats, may be NULL)

@@ -536,6 +536,31 @@ def test_empty_swarm(dev):
     sim.close()
 
 
+def test_zero_steps_change_nothing(dev):
+    """nsteps = 0 through every stepping entry point leaves the state as it was; a rollout needs at
+    least one step."""
+    from paper_2308_12698_b300.sim import Sim, SimError, planar
+    wl = W.closed_loop(n=333, nsteps=0)
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    x0 = planar(torch.from_numpy(wl.x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    x = x0.clone()
+    sim.step(x, cmd, wl.dt, 0, K=10)
+    assert sim.launches(0, K=10) == 0
+    g = sim.graph(x, cmd, wl.dt, 0, K=10)
+    g.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(x, x0)
+    h_state = planar(torch.from_numpy(wl.x0)).pin_memory()
+    h_cmd = torch.from_numpy(wl.cmd).reshape(-1).contiguous().pin_memory()
+    sim.step_host(h_state, h_cmd, torch.empty_like(x0), torch.empty_like(cmd), wl.dt, 0, K=10)
+    assert torch.equal(h_state, x0.cpu())
+    with pytest.raises(SimError):
+        sim.rollout_forward(x0, cmd, wl.dt, 0)
+    g.close()
+    sim.close()
+
+
 def test_checkpoint_resume_is_bitwise(dev):
     """State (the caller's planar buffer) plus status bytes are the whole swarm: saving both
     after 100 steps and resuming, in the same handle or a fresh one, gives bit for bit the
