@@ -74,35 +74,3 @@ def test_shard_by_groups_prefers_group_boundaries():
     assert cuts[0][0] == 0 and cuts[-1][1] == gid.size and cuts[0][1] == cuts[1][0]
     assert cuts[0][1] in (2000,)
 
-
-def _bench_worker(rank, world, port, out):
-    import torch.distributed as dist
-
-    import bench
-    os.environ["MASTER_ADDR"] = "127.0.0.1"
-    os.environ["MASTER_PORT"] = str(port)
-    dist.init_process_group("gloo", rank=rank, world_size=world)
-    bench.barrier(world)
-    ms = 100.0 + 25.0 * rank  # the ranks' timed totals differ
-    m = bench.max_over_ranks(ms, world)
-    out[rank] = (m, bench.job_rate(world, 1000, 10, 4, m))
-    dist.destroy_process_group()
-
-
-def test_bench_job_rate_over_two_ranks():
-    """bench.py's timing across ranks: every rank sees the slowest rank's time, and the job rate is
-    all ranks' agent-steps over that time (weak scaling: agents per rank fixed)."""
-    ctx = mp.get_context("spawn")
-    mgr = ctx.Manager()
-    out = mgr.dict()
-    port = _free_port()
-    procs = [ctx.Process(target=_bench_worker, args=(r, 2, port, out)) for r in range(2)]
-    for p in procs:
-        p.start()
-    for p in procs:
-        p.join(timeout=120)
-        assert p.exitcode == 0
-    for r in range(2):
-        m, rate = out[r]
-        assert m == 125.0
-        assert rate == 2 * 1000 * 10 * 4 / 0.125
