@@ -124,3 +124,36 @@ def test_deterministic_and_full_size_sampled(dev, orc):
     ref = orc.collisions(wl.x0[:, 0:3], _radii(wl), np.ones(wl.n), idx=idx)
     np.testing.assert_array_equal((a[idx] == 2).astype(np.uint8), ref)
     assert ref.sum() >= 256
+
+
+def test_detection_between_rounds_of_flight(dev, orc):
+    """Detection outside the main loop, every 500 steps, while the swarm flies: each agent's waypoint
+    is another agent's start, so paths cross.  At every check the new flags equal brute force over
+    the live agents at the GPU's positions, agents already dead keep their status and their state
+    through later steps, and agents keep dying round after round."""
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    wl = W.collision_field(20_000, spacing=2.0, planted=0.0)
+    cmd = wl.cmd.copy()
+    cmd[:, 0:3] = wl.x0[np.random.default_rng(11).permutation(wl.n), 0:3]
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    x = planar(torch.from_numpy(wl.x0)).to(dev)
+    c = torch.from_numpy(cmd).reshape(-1).to(dev)
+    radii = _radii(wl)
+    prev_x, prev_st, deaths = None, None, []
+    for _ in range(5):
+        sim.step(x, c, wl.dt, 500, K=100)
+        xs = unplanar(x, wl.n).cpu().numpy()
+        st0 = sim.status().cpu().numpy()
+        if prev_x is not None:
+            dead = prev_st != 0
+            np.testing.assert_array_equal(st0, prev_st)
+            np.testing.assert_array_equal(xs[dead], prev_x[dead])
+        sim.collide(x, 1.0)
+        st = sim.status().cpu().numpy()
+        ref = orc.collisions(xs[:, 0:3], radii, (st0 == 0).astype(np.uint8)).astype(bool)
+        np.testing.assert_array_equal((st == 2) & (st0 == 0), ref)
+        np.testing.assert_array_equal(st[st0 != 0], st0[st0 != 0])
+        deaths.append(int(ref.sum()))
+        prev_x, prev_st = xs, st
+    assert all(d > 0 for d in deaths), deaths
+    sim.close()
