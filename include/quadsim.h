@@ -223,7 +223,13 @@ size_t sim_workspace_bytes(sim_handle_t h, int ckpt_C);
  * per-group sums are deterministic (fixed reduction order, no atomics).
  * d_workspace must hold sim_workspace_bytes(h, ckpt_C) bytes, 256-byte
  * aligned.  In SIM_CLOSED_LOOP_PID the integrator's clamp passes the gradient
- * on its closed interval too; kI, kD and xi_max are not differentiated. */
+ * on its closed interval too; kI, kD and xi_max are not differentiated.
+ * Agents marked dead when the call runs are frozen over the rollout, as
+ * sim_rollout_forward treats them (x_T = x_0, running cost 0): their dL/dx_0
+ * is their dL/dx_T, their per-agent rows are 0 and they add nothing to
+ * d_dL_dtheta.  (An agent whose state turned non-finite during the forward
+ * rollout is marked by it and gets the same frozen gradient, which then has
+ * no meaning.) */
 int sim_rollout_backward(sim_handle_t h, const float* d_ckpt, const float* d_cmd, float dt, int64_t nsteps,
                          int ckpt_C, const float* d_dL_dxT, const float* d_w_run, float* d_dL_dx0,
                          float* d_dL_dtheta, float* d_dL_dtheta_agent, void* d_workspace, size_t ws_bytes,

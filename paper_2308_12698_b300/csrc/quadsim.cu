@@ -167,6 +167,16 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
 #pragma unroll
         for (int q = 0; q < NTH; ++q) A.th_agent[i * NTH + q] = tb[q];
       }
+    } else if (i < A.n) {
+      // a dead agent is frozen over the rollout (x_T = x_0, no running
+      // cost): dL/dx_0 = dL/dx_T, and it adds nothing to theta
+      St lam;
+      load_state<NS>(A.dLdxT, A.n, i, lam);
+      store_state<NS>(A.dLdx0, A.n, i, lam);
+      if (A.th_agent) {
+#pragma unroll
+        for (int q = 0; q < NTH; ++q) A.th_agent[i * NTH + q] = 0.f;
+      }
     }
     unsigned todo = __ballot_sync(0xffffffffu, g >= 0);
     while (todo) {

@@ -340,3 +340,53 @@ def test_adjoint_thrust_pointing_down(dev, orc):
         check_block(dx0[a], rdx0[a], f"x0 agent {a}")
     for a in np.flatnonzero(fl):
         check_loose(dx0[a], rdx0[a], f"x0 agent {a} (near a kink)")
+
+
+@pytest.mark.parametrize("pid", [False, True])
+def test_dead_agents_get_the_frozen_gradient(dev, pid):
+    """Agents marked dead before the rollout are frozen through it (checkpoints x_0, running cost 0),
+    so the adjoint gives them dL/dx_0 = dL/dx_T, zero per-agent theta rows and no share of the group
+    sums (the output buffers start as NaN: every element is written).  The live agents' gradients
+    are bit for bit those of the same swarm with nobody dead."""
+    import ctypes
+
+    from paper_2308_12698_b300 import _lib
+    from paper_2308_12698_b300.sim import Sim, planar
+    wl = (W.differentiable_pid if pid else W.differentiable)(n_per_group=300, n_groups=2, nsteps=120)
+    gid = torch.from_numpy(wl.gid).to(dev)
+    x0 = planar(torch.from_numpy(wl.x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    gT = torch.randn(x0.numel(), generator=torch.Generator().manual_seed(3)).to(dev)
+    w = torch.full((wl.n,), wl.w_omega, device=dev)
+    dead = np.zeros(wl.n, np.uint8)
+    dead[::5] = 2
+    out = {}
+    for name, status in (("all_alive", np.zeros(wl.n, np.uint8)), ("some_dead", dead)):
+        sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
+        sim.load_status(torch.from_numpy(status).to(dev))
+        ckpt, rc = sim.rollout_forward(x0, cmd, wl.dt, wl.nsteps, C=40)
+        ws = sim.workspace_bytes(40)
+        buf = torch.empty(ws, dtype=torch.uint8, device=dev)
+        dx0 = torch.full_like(x0, float("nan"))
+        dth = torch.full((2, 16), float("nan"), device=dev)
+        dtha = torch.full((wl.n, 16), float("nan"), device=dev)
+        p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+        assert _lib.lib().sim_rollout_backward(sim.handle, p(ckpt), p(cmd), wl.dt, wl.nsteps, 40, p(gT), p(w),
+                                               p(dx0), p(dth), p(dtha), p(buf), ws, None) == _lib.SIM_OK
+        torch.cuda.synchronize()
+        out[name] = (ckpt, rc, dx0, dth, dtha)
+        sim.close()
+    from paper_2308_12698_b300.sim import unplanar
+    ckpt, rc, dx0, dth, dtha = out["some_dead"]
+    d = torch.from_numpy(dead != 0).to(dev)
+    assert torch.equal(unplanar(ckpt[-1], wl.n)[d], unplanar(x0, wl.n)[d])
+    assert torch.all(rc[d] == 0)
+    assert torch.equal(unplanar(dx0, wl.n)[d], unplanar(gT, wl.n)[d])
+    assert torch.all(dtha[d] == 0)
+    a = out["all_alive"]
+    assert torch.equal(unplanar(dx0, wl.n)[~d], unplanar(a[2], wl.n)[~d])
+    assert torch.equal(dtha[~d], a[4][~d])
+    assert bool(torch.isfinite(dth).all())
+    live = ~d.cpu().numpy()
+    ref = np.stack([dtha.cpu().numpy()[live & (wl.gid == g)].astype(np.float64).sum(axis=0) for g in range(2)])
+    np.testing.assert_allclose(dth.cpu().numpy(), ref, rtol=1e-4, atol=1e-4 * np.abs(ref).max())
