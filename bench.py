@@ -540,8 +540,7 @@ def run_adjoint_only(args, world, rank, dev):
         C = args.C
     else:
         C = autotune.tune_adjoint(sim, x0, cmd, DT, TS)["C"]
-    S = sim.n_segments(TS, C)
-    ckpt = torch.empty((S + 1, 17 * sim.n), dtype=torch.float32, device=dev)
+    ckpt = sim.ckpt_buffer(TS, C, device=dev)
     rc = torch.empty(sim.n, dtype=torch.float32, device=dev)
     gT = torch.zeros(17 * sim.n, dtype=torch.float32, device=dev)
     gT[: 3 * sim.n] = 1.0
@@ -637,8 +636,7 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     # checkpointed forward + adjoint, 1e6 agents x 1000 steps, loss |p_T - goal|^2 + w sum Omega^2
     cfg = autotune.tune_adjoint(sim, x0, cmd, DT, T_STEPS)
     C = cfg["C"]
-    S = sim.n_segments(T_STEPS, C)
-    ckpt = torch.empty((S + 1, 17 * sim.n), dtype=torch.float32, device=x0.device)
+    ckpt = sim.ckpt_buffer(T_STEPS, C, device=x0.device)
     rc = torch.empty(sim.n, dtype=torch.float32, device=x0.device)
     gT = torch.zeros(17 * sim.n, dtype=torch.float32, device=x0.device)
     gT[: 3 * sim.n] = 1.0

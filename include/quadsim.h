@@ -197,8 +197,10 @@ int sim_run_rounds(sim_handle_t h, float* d_state, float* d_cmd2, const float* h
 /* Forward rollout with checkpoints, one launch (nsteps >= 1; ckpt_C >= 0,
  * 0 = the handle's tuned interval).  Reads d_state0, writes
  * S+1 planar states into d_ckpt (S = ceil(nsteps/ckpt_C)): x_0, x_C, ...,
- * x_{(S-1)C}, then x_nsteps last.  d_ckpt holds (S+1)*17*N floats
- * ((S+1)*20*N in SIM_CLOSED_LOOP_PID).  d_run_cost (N floats, may be NULL)
+ * x_{(S-1)C}, then x_nsteps last.  State s starts at float offset s*P, with
+ * P = 17*N (20*N in SIM_CLOSED_LOOP_PID) rounded up to a multiple of 4, so
+ * that each state starts 16-byte aligned; d_ckpt holds S*P + 17*N (20*N)
+ * floats, which is (S+1)*17*N when N is a multiple of 4.  d_run_cost (N floats, may be NULL)
  * receives, per agent, the sum over step ends n = 1..nsteps of
  * sum_i Omega_{n,i}^2. */
 int sim_rollout_forward(sim_handle_t h, const float* d_state0, const float* d_cmd, float dt, int64_t nsteps,

@@ -46,6 +46,11 @@ struct CkptArgs {
   const DevGroup* groups;
 };
 
+// Floats from one checkpoint to the next: a planar state (NS N floats)
+// rounded up to a multiple of 4, so that every checkpoint starts on a 16-byte
+// boundary as its float4 planes need (N not a multiple of 4 leaves a gap).
+__host__ __device__ constexpr int64_t ckpt_stride(int ns, int64_t n) { return ((int64_t)ns * n + 3) & ~(int64_t)3; }
+
 // Whole forward rollout in one launch, checkpoint every C steps.
 template <int MODE, bool HETERO>
 __global__ void __launch_bounds__(256) ckpt_kernel(CkptArgs A, const DevGroup P0) {
@@ -54,13 +59,13 @@ __global__ void __launch_bounds__(256) ckpt_kernel(CkptArgs A, const DevGroup P0
   load_groups<HETERO>(sg, A.groups, A.n_groups);
   constexpr int NS = state_dim<MODE>();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t plane = (int64_t)NS * A.n;
+  const int64_t cstride = ckpt_stride(NS, A.n);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) {
     St x;
     load_state<NS>(A.x0, A.n, i, x);
     store_state<NS>(A.ckpt, A.n, i, x);
     if (A.status[i]) {  // frozen: every checkpoint is the current state
-      for (int s = 1; s <= A.S; ++s) store_state<NS>(A.ckpt + s * plane, A.n, i, x);
+      for (int s = 1; s <= A.S; ++s) store_state<NS>(A.ckpt + s * cstride, A.n, i, x);
       if (A.run_cost) A.run_cost[i] = 0.f;
       continue;
     }
@@ -75,7 +80,7 @@ __global__ void __launch_bounds__(256) ckpt_kernel(CkptArgs A, const DevGroup P0
         step<MODE>(P, x, c, hd, A.H, L);
         rc += (x.a[OM] * x.a[OM] + x.a[OM + 1] * x.a[OM + 1]) + (x.a[OM + 2] * x.a[OM + 2] + x.a[OM + 3] * x.a[OM + 3]);
       }
-      store_state<NS>(A.ckpt + (s + 1) * plane, A.n, i, x);
+      store_state<NS>(A.ckpt + (s + 1) * cstride, A.n, i, x);
     }
     if (A.run_cost) A.run_cost[i] = rc;
     if (!all_finite<NS>(x)) A.status[i] = 1;
@@ -126,7 +131,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
   const int64_t slot = SMEMS ? (int64_t)threadIdx.x : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   constexpr int NS = state_dim<MODE>();
   const int64_t sstep = (int64_t)NS * scols;
-  const int64_t plane = (int64_t)NS * A.n;
+  const int64_t cstride = ckpt_stride(NS, A.n);
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < A.n; base += nthreads) {
     const int64_t i = base + threadIdx.x;
     float tb[NTH];
@@ -142,13 +147,13 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
       const float w = A.w_run ? A.w_run[i] : 0.f;
       St lam, x;
       load_state<NS>(A.dLdxT, A.n, i, lam);
-      load_state<NS>(A.ckpt + (int64_t)A.S * plane, A.n, i, x);
+      load_state<NS>(A.ckpt + (int64_t)A.S * cstride, A.n, i, x);
 #pragma unroll
       for (int q = 0; q < 4; ++q) lam.a[OM + q] += 2.f * w * x.a[OM + q];
       for (int s = A.S - 1; s >= 0; --s) {
         const int64_t n0 = (int64_t)s * A.C;
         const int len = (int)min((int64_t)A.C, A.nsteps - n0);
-        load_state<NS>(A.ckpt + (int64_t)s * plane, A.n, i, x);
+        load_state<NS>(A.ckpt + (int64_t)s * cstride, A.n, i, x);
         for (int j = 0; j < len; ++j) {
           store_state<NS>(scratch + j * sstep, scols, slot, x);
           if (j + 1 < len) step<MODE>(P, x, c, hd, A.H, L);

@@ -167,14 +167,34 @@ class Sim:
         C = C or self.launch()["C"]
         return (int(nsteps) + C - 1) // C
 
+    def ckpt_stride(self) -> int:
+        """Floats from one checkpoint state to the next: nx N rounded up to a multiple of 4."""
+        return (self.nx * self.n + 3) & ~3
+
+    def ckpt_buffer(self, nsteps: int, C: int = 0, device=None) -> torch.Tensor:
+        """An uninitialised checkpoint buffer: (S+1, nx N) rows, one planar state each, ckpt_stride()
+        floats apart (contiguous when N is a multiple of 4)."""
+        S = self.n_segments(nsteps, C)
+        P = self.ckpt_stride()
+        buf = torch.empty(S * P + self.nx * self.n, dtype=torch.float32, device=device)
+        return buf.as_strided((S + 1, self.nx * self.n), (P, 1))
+
+    def _check_ckpt(self, ckpt: torch.Tensor, nsteps: int, C: int):
+        S = self.n_segments(nsteps, C)
+        if not (ckpt.is_cuda and ckpt.dtype == torch.float32 and tuple(ckpt.shape) == (S + 1, self.nx * self.n)
+                and (self.n == 0 or ckpt.stride() == (self.ckpt_stride(), 1))):
+            raise SimError(f"ckpt: expected a float32 CUDA tensor ({S + 1}, {self.nx * self.n}) with row stride "
+                           f"{self.ckpt_stride()} (see ckpt_buffer)")
+
     def rollout_forward(self, x0: torch.Tensor, cmd: torch.Tensor, dt: float, nsteps: int, C: int = 0,
                         ckpt: torch.Tensor | None = None, run_cost: torch.Tensor | None = None, stream=None):
-        """Returns (ckpt, run_cost): ckpt is (S+1, nx N), ckpt[-1] the final state."""
+        """Returns (ckpt, run_cost): ckpt is (S+1, nx N) rows of planar states (ckpt_buffer),
+        ckpt[-1] the final state."""
         _check_f32(x0, self.nx * self.n, "x0")
         _check_f32(cmd, 4 * self.n, "cmd")
-        S = self.n_segments(nsteps, C)
         if ckpt is None:
-            ckpt = torch.empty((S + 1, self.nx * self.n), dtype=torch.float32, device=x0.device)
+            ckpt = self.ckpt_buffer(nsteps, C, device=x0.device)
+        self._check_ckpt(ckpt, nsteps, C)
         if run_cost is None:
             run_cost = torch.empty(self.n, dtype=torch.float32, device=x0.device)
         check(lib().sim_rollout_forward(self._h, _ptr(x0), _ptr(cmd), float(dt), int(nsteps), int(C), _ptr(ckpt),
@@ -189,6 +209,7 @@ class Sim:
                          w_run: torch.Tensor | None = None, C: int = 0, per_agent: bool = False,
                          workspace: torch.Tensor | None = None, stream=None):
         """Returns (dL/dx0 planar, dL/dtheta (G, 16), per-agent (N, 16) or None)."""
+        self._check_ckpt(ckpt, nsteps, C)
         _check_f32(dL_dxT, self.nx * self.n, "dL_dxT")
         if w_run is not None:
             _check_f32(w_run, self.n, "w_run")

@@ -390,3 +390,42 @@ def test_dead_agents_get_the_frozen_gradient(dev, pid):
     live = ~d.cpu().numpy()
     ref = np.stack([dtha.cpu().numpy()[live & (wl.gid == g)].astype(np.float64).sum(axis=0) for g in range(2)])
     np.testing.assert_allclose(dth.cpu().numpy(), ref, rtol=1e-4, atol=1e-4 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("n,pid", [(1, False), (3, False), (5, False), (33, False), (1001, False), (3, True),
+                                   (1001, True)])
+def test_rollout_and_adjoint_any_agent_count(dev, orc, n, pid):
+    """Checkpoint states start 16-byte aligned whatever the agent count: the stride from one to the
+    next is the state's 17 N (20 N) floats rounded up to a multiple of 4.  A swarm of N agents, N not
+    a multiple of 4, gives bit for bit the checkpoints and per-agent gradients of the same agents in
+    a swarm whose count is (whose checkpoints need no gap), and the unflagged agents meet the strict
+    bar against the checker's reverse mode."""
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    nx = 20 if pid else 17
+    big = (W.differentiable_pid if pid else W.differentiable)(n_per_group=(n + 3) // 4 * 4 + 4, n_groups=1,
+                                                              nsteps=90)
+    cut = lambda v: np.ascontiguousarray(v[:n])  # noqa: E731
+    wl = W.Workload("odd", big.mode, big.groups, cut(big.gid), cut(big.x0), cut(big.cmd), big.dt, big.nsteps,
+                    goal=cut(big.goal), w_omega=big.w_omega)
+    res = {}
+    for name, w in (("odd", wl), ("aligned", big)):
+        sim = Sim(w.groups, w.n, w.mode)
+        x0 = planar(torch.from_numpy(w.x0)).to(dev)
+        ckpt, _ = sim.rollout_forward(x0, torch.from_numpy(w.cmd).to(dev).reshape(-1), w.dt, w.nsteps, C=20)
+        torch.cuda.synchronize()
+        assert ckpt.shape == (6, nx * w.n) and ckpt.stride(0) == (nx * w.n + 3) // 4 * 4
+        cks = np.stack([unplanar(ckpt[s], w.n).cpu().numpy()[:n] for s in range(6)])
+        sim.close()
+        r = gpu_grad(w, dev, C=20)
+        dx0, _, dth_a = r["outs"][0]
+        res[name] = (cks, dx0[:n], dth_a[:n])
+    for a, b in zip(res["odd"], res["aligned"]):
+        np.testing.assert_array_equal(a, b)
+    _, rdx0, rdth = orc.grad(wl.groups, wl.gid, wl.x0, wl.cmd, wl.dt, wl.nsteps, wl.mode, wl.goal, wl.w_omega)
+    m = orc.clamp_margins(wl.groups, wl.gid, wl.x0, wl.cmd, wl.dt, wl.nsteps, mode=wl.mode)
+    fl = (m[:, 0] < SQRT_MARGIN) | (m[:, 1] < CLAMP_MARGIN) | (m[:, 2] < CLAMP_MARGIN)
+    _, dx0, dth_a = res["odd"]
+    for a in np.flatnonzero(~fl):
+        chk = check_loose if pid else check_block
+        chk(dth_a[a], rdth[a], f"theta agent {a}")
+        chk(dx0[a], rdx0[a], f"x0 agent {a}")
