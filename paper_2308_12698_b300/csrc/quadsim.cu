@@ -107,13 +107,55 @@ struct AdjArgs {
   const DevGroup* groups;
 };
 
+// Asynchronous global -> shared copies (cp.async, sm_80 and later), each
+// thread copying its own data; cp.async.wait_group 0 makes the thread's own
+// copies visible to it.  No barrier is involved.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Starts copying agent i's state out of the planar checkpoint `src` (n
+// agents) into this thread's prefetch slot: five float4 slots, `bd` apart
+// (plane 4 of a 17-float state is one float, copied into the slot's first
+// four bytes).
+template <int NS>
+__device__ __forceinline__ void prefetch_state(float4* dst, int bd, const float* src, int64_t n, int64_t i) {
+  const float4* P = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) cp_async16(dst + k * bd, P + k * n + i);
+  if (NS == NXP)
+    cp_async16(dst + 4 * bd, P + 4 * n + i);
+  else
+    cp_async4(dst + 4 * bd, src + 16 * n + i);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+template <int NS>
+__device__ __forceinline__ void read_prefetched(const float4* src, int bd, St& x) {
+  const float4 a = src[0], b = src[bd], c = src[2 * bd], d = src[3 * bd], e = src[4 * bd];
+  x.a[0] = a.x; x.a[1] = a.y; x.a[2] = a.z; x.a[3] = a.w;
+  x.a[4] = b.x; x.a[5] = b.y; x.a[6] = b.z; x.a[7] = b.w;
+  x.a[8] = c.x; x.a[9] = c.y; x.a[10] = c.z; x.a[11] = c.w;
+  x.a[12] = d.x; x.a[13] = d.y; x.a[14] = d.z; x.a[15] = d.w;
+  x.a[16] = e.x;
+  if (NS == NXP) { x.a[17] = e.y; x.a[18] = e.z; x.a[19] = e.w; }
+}
+
 // Discrete adjoint: per agent, segments in reverse; each segment is
 // recomputed from its checkpoint into this thread's scratch column, then
 // swept backwards step by step.  Per-agent theta cotangents are reduced per
 // group inside each warp (fixed butterfly order), accumulated per warp in
 // shared memory, and written as one partial per block.
 // SMEMS: the segment's step-start states live in shared memory (small C)
-// rather than in the global scratch.
+// rather than in the global scratch, and each segment's checkpoint is
+// prefetched into shared memory (cp.async, double-buffered) while the
+// segment before it in the sweep is being processed.
 template <int MODE, bool SMEMS>
 __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
   extern __shared__ float4 smem4[];
@@ -132,6 +174,9 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
   constexpr int NS = state_dim<MODE>();
   const int64_t sstep = (int64_t)NS * scols;
   const int64_t cstride = ckpt_stride(NS, A.n);
+  // checkpoint prefetch slots (SMEMS): [2 buffers][5 planes][block] float4, after the scratch
+  const int bd = blockDim.x;
+  float4* const mypf = reinterpret_cast<float4*>(sscr + (SMEMS ? (int64_t)A.C * sstep : 0)) + threadIdx.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < A.n; base += nthreads) {
     const int64_t i = base + threadIdx.x;
     float tb[NTH];
@@ -150,10 +195,19 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
       load_state<NS>(A.ckpt + (int64_t)A.S * cstride, A.n, i, x);
 #pragma unroll
       for (int q = 0; q < 4; ++q) lam.a[OM + q] += 2.f * w * x.a[OM + q];
+      if (SMEMS) prefetch_state<NS>(mypf, bd, A.ckpt + (int64_t)(A.S - 1) * cstride, A.n, i);
       for (int s = A.S - 1; s >= 0; --s) {
         const int64_t n0 = (int64_t)s * A.C;
         const int len = (int)min((int64_t)A.C, A.nsteps - n0);
-        load_state<NS>(A.ckpt + (int64_t)s * cstride, A.n, i, x);
+        if (SMEMS) {
+          // this segment's checkpoint has arrived; start fetching the next one
+          const int b = (A.S - 1 - s) & 1;
+          cp_async_wait_all();
+          read_prefetched<NS>(mypf + b * 5 * bd, bd, x);
+          if (s > 0) prefetch_state<NS>(mypf + (b ^ 1) * 5 * bd, bd, A.ckpt + (int64_t)(s - 1) * cstride, A.n, i);
+        } else {
+          load_state<NS>(A.ckpt + (int64_t)s * cstride, A.n, i, x);
+        }
         for (int j = 0; j < len; ++j) {
           store_state<NS>(scratch + j * sstep, scols, slot, x);
           if (j + 1 < len) step<MODE>(P, x, c, hd, A.H, L);
@@ -488,13 +542,17 @@ int fwd_grid(const sim_s* h, size_t smem, int64_t count, bool plain = false) {
 // Shared-memory budget per block for the segment scratch (small C).
 constexpr size_t kSmemScratchMax = 96 * 1024;
 
-bool adj_smem_scratch(const sim_s* h, int C) {
-  return (size_t)C * h->nx * sizeof(float) * h->block_adj <= kSmemScratchMax;
+// Shared-memory scratch of one block: the segment's step-start states plus the
+// double-buffered checkpoint prefetch slots (2 x 5 float4 per thread).
+size_t adj_smem_scratch_bytes(const sim_s* h, int C) {
+  return ((size_t)C * h->nx * sizeof(float) + 2 * 5 * sizeof(float4)) * h->block_adj;
 }
+
+bool adj_smem_scratch(const sim_s* h, int C) { return adj_smem_scratch_bytes(h, C) <= kSmemScratchMax; }
 
 size_t adj_smem(const sim_s* h, int C) {
   size_t b = sizeof(DevGroup) * h->n_groups + (size_t)(h->block_adj / 32) * h->n_groups * NTH * sizeof(float);
-  if (adj_smem_scratch(h, C)) b = ((b + 15) & ~(size_t)15) + (size_t)C * h->nx * sizeof(float) * h->block_adj;
+  if (adj_smem_scratch(h, C)) b = ((b + 15) & ~(size_t)15) + adj_smem_scratch_bytes(h, C);
   return b;
 }
 
