@@ -107,19 +107,6 @@ struct AdjArgs {
   const DevGroup* groups;
 };
 
-// Asynchronous global -> shared copies (cp.async, sm_80 and later), each
-// thread copying its own data; cp.async.wait_group 0 makes the thread's own
-// copies visible to it.  No barrier is involved.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
 // Starts copying agent i's state out of the planar checkpoint `src` (n
 // agents) into this thread's prefetch slot: five float4 slots, `bd` apart
 // (plane 4 of a 17-float state is one float, copied into the slot's first
@@ -512,6 +499,9 @@ bool hetero(const sim_s* h) { return h->n_groups > 1; }
 
 size_t group_smem(const sim_s* h) { return hetero(h) ? sizeof(DevGroup) * h->n_groups : 0; }
 
+// The plain form's per-thread prefetch slots: 2 x kPlainSlotF4 float4.
+size_t plain_smem(const sim_s* h) { return (size_t)2 * kPlainSlotF4 * sizeof(float4) * h->block_fwd; }
+
 // The plain (K = 1) instantiation for one quadrotor group, open or P closed loop.
 bool plain_path(const sim_s* h, int K) {
   return K == 1 && !hetero(h) && !h->multi && h->mode != SIM_CLOSED_LOOP_PID;
@@ -607,8 +597,8 @@ int launch_step(sim_s* h, float* d_state, const float* d_cmd, StepH H, int K, cu
   A.n_groups = h->n_groups;
   A.H = H;
   A.groups = h->d_groups;
-  const size_t smem = group_smem(h);
   const bool plain = plain_path(h, K);
+  const size_t smem = plain ? plain_smem(h) : group_smem(h);
   const int grid = fwd_grid(h, smem, count, plain);
   const DevGroup& P0 = h->host_group0;
   if (plain) {

@@ -24,6 +24,20 @@ struct StepArgs {
   const DevGroup* groups;  // device table (several groups)
 };
 
+// Asynchronous global -> shared copies (cp.async, sm_80 and later), each
+// thread copying its own data; cp.async.wait_group 0 makes the thread's own
+// copies visible to it.  No barrier is involved.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 template <int NS = NX>
 __device__ __forceinline__ bool all_finite(const St& x) {
   float s = 0.f;
@@ -56,15 +70,69 @@ __device__ __forceinline__ void load_groups(DevGroup* sg, const DevGroup* src, i
   }
 }
 
+// Shared memory of the plain form: per thread two slots of six float4 (the
+// state's five planes and the command).
+constexpr int kPlainSlotF4 = 6;
+
+// The plain form (K = 1, one 17-float group): each thread copies its next
+// agent's state and command into its own shared-memory slot with cp.async
+// while it steps the current agent (double-buffered), so every warp keeps a
+// load in flight through its arithmetic.  Same arithmetic and results as the
+// register path.
+template <int MODE>
+__device__ __forceinline__ void fetch_agent(float4* slot, int bd, const StepArgs& A, int64_t i) {
+  const float4* P = reinterpret_cast<const float4*>(A.state);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) cp_async16(slot + k * bd, P + k * A.n + i);
+  cp_async4(slot + 4 * bd, A.state + 16 * A.n + i);
+  cp_async16(slot + 5 * bd, A.cmd + i);
+  cp_async_commit();
+}
+
+template <int MODE>
+__device__ __forceinline__ void plain_loop(const StepArgs& A, const DevGroup& P0, float4* smem) {
+  const int bd = blockDim.x;
+  float4* const slot = smem + threadIdx.x;  // [2 buffers][kPlainSlotF4][bd]
+  const int64_t stride = (int64_t)gridDim.x * bd;
+  const int64_t end = A.first + A.count;
+  const LagCoef L = lag_coef(P0.inv_tau, A.H);
+  int64_t i = A.first + first_agent();
+  if (i < end) fetch_agent<MODE>(slot, bd, A, i);
+  for (int b = 0; i < end; i += stride, b ^= 1) {
+    cp_async_wait_all();  // agent i has arrived in buffer b
+    if (i + stride < end) fetch_agent<MODE>(slot + (b ^ 1) * kPlainSlotF4 * bd, bd, A, i + stride);
+    if (A.status[i]) continue;  // dead agents are frozen
+    const float4* s = slot + b * kPlainSlotF4 * bd;
+    const float4 p0 = s[0], p1 = s[bd], p2 = s[2 * bd], p3 = s[3 * bd], c = s[5 * bd];
+    St x;
+    x.a[0] = p0.x; x.a[1] = p0.y; x.a[2] = p0.z; x.a[3] = p0.w;
+    x.a[4] = p1.x; x.a[5] = p1.y; x.a[6] = p1.z; x.a[7] = p1.w;
+    x.a[8] = p2.x; x.a[9] = p2.y; x.a[10] = p2.z; x.a[11] = p2.w;
+    x.a[12] = p3.x; x.a[13] = p3.y; x.a[14] = p3.z; x.a[15] = p3.w;
+    x.a[16] = s[4 * bd].x;
+    const Hd hd = heading(MODE != 0 ? c.w : 0.f);
+    step<MODE>(P0, x, c, hd, A.H, L);
+    if (all_finite<NX>(x)) {
+      store_state<NX>(A.state, A.n, i, x);
+    } else {
+      A.status[i] = 1;  // keep the last finite state
+    }
+  }
+}
+
 // K fused RK4 steps per launch; the state touches HBM once per launch.
 // MULTI: some groups are cars or fixed-wing drones (closed loop only); each
 // agent runs its group's model.  PLAIN: one step per launch (K = 1), where
-// HBM bounds the kernel: registers capped so that 3 blocks of 256 stay
-// resident and keep more loads in flight (the fused form runs faster with
-// the few more registers it takes uncapped).
+// HBM bounds the kernel (plain_loop): registers capped so that 3 blocks of
+// 256 stay resident and keep more loads in flight (the fused form runs
+// faster with the few more registers it takes uncapped).
 template <int MODE, bool HETERO, bool MULTI = false, bool PLAIN = false>
 __global__ void __launch_bounds__(256, PLAIN ? 3 : 1) step_kernel(StepArgs A, const DevGroup P0) {
   extern __shared__ float4 smem4[];
+  if (PLAIN) {
+    plain_loop<MODE>(A, P0, smem4);
+    return;
+  }
   DevGroup* sg = reinterpret_cast<DevGroup*>(smem4);
   load_groups<HETERO>(sg, A.groups, A.n_groups);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
