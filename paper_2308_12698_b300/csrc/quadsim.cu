@@ -511,8 +511,8 @@ int fwd_grid(const sim_s* h, size_t smem, int64_t count, bool plain = false) {
   // one resident wave of blocks, grid-stride over the agents
   int occ;
   if (plain)
-    occ = h->mode == SIM_CLOSED_LOOP ? occupancy(step_kernel<1, false, false, true>, h->block_fwd, smem)
-                                     : occupancy(step_kernel<0, false, false, true>, h->block_fwd, smem);
+    occ = h->mode == SIM_CLOSED_LOOP ? occupancy(step_kernel<1, false, false, 2>, h->block_fwd, smem)
+                                     : occupancy(step_kernel<0, false, false, 2>, h->block_fwd, smem);
   else if (h->multi)
     occ = hetero(h) ? occupancy(step_kernel<1, true, true>, h->block_fwd, smem)
                     : occupancy(step_kernel<1, false, true>, h->block_fwd, smem);
@@ -601,9 +601,12 @@ int launch_step(sim_s* h, float* d_state, const float* d_cmd, StepH H, int K, cu
   const size_t smem = plain ? plain_smem(h) : group_smem(h);
   const int grid = fwd_grid(h, smem, count, plain);
   const DevGroup& P0 = h->host_group0;
-  if (plain) {
-    if (h->mode == SIM_CLOSED_LOOP) step_kernel<1, false, false, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
-    else step_kernel<0, false, false, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
+  if (plain && count > (int64_t)grid * h->block_fwd) {  // several agents per thread: prefetch
+    if (h->mode == SIM_CLOSED_LOOP) step_kernel<1, false, false, 2><<<grid, h->block_fwd, smem, st>>>(A, P0);
+    else step_kernel<0, false, false, 2><<<grid, h->block_fwd, smem, st>>>(A, P0);
+  } else if (plain) {
+    if (h->mode == SIM_CLOSED_LOOP) step_kernel<1, false, false, 1><<<grid, h->block_fwd, 0, st>>>(A, P0);
+    else step_kernel<0, false, false, 1><<<grid, h->block_fwd, 0, st>>>(A, P0);
   } else if (h->multi) {
     if (hetero(h)) step_kernel<1, true, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
     else step_kernel<1, false, true><<<grid, h->block_fwd, smem, st>>>(A, P0);

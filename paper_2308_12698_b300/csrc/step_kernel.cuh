@@ -122,14 +122,16 @@ __device__ __forceinline__ void plain_loop(const StepArgs& A, const DevGroup& P0
 
 // K fused RK4 steps per launch; the state touches HBM once per launch.
 // MULTI: some groups are cars or fixed-wing drones (closed loop only); each
-// agent runs its group's model.  PLAIN: one step per launch (K = 1), where
-// HBM bounds the kernel (plain_loop): registers capped so that 3 blocks of
-// 256 stay resident and keep more loads in flight (the fused form runs
-// faster with the few more registers it takes uncapped).
-template <int MODE, bool HETERO, bool MULTI = false, bool PLAIN = false>
+// agent runs its group's model.  PLAIN (1 or 2): one step per launch (K =
+// 1), where HBM bounds the kernel: registers capped so that 3 blocks of 256
+// stay resident and keep more loads in flight (the fused form runs faster
+// with the few more registers it takes uncapped).  PLAIN 2 prefetches each
+// thread's next agent (plain_loop); the host takes it when the agents exceed
+// one resident wave, PLAIN 1 (nothing to overlap) otherwise.
+template <int MODE, bool HETERO, bool MULTI = false, int PLAIN = 0>
 __global__ void __launch_bounds__(256, PLAIN ? 3 : 1) step_kernel(StepArgs A, const DevGroup P0) {
   extern __shared__ float4 smem4[];
-  if (PLAIN) {
+  if (PLAIN == 2) {
     plain_loop<MODE>(A, P0, smem4);
     return;
   }
