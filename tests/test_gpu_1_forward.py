@@ -223,6 +223,35 @@ def test_several_rounds_every_agent_stepped(dev, orc, rounds_ref):
     assert np.all(np.any(got[idx] != wl.x0[idx], axis=1))
 
 
+def test_plain_prefetching_form_over_several_waves(dev, orc):
+    """K = 1 over more agents than one resident wave takes the prefetching plain instantiation
+    (each thread copies its next agent into shared memory while stepping the current one).  20
+    single steps equal 20 fused steps bit for bit for all 300,001 agents; agents with a NaN
+    velocity are marked dead by their first step and frozen; a sample meets the checker's bar."""
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    wl = W.closed_loop(n=300_001, nsteps=20)
+    x0 = wl.x0.copy()
+    bad = np.arange(5, wl.n, 9973)
+    x0[bad, 3] = np.nan
+    out = {}
+    for K in (1, 20):
+        sim = Sim(wl.groups, wl.n, wl.mode)
+        x = planar(torch.from_numpy(x0)).to(dev)
+        sim.step(x, torch.from_numpy(wl.cmd).to(dev).reshape(-1), wl.dt, 20, K=K)
+        torch.cuda.synchronize()
+        out[K] = (unplanar(x, wl.n).cpu().numpy(), sim.status().cpu().numpy())
+        sim.close()
+    np.testing.assert_array_equal(out[1][0], out[20][0])
+    np.testing.assert_array_equal(out[1][1], out[20][1])
+    got, st = out[1]
+    assert set(np.flatnonzero(st)) == set(bad)
+    np.testing.assert_array_equal(got[bad], x0[bad])
+    idx = np.setdiff1d(np.concatenate([[0, 1, wl.n - 1], np.random.default_rng(4).choice(wl.n, 400, replace=False)]),
+                       bad)
+    ref = orc.rollout(wl.groups, wl.gid[idx], x0[idx], wl.cmd[idx], wl.dt, 20, wl.mode)
+    check_traj(got[idx], ref, tol=1e-4)
+
+
 def test_graph_replay_matches_direct(dev):
     from paper_2308_12698_b300.sim import Sim, planar, unplanar
     wl = W.closed_loop(n=2048, nsteps=100)
