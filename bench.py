@@ -675,9 +675,14 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     timed_steps(hg.launch, 2, hreset)
     t = timed_steps(hg.launch, reps, hreset)
     ms = max_over_ranks(sum(t), world) / reps
-    out["hetero"] = {"value": world * hw.n * T_STEPS / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+    hrate = hw.n * T_STEPS / (ms / 1e3)
+    out["hetero"] = {"value": world * hrate, "unit": UNIT, "ms_per_step": ms,
                      "n_agents": hw.n, "groups": len(hw.groups), "sizes": list(W.HETERO_SIZES), "K": ht["K"],
-                     "block": ht["block"]}
+                     "block": ht["block"],
+                     "roofline": {"bound": "alu", "achieved": FLOPS_PER_AGENT_STEP * hrate / 1e12, "peak": peak_tf,
+                                  "unit": "TFLOP/s", "frac": FLOPS_PER_AGENT_STEP * hrate / 1e12 / peak_tf,
+                                  "flops_per_agent_step": FLOPS_PER_AGENT_STEP,
+                                  "note": "the quadrotor step's count; every group runs the same operations"}}
     hg.close()
     hs.close()
 
