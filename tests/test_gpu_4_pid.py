@@ -133,7 +133,7 @@ def test_pid_heterogeneous_is_bitwise_each_group_alone(dev):
         np.testing.assert_array_equal(both[idx], gpu_run(one, dev, 100, K=100))
 
 
-def test_pid_graph_and_host_entry_are_bitwise_sim_step(dev):
+def test_pid_graph_host_entry_and_rounds_are_bitwise_sim_step(dev):
     from paper_2308_12698_b300.sim import Sim, planar, unplanar
     wl = W.closed_loop_pid(n=150_001)
     direct = gpu_run(wl, dev, 30, K=10)
@@ -151,6 +151,14 @@ def test_pid_graph_and_host_entry_are_bitwise_sim_step(dev):
     d_cmd = torch.empty(4 * wl.n, device=dev)
     sim.step_host(h_state, h_cmd, d_state, d_cmd, wl.dt, 30, K=10)
     np.testing.assert_array_equal(unplanar(h_state, wl.n).numpy(), direct)
+    # decision rounds: 3 rounds of 10 steps with the same commands, positions observed after each
+    x = planar(torch.from_numpy(wl.x0)).to(dev)
+    h_cmds = torch.from_numpy(np.tile(wl.cmd.reshape(1, -1), (3, 1))).contiguous().pin_memory()
+    h_obs = torch.empty((3, 4 * wl.n), dtype=torch.float32).pin_memory()
+    sim.run_rounds(x, h_cmds, 10, wl.dt, K=10, h_obs=h_obs)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(unplanar(x, wl.n).cpu().numpy(), direct)
+    np.testing.assert_array_equal(h_obs[2].numpy().reshape(wl.n, 4), direct[:, 0:4])
     sim.close()
 
 
