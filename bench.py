@@ -378,7 +378,10 @@ def main():
     ap.add_argument("--block-adj", type=int, default=0, help="fix the adjoint block size (with --adjoint-only)")
     ap.add_argument("--pid-only", action="store_true",
                     help="time only the PID-rate-loop swarm at --agents x --physics-steps (profiling case)")
-    ap.add_argument("--block", type=int, default=0, help="fix the forward block size (with --pid-only)")
+    ap.add_argument("--multi-only", action="store_true",
+                    help="time only the quadrotor / car / fixed-wing swarm (equal thirds) at --agents x "
+                         "--physics-steps (profiling case)")
+    ap.add_argument("--block", type=int, default=0, help="fix the forward block size (with --pid-only, --multi-only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -403,8 +406,8 @@ def main():
     if args.adjoint_only:
         run_adjoint_only(args, world, rank, dev)
         return
-    if args.pid_only:
-        run_pid_only(args, world, rank, dev)
+    if args.pid_only or args.multi_only:
+        run_swarm_only(args, world, rank, dev, "pid" if args.pid_only else "multi")
         return
     stream = torch.cuda.current_stream()
     props = torch.cuda.get_device_properties(dev)
@@ -567,16 +570,25 @@ def run_adjoint_only(args, world, rank, dev):
     sim.close()
 
 
-def run_pid_only(args, world, rank, dev):
-    """The PID-rate-loop swarm on --agents x --physics-steps, --K and --block (or tuned)."""
+def run_swarm_only(args, world, rank, dev, kind: str):
+    """One swarm on --agents x --physics-steps, --K and --block (or tuned): kind "pid" is the
+    PID-rate-loop swarm, "multi" the quadrotor / car / fixed-wing swarm in equal thirds."""
     import torch
 
     from paper_2308_12698_b300 import autotune
     from paper_2308_12698_b300 import workload as W
     from paper_2308_12698_b300.sim import Sim, planar
     NA, TS = args.agents, args.physics_steps
-    wl = W.closed_loop_pid(n=NA, nsteps=TS)
-    sim = Sim(wl.groups, wl.n, wl.mode)
+    if kind == "pid":
+        wl = W.closed_loop_pid(n=NA, nsteps=TS)
+        flops = FLOPS_PER_AGENT_STEP_PID
+    else:
+        sizes = (NA // 3, NA // 3, NA - 2 * (NA // 3))
+        wl = W.multi_type(sizes=sizes, nsteps=TS)
+        flops = (sizes[0] * FLOPS_PER_AGENT_STEP + sizes[1] * FLOPS_PER_AGENT_STEP_CAR +
+                 sizes[2] * FLOPS_PER_AGENT_STEP_FIXED_WING) / NA
+    gid = torch.from_numpy(wl.gid).to(dev) if len(wl.groups) > 1 else None
+    sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
     x0 = planar(torch.from_numpy(wl.x0)).to(dev)
     cmd = torch.from_numpy(wl.cmd).reshape(-1).to(dev)
     x = x0.clone()
@@ -602,9 +614,9 @@ def run_pid_only(args, world, rank, dev):
         ms += a.elapsed_time(b) / args.steps
     if rank == 0:
         rate = NA * TS / (ms / 1e3)
-        print(json.dumps({"leg": "pid", "agents": NA, "physics_steps": TS, "ms_per_step": ms, "value": rate,
-                          "unit": UNIT, "flops_per_agent_step": FLOPS_PER_AGENT_STEP_PID,
-                          "tflops": FLOPS_PER_AGENT_STEP_PID * rate / 1e12, "launch": sim.launch()}), flush=True)
+        print(json.dumps({"leg": kind, "agents": NA, "physics_steps": TS, "ms_per_step": ms, "value": rate,
+                          "unit": UNIT, "flops_per_agent_step": flops, "tflops": flops * rate / 1e12,
+                          "launch": sim.launch()}), flush=True)
     g.close()
     sim.close()
 
