@@ -218,3 +218,28 @@ def test_mixed_swarm_full_size_sampled(dev, orc):
     check_vehicles(got[ok], ref[ok], 1000)
     assert sim.n_dead() == 0
     sim.close()
+
+
+def test_vehicles_at_and_near_their_waypoints(dev, orc):
+    """Degenerate guidance geometry: a car or a drone exactly on its waypoint (zero distance: no
+    curvature, no course error), a car inside the look-ahead floor l_min (the floor sets the
+    pursuit radius), and both types straight ahead of the waypoint's direction.  One step and 50
+    steps against the checker."""
+    cars = W.multi_type(sizes=(0, 6, 0))
+    drones = W.multi_type(sizes=(0, 0, 6))
+    for base, kind in ((cars, W.TYPE_CAR), (drones, W.TYPE_FIXED_WING)):
+        x0, cmd = base.x0.copy(), base.cmd.copy()
+        c, s = x0[:, 6], x0[:, 7]
+        cmd[0, 0:2] = x0[0, 0:2]                                   # on the waypoint
+        cmd[1, 0:2] = x0[1, 0:2] + 0.5 * np.array([-s[1], c[1]])   # 0.5 m to the side: inside l_min
+        cmd[2, 0:2] = x0[2, 0:2] + 50.0 * np.array([c[2], s[2]])   # straight ahead
+        cmd[3, 0:2] = x0[3, 0:2] + 0.3 * np.array([c[3], s[3]])    # just ahead, inside l_min
+        if kind == W.TYPE_FIXED_WING:
+            cmd[:, 2] = x0[:, 2]                                   # hold altitude as well
+        wl = W.Workload("wp", W.CLOSED_LOOP, [base.groups[kind]], np.zeros(6, np.uint8), x0, cmd, base.dt, 50)
+        got, ref = gpu_run(wl, dev, 1, K=1), ref_run(orc, wl, 1)
+        tol = 1e-5 * np.maximum(np.abs(ref), 1.0)
+        assert (np.abs(got.astype(np.float64) - ref) <= tol).all(), (kind, (np.abs(got - ref) / tol).max())
+        got, ref = gpu_run(wl, dev, 50, K=10), ref_run(orc, wl, 50)
+        dp = np.abs(got[:, 0:3].astype(np.float64) - ref[:, 0:3]).max(axis=1)
+        assert (dp <= 1e-3 + 50 * 2.0 ** -24 * np.abs(ref[:, 0:3]).max(axis=1)).all(), (kind, dp)
