@@ -642,3 +642,30 @@ def test_size_beyond_int32_plane_offsets(dev, orc):
     check_traj(got, ref, tol=1e-4)
     assert sim.n_dead() == 0
     sim.close()
+
+
+@pytest.mark.parametrize("mode", [W.OPEN_LOOP, W.CLOSED_LOOP])
+def test_hover_stays_put(dev, orc, mode):
+    """Hover as an equilibrium on the GPU, for each of the eight scaled airframes: level, at rest,
+    rotors at the hover speed (rounded to FP32 once); open loop with the hover speed commanded, or
+    closed loop with the waypoint at the agent and its heading held.  After 1000 steps every agent
+    is within 1e-6 m of where it started and of the checker's FP64 run from the same inputs (the
+    residual is the FP32 rounding of the hover speed and of the thrust)."""
+    het = W.heterogeneous(sizes=(40,) * 8, nsteps=1000)
+    n = het.n
+    x0 = np.zeros((n, 17), np.float32)
+    x0[:, 0:3] = np.random.default_rng(8).uniform(-10, 10, (n, 3))
+    psi = np.random.default_rng(9).uniform(-np.pi, np.pi, n)
+    x0[:, 6], x0[:, 9] = np.cos(psi / 2), np.sin(psi / 2)  # yaw only: level
+    wh = np.array([W.hover_speed(g) for g in het.groups], np.float32)[het.gid]
+    x0[:, 13:17] = wh[:, None]
+    if mode == W.OPEN_LOOP:
+        cmd = np.repeat(wh[:, None], 4, axis=1).astype(np.float32)
+    else:
+        cmd = np.concatenate([x0[:, 0:3], psi[:, None]], axis=1).astype(np.float32)
+    wl = W.Workload("hover", mode, het.groups, het.gid, x0, cmd, het.dt, 1000)
+    got = gpu_run(wl, dev, 1000, K=100)
+    ref = ref_run(orc, wl, 1000)
+    assert np.abs(got[:, 0:3].astype(np.float64) - x0[:, 0:3]).max() <= 1e-6
+    assert np.abs(got[:, 0:3].astype(np.float64) - ref[:, 0:3]).max() <= 1e-6
+    assert attitude_err(got[:, 6:10].astype(np.float64), x0[:, 6:10].astype(np.float64)).max() <= 1e-6
