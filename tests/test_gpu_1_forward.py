@@ -669,3 +669,47 @@ def test_hover_stays_put(dev, orc, mode):
     assert np.abs(got[:, 0:3].astype(np.float64) - x0[:, 0:3]).max() <= 1e-6
     assert np.abs(got[:, 0:3].astype(np.float64) - ref[:, 0:3]).max() <= 1e-6
     assert attitude_err(got[:, 6:10].astype(np.float64), x0[:, 6:10].astype(np.float64)).max() <= 1e-6
+
+
+def test_closed_forms_without_the_checker(dev):
+    """Rotors off, so only drag, gravity and free rotation act, checked against closed forms rather
+    than the checker.  Translation: v(t) = v_inf + (v_0 - v_inf) e^(-c t/m) with v_inf = -(m g/c) e_3,
+    and p(t) = p_0 + v_inf t + (v_0 - v_inf)(m/c)(1 - e^(-c t/m)).  Rotation about the body z axis (a
+    principal axis): omega stays (0, 0, w_0) exactly and q(t) = q_0 o (cos(w_0 t/2), 0, 0,
+    sin(w_0 t/2)).  1000 RK4 steps of 1 ms; RK4's own error is below 1e-12 here, so the bars
+    are FP32 rounding accumulated over the steps."""
+    g = W.base_group()
+    n = 512
+    rng = np.random.default_rng(21)
+    x0 = np.zeros((n, 17), np.float32)
+    x0[:, 0:3] = rng.uniform(-10, 10, (n, 3))
+    x0[:, 3:6] = rng.normal(0, 2, (n, 3))
+    u = rng.normal(size=(n, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    ang = rng.uniform(0, np.pi, n)
+    x0[:, 6] = np.cos(ang / 2)
+    x0[:, 7:10] = u * np.sin(ang / 2)[:, None]
+    x0[:, 12] = rng.uniform(-5, 5, n)  # w_0 about body z
+    wl = W.Workload("free", W.OPEN_LOOP, [g], np.zeros(n, np.uint8), x0, np.zeros((n, 4), np.float32), 1e-3, 1000)
+    got = gpu_run(wl, dev, 1000, K=100).astype(np.float64)
+    x = x0.astype(np.float64)
+    t, m, c, grav = 1.0, np.float64(np.float32(g["m"])), np.float64(np.float32(g["c_d"])), np.float64(np.float32(g["g"]))
+    vinf = np.array([0.0, 0.0, -m * grav / c])
+    e = np.exp(-c * t / m)
+    v = vinf + (x[:, 3:6] - vinf) * e
+    p = x[:, 0:3] + vinf * t + (x[:, 3:6] - vinf) * (m / c) * (1 - e)
+    # FP32 rounding: at most half an ulp of each component per step, 1000 steps
+    bar = lambda ref: 1e-5 + 1000 * 2.0 ** -24 * np.abs(ref).max(axis=1, keepdims=True)  # noqa: E731
+    assert (np.abs(got[:, 3:6] - v) <= bar(v)).all(), (np.abs(got[:, 3:6] - v) / bar(v)).max()
+    assert (np.abs(got[:, 0:3] - p) <= bar(p)).all(), (np.abs(got[:, 0:3] - p) / bar(p)).max()
+    print(f"drag closed form: |dv| {np.abs(got[:, 3:6] - v).max():.2e}, |dp| {np.abs(got[:, 0:3] - p).max():.2e}")
+    np.testing.assert_array_equal(got[:, 10:12], 0.0)
+    np.testing.assert_array_equal(got[:, 12], x[:, 12])
+    half = x[:, 12] * t / 2
+    w0, v0 = x[:, 6], x[:, 7:10]
+    # q_0 o (cos h, 0, 0, sin h): scalar w0 cos h - v0_z sin h, vector w0 sin h e_z + cos h v0 + sin h v0 x e_z
+    qw = w0 * np.cos(half) - v0[:, 2] * np.sin(half)
+    qv = (np.cos(half)[:, None] * v0 + np.sin(half)[:, None] * np.stack([v0[:, 1], -v0[:, 0], w0], axis=1))
+    q = np.concatenate([qw[:, None], qv], axis=1)
+    assert np.abs(got[:, 6:10] - q).max() <= 1e-5 + 1000 * 2.0 ** -24, np.abs(got[:, 6:10] - q).max()
+    print(f"spin closed form: |dq| {np.abs(got[:, 6:10] - q).max():.2e}")
