@@ -754,3 +754,35 @@ def test_torque_free_invariants(dev):
     dn = np.abs(np.linalg.norm(got[:, 6:10], axis=1) - 1)
     print(f"torque-free: energy {de.max():.2e}, momentum {dl.max():.2e}, |q| - 1 {dn.max():.2e}")
     assert de.max() <= 1e-5 and dl.max() <= 1e-5 and dn.max() <= 1e-5, (de.max(), dl.max(), dn.max())
+
+
+def test_allocation_rows_and_signs(dev):
+    """Eq. 3's torque rows through the GPU step, against the closed form: rotor speeds held
+    (commands equal to the speeds, so the lag does nothing), level and at rest; a pattern that
+    torques one axis only gives omega(t) = t tau / J exactly (omega x J omega stays 0 and RK4 is
+    exact for linear growth).  tau_x = L sin(a) k_t (s1 - s2 - s3 + s4), tau_y = L cos(a) k_t
+    (-s1 - s2 + s3 + s4), tau_z = k_q (s1 - s2 + s3 - s4), s_i = Omega_i^2: rotors 1 and 4 faster
+    roll positive, 3 and 4 pitch positive, 1 and 3 yaw positive."""
+    g = W.base_group()
+    wh, d = W.hover_speed(g), 30.0
+    pats = {10: [wh + d, wh - d, wh - d, wh + d], 11: [wh - d, wh - d, wh + d, wh + d],
+            12: [wh + d, wh - d, wh + d, wh - d]}
+    f = lambda k: np.float64(np.float32(g[k]))  # noqa: E731
+    L, a, kt, kq = f("L"), f("alpha"), f("kt"), f("kq")
+    J = {10: f("Jxx"), 11: f("Jyy"), 12: f("Jzz")}
+    for axis, om in pats.items():
+        om32 = np.array(om, np.float32)
+        x0 = np.zeros((1, 17), np.float32)
+        x0[0, 6] = 1.0
+        x0[0, 13:17] = om32
+        wl = W.Workload("alloc", W.OPEN_LOOP, [g], np.zeros(1, np.uint8), x0, om32[None, :], 1e-3, 100)
+        got = gpu_run(wl, dev, 100, K=100).astype(np.float64)[0]
+        s = om32.astype(np.float64) ** 2
+        tau = {10: L * np.sin(a) * kt * (s[0] - s[1] - s[2] + s[3]),
+               11: L * np.cos(a) * kt * (-s[0] - s[1] + s[2] + s[3]),
+               12: kq * (s[0] - s[1] + s[2] - s[3])}[axis]
+        expect = 0.1 * tau / J[axis]
+        assert expect > 0
+        assert abs(got[axis] - expect) <= 1e-5 * abs(expect) + 1e-6, (axis, got[axis], expect)
+        others = [k for k in (10, 11, 12) if k != axis]
+        assert np.all(np.abs(got[others]) <= 1e-6 * abs(expect)), (axis, got[10:13])
