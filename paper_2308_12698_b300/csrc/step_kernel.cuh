@@ -79,7 +79,6 @@ constexpr int kPlainSlotF4 = 6;
 // while it steps the current agent (double-buffered), so every warp keeps a
 // load in flight through its arithmetic.  Same arithmetic and results as the
 // register path.
-template <int MODE>
 __device__ __forceinline__ void fetch_agent(float4* slot, int bd, const StepArgs& A, int64_t i) {
   const float4* P = reinterpret_cast<const float4*>(A.state);
 #pragma unroll
@@ -97,10 +96,10 @@ __device__ __forceinline__ void plain_loop(const StepArgs& A, const DevGroup& P0
   const int64_t end = A.first + A.count;
   const LagCoef L = lag_coef(P0.inv_tau, A.H);
   int64_t i = A.first + first_agent();
-  if (i < end) fetch_agent<MODE>(slot, bd, A, i);
+  if (i < end) fetch_agent(slot, bd, A, i);
   for (int b = 0; i < end; i += stride, b ^= 1) {
     cp_async_wait_all();  // agent i has arrived in buffer b
-    if (i + stride < end) fetch_agent<MODE>(slot + (b ^ 1) * kPlainSlotF4 * bd, bd, A, i + stride);
+    if (i + stride < end) fetch_agent(slot + (b ^ 1) * kPlainSlotF4 * bd, bd, A, i + stride);
     if (A.status[i]) continue;  // dead agents are frozen
     const float4* s = slot + b * kPlainSlotF4 * bd;
     const float4 p0 = s[0], p1 = s[bd], p2 = s[2 * bd], p3 = s[3 * bd], c = s[5 * bd];
