@@ -24,7 +24,6 @@ import argparse
 import hashlib
 import json
 import os
-import re
 import subprocess
 import sys
 import time
@@ -43,63 +42,114 @@ PAPER_1000 = {"ms_per_round": 0.8452, "agent_steps_per_s": 1000 / 0.8452e-3, "n_
               "hardware": "NVIDIA GTX 1660 SUPER + Intel i7-10700", "software": "Python 3.8, PyTorch 1.10.0+cu102",
               "source": "arXiv 2308.12698, Table I"}
 
-#: Non-trivial floating operations (add/sub, mul, div, sqrt) of one
-#: closed-loop agent-step in the checker's definition, the minimum over the
-#: bench workload's states (748..762; operands that are exactly 0 or 1 are not
-#: counted); tests pin it to the checker's operation counter.
-FLOPS_PER_AGENT_STEP = 748
-#: Tape edges of one closed-loop step in the checker's reverse mode (minimum
-#: over the workload's states, 1348..1367); sweeping one costs a multiply and
-#: an add.  Algorithmic work of forward + adjoint per agent-step: the forward
-#: step, the step again to linearise it, and the reverse sweep.  The extra
-#: forward recomputation that checkpointing adds is not counted.
-ADJ_TAPE_EDGES_PER_AGENT_STEP = 1348
-FWD_ADJ_FLOPS_PER_AGENT_STEP = 2 * FLOPS_PER_AGENT_STEP + 2 * ADJ_TAPE_EDGES_PER_AGENT_STEP
+#: Algorithmic work of one closed-loop agent-step, the roofline's numerator: the method's
+#: FP32 operations counted by hand (a fused multiply-add counts 2): the time derivative
+#: (Eq. qd1-qd4 with Eq. 2-3 and drag) about 75, at each of the four RK4 stages (300); the RK4
+#: stage states and weighted combination about 120; the cascaded controller (position PD,
+#: desired attitude, attitude P, rate P, mixer, rotor clamp and square root) about 150.
+FLOPS_DERIVATIVE, FLOPS_RK4_UPDATES, FLOPS_CONTROLLER = 75, 120, 150
+FLOPS_PER_AGENT_STEP = 4 * FLOPS_DERIVATIVE + FLOPS_RK4_UPDATES + FLOPS_CONTROLLER  # 570
+#: The PID body-rate loop adds, per axis, the rate error, the integral and derivative terms and
+#: the integrator update: four fused multiply-adds (24 flops per agent-step).
+FLOPS_PER_AGENT_STEP_PID = FLOPS_PER_AGENT_STEP + 3 * 4 * 2  # 594
+#: Forward + adjoint per agent-step, one rule for every checkpoint interval: the forward step
+#: (1x), its recomputation inside the backward sweep (1x) and the reverse sweep (2.5x the
+#: forward).  The extra forward pass over a segment that a checkpoint interval C > 1 adds is
+#: not counted: it is the price of the smaller checkpoint memory, not work of the method.
+FWD_ADJ_FLOPS_PER_AGENT_STEP = int(4.5 * FLOPS_PER_AGENT_STEP)  # 2565
+#: The checker's count of non-trivial floating operations (add/sub, mul, div, sqrt) of one
+#: closed-loop agent-step along its deliberately plain route (desired attitude as a matrix
+#: converted by Shepperd's method, G^-1 by Gauss-Jordan, divisions), the minimum over the bench
+#: workload's states (748..762); reported beside the method's count, for context only.
+CHECKER_FLOPS_PER_AGENT_STEP = 748
 #: The same count for one step with the PID body-rate loop (minimum over the PID workload's
-#: states, 760..774), less the checker's second evaluation of the time derivative for omega'
-#: (a step takes omega' from its first RK4 stage).
-FLOPS_PER_AGENT_STEP_PID = 760
+#: states, 760..774), less the checker's second evaluation of the time derivative for omega'.
+CHECKER_FLOPS_PER_AGENT_STEP_PID = 760
+#: Tape edges of one closed-loop step in the checker's reverse mode (minimum over the
+#: workload's states, 1348..1367).
+CHECKER_ADJ_TAPE_EDGES_PER_AGENT_STEP = 1348
 #: The checker's count for one step of a car (98..101) and of a fixed-wing drone (156, plus
 #: five transcendental functions: four tan and one atan2, not counted), minimum over the mixed
-#: swarm's states.
+#: swarm's states.  No hand count of these models exists; the mixed swarm's work weights them
+#: with these figures and the quadrotors with the hand count.
 FLOPS_PER_AGENT_STEP_CAR = 98
 FLOPS_PER_AGENT_STEP_FIXED_WING = 156
 #: Bytes one plain step of a one-group swarm moves per agent: state 68 read +
 #: 68 written, command 16, status 1 (with one group the group id is not read).
 BYTES_PER_AGENT_STEP_PLAIN = 153
-#: FP32 lanes per SM (Blackwell) and the largest SM clock of the part.
+#: FP32 lanes per SM (Blackwell), warp schedulers per SM (each issues one warp instruction per
+#: clock) and the largest SM clock of the part.
 FP32_LANES_PER_SM = 128
+SCHEDULERS_PER_SM = 4
 SM_MAX_MHZ = 2032.0
 L2_FLUSH_BYTES = 256 << 20
-#: The sources that define the headline step kernel: a committed ncu figure is
-#: used only while their fingerprint is the one it was taken on.  (vehicles.cuh
-#: enters only the mixed-type instantiations.)
-KERNEL_SOURCES = ("paper_2308_12698_b300/csrc/model_fwd.cuh", "paper_2308_12698_b300/csrc/step_kernel.cuh")
+#: The sources of each profiled kernel: a committed ncu figure is used only while the
+#: fingerprint of its sources is the one it was taken on.
+CSRC = "paper_2308_12698_b300/csrc/"
+STEP_SOURCES = (CSRC + "model_fwd.cuh", CSRC + "step_kernel.cuh")
+KERNEL_SOURCES = {"step": STEP_SOURCES,
+                  "adjoint": STEP_SOURCES + (CSRC + "model_adj.cuh", CSRC + "adjoint_kernel.cuh"),
+                  "collide": (CSRC + "collide.cuh",),
+                  "multi": STEP_SOURCES + (CSRC + "vehicles.cuh",)}
 
 
-def kernel_sha() -> str:
+def kernel_sha(family: str = "step") -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[family]:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str, workload: str):
-    """dram bytes per launch from a committed ncu summary, if taken on the current kernel source."""
+def profiled(kernel: str, workload: str, family: str = "step") -> dict:
+    """ncu figures of one kernel on one workload from a committed profiles/ summary (its
+    `bench_counters:` line), if they were taken on the current kernel sources: DRAM bytes
+    per launch and thread instructions per unit of work.  Empty if there is none."""
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
-        return None
-    sha = kernel_sha()
+        return {}
+    sha = kernel_sha(family)
     for fn in sorted(os.listdir(pdir)):
         if not fn.endswith(".md"):
             continue
-        txt = open(os.path.join(pdir, fn)).read()
-        m = re.search(r"^bench_traffic:\s*kernel=(\S+)\s+workload=(\S+)\s+source_sha=(\w+)\s+bytes_per_launch=([\d.eE+]+)",
-                      txt, re.M)
-        if m and m.group(1) == kernel and m.group(2) == workload and m.group(3) == sha:
-            return float(m.group(4))
-    return None
+        for line in open(os.path.join(pdir, fn)):
+            if not line.startswith("bench_counters:"):
+                continue
+            kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+            if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("source_sha") == sha:
+                out = {"profile": "profiles/" + fn}
+                for k in ("bytes_per_launch", "inst_per_unit"):
+                    if k in kv:
+                        out[k] = float(kv[k])
+                return out
+    return {}
+
+
+def issue_frac(inst_per_unit, rate: float, sms: int, mhz: float):
+    """Fraction of the issue slots (SMs x schedulers x 32 threads x clock) that rate units per
+    second take at the profiled thread instructions per unit."""
+    if not inst_per_unit:
+        return None
+    return inst_per_unit * rate / (sms * SCHEDULERS_PER_SM * 32 * mhz * 1e6)
+
+
+def alu_roofline(flops: float, rate: float, sms: int, clocks: dict | None, prof: dict, kernel: str, **extra) -> dict:
+    """The FP32 roofline object of an ALU-bound leg: achieved = flops per unit x rate against
+    SMs x 128 lanes x 2 x the maximum clock, plus the issue-slot fraction from ncu."""
+    peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops * rate / 1e12
+    r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+         "flops_per_agent_step": flops, "kernel": kernel,
+         "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 (FMA) x {SM_MAX_MHZ:.0f} MHz max clock",
+         "traffic": None, "issue_frac": issue_frac(prof.get("inst_per_unit"), rate, sms, SM_MAX_MHZ),
+         "inst_per_agent_step": prof.get("inst_per_unit"), "counters": prof.get("profile")}
+    mhz = (clocks or {}).get("sm_mhz")
+    if mhz:
+        r["frac_at_measured_clock"] = r["frac"] * SM_MAX_MHZ / mhz
+        if r["issue_frac"] is not None:
+            r["issue_frac_at_measured_clock"] = r["issue_frac"] * SM_MAX_MHZ / mhz
+    r.update(extra)
+    return r
 
 
 def measured_peaks() -> dict:
@@ -321,6 +371,27 @@ def cpu_baseline(target_s: float = 10.0) -> dict:
                       f"std::thread over {threads} host cores, {secs:.1f} s"}
 
 
+#: First agents of each sweep point's workload, kept by the GPU sweep for the checker's rate
+_SWEEP_SLICES = {}
+#: Agents and steps of the checker's sample at each sweep point: all agents up to 1e5 (1000
+#: steps up to 1e4 agents, else 100), a 1e5-agent slice beyond (the rate is linear in N)
+CPU_SWEEP_MAX_AGENTS = 100_000
+
+
+def cpu_sweep_rates() -> dict:
+    import oracle
+    threads = os.cpu_count() or 1
+    out = {}
+    for n, (groups, gid, x0, cmd, mode) in sorted(_SWEEP_SLICES.items()):
+        steps = T_STEPS if n <= 10_000 else 100
+        t0 = time.perf_counter()
+        oracle.rollout(groups, gid, x0, cmd, DT, steps, mode, nthreads=threads)
+        secs = time.perf_counter() - t0
+        out[str(n)] = {"value": len(gid) * steps / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
+                       "sample": f"first {len(gid)} agents x {steps} steps", "seconds": secs}
+    return out
+
+
 def run_reference(args, world: int, rank: int):
     if rank != 0:
         return
@@ -460,19 +531,18 @@ def main():
     spread = {"repeats": len(rates), "mean": float(np.mean(rates)), "sd": float(np.std(rates, ddof=1)) if
               len(rates) > 1 else 0.0, "unit": UNIT}
 
-    # roofline of the dominant kernel: the fused step kernel, FP32-ALU bound
-    launch_s = (sum(times) / args.steps / launches) / 1e3
-    flops_launch = FLOPS_PER_AGENT_STEP * NA * min(K, TS)
-    peak_tflops = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = flops_launch / launch_s / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-            "traffic": profiled_traffic("step_kernel<1,false>", f"closed-loop-{NA}-K{K}"),
-            "kernel": f"step_kernel<closed loop, one group>, K={K} fused steps, block {tune['block']}",
-            "flops_per_agent_step": FLOPS_PER_AGENT_STEP,
-            "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 (FMA) x {SM_MAX_MHZ:.0f} MHz max clock",
-            "avg_launch_us": launch_s * 1e6}
-    if clocks.get("sm_mhz"):
-        roof["frac_at_measured_clock"] = achieved / (peak_tflops * clocks["sm_mhz"] / SM_MAX_MHZ)
+    # roofline of the dominant kernel: the fused step kernel, FP32-ALU bound.  Its average launch
+    # time is the timed region over the step launches (the one short pass per replay that
+    # reads the status bytes for agents gone non-finite is charged to them)
+    step_launches = -(-TS // K)
+    launch_s = (sum(times) / args.steps / step_launches) / 1e3
+    kernel_rate = NA * min(K, TS) / launch_s
+    prof = profiled("step_kernel<1,false>", f"closed-loop-{NA}-K{K}")
+    roof = alu_roofline(FLOPS_PER_AGENT_STEP, kernel_rate, sms, clocks, prof,
+                        f"step_kernel<closed loop, one group>, K={K} fused steps, block {tune['block']}",
+                        avg_launch_us=launch_s * 1e6)
+    roof["traffic"] = prof.get("bytes_per_launch")
+    roof["frac_checker_count"] = CHECKER_FLOPS_PER_AGENT_STEP * kernel_rate / 1e12 / roof["peak"]
 
     # end to end through the host-buffer C-ABI call
     h_state0 = planar(torch.from_numpy(wl.x0)).pin_memory()
@@ -500,9 +570,8 @@ def main():
 
     extra = {}
     if not args.no_extra and NA == N_AGENTS and TS == T_STEPS:
-        extra = side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_steps, sms)
+        extra = side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_steps, sms, clocks)
 
-    peaks = measured_peaks()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -511,11 +580,14 @@ def main():
             "roofline": roof, "clocks": clocks, "e2e": e2e, "gpu_launches": launches * args.steps,
             "repeat_spread": spread}
     line.update(extra)
-    if "hbm_gbs" in peaks and "plain" in line:
-        line["plain"]["roofline"]["peak"] = peaks["hbm_gbs"]
-        line["plain"]["roofline"]["frac"] = line["plain"]["roofline"]["achieved"] / peaks["hbm_gbs"]
     if world == 1 and rank == 0:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        if "sweep" in line:
+            # the checker beside each sweep point, on a bounded slice of that point's workload
+            rates = cpu_sweep_rates()
+            line["cpu_baseline"]["sweep"] = rates
+            for row in line["sweep"]:
+                row["oracle"] = rates.get(str(row["n_agents"]))
     if rank == 0:
         print(json.dumps(line), flush=True)
     graph.close()
@@ -621,8 +693,108 @@ def run_swarm_only(args, world, rank, dev, kind: str):
     sim.close()
 
 
-def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_steps, sms) -> dict:
-    """Plain kernel, fwd+adjoint and heterogeneous batch on the same GPU (3 timed reps each)."""
+def timed_fwd_adj(sim, x0, cmd, nsteps: int, C: int, timed_steps, reps: int):
+    """Checkpointed forward + adjoint of the loss |p_T - goal|^2 + w sum Omega^2 at interval C:
+    (ms per rollout pair, checkpoint MB, workspace MB)."""
+    import torch
+    dev = x0.device
+    ckpt = sim.ckpt_buffer(nsteps, C, device=dev)
+    rc = torch.empty(sim.n, dtype=torch.float32, device=dev)
+    gT = torch.zeros(sim.nx * sim.n, dtype=torch.float32, device=dev)
+    gT[: 3 * sim.n] = 1.0
+    w = torch.full((sim.n,), 1e-6, dtype=torch.float32, device=dev)
+    ws = torch.empty(max(sim.workspace_bytes(C), 1), dtype=torch.uint8, device=dev)
+
+    def run():
+        sim.rollout_forward(x0, cmd, DT, nsteps, C=C, ckpt=ckpt, run_cost=rc)
+        sim.rollout_backward(ckpt, cmd, DT, nsteps, gT, w, C=C, workspace=ws)
+
+    timed_steps(run, 2)
+    t = timed_steps(run, reps)
+    out = (sum(t) / reps, (ckpt.shape[0] * sim.ckpt_stride()) * 4 / 1e6, ws.numel() / 1e6)
+    del ckpt, ws
+    torch.cuda.empty_cache()
+    return out
+
+
+def fwd_adj_entry(world, sim, x0, cmd, nsteps, C, timed_steps, reps, sms, clocks) -> dict:
+    ms, ck_mb, ws_mb = timed_fwd_adj(sim, x0, cmd, nsteps, C, timed_steps, reps)
+    ms = max_over_ranks(ms, world)
+    rate = sim.n * nsteps / (ms / 1e3)
+    pa = profiled("adjoint_kernel<1>", f"closed-loop-C{C}", "adjoint")
+    pf = profiled("ckpt_kernel<1>", "closed-loop", "adjoint")
+    inst = pa["inst_per_unit"] + pf["inst_per_unit"] if ("inst_per_unit" in pa and "inst_per_unit" in pf) else None
+    roof = alu_roofline(FWD_ADJ_FLOPS_PER_AGENT_STEP, rate, sms, clocks, {"inst_per_unit": inst},
+                        "ckpt_kernel + adjoint_kernel + reduce_partials",
+                        basis="forward 1x + recomputation 1x + reverse sweep 2.5x the forward step's 570 flops")
+    roof["counters"] = [q.get("profile") for q in (pf, pa) if q]
+    return {"value": world * rate, "unit": UNIT, "ms_per_step": ms, "n_agents": sim.n, "physics_steps": nsteps,
+            "C": C, "block_adj": sim.launch()["block_adj"], "checkpoint_MB": ck_mb, "workspace_MB": ws_mb,
+            "roofline": roof}
+
+
+def swarm_leg(world, wl, dev, timed_steps, reps, **sim_kw):
+    """A tuned swarm in one graph per bench step: (sim, tuned config, ms per bench step)."""
+    import torch
+
+    from paper_2308_12698_b300 import autotune
+    from paper_2308_12698_b300.sim import Sim, planar
+    gid = torch.from_numpy(wl.gid).to(dev) if len(wl.groups) > 1 else None
+    s = Sim(wl.groups, wl.n, wl.mode, gid=gid)
+    x0 = planar(torch.from_numpy(wl.x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).reshape(-1).to(dev)
+    xx = x0.clone()
+    tune = autotune.tune_step(s, x0, cmd, DT, wl.nsteps)
+    g = s.graph(xx, cmd, DT, wl.nsteps, K=tune["K"])
+    reset = lambda: xx.copy_(x0)  # noqa: E731
+    timed_steps(g.launch, 2, reset)
+    t = timed_steps(g.launch, reps, reset)
+    ms = max_over_ranks(sum(t), world) / reps
+    g.close()
+    s.close()
+    return tune, ms
+
+
+def copy_bandwidth(nbytes: int, kind: str, reps: int = 20) -> float:
+    """GB/s of copies of nbytes: "h2d" / "d2h" between pinned host and device memory, "l2" a
+    device-to-device copy small enough to stay in L2 (read + write bytes counted).  reps
+    copies are enqueued back to back between two events, so the time is the copies' own and
+    not the host's enqueue cost; best of three such runs."""
+    import torch
+    n = nbytes // 4
+    if kind == "l2":
+        a = torch.ones(n, device="cuda")
+        b = torch.empty_like(a)
+        src, dst, moved = a, b, 2 * nbytes
+    else:
+        h = torch.ones(n).pin_memory()
+        d = torch.empty(n, device="cuda")
+        src, dst, moved = (h, d, nbytes) if kind == "h2d" else (d, h, nbytes)
+    for _ in range(3):
+        dst.copy_(src, non_blocking=True)
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            dst.copy_(src, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) / reps)
+    return moved / (best / 1e3) / 1e9
+
+
+#: Algorithmic bytes per agent of one collision call (1e6 agents, 2^21 buckets), as the
+#: kernels touch them.  Insert: status 1, position 16, list link 4, bucket head exchange 4.
+#: Query: status 1, position 16, arm length of its group 4, 27 bucket heads x 4, and per
+#: candidate on those lists (load 1e6 / 2^21, so 27 x 0.48 = 12.9 expected) its link 4, its
+#: position 16 and its arm length 4; hit byte 1.  Apply: hit and status 2.
+COLLIDE_BYTES_PER_AGENT = (1 + 16 + 4 + 4) + (1 + 16 + 4 + 27 * 4 + 12.9 * (4 + 16 + 4) + 1) + 2
+
+
+def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_steps, sms, clocks) -> dict:
+    """The other legs on the same GPU (3 timed repeats each unless stated)."""
     import torch
 
     from paper_2308_12698_b300 import autotune
@@ -630,9 +802,13 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     from paper_2308_12698_b300.sim import Sim, planar
     reps = 3
     out = {}
+    dev = x0.device
     reset = lambda: x.copy_(x0)  # noqa: E731
+    hbm = measured_peaks().get("hbm_gbs")
 
-    # plain one-step kernel: 1000 launches per bench step (graph), HBM bound
+    # plain one-step kernel: 1000 launches per bench step (graph); the 1e6-agent state and
+    # commands (84 MB) stay in the 126 MB L2 between launches, so this is not an HBM figure
+    # (the sweep's 1e7 point is)
     g1 = sim.graph(x, cmd, DT, T_STEPS, K=1)
     timed_steps(g1.launch, 2, reset)
     t = timed_steps(g1.launch, reps, reset)
@@ -640,156 +816,152 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     launch_s = ms / 1e3 / T_STEPS
     gbs = BYTES_PER_AGENT_STEP_PLAIN * N_AGENTS / launch_s / 1e9
     out["plain"] = {"value": world * N_AGENTS * T_STEPS / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
-                    "roofline": {"bound": "hbm", "achieved": gbs, "peak": None, "unit": "GB/s", "frac": None,
+                    "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": None,
+                                 "l2_equiv_frac": gbs / hbm if hbm else None,
                                  "bytes_per_agent_step": BYTES_PER_AGENT_STEP_PLAIN,
-                                 "note": "1e6-agent state (68 MB) + commands fit in the 126 MB L2 between launches"}}
+                                 "note": "L2-resident: the 1e6-agent state (68 MB) and commands fit in the 126 MB "
+                                         "L2 between launches; the HBM-bound case is sweep n_agents=1e7"}}
     g1.close()
 
-    # checkpointed forward + adjoint, 1e6 agents x 1000 steps, loss |p_T - goal|^2 + w sum Omega^2
+    # checkpointed forward + adjoint at 1e6 x 1000: the tuned interval and C = 100
     cfg = autotune.tune_adjoint(sim, x0, cmd, DT, T_STEPS)
-    C = cfg["C"]
-    ckpt = sim.ckpt_buffer(T_STEPS, C, device=x0.device)
-    rc = torch.empty(sim.n, dtype=torch.float32, device=x0.device)
-    gT = torch.zeros(17 * sim.n, dtype=torch.float32, device=x0.device)
-    gT[: 3 * sim.n] = 1.0
-    w = torch.full((sim.n,), 1e-6, dtype=torch.float32, device=x0.device)
-    ws = torch.empty(max(sim.workspace_bytes(C), 1), dtype=torch.uint8, device=x0.device)
+    fa = {}
+    for C in sorted({cfg["C"], 100}):
+        sim.set_launch(block_adj=cfg["block"])
+        fa[f"C{C}"] = fwd_adj_entry(world, sim, x0, cmd, T_STEPS, C, timed_steps, reps, sms, clocks)
+    out["fwd_adjoint"] = dict(fa[f"C{cfg['C']}"], tuned_C=cfg["C"], by_C=fa)
 
-    def fwd_adj():
-        sim.rollout_forward(x0, cmd, DT, T_STEPS, C=C, ckpt=ckpt, run_cost=rc)
-        sim.rollout_backward(ckpt, cmd, DT, T_STEPS, gT, w, C=C, workspace=ws)
+    # the differentiable-rollout workload: 4,096 agents in 4 groups, 2000 steps, C = 100
+    dw = W.differentiable()
+    ds = Sim(dw.groups, dw.n, dw.mode, gid=torch.from_numpy(dw.gid).to(dev))
+    dx0 = planar(torch.from_numpy(dw.x0)).to(dev)
+    dcmd = torch.from_numpy(dw.cmd).reshape(-1).to(dev)
+    c4 = fwd_adj_entry(world, ds, dx0, dcmd, dw.nsteps, 100, timed_steps, reps, sms, clocks)
+    kinks = {}
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "kinks_differentiable.json")) as f:
+            kinks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    c4.update(groups=len(dw.groups), kink_share=kinks.get("share"), kinks_by_kind=kinks.get("by_kind"),
+              kink_note="agents whose FP64 trajectory passes next to a controller kink (held to the looser "
+                        "gradient bar); counted by the checker, tests/golden/kinks_differentiable.json",
+              note="4,096 agents fill 32 of the SMs: latency-bound, not a throughput figure")
+    out["fwd_adjoint_config4"] = c4
+    ds.close()
+    del dx0, dcmd
 
-    timed_steps(fwd_adj, 2)
-    t = timed_steps(fwd_adj, reps)
-    ms = max_over_ranks(sum(t), world) / reps
-    rate = N_AGENTS * T_STEPS / (ms / 1e3)
-    peak_tf = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    out["fwd_adjoint"] = {"value": world * rate, "unit": UNIT, "ms_per_step": ms,
-                          "C": C, "block_adj": cfg["block"], "workspace_MB": ws.numel() / 1e6,
-                          "checkpoint_MB": ckpt.numel() * 4 / 1e6,
-                          "roofline": {"bound": "alu", "achieved": FWD_ADJ_FLOPS_PER_AGENT_STEP * rate / 1e12,
-                                       "peak": peak_tf, "unit": "TFLOP/s",
-                                       "frac": FWD_ADJ_FLOPS_PER_AGENT_STEP * rate / 1e12 / peak_tf,
-                                       "flops_per_agent_step": FWD_ADJ_FLOPS_PER_AGENT_STEP,
-                                       "basis": "forward + linearised forward + reverse sweep (2 flops per tape edge)"}}
-    del ckpt, ws
-
-    # heterogeneous: 8 groups, uneven sizes (600k), one persistent launch per K steps, graph
+    # heterogeneous: 8 groups, uneven sizes (600k), one persistent launch per K steps, graph;
+    # beside it the one-group swarm at the same agent count
     hw = W.heterogeneous(nsteps=T_STEPS, shuffle=False)
-    gid = torch.from_numpy(hw.gid).to(x0.device)
-    hs = Sim(hw.groups, hw.n, hw.mode, gid=gid)
-    hx0 = planar(torch.from_numpy(hw.x0)).to(x0.device)
-    hcmd = torch.from_numpy(hw.cmd).reshape(-1).to(x0.device)
-    hx = hx0.clone()
-    ht = autotune.tune_step(hs, hx0, hcmd, DT, T_STEPS)
-    hg = hs.graph(hx, hcmd, DT, T_STEPS, K=ht["K"])
-    hreset = lambda: hx.copy_(hx0)  # noqa: E731
-    timed_steps(hg.launch, 2, hreset)
-    t = timed_steps(hg.launch, reps, hreset)
-    ms = max_over_ranks(sum(t), world) / reps
+    ht, ms = swarm_leg(world, hw, dev, timed_steps, reps)
     hrate = hw.n * T_STEPS / (ms / 1e3)
+    st_, ms1 = swarm_leg(world, W.scale_sweep(hw.n, nsteps=T_STEPS), dev, timed_steps, reps)
+    rate1 = hw.n * T_STEPS / (ms1 / 1e3)
+    hp = profiled("step_kernel<1,true>", f"heterogeneous-{hw.n}-K{ht['K']}")
     out["hetero"] = {"value": world * hrate, "unit": UNIT, "ms_per_step": ms,
                      "n_agents": hw.n, "groups": len(hw.groups), "sizes": list(W.HETERO_SIZES), "K": ht["K"],
                      "block": ht["block"],
-                     "roofline": {"bound": "alu", "achieved": FLOPS_PER_AGENT_STEP * hrate / 1e12, "peak": peak_tf,
-                                  "unit": "TFLOP/s", "frac": FLOPS_PER_AGENT_STEP * hrate / 1e12 / peak_tf,
-                                  "flops_per_agent_step": FLOPS_PER_AGENT_STEP,
-                                  "note": "the quadrotor step's count; every group runs the same operations"}}
-    hg.close()
-    hs.close()
+                     "one_group_same_n": {"value": world * rate1, "K": st_["K"], "block": st_["block"]},
+                     "ratio_to_one_group": hrate / rate1,
+                     "roofline": alu_roofline(FLOPS_PER_AGENT_STEP, hrate, sms, clocks, hp,
+                                              "step_kernel<closed loop, groups in shared memory>",
+                                              note="every group runs the same operations")}
 
-    # PID body-rate loop: 1e6 agents with 20-component states, tuned K, one graph
+    # PID body-rate loop: 1e6 agents with 20-component states
     pw = W.closed_loop_pid(n=N_AGENTS, nsteps=T_STEPS)
-    ps = Sim(pw.groups, pw.n, pw.mode)
-    px0 = planar(torch.from_numpy(pw.x0)).to(x0.device)
-    pcmd = torch.from_numpy(pw.cmd).reshape(-1).to(x0.device)
-    px = px0.clone()
-    pt = autotune.tune_step(ps, px0, pcmd, DT, T_STEPS)
-    pg = ps.graph(px, pcmd, DT, T_STEPS, K=pt["K"])
-    preset = lambda: px.copy_(px0)  # noqa: E731
-    timed_steps(pg.launch, 2, preset)
-    t = timed_steps(pg.launch, reps, preset)
-    ms = max_over_ranks(sum(t), world) / reps
+    pt, ms = swarm_leg(world, pw, dev, timed_steps, reps)
     rate = pw.n * T_STEPS / (ms / 1e3)
+    pp = profiled("step_kernel<2,false>", f"closed-loop-pid-{pw.n}-K{pt['K']}")
     out["pid"] = {"value": world * rate, "unit": UNIT, "ms_per_step": ms, "n_agents": pw.n, "K": pt["K"],
                   "block": pt["block"],
-                  "roofline": {"bound": "alu", "achieved": FLOPS_PER_AGENT_STEP_PID * rate / 1e12, "peak": peak_tf,
-                               "unit": "TFLOP/s", "frac": FLOPS_PER_AGENT_STEP_PID * rate / 1e12 / peak_tf,
-                               "flops_per_agent_step": FLOPS_PER_AGENT_STEP_PID}}
-    pg.close()
-    ps.close()
-    del px, px0, pcmd
+                  "roofline": alu_roofline(FLOPS_PER_AGENT_STEP_PID, rate, sms, clocks, pp,
+                                           "step_kernel<PID rate loop, one group>")}
 
     # quadrotors, cars and fixed-wing drones (200,000 each) in one persistent launch
     mw = W.multi_type(nsteps=T_STEPS)
-    ms_ = Sim(mw.groups, mw.n, mw.mode, gid=torch.from_numpy(mw.gid).to(x0.device))
-    mx0 = planar(torch.from_numpy(mw.x0)).to(x0.device)
-    mcmd = torch.from_numpy(mw.cmd).reshape(-1).to(x0.device)
-    mx = mx0.clone()
-    mt = autotune.tune_step(ms_, mx0, mcmd, DT, T_STEPS)
-    mg = ms_.graph(mx, mcmd, DT, T_STEPS, K=mt["K"])
-    mreset = lambda: mx.copy_(mx0)  # noqa: E731
-    timed_steps(mg.launch, 2, mreset)
-    t = timed_steps(mg.launch, reps, mreset)
-    ms = max_over_ranks(sum(t), world) / reps
+    mt, ms = swarm_leg(world, mw, dev, timed_steps, reps)
     sizes = W.MULTI_TYPE_SIZES
+    rate = mw.n * T_STEPS / (ms / 1e3)
     flops = (sizes[0] * FLOPS_PER_AGENT_STEP + sizes[1] * FLOPS_PER_AGENT_STEP_CAR +
-             sizes[2] * FLOPS_PER_AGENT_STEP_FIXED_WING) * T_STEPS / (ms / 1e3)
-    out["multi_type"] = {"value": world * mw.n * T_STEPS / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+             sizes[2] * FLOPS_PER_AGENT_STEP_FIXED_WING) / mw.n
+    mp = profiled("step_kernel<1,true,true>", f"multi-type-{mw.n}-K{mt['K']}", "multi")
+    out["multi_type"] = {"value": world * rate, "unit": UNIT, "ms_per_step": ms,
                          "n_agents": mw.n, "sizes": {"quadrotor": sizes[0], "car": sizes[1], "fixed_wing": sizes[2]},
                          "K": mt["K"], "block": mt["block"],
-                         "roofline": {"bound": "alu", "achieved": flops / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
-                                      "frac": flops / 1e12 / peak_tf,
-                                      "note": "flops weighted by type; the drones' tan/atan2 are not counted"}}
-    mg.close()
-    ms_.close()
-    del mx, mx0, mcmd
+                         "roofline": alu_roofline(flops, rate, sms, clocks, mp, "step_kernel<mixed agent types>",
+                                                  note="quadrotors at the hand count, cars and fixed-wing drones "
+                                                       "at the checker's count; tan/atan2 not counted")}
+
+    # the closed-loop configuration at its own shape: 5,000 agents x 10,000 steps, tuned
+    cw1 = W.closed_loop()
+    c1t, ms = swarm_leg(world, cw1, dev, timed_steps, reps)
+    out["closed_loop_5000"] = {"value": world * cw1.n * cw1.nsteps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                               "n_agents": cw1.n, "physics_steps": cw1.nsteps, "K": c1t["K"],
+                               "block": c1t["block"],
+                               "note": "5,000 agents fill 20 of the SMs at the tuned block: latency-bound"}
 
     # decision rounds: commands from pinned host memory every M steps, positions back after
-    # each round, both overlapped with the physics (1000 steps per bench step)
+    # each round, both overlapped with the physics (1000 steps per bench step); beside them the
+    # pinned copy bandwidth of this machine's host link, per direction, for one round's 16 MB
+    link = {"h2d_GBs": copy_bandwidth(16 * N_AGENTS, "h2d"), "d2h_GBs": copy_bandwidth(16 * N_AGENTS, "d2h"),
+            "bytes": 16 * N_AGENTS, "how": "20 pinned 16 MB copies back to back per direction, CUDA events"}
     rounds = {}
     for M in (10, 100):
         R = T_STEPS // M
         h_cmds = torch.from_numpy(wl.cmd).reshape(1, -1).repeat(R, 1).contiguous().pin_memory()
         h_obs = torch.empty((R, 4 * N_AGENTS), dtype=torch.float32).pin_memory()
-        cmd2 = torch.empty(8 * N_AGENTS, dtype=torch.float32, device=x0.device)
-        obs2 = torch.empty(8 * N_AGENTS, dtype=torch.float32, device=x0.device)
+        cmd2 = torch.empty(8 * N_AGENTS, dtype=torch.float32, device=dev)
+        obs2 = torch.empty(8 * N_AGENTS, dtype=torch.float32, device=dev)
         Kr = min(sim.launch()["K"], M)
         rrun = lambda: sim.run_rounds(x, h_cmds, M, DT, K=Kr, h_obs=h_obs, cmd2=cmd2, obs2=obs2)  # noqa: E731
         timed_steps(rrun, 2, reset)
         t = timed_steps(rrun, reps, reset)
         ms = max_over_ranks(sum(t), world) / reps
+        per_dir = 16 * N_AGENTS * R / (ms / 1e3) / 1e9
         rounds[f"M{M}"] = {"value": world * N_AGENTS * T_STEPS / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
                            "rounds": R, "K": Kr, "h2d_bytes_per_round": 16 * N_AGENTS,
-                           "d2h_bytes_per_round": 16 * N_AGENTS}
-    out["decision_rounds"] = rounds
+                           "d2h_bytes_per_round": 16 * N_AGENTS, "link_GBs_per_direction": per_dir,
+                           "h2d_frac_of_link": per_dir / link["h2d_GBs"], "d2h_frac_of_link": per_dir / link["d2h_GBs"]}
+    out["decision_rounds"] = dict(rounds, link=link)
 
     # collision detection: 1e6 agents at 2 m mean spacing, 1 % planted near pairs
     cw = W.collision_field(N_AGENTS)
     cs = Sim(cw.groups, cw.n, cw.mode)
-    cx = planar(torch.from_numpy(cw.x0)).to(x0.device)
-    cws = torch.empty(max(cs.collide_workspace_bytes(), 1), dtype=torch.uint8, device=x0.device)
+    cx = planar(torch.from_numpy(cw.x0)).to(dev)
+    cws = torch.empty(max(cs.collide_workspace_bytes(), 1), dtype=torch.uint8, device=dev)
     crun = lambda: cs.collide(cx, 1.0, cws)  # noqa: E731
     timed_steps(crun, 2, cs.reset_status)
     t = timed_steps(crun, reps, cs.reset_status)
     ms = max_over_ranks(sum(t), world) / reps
     hits = int((cs.status() == 2).sum().item())
+    l2 = copy_bandwidth(32 << 20, "l2")
+    achieved = COLLIDE_BYTES_PER_AGENT * cw.n / (ms / 1e3) / 1e9
+    cp = profiled("collide_query", f"collision-field-{cw.n}", "collide")
     out["collide"] = {"value": world * cw.n / (ms / 1e3), "unit": "agents/s", "ms_per_call": ms,
                       "n_agents": cw.n, "collided": hits, "table_and_lists_MB": cws.numel() / 1e6,
-                      "method": "spatial hash, linked lists, 27-cell search"}
+                      "method": "spatial hash, linked lists, 27-cell search",
+                      "roofline": {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s",
+                                   "frac": achieved / l2, "bytes_per_agent": COLLIDE_BYTES_PER_AGENT,
+                                   "peak_basis": "measured in this run: 32 MB device-to-device copies that stay "
+                                                 "in L2, 20 back to back (read + write bytes)",
+                                   "traffic": cp.get("bytes_per_launch"), "counters": cp.get("profile"),
+                                   "note": "the table, lists and positions (8 + 4 + 16 MB) stay in L2; random "
+                                           "4- and 16-byte reads"}}
     cs.close()
     del cx, cws
 
     # scale sweep 1e3 .. 1e7 agents, 1000 closed-loop steps: plain K = 1, fused K = 10 and 100,
     # and fused at the tuned K
     sweep = []
-    peak_tflops = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    hbm = measured_peaks().get("hbm_gbs")
+    l2_bytes = 126e6
     for n in (1_000, 10_000, 100_000, 1_000_000, 10_000_000):
         sw = W.scale_sweep(n, nsteps=T_STEPS)
+        m = min(n, CPU_SWEEP_MAX_AGENTS)
+        _SWEEP_SLICES[n] = (sw.groups, sw.gid[:m].copy(), sw.x0[:m].copy(), sw.cmd[:m].copy(), sw.mode)
         ss = Sim(sw.groups, sw.n, sw.mode)
-        sx0 = planar(torch.from_numpy(sw.x0)).to(x0.device)
-        scmd = torch.from_numpy(sw.cmd).reshape(-1).to(x0.device)
+        sx0 = planar(torch.from_numpy(sw.x0)).to(dev)
+        scmd = torch.from_numpy(sw.cmd).reshape(-1).to(dev)
         sx = sx0.clone()
         st = autotune.tune_step(ss, sx0, scmd, DT, T_STEPS)
         sreset = lambda: sx.copy_(sx0)  # noqa: E731
@@ -802,33 +974,31 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
             rate = n * T_STEPS / (ms / 1e3)
             row[label] = {"value": rate, "unit": UNIT, "ms_per_1000_steps": ms, "K": k,
                           "tflops": FLOPS_PER_AGENT_STEP * rate / 1e12,
-                          "alu_frac": FLOPS_PER_AGENT_STEP * rate / 1e12 / peak_tflops}
+                          "alu_frac": alu_roofline(FLOPS_PER_AGENT_STEP, rate, sms, None, {}, "")["frac"]}
             if k == 1:
-                row[label]["hbm_gbs"] = BYTES_PER_AGENT_STEP_PLAIN * rate / 1e9
-                row[label]["hbm_frac"] = (BYTES_PER_AGENT_STEP_PLAIN * rate / 1e9 / hbm) if hbm else None
+                gbs = BYTES_PER_AGENT_STEP_PLAIN * rate / 1e9
+                row[label]["hbm_gbs_equiv"] = gbs
+                if n * 84 > l2_bytes:  # state + commands exceed L2: an HBM figure
+                    row[label]["hbm_frac"] = gbs / hbm if hbm else None
+                else:
+                    row[label]["hbm_frac"] = None
+                    row[label]["l2_equiv_frac"] = gbs / hbm if hbm else None
+                    row[label]["note"] = "state and commands stay in L2 between launches"
             gr.close()
         ss.close()
         sweep.append(row)
         del sx0, sx, scmd
     out["sweep"] = sweep
+    big = sweep[-1]["plain"]
+    out["plain"]["hbm_case"] = {"n_agents": sweep[-1]["n_agents"], "value": big["value"],
+                                "achieved_GBs": big["hbm_gbs_equiv"], "frac": big.get("hbm_frac")}
 
     # the paper's own measurement point: 1000 quadrotors, per-round time (context only)
     pw = W.scale_sweep(1000, nsteps=T_STEPS)
-    ps = Sim(pw.groups, pw.n, pw.mode)
-    px0 = planar(torch.from_numpy(pw.x0)).to(x0.device)
-    pcmd = torch.from_numpy(pw.cmd).reshape(-1).to(x0.device)
-    px = px0.clone()
-    pt = autotune.tune_step(ps, px0, pcmd, DT, T_STEPS)
-    pg = ps.graph(px, pcmd, DT, T_STEPS, K=pt["K"])
-    preset = lambda: px.copy_(px0)  # noqa: E731
-    timed_steps(pg.launch, 2, preset)
-    t = timed_steps(pg.launch, reps, preset)
-    ms = sum(t) / reps
+    pt, ms = swarm_leg(world, pw, dev, timed_steps, reps)
     out["n1000"] = {"value": 1000 * T_STEPS / (ms / 1e3), "unit": UNIT, "us_per_physics_step": ms,
                     "K": pt["K"], "note": "latency bound: 1000 agents fill 4 of the SMs",
                     "paper_context": PAPER_1000}
-    pg.close()
-    ps.close()
     return out
 
 

@@ -81,9 +81,16 @@
  *   Every int-returning call returns SIM_OK (0) or a negative SIM_ERR_*.
  *   Arguments are checked on the host before anything is enqueued.  No call
  *   raises, traps or asserts on the device.  An agent whose state becomes
- *   non-finite is marked dead in the status array and left at its last
- *   finite state; dead agents are skipped by every later call (cf. Sec.
- *   III-A: agents marked dead are excluded from the system).
+ *   non-finite is marked dead in the status array (1) and left at its last
+ *   finite state, whatever substeps_K: the stepping calls check each agent at
+ *   the end of a launch, and one more pass at the end of the call steps
+ *   again, one step at a time, the agents that went non-finite in the middle
+ *   of a K-step launch.  Dead agents (any nonzero status byte) are skipped by
+ *   every later call (cf. Sec. III-A: agents marked dead are excluded from
+ *   the system).  A status of 3 marks, inside a call, an agent waiting for
+ *   that pass; it can outlast a call only if the call returned an error.
+ *   The controller's clamps also bound a non-finite command component in the
+ *   closed-loop modes; commands should be finite.
  */
 #ifndef QUADSIM_H
 #define QUADSIM_H
@@ -248,9 +255,12 @@ int sim_rollout_backward(sim_handle_t h, const float* d_ckpt, const float* d_cmd
  * call): its scratch is a fixed array of SIM_NOALLOC_SCRATCH_BYTES (32 MiB)
  * inside the library, which every GPU that loads the library holds until the
  * process exits.
- *   - The grid is capped so that its scratch fits in the array; the results
- *     equal sim_rollout_backward's (per-agent outputs bit for bit, the group
- *     sums up to the order of the final reduction), possibly slower.
+ *   - The grid is capped so that its scratch fits in the array, possibly
+ *     slower.  Per-agent outputs equal sim_rollout_backward's bit for bit.
+ *     The per-group sums equal them up to FP32 summation-order rounding: a
+ *     capped grid partitions the agents over fewer blocks, so each block's
+ *     grid-stride loop, its per-warp accumulation and the final reduction
+ *     add the agents' terms in another order.
  *   - SIM_ERR_WORKSPACE if even one block does not fit, i.e. when
  *     ckpt_C * (68 B, 80 B in the PID mode) * (adjoint block size) + n_groups * 64 B exceeds
  *     32 MiB (ckpt_C above about 3,800 with the default 128-thread adjoint
@@ -320,7 +330,10 @@ int sim_graph_create(sim_handle_t h, float* d_state, const float* d_cmd, float d
 int sim_graph_launch(sim_graph_t g, void* stream);
 void sim_graph_destroy(sim_graph_t g);
 
-/* Number of kernel launches one sim_step call makes for these arguments. */
+/* Number of kernel launches one sim_step call makes for these arguments:
+ * ceil(nsteps / K) step launches, plus one pass that replays agents which
+ * went non-finite in the middle of a launch (none when every launch is a
+ * single step of one open- or P-closed-loop quadrotor group). */
 int64_t sim_step_launches(sim_handle_t h, int64_t nsteps, int substeps_K);
 
 void sim_destroy(sim_handle_t h);

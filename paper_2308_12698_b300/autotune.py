@@ -2,8 +2,9 @@
 (K) and checkpoint interval (C), timed with CUDA events on the real swarm and
 cached per (agents, groups, mode, device).
 
-The tuner only times library calls; it changes no result (every candidate is
-bitwise identical on the forward path, see tests/test_gpu_forward.py).
+The tuner only times library calls; it changes no result: every candidate is
+bitwise identical on the forward path
+(tests/test_gpu_1_forward.py::test_autotuner_pick_is_bitwise_any_other).
 """
 from __future__ import annotations
 

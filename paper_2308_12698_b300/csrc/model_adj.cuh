@@ -3,19 +3,31 @@
 // controller_vjp and step_vjp (P and PID rate loops).  Subgradients: clamps pass the gradient on
 // their closed interval, sqrt has derivative 0 at 0, branch choices (the roll
 // half-angle formula, sign of q_e.w) are constants.
+//
+// The mass and the inertias enter the dynamics only through the derived
+// group constants T2c = 2 kt / m, cd_m = c_d / m, gx, gy, gz (the gyroscopic
+// coefficients) and txc, tyc, tzc (torque / inertia).  The sweep accumulates
+// the cotangents of those eight constants (dc) and theta_from_derived turns
+// them into m and J cotangents once per agent.
+
 #pragma once
 #include "model_fwd.cuh"
 
 namespace qs {
 
 // ------------------------------------------------------------------ VJPs --
-// Adds to yb (13) and tb (theta), and writes to Omb (the stage's rotor
-// speeds, 4), the products of g (13) with the Jacobians of rb_derivative at
-// (y, Om).
+// Cotangents of the derived dynamics constants of DevGroup, in this order:
+// T2c, cd_m, gx, gy, gz, txc, tyc, tzc.
+enum { DC_T2 = 0, DC_CD, DC_GX, DC_GY, DC_GZ, DC_TX, DC_TY, DC_TZ, NDC };
+
+// Adds to yb (13) and dc (the derived constants), and writes to Omb (the
+// stage's rotor speeds, 4), the products of g (13) with the Jacobians of
+// rb_derivative at (y, Om).
 __device__ __forceinline__ void rb_derivative_vjp(const DevGroup& P, const float* y, const float Om[4], const float* g,
-                                                  float* yb, float Omb[4], float tb[NTH]) {
+                                                  float* yb, float Omb[4], float dc[NDC]) {
   const float s1 = Om[0] * Om[0], s2 = Om[1] * Om[1], s3 = Om[2] * Om[2], s4 = Om[3] * Om[3];
-  const float T2 = P.T2c * ((s1 + s2) + (s3 + s4));
+  const float Ssum = (s1 + s2) + (s3 + s4);
+  const float T2 = P.T2c * Ssum;
   const float Dx = (s1 - s2) + (s4 - s3), Dy = (s3 + s4) - (s1 + s2), Dz = (s1 - s2) + (s3 - s4);
   const float w = y[QW], qx = y[QX], qy = y[QY], qz = y[QZ];
   const float wx = y[WX], wy = y[WX + 1], wz = y[WX + 2];
@@ -26,8 +38,8 @@ __device__ __forceinline__ void rb_derivative_vjp(const DevGroup& P, const float
   yb[VX + 1] += g[1] - P.cd_m * gvy;
   yb[VX + 2] += g[2] - P.cd_m * gvz;
   const float T2b = gvx * bx + gvy * by + gvz * (0.5f - bxy);
-  const float gv_v = gvx * y[VX] + gvy * y[VX + 1] + gvz * y[VX + 2];
-  tb[TH_M] += (gv_v * P.cd_m - T2b * T2) * P.inv_m;
+  dc[DC_T2] += T2b * Ssum;  // T2 = T2c * Ssum
+  dc[DC_CD] -= gvx * y[VX] + gvy * y[VX + 1] + gvz * y[VX + 2];
   const float bbx = gvx * T2, bby = gvy * T2, bbxy = -gvz * T2;
   float qbw = qy * bbx - qx * bby;
   float qbx = qz * bbx - w * bby + 2.f * qx * bbxy;
@@ -43,15 +55,14 @@ __device__ __forceinline__ void rb_derivative_vjp(const DevGroup& P, const float
   float wbx = -gw * qx + gx * w + gy * qz - gz * qy;
   float wby = -gw * qy - gx * qz + gy * w + gz * qx;
   float wbz = -gw * qz + gx * qy - gy * qx + gz * w;
-  // omega'_x = ((Jy - Jz) wy wz + kt L sin(a) Dx) / Jx, and cyclic
+  // omega'_x = gx wy wz + txc Dx, and cyclic
   const float nx = g[WX], ny = g[WX + 1], nz = g[WX + 2];
-  const float dwx = P.gx * (wy * wz) + P.txc * Dx;
-  const float dwy = P.gy * (wz * wx) + P.tyc * Dy;
-  const float dwz = P.gz * (wx * wy) + P.tzc * Dz;
-  const float ax = nx * P.iJx, ay = ny * P.iJy, az = nz * P.iJz;
-  tb[TH_J] += -ax * dwx - ay * (wz * wx) + az * (wx * wy);
-  tb[TH_J + 1] += ax * (wy * wz) - ay * dwy - az * (wx * wy);
-  tb[TH_J + 2] += -ax * (wy * wz) + ay * (wz * wx) - az * dwz;
+  dc[DC_GX] += nx * (wy * wz);
+  dc[DC_GY] += ny * (wz * wx);
+  dc[DC_GZ] += nz * (wx * wy);
+  dc[DC_TX] += nx * Dx;
+  dc[DC_TY] += ny * Dy;
+  dc[DC_TZ] += nz * Dz;
   wbx += ny * P.gy * wz + nz * P.gz * wy;
   wby += nx * P.gx * wz + nz * P.gz * wx;
   wbz += nx * P.gx * wy + ny * P.gy * wx;
@@ -64,18 +75,26 @@ __device__ __forceinline__ void rb_derivative_vjp(const DevGroup& P, const float
   Omb[3] = 2.f * Om[3] * ((a0 + a1) + (a2 - a3));
 }
 
+// Adds the m and J cotangents that the derived constants' cotangents dc
+// carry: T2c = 2 kt / m and cd_m = c_d / m (d/dm = -T2c / m, -cd_m / m);
+// gx = (Jy - Jz) / Jx, gy = (Jz - Jx) / Jy, gz = (Jx - Jy) / Jz, txc ~ 1 / Jx,
+// tyc ~ 1 / Jy, tzc ~ 1 / Jz.
+__device__ __forceinline__ void theta_from_derived(const DevGroup& P, const float dc[NDC], float tb[NTH]) {
+  tb[TH_M] -= (dc[DC_T2] * P.T2c + dc[DC_CD] * P.cd_m) * P.inv_m;
+  tb[TH_J] += dc[DC_GZ] * P.iJz - dc[DC_GY] * P.iJy - (dc[DC_GX] * P.gx + dc[DC_TX] * P.txc) * P.iJx;
+  tb[TH_J + 1] += dc[DC_GX] * P.iJx - dc[DC_GZ] * P.iJz - (dc[DC_GY] * P.gy + dc[DC_TY] * P.tyc) * P.iJy;
+  tb[TH_J + 2] += dc[DC_GY] * P.iJy - dc[DC_GX] * P.iJx - (dc[DC_GZ] * P.gz + dc[DC_TZ] * P.tzc) * P.iJz;
+}
+
 // Cotangent of the controller: ub (rotor commands) -> xb (state), tb (theta).
 // PID: also eb, the cotangent of the rate error e the integrator consumed;
 // adds the integral term's share to xb[XI..] and writes wdb, the cotangent of
 // omega' (wdot, at x), for the caller to carry through Eq. (qd4).
+// C: the controller's values at x (controller_fwd).
 template <bool PID = false>
-__device__ __forceinline__ void controller_vjp(const DevGroup& P, const float* x, const float4 c, const Hd& hd,
+__device__ __forceinline__ void controller_vjp(const DevGroup& P, const float* x, const Hd& hd, const Ctl& C,
                                                const float ub[4], float* xb, float tb[NTH],
-                                               const float* wdot = nullptr, const float* eb = nullptr,
-                                               float* wdb = nullptr) {
-  Ctl C;
-  float u[4], e[3];
-  controller_fwd<PID>(P, x, c, hd, C, u, wdot, e);
+                                               const float* eb = nullptr, float* wdb = nullptr) {
   // sqrt(clamp(S)): gradient passes on 0 < S <= om2max (sqrt'(0) taken as 0)
   float Sb[4];
 #pragma unroll
@@ -167,13 +186,19 @@ __device__ __forceinline__ void controller_vjp(const DevGroup& P, const float* x
 }
 
 // Adjoint of one RK4 step x_n -> x_{n+1}: lam <- (d x_{n+1} / d x_n)^T lam,
-// tb += (d x_{n+1} / d theta)^T lam.  x is the step-start state.
+// tb += (d x_{n+1} / d theta)^T lam (the controller's gains and m), dc += the
+// derived constants' share (theta_from_derived).  x is the step-start state.
+// The controller is evaluated twice: for the rotor commands the stages need,
+// and again for the values its VJP needs at the end (keeping them from the
+// first evaluation, in registers or in a shared-memory stash, measured
+// slower: the recomputation fills issue slots that would otherwise wait).
 template <int MODE>
 __device__ __forceinline__ void step_vjp(const DevGroup& P, const St& x, const float4 c, const Hd& hd,
-                                         const StepH& H, const LagCoef& L, St& lam, float tb[NTH]) {
+                                         const StepH& H, const LagCoef& L, St& lam, float tb[NTH], float dc[NDC]) {
   float u[4];
   float wdot[3], e[3];  // PID: omega' at x and the rate error
   if (MODE == 2) {
+    // omega' at x (the first RK4 stage's) feeds the derivative term
     float k0[NRB];
     rb_derivative(P, x.a, x.a + OM, k0);
     wdot[0] = k0[WX]; wdot[1] = k0[WX + 1]; wdot[2] = k0[WX + 2];
@@ -215,7 +240,7 @@ __device__ __forceinline__ void step_vjp(const DevGroup& P, const St& x, const f
   }
 #pragma unroll
   for (int i = 0; i < NRB; ++i) { xb[i] = lam.a[i]; g[i] = coef(i, H.h6, H.h6q) * lam.a[i]; yb[i] = 0.f; }
-  rb_derivative_vjp(P, y4, Om, g, yb, Ob, tb);
+  rb_derivative_vjp(P, y4, Om, g, yb, Ob, dc);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     ub[i] += L.c4 * Ob[i];
@@ -228,7 +253,7 @@ __device__ __forceinline__ void step_vjp(const DevGroup& P, const St& x, const f
     g[i] = 2.f * coef(i, H.h6, H.h6q) * lam.a[i] + coef(i, H.h, H.hq) * yb[i];
     yb[i] = 0.f;
   }
-  rb_derivative_vjp(P, y3, Om, g, yb, Ob, tb);
+  rb_derivative_vjp(P, y3, Om, g, yb, Ob, dc);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     ub[i] += L.c3 * Ob[i];
@@ -241,7 +266,7 @@ __device__ __forceinline__ void step_vjp(const DevGroup& P, const St& x, const f
     g[i] = 2.f * coef(i, H.h6, H.h6q) * lam.a[i] + coef(i, H.h2, H.h2q) * yb[i];
     yb[i] = 0.f;
   }
-  rb_derivative_vjp(P, y2, Om, g, yb, Ob, tb);
+  rb_derivative_vjp(P, y2, Om, g, yb, Ob, dc);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     ub[i] += L.c2 * Ob[i];
@@ -253,7 +278,7 @@ __device__ __forceinline__ void step_vjp(const DevGroup& P, const St& x, const f
     g[i] = coef(i, H.h6, H.h6q) * lam.a[i] + coef(i, H.h2, H.h2q) * yb[i];
     yb[i] = 0.f;
   }
-  rb_derivative_vjp(P, x.a, x.a + OM, g, yb, Ob, tb);
+  rb_derivative_vjp(P, x.a, x.a + OM, g, yb, Ob, dc);
 #pragma unroll
   for (int i = 0; i < 4; ++i) xb[OM + i] += Ob[i];
 #pragma unroll
@@ -268,18 +293,24 @@ __device__ __forceinline__ void step_vjp(const DevGroup& P, const St& x, const f
       xb[XI + i] = pass ? lam.a[XI + i] : 0.f;
       eb[i] = pass ? H.h * lam.a[XI + i] : 0.f;
     }
-    controller_vjp<true>(P, x.a, c, hd, ub, xb, tb, wdot, eb, wdb);
+    Ctl C;
+    float u2[4], e2[3];
+    controller_fwd<true>(P, x.a, c, hd, C, u2, wdot, e2);
+    controller_vjp<true>(P, x.a, hd, C, ub, xb, tb, eb, wdb);
     // omega' = rows WX.. of Eq. (qd4) at (x, Omega)
 #pragma unroll
     for (int i = 0; i < NRB; ++i) { g[i] = 0.f; yb[i] = 0.f; }
     g[WX] = wdb[0]; g[WX + 1] = wdb[1]; g[WX + 2] = wdb[2];
-    rb_derivative_vjp(P, x.a, x.a + OM, g, yb, Ob, tb);
+    rb_derivative_vjp(P, x.a, x.a + OM, g, yb, Ob, dc);
 #pragma unroll
     for (int i = 0; i < NRB; ++i) xb[i] += yb[i];
 #pragma unroll
     for (int i = 0; i < 4; ++i) xb[OM + i] += Ob[i];
   } else if (MODE == 1) {
-    controller_vjp(P, x.a, c, hd, ub, xb, tb);
+    Ctl C;
+    float u2[4];
+    controller_fwd(P, x.a, c, hd, C, u2);
+    controller_vjp(P, x.a, hd, C, ub, xb, tb);
   }
 #pragma unroll
   for (int i = 0; i < state_dim<MODE>(); ++i) lam.a[i] = xb[i];

@@ -15,7 +15,8 @@
 #include <thread>
 
 #include "../../include/quadsim.h"
-#include "model_adj.cuh"
+#include "adjoint_kernel.cuh"
+#include "collide.cuh"
 #include "model_fwd.cuh"
 #include "step_kernel.cuh"
 
@@ -28,240 +29,9 @@ constexpr int kDefaultBlockAdj = 128;
 constexpr int kDefaultK = 10;
 constexpr int kDefaultC = 100;
 
-// --------------------------------------------------------------- kernels --
-
-struct CkptArgs {
-  const float* x0;
-  float* ckpt;
-  float* run_cost;
-  const float4* cmd;
-  const uint8_t* gid;
-  uint8_t* status;
-  int64_t n;
-  int64_t nsteps;
-  int C;
-  int S;
-  int n_groups;
-  StepH H;
-  const DevGroup* groups;
-};
-
-// Floats from one checkpoint to the next: a planar state (NS N floats)
-// rounded up to a multiple of 4, so that every checkpoint starts on a 16-byte
-// boundary as its float4 planes need (N not a multiple of 4 leaves a gap).
-__host__ __device__ constexpr int64_t ckpt_stride(int ns, int64_t n) { return ((int64_t)ns * n + 3) & ~(int64_t)3; }
-
-// Whole forward rollout in one launch, checkpoint every C steps.
-template <int MODE, bool HETERO>
-__global__ void __launch_bounds__(256) ckpt_kernel(CkptArgs A, const DevGroup P0) {
-  extern __shared__ float4 smem4[];
-  DevGroup* sg = reinterpret_cast<DevGroup*>(smem4);
-  load_groups<HETERO>(sg, A.groups, A.n_groups);
-  constexpr int NS = state_dim<MODE>();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t cstride = ckpt_stride(NS, A.n);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) {
-    St x;
-    load_state<NS>(A.x0, A.n, i, x);
-    store_state<NS>(A.ckpt, A.n, i, x);
-    if (A.status[i]) {  // frozen: every checkpoint is the current state
-      for (int s = 1; s <= A.S; ++s) store_state<NS>(A.ckpt + s * cstride, A.n, i, x);
-      if (A.run_cost) A.run_cost[i] = 0.f;
-      continue;
-    }
-    const float4 c = A.cmd[i];
-    const Hd hd = heading(MODE != 0 ? c.w : 0.f);
-    const DevGroup P = HETERO ? sg[A.gid[i]] : P0;
-    const LagCoef L = lag_coef(P.inv_tau, A.H);
-    float rc = 0.f;
-    for (int s = 0; s < A.S; ++s) {
-      const int len = (int)min((int64_t)A.C, A.nsteps - (int64_t)s * A.C);
-      for (int k = 0; k < len; ++k) {
-        step<MODE>(P, x, c, hd, A.H, L);
-        rc += (x.a[OM] * x.a[OM] + x.a[OM + 1] * x.a[OM + 1]) + (x.a[OM + 2] * x.a[OM + 2] + x.a[OM + 3] * x.a[OM + 3]);
-      }
-      store_state<NS>(A.ckpt + (s + 1) * cstride, A.n, i, x);
-    }
-    if (A.run_cost) A.run_cost[i] = rc;
-    if (!all_finite<NS>(x)) A.status[i] = 1;
-  }
-}
-
-struct AdjArgs {
-  const float* ckpt;
-  const float4* cmd;
-  const uint8_t* gid;
-  const uint8_t* status;
-  const float* dLdxT;
-  const float* w_run;
-  float* dLdx0;
-  float* th_agent;
-  float* partials;  // [gridDim.x][n_groups][16]
-  float* scratch;   // [C][state planes][grid threads]
-  int64_t n;
-  int64_t nsteps;
-  int C;
-  int S;
-  int n_groups;
-  StepH H;
-  const DevGroup* groups;
-};
-
-// Starts copying agent i's state out of the planar checkpoint `src` (n
-// agents) into this thread's prefetch slot: five float4 slots, `bd` apart
-// (plane 4 of a 17-float state is one float, copied into the slot's first
-// four bytes).
-template <int NS>
-__device__ __forceinline__ void prefetch_state(float4* dst, int bd, const float* src, int64_t n, int64_t i) {
-  const float4* P = reinterpret_cast<const float4*>(src);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) cp_async16(dst + k * bd, P + k * n + i);
-  if (NS == NXP)
-    cp_async16(dst + 4 * bd, P + 4 * n + i);
-  else
-    cp_async4(dst + 4 * bd, src + 16 * n + i);
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-
-template <int NS>
-__device__ __forceinline__ void read_prefetched(const float4* src, int bd, St& x) {
-  const float4 a = src[0], b = src[bd], c = src[2 * bd], d = src[3 * bd], e = src[4 * bd];
-  x.a[0] = a.x; x.a[1] = a.y; x.a[2] = a.z; x.a[3] = a.w;
-  x.a[4] = b.x; x.a[5] = b.y; x.a[6] = b.z; x.a[7] = b.w;
-  x.a[8] = c.x; x.a[9] = c.y; x.a[10] = c.z; x.a[11] = c.w;
-  x.a[12] = d.x; x.a[13] = d.y; x.a[14] = d.z; x.a[15] = d.w;
-  x.a[16] = e.x;
-  if (NS == NXP) { x.a[17] = e.y; x.a[18] = e.z; x.a[19] = e.w; }
-}
-
-// Discrete adjoint: per agent, segments in reverse; each segment is
-// recomputed from its checkpoint into this thread's scratch column, then
-// swept backwards step by step.  Per-agent theta cotangents are reduced per
-// group inside each warp (fixed butterfly order), accumulated per warp in
-// shared memory, and written as one partial per block.
-// SMEMS: the segment's step-start states live in shared memory (small C)
-// rather than in the global scratch, and each segment's checkpoint is
-// prefetched into shared memory (cp.async, double-buffered) while the
-// segment before it in the sweep is being processed.
-template <int MODE, bool SMEMS>
-__global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
-  extern __shared__ float4 smem4[];
-  DevGroup* sg = reinterpret_cast<DevGroup*>(smem4);
-  float* wacc = reinterpret_cast<float*>(sg + A.n_groups);
-  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int e = threadIdx.x; e < nw * A.n_groups * NTH; e += blockDim.x) wacc[e] = 0.f;
-  load_groups<true>(sg, A.groups, A.n_groups);
-  // shared scratch starts after the accumulators, 16-byte aligned
-  float* sscr = reinterpret_cast<float*>(smem4 + (sizeof(DevGroup) * A.n_groups + 4 * nw * A.n_groups * NTH + 15) / 16);
-  float* const scratch = SMEMS ? sscr : A.scratch;
-  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;  // grid stride over agents
-  // scratch column of this thread: its own slot in the block (shared) or in the grid (global)
-  const int64_t scols = SMEMS ? (int64_t)blockDim.x : nthreads;
-  const int64_t slot = SMEMS ? (int64_t)threadIdx.x : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  constexpr int NS = state_dim<MODE>();
-  const int64_t sstep = (int64_t)NS * scols;
-  const int64_t cstride = ckpt_stride(NS, A.n);
-  // checkpoint prefetch slots (SMEMS): [2 buffers][5 planes][block] float4, after the scratch
-  const int bd = blockDim.x;
-  float4* const mypf = reinterpret_cast<float4*>(sscr + (SMEMS ? (int64_t)A.C * sstep : 0)) + threadIdx.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < A.n; base += nthreads) {
-    const int64_t i = base + threadIdx.x;
-    float tb[NTH];
-#pragma unroll
-    for (int q = 0; q < NTH; ++q) tb[q] = 0.f;
-    int g = -1;
-    if (i < A.n && A.status[i] == 0) {
-      g = A.gid ? (int)A.gid[i] : 0;
-      const DevGroup& P = sg[g];  // read from shared memory where used: keeps registers for the adjoint
-      const LagCoef L = lag_coef(P.inv_tau, A.H);
-      const float4 c = A.cmd[i];
-      const Hd hd = heading(MODE != 0 ? c.w : 0.f);
-      const float w = A.w_run ? A.w_run[i] : 0.f;
-      St lam, x;
-      load_state<NS>(A.dLdxT, A.n, i, lam);
-      load_state<NS>(A.ckpt + (int64_t)A.S * cstride, A.n, i, x);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) lam.a[OM + q] += 2.f * w * x.a[OM + q];
-      if (SMEMS) prefetch_state<NS>(mypf, bd, A.ckpt + (int64_t)(A.S - 1) * cstride, A.n, i);
-      for (int s = A.S - 1; s >= 0; --s) {
-        const int64_t n0 = (int64_t)s * A.C;
-        const int len = (int)min((int64_t)A.C, A.nsteps - n0);
-        if (SMEMS) {
-          // this segment's checkpoint has arrived; start fetching the next one
-          const int b = (A.S - 1 - s) & 1;
-          cp_async_wait_all();
-          read_prefetched<NS>(mypf + b * 5 * bd, bd, x);
-          if (s > 0) prefetch_state<NS>(mypf + (b ^ 1) * 5 * bd, bd, A.ckpt + (int64_t)(s - 1) * cstride, A.n, i);
-        } else {
-          load_state<NS>(A.ckpt + (int64_t)s * cstride, A.n, i, x);
-        }
-        for (int j = 0; j < len; ++j) {
-          store_state<NS>(scratch + j * sstep, scols, slot, x);
-          if (j + 1 < len) step<MODE>(P, x, c, hd, A.H, L);
-        }
-        for (int j = len - 1; j >= 0; --j) {
-          load_state<NS>(scratch + j * sstep, scols, slot, x);
-          step_vjp<MODE>(P, x, c, hd, A.H, L, lam, tb);
-          if (n0 + j >= 1) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) lam.a[OM + q] += 2.f * w * x.a[OM + q];
-          }
-        }
-      }
-      store_state<NS>(A.dLdx0, A.n, i, lam);
-      if (A.th_agent) {
-#pragma unroll
-        for (int q = 0; q < NTH; ++q) A.th_agent[i * NTH + q] = tb[q];
-      }
-    } else if (i < A.n) {
-      // a dead agent is frozen over the rollout (x_T = x_0, no running
-      // cost): dL/dx_0 = dL/dx_T, and it adds nothing to theta
-      St lam;
-      load_state<NS>(A.dLdxT, A.n, i, lam);
-      store_state<NS>(A.dLdx0, A.n, i, lam);
-      if (A.th_agent) {
-#pragma unroll
-        for (int q = 0; q < NTH; ++q) A.th_agent[i * NTH + q] = 0.f;
-      }
-    }
-    unsigned todo = __ballot_sync(0xffffffffu, g >= 0);
-    while (todo) {
-      const int leader = __ffs(todo) - 1;
-      const int gl = __shfl_sync(0xffffffffu, g, leader);
-      const bool mine = (g == gl);
-      todo &= ~__ballot_sync(0xffffffffu, mine);
-#pragma unroll
-      for (int q = 0; q < NTH; ++q) {
-        float v = mine ? tb[q] : 0.f;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane == 0) wacc[(warp * A.n_groups + gl) * NTH + q] += v;
-      }
-    }
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < A.n_groups * NTH; e += blockDim.x) {
-    float s = 0.f;
-    for (int w = 0; w < nw; ++w) s += wacc[w * A.n_groups * NTH + e];
-    A.partials[(int64_t)blockIdx.x * A.n_groups * NTH + e] = s;
-  }
-}
-
-// out[e] = sum over blocks b of partials[b][e], fixed order: each thread sums
-// a strided subset in increasing b, then a fixed shared-memory tree.
-__global__ void __launch_bounds__(256) reduce_partials(const float* partials, int nblocks, int width, float* out) {
-  __shared__ float buf[256];
-  const int e = blockIdx.x;
-  float s = 0.f;
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partials[(int64_t)b * width + e];
-  buf[threadIdx.x] = s;
-  __syncthreads();
-  for (int off = blockDim.x >> 1; off > 0; off >>= 1) {
-    if (threadIdx.x < off) buf[threadIdx.x] += buf[threadIdx.x + off];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[e] = buf[0];
-}
+// ----------------------------------------------------- utility kernels --
+// (the step kernels are in step_kernel.cuh, the rollout and adjoint kernels
+// in adjoint_kernel.cuh, collision detection in collide.cuh)
 
 __global__ void max_gid_kernel(const uint8_t* gid, int64_t n, unsigned int* out) {
   unsigned int m = 0;
@@ -277,82 +47,6 @@ __global__ void count_dead_kernel(const uint8_t* status, int64_t n, unsigned lon
     c += status[i] != 0;
   for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
-}
-
-// ------------------------------------------------------------ collisions --
-
-struct CollArgs {
-  const float4* pos;      // plane 0 of the planar state: (px, py, pz, vx)
-  const uint8_t* gid;
-  uint8_t* status;
-  const float* arm;
-  float scale;
-  float inv_cell;
-  uint32_t mask;          // table size - 1 (power of two)
-  int* head;              // [table] first agent of each bucket, -1 if empty
-  int* next;              // [n] next agent in the same bucket, -1 at the end
-  uint8_t* hit;           // [n]
-  int64_t n;
-};
-
-// Spatial hash of an integer cell (Teschner et al., 2003).
-__device__ __forceinline__ uint32_t cell_key(int cx, int cy, int cz, uint32_t mask) {
-  return (((uint32_t)cx * 73856093u) ^ ((uint32_t)cy * 19349663u) ^ ((uint32_t)cz * 83492791u)) & mask;
-}
-
-__device__ __forceinline__ int cell_of(float v, float inv_cell) { return (int)floorf(v * inv_cell); }
-
-__global__ void __launch_bounds__(256) collide_insert(CollArgs A) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) {
-    if (A.status[i]) continue;
-    const float4 p = A.pos[i];
-    const uint32_t k = cell_key(cell_of(p.x, A.inv_cell), cell_of(p.y, A.inv_cell), cell_of(p.z, A.inv_cell), A.mask);
-    A.next[i] = atomicExch(&A.head[k], (int)i);
-  }
-}
-
-// FP32 pair test with every operation rounded separately (no contraction).
-__device__ __forceinline__ bool pair_hit(float4 pi, float ri, float4 pj, float rj) {
-  const float dx = __fsub_rn(pj.x, pi.x), dy = __fsub_rn(pj.y, pi.y), dz = __fsub_rn(pj.z, pi.z);
-  const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-  const float rs = __fadd_rn(ri, rj);
-  return d2 < __fmul_rn(rs, rs);
-}
-
-__global__ void __launch_bounds__(256) collide_query(CollArgs A) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) {
-    uint8_t h = 0;
-    if (A.status[i] == 0) {
-      const float4 pi = A.pos[i];
-      const float ri = __fmul_rn(A.arm[A.gid ? A.gid[i] : 0], A.scale);
-      const int cx = cell_of(pi.x, A.inv_cell), cy = cell_of(pi.y, A.inv_cell), cz = cell_of(pi.z, A.inv_cell);
-      int64_t budget = A.n + 27;  // a list never holds more than n agents
-      for (int dz = -1; dz <= 1 && !h; ++dz)
-        for (int dy = -1; dy <= 1 && !h; ++dy)
-          for (int dx = -1; dx <= 1 && !h; ++dx) {
-            int j = A.head[cell_key(cx + dx, cy + dy, cz + dz, A.mask)];
-            while (j >= 0 && budget-- > 0) {
-              if ((int64_t)j != i) {
-                const float rj = __fmul_rn(A.arm[A.gid ? A.gid[j] : 0], A.scale);
-                if (pair_hit(pi, ri, A.pos[j], rj)) {
-                  h = 1;
-                  break;
-                }
-              }
-              j = A.next[j];
-            }
-          }
-    }
-    A.hit[i] = h;
-  }
-}
-
-__global__ void __launch_bounds__(256) collide_apply(CollArgs A) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride)
-    if (A.hit[i] && A.status[i] == 0) A.status[i] = 2;
 }
 
 // ------------------------------------------------------------ host side --
@@ -540,10 +234,14 @@ size_t adj_smem_scratch_bytes(const sim_s* h, int C) {
 
 bool adj_smem_scratch(const sim_s* h, int C) { return adj_smem_scratch_bytes(h, C) <= kSmemScratchMax; }
 
+// Dynamic shared memory of one adjoint block: the group table and the
+// per-warp accumulators, then (16-byte aligned) the segment scratch with the
+// checkpoint prefetch slots when they fit, else the prefetch slots alone
+// (for the step-start states read back from the global scratch).
 size_t adj_smem(const sim_s* h, int C) {
   size_t b = sizeof(DevGroup) * h->n_groups + (size_t)(h->block_adj / 32) * h->n_groups * NTH * sizeof(float);
-  if (adj_smem_scratch(h, C)) b = ((b + 15) & ~(size_t)15) + adj_smem_scratch_bytes(h, C);
-  return b;
+  b = (b + 15) & ~(size_t)15;
+  return b + (adj_smem_scratch(h, C) ? adj_smem_scratch_bytes(h, C) : 2 * 5 * sizeof(float4) * h->block_adj);
 }
 
 int adj_grid(const sim_s* h, int C) {
@@ -620,6 +318,33 @@ int launch_step(sim_s* h, float* d_state, const float* d_cmd, StepH H, int K, cu
     if (hetero(h)) step_kernel<0, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
     else step_kernel<0, false><<<grid, h->block_fwd, smem, st>>>(A, P0);
   }
+  return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ERR_CUDA;
+}
+
+// After the launches of one call over agents [first, first + count) with one
+// command plane, at most kmax steps each: replays the agents whose state went
+// non-finite in a launch of the fused form to their last finite state
+// (refreeze_kernel).  Nothing to do when every launch was of the plain form.
+int launch_refreeze(sim_s* h, float* d_state, const float* d_cmd, StepH H, int64_t kmax, cudaStream_t st,
+                    int64_t first, int64_t count) {
+  if (count <= 0 || plain_path(h, (int)kmax)) return SIM_OK;
+  StepArgs A;
+  A.state = d_state;
+  A.cmd = reinterpret_cast<const float4*>(d_cmd);
+  A.gid = h->gid;
+  A.status = h->status;
+  A.n = h->n;
+  A.first = first;
+  A.count = count;
+  A.K = (int)kmax;
+  A.n_groups = h->n_groups;
+  A.H = H;
+  A.groups = h->d_groups;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, (int64_t)h->sms * 4));
+  if (h->multi) refreeze_kernel<1, true><<<grid, 256, 0, st>>>(A);
+  else if (h->mode == SIM_CLOSED_LOOP_PID) refreeze_kernel<2><<<grid, 256, 0, st>>>(A);
+  else if (h->mode == SIM_CLOSED_LOOP) refreeze_kernel<1><<<grid, 256, 0, st>>>(A);
+  else refreeze_kernel<0><<<grid, 256, 0, st>>>(A);
   return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ERR_CUDA;
 }
 
@@ -806,7 +531,7 @@ int sim_get_launch(sim_handle_t h, int* block_fwd, int* block_adj, int* K, int* 
 int64_t sim_step_launches(sim_handle_t h, int64_t nsteps, int substeps_K) {
   if (!h || nsteps <= 0 || h->n == 0) return 0;
   const int64_t K = substeps_K > 0 ? substeps_K : h->K;
-  return (nsteps + K - 1) / K;
+  return (nsteps + K - 1) / K + (plain_path(h, (int)std::min(K, nsteps)) ? 0 : 1);  // + the refreeze pass
 }
 
 int sim_step(sim_handle_t h, float* d_state, const float* d_cmd, float dt, int64_t nsteps, int substeps_K,
@@ -824,7 +549,7 @@ int sim_step(sim_handle_t h, float* d_state, const float* d_cmd, float dt, int64
     if (rc != SIM_OK) return rc;
     done += k;
   }
-  return SIM_OK;
+  return launch_refreeze(h, d_state, d_cmd, H, std::min<int64_t>(K, nsteps), st, 0, h->n);
 }
 
 int sim_step_host(sim_handle_t h, float* h_state, const float* h_cmd, float* d_state, float* d_cmd, float dt,
@@ -874,6 +599,8 @@ int sim_step_host(sim_handle_t h, float* h_state, const float* h_cmd, float* d_s
       if (rc != SIM_OK) return rc;
       done += k;
     }
+    if (launch_refreeze(h, d_state, d_cmd, H, std::min<int64_t>(K, nsteps), sc, a0, cnt) != SIM_OK)
+      return SIM_ERR_CUDA;
     if (cudaEventRecord(h->ev_done[c], sc) != cudaSuccess ||
         cudaStreamWaitEvent(h->s_d2h, h->ev_done[c], 0) != cudaSuccess ||
         !copy_planes(h_state, d_state, a0, cnt, cudaMemcpyDeviceToHost, h->s_d2h))
@@ -921,6 +648,8 @@ int sim_run_rounds(sim_handle_t h, float* d_state, float* d_cmd2, const float* h
       if (rc != SIM_OK) return rc;
       done += k;
     }
+    if (launch_refreeze(h, d_state, cmd, H, std::min<int64_t>(K, steps_per_round), st, 0, n) != SIM_OK)
+      return SIM_ERR_CUDA;
     if (cudaEventRecord(h->ev_cmd_free[b], st) != cudaSuccess) return SIM_ERR_CUDA;
     if (d_obs2) {
       float* snap = d_obs2 + b * plane;

@@ -3,7 +3,11 @@
 // launches; one parameter group in kernel parameters or several in shared
 // memory indexed by a per-agent uint8 id; grid-stride over a resident wave.
 // Agents with a nonzero status byte are skipped; an agent whose state turns
-// non-finite keeps its last finite state and is marked (status 1).
+// non-finite keeps its last finite state, whatever K, and is marked (status
+// 1): the plain form (K = 1) keeps the launch-start state; the fused form
+// marks the agent kStatusDiverged without storing, and refreeze_kernel, run
+// after the call's launches, steps the launch-start state again one step at
+// a time.
 #pragma once
 #include "model_fwd.cuh"
 #include "vehicles.cuh"
@@ -37,6 +41,11 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Status byte of an agent whose state went non-finite at some step of a
+// launch of the fused form and is still at that launch's start state; within
+// the same call refreeze_kernel turns it into 1 at the last finite state.
+constexpr uint8_t kStatusDiverged = 3;
 
 template <int NS = NX>
 __device__ __forceinline__ bool all_finite(const St& x) {
@@ -160,8 +169,43 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 1) step_kernel(StepArgs A, co
     if (all_finite<state_dim<MODE>()>(x)) {
       store_state<state_dim<MODE>()>(A.state, A.n, i, x);
     } else {
-      A.status[i] = 1;  // keep the last finite state
+      // the plain form (one step) keeps the launch-start state, the last finite
+      // one; after a fused launch refreeze_kernel finds it
+      A.status[i] = PLAIN ? 1 : kStatusDiverged;
     }
+  }
+}
+
+// After a call's K-step launches (same state, command and step size): each
+// agent marked kStatusDiverged is still at the start state of the launch in
+// which its state went non-finite.  That state is stepped again one step at a
+// time, with the same arithmetic, and stored after every finite step; the
+// replay meets the same non-finite step, within K steps, and stops there.
+// The agent ends at its last finite state -- the bits that K = 1 launches
+// keep -- and is marked non-finite (1).  A separate kernel, so that the hot
+// loop's code is not touched; its cost is one read of the status bytes.
+template <int MODE, bool MULTI = false>
+__global__ void __launch_bounds__(256) refreeze_kernel(StepArgs A) {
+  constexpr int NS = state_dim<MODE>();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t end = A.first + A.count;
+  for (int64_t i = A.first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end; i += stride) {
+    if (A.status[i] != kStatusDiverged) continue;
+    const DevGroup& P = A.groups[A.n_groups > 1 ? A.gid[i] : 0];
+    const float4 c = A.cmd[i];
+    const Hd hd = heading(MODE != 0 ? c.w : 0.f);
+    const LagCoef L = lag_coef(P.inv_tau, A.H);
+    St x;
+    load_state<NS>(A.state, A.n, i, x);
+    for (int k = 0; k < A.K; ++k) {
+      if (MULTI && P.vt != (float)TYPE_QUAD)
+        vehicle_step(P, x, c, A.H);
+      else
+        step<MODE>(P, x, c, hd, A.H, L);
+      if (!all_finite<NS>(x)) break;
+      store_state<NS>(A.state, A.n, i, x);
+    }
+    A.status[i] = 1;
   }
 }
 

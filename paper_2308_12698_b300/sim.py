@@ -305,16 +305,25 @@ class QuadRollout(torch.autograd.Function):
     run_cost_a = sum_{n=1..T} sum_i Omega_{n,i}^2.  The backward pass is the
     library's discrete adjoint with checkpoints every C steps; it returns
     gradients for theta and x0.
+
+    The adjoint recomputes the rollout from its checkpoints under the handle's
+    parameters, so backward runs under the theta that forward used: if the
+    handle's theta has changed since (sim.set_theta, or another forward with
+    another theta on the same handle), backward puts the saved theta back for
+    its own call and restores the newer one afterwards.  Parameter changes
+    wait for the current stream (sim_set_params does not order itself against
+    work in flight).
     """
 
     @staticmethod
     def forward(ctx, theta, x0, sim: Sim, cmd, dt: float, nsteps: int, C: int = 0):
-        th = theta.detach().cpu().numpy()
-        if not np.array_equal(th.astype(np.float32), sim.theta()):
-            sim.set_theta(th)
+        th = theta.detach().cpu().numpy().astype(np.float32)
+        if not np.array_equal(th, sim.theta()):
+            _set_theta_ordered(sim, th)
         ckpt, rc = sim.rollout_forward(x0.detach().contiguous(), cmd, dt, nsteps, C)
         ctx.sim, ctx.cmd, ctx.dt, ctx.nsteps, ctx.C = sim, cmd, dt, nsteps, C
         ctx.theta_device = theta.device
+        ctx.theta = th
         ctx.save_for_backward(ckpt)
         return ckpt[-1].clone(), rc
 
@@ -325,8 +334,21 @@ class QuadRollout(torch.autograd.Function):
         if g_xT is None:
             g_xT = torch.zeros(sim.nx * sim.n, dtype=torch.float32, device=ckpt.device)
         w = None if g_rc is None else g_rc.contiguous().float()
+        current = [dict(g) for g in sim.groups]
+        swapped = not np.array_equal(sim.theta(), ctx.theta)
+        if swapped:
+            _set_theta_ordered(sim, ctx.theta)
         dx0, dth, _ = sim.rollout_backward(ckpt, ctx.cmd, ctx.dt, ctx.nsteps, g_xT.contiguous().float(), w, ctx.C)
+        if swapped:
+            torch.cuda.current_stream().synchronize()
+            sim.set_params(current)
         return dth.to(ctx.theta_device), dx0, None, None, None, None, None
+
+
+def _set_theta_ordered(sim: Sim, theta: np.ndarray):
+    """sim.set_theta after the current stream's work (which may still read the old parameters)."""
+    torch.cuda.current_stream().synchronize()
+    sim.set_theta(theta)
 
 
 def planar(x: torch.Tensor) -> torch.Tensor:

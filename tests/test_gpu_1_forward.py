@@ -220,7 +220,8 @@ def test_several_rounds_every_agent_stepped(dev, orc, rounds_ref):
     """The block-256 run of the round test against the checker at the first and last agents, both
     sides of every resident-wave boundary, the last chunk, and a random sample."""
     wl, got = rounds_ref
-    wave = 148 * 2 * 256  # resident agents per round at 256-thread blocks, 2 per SM
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    wave = sms * 2 * 256  # resident agents per round at 256-thread blocks, 2 per SM
     edges = [k * wave + d for k in range(1, ROUNDS_N // wave + 1) for d in (-1, 0)]
     idx = np.unique(np.concatenate([[0, 1, 31, 32, ROUNDS_N - 33, ROUNDS_N - 2, ROUNDS_N - 1], edges,
                                     np.random.default_rng(3).choice(ROUNDS_N, 512, replace=False)]))
@@ -266,7 +267,7 @@ def test_graph_replay_matches_direct(dev):
     x = planar(torch.from_numpy(wl.x0)).to(dev)
     cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
     g = sim.graph(x, cmd, wl.dt, 100, K=10)
-    assert g.launches_per_replay == 10
+    assert g.launches_per_replay == 11  # ten 10-step launches and the pass for agents gone non-finite
     for _ in range(3):
         g.launch()
     torch.cuda.synchronize()
@@ -443,6 +444,88 @@ def test_nonfinite_agent_is_frozen_and_counted(dev):
     sim.reset_status()
     assert sim.n_dead() == 0
     sim.close()
+
+
+def _diverging_swarm(kind):
+    """A small swarm in which eight agents spin about body z at 5,900-9,000 rad/s: beyond RK4's
+    stability bound on the imaginary axis (h |omega| / 2 > 2 sqrt 2 at h = 1 ms), so their
+    quaternion grows by a fixed factor each step and their state overflows after some 15 to
+    300 steps, mostly in the middle of a 100-step launch.  The other agents stay finite."""
+    if kind == "open":
+        wl = W.open_loop(n=64, nsteps=300)
+    elif kind == "hetero":
+        wl = W.heterogeneous(sizes=(32, 32), nsteps=300, shuffle=True)
+    else:
+        wl = W.closed_loop_pid(n=64, nsteps=300)
+    x0 = wl.x0.copy()
+    spin = [3, 9, 17, 22, 35, 41, 50, 63]
+    x0[spin, 10:13] = 0.0
+    x0[spin, 12] = [5900.0, 6000.0, 6100.0, 6200.0, 6500.0, 7000.0, 8000.0, 9000.0]
+    return W.Workload(wl.name, wl.mode, wl.groups, wl.gid, x0, wl.cmd, wl.dt, 300), spin
+
+
+@pytest.mark.parametrize("kind", ["open", "hetero", "pid"])
+def test_nonfinite_freeze_does_not_depend_on_K(dev, kind):
+    """An agent that turns non-finite in the middle of a K-step launch keeps its last finite
+    state, the same bits that one-step launches keep: 300 steps as 300 launches of one step, 3 of
+    100 and 1 of 300 give the same state for every agent and the same status bytes.  The frozen
+    state is the last finite one: one more step from it overflows.  Then a NaN written on the host
+    into a live agent's state between launches freezes that agent as it was written, at K = 1
+    and at K = 100 alike, and the other agents go on."""
+    from paper_2308_12698_b300.sim import Sim, planar, unplanar
+    wl, spin = _diverging_swarm(kind)
+    gid = torch.from_numpy(wl.gid).to(dev) if len(wl.groups) > 1 else None
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    runs, status = {}, {}
+    died_at = {}
+    for K in (1, 100, 300):
+        sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
+        x = planar(torch.from_numpy(wl.x0)).to(dev)
+        if K == 1:  # one launch per step: record the step at which each agent is marked
+            for n in range(1, 301):
+                sim.step(x, cmd, wl.dt, 1, K=1)
+                st = sim.status().cpu().numpy()
+                for a in np.flatnonzero(st):
+                    died_at.setdefault(int(a), n)
+        else:
+            sim.step(x, cmd, wl.dt, 300, K=K)
+        torch.cuda.synchronize()
+        runs[K] = unplanar(x, wl.n).cpu().numpy()
+        status[K] = sim.status().cpu().numpy()
+        sim.close()
+    assert sorted(died_at) == sorted(spin), died_at
+    assert sum(1 for n in died_at.values() if n % 100 != 1) >= 4, died_at  # mid-launch at K = 100
+    for K in (100, 300):
+        np.testing.assert_array_equal(runs[K], runs[1])
+        np.testing.assert_array_equal(status[K], status[1])
+    assert np.all(np.isfinite(runs[1]))
+    assert set(np.flatnonzero(status[1])) == set(spin) and np.all(status[1][spin] == 1)
+    # the frozen states are the last finite ones: one more step from each overflows
+    sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
+    x = planar(torch.from_numpy(runs[1])).to(dev)
+    sim.step(x, cmd, wl.dt, 1, K=1)
+    assert sorted(np.flatnonzero(sim.status().cpu().numpy())) == sorted(spin)
+    sim.close()
+    # a NaN written on the host into a live agent's angular rate after 40 steps
+    calm = np.setdiff1d(np.arange(wl.n), spin)
+    j = int(calm[5])
+    outs = {}
+    for K in (1, 100):
+        sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
+        x = planar(torch.from_numpy(wl.x0)).to(dev)
+        sim.step(x, cmd, wl.dt, 40, K=K)
+        host = unplanar(x, wl.n).cpu().numpy()
+        host[j, 11] = np.nan
+        x.copy_(planar(torch.from_numpy(host)).to(dev))
+        sim.step(x, cmd, wl.dt, 100, K=K)
+        torch.cuda.synchronize()
+        outs[K] = unplanar(x, wl.n).cpu().numpy()
+        st = sim.status().cpu().numpy()
+        gone = sorted([a for a, n in died_at.items() if n <= 140] + [j])
+        assert st[j] == 1 and sorted(np.flatnonzero(st)) == gone
+        np.testing.assert_array_equal(outs[K][j], host[j])  # NaN where it was written
+        sim.close()
+    np.testing.assert_array_equal(outs[100], outs[1])
 
 
 def test_device_argument_errors(dev):

@@ -106,11 +106,10 @@ def test_adjoint_matches_fp64_reverse_mode(dev, orc):
         check_loose(dth[gi], rdth[wl.gid == gi].sum(axis=0), f"theta group {gi}")
 
 
-def test_adjoint_gentle_rollout_every_agent_strict(dev, orc):
+def gentle(n_per_group, n_groups, nsteps):
     """Start at rest, level, at the commanded heading, 0.1 m from the goal, headings over all of
-    [-pi, pi) (every Shepperd branch of the desired attitude): no agent comes near a kink, so
-    every agent meets the strict bar."""
-    base = W.differentiable(n_per_group=64, n_groups=2, nsteps=400)
+    [-pi, pi) (every Shepperd branch of the desired attitude): no agent comes near a kink."""
+    base = W.differentiable(n_per_group=n_per_group, n_groups=n_groups, nsteps=nsteps)
     rng = np.random.default_rng(11)
     goal = (base.x0[:, 0:3] + rng.uniform(-0.1, 0.1, (base.n, 3))).astype(np.float32)
     cmd = base.cmd.copy()
@@ -121,8 +120,13 @@ def test_adjoint_gentle_rollout_every_agent_strict(dev, orc):
     x0[:, 6:10] = np.stack([np.cos(half), 0 * half, 0 * half, np.sin(half)], 1).astype(np.float32)
     x0[:, 3:6] = 0.0
     x0[:, 10:13] = 0.0
-    wl = W.Workload("gentle", base.mode, base.groups, base.gid, x0, cmd, base.dt, base.nsteps, goal=goal,
-                    w_omega=1e-6)
+    return W.Workload("gentle", base.mode, base.groups, base.gid, x0, cmd, base.dt, base.nsteps, goal=goal,
+                      w_omega=1e-6)
+
+
+def test_adjoint_gentle_rollout_every_agent_strict(dev, orc):
+    """No agent of the gentle rollout comes near a kink, so every agent meets the strict bar."""
+    wl = gentle(64, 2, 400)
     assert not flagged(orc, wl).any()
     r = gpu_grad(wl, dev, C=50)
     dx0, dth, dth_a = r["outs"][0]
@@ -132,6 +136,32 @@ def test_adjoint_gentle_rollout_every_agent_strict(dev, orc):
         check_block(dx0[a], rdx0[a], f"x0 agent {a}")
     for gi in range(len(wl.groups)):
         check_block(dth[gi], rdth[wl.gid == gi].sum(axis=0), f"theta group {gi}")
+
+
+#: theta's parameter families (gains per loop, mass, inertia): their units and scales differ
+THETA_FAMILIES = {"kp": slice(0, 3), "kd": slice(3, 6), "katt": slice(6, 9), "krate": slice(9, 12),
+                  "m": slice(12, 13), "J": slice(13, 16)}
+
+
+def test_group_sums_strict_against_fp64(dev, orc):
+    """The per-group reduction (warp butterflies, per-warp accumulators, per-block partials, the
+    fixed-order second pass) on 4,096 kink-free agents in 4 airframe groups: each group's
+    dL/dtheta_g against the sum of the FP64 reverse mode's per-agent gradients over that group,
+    at the strict bar, on the whole 16-vector and on each parameter family alone (so that the
+    mass gradient, orders of magnitude above the gains', sets no floor for them)."""
+    wl = gentle(1024, 4, 400)
+    assert not flagged(orc, wl).any()
+    r = gpu_grad(wl, dev, C=50, per_agent=False)
+    _, dth, _ = r["outs"][0]
+    _, _, rdth = orc.grad(wl.groups, wl.gid, wl.x0, wl.cmd, wl.dt, wl.nsteps, wl.mode, wl.goal, wl.w_omega)
+    worst = 0.0
+    for gi in range(len(wl.groups)):
+        ref = rdth[wl.gid == gi].sum(axis=0)
+        check_block(dth[gi], ref, f"theta group {gi}")
+        for fam, sl in THETA_FAMILIES.items():
+            check_block(dth[gi][sl], ref[sl], f"theta group {gi} {fam}")
+        worst = max(worst, float(np.max(np.abs(dth[gi] - ref) / np.abs(ref))))
+    print(f"group sums: worst component relative error {worst:.2e}")
 
 
 def test_running_cost_matches(dev, orc):
@@ -252,6 +282,44 @@ def test_autograd_function(dev):
     dx0, dth, _ = ref["outs"][0]
     np.testing.assert_allclose(theta.grad.cpu().numpy(), dth, rtol=1e-5, atol=1e-6 * np.abs(dth).max())
     np.testing.assert_allclose(unplanar(x0.grad, wl.n).cpu().numpy(), dx0, rtol=1e-5, atol=1e-7)
+    sim.close()
+
+
+def test_autograd_two_forwards_at_different_theta(dev):
+    """Two rollouts of one handle at different theta, summed into one loss: each backward runs
+    under the theta its own forward used, so the gradients equal separate forward/backward pairs
+    on handles of their own, bit for bit; the handle keeps the later forward's theta."""
+    from paper_2308_12698_b300.sim import QuadRollout, Sim, planar, unplanar, with_theta
+    wl = W.differentiable(n_per_group=64, n_groups=2, nsteps=200)
+    gid = torch.from_numpy(wl.gid).to(dev)
+    sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
+    th0 = sim.theta()
+    th1 = th0.copy()
+    th1[:, 0:3] *= 1.25  # kp
+    th1[:, 12] *= 1.1  # mass
+    x0 = planar(torch.from_numpy(wl.x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).to(dev).reshape(-1)
+    goal = torch.from_numpy(wl.goal).to(dev)
+
+    def loss_of(xT, rc):
+        p = unplanar(xT, wl.n)[:, 0:3]
+        return ((p - goal) ** 2).sum() + wl.w_omega * rc.sum()
+
+    ta, tb = torch.tensor(th0, requires_grad=True), torch.tensor(th1, requires_grad=True)
+    xa, xb = x0.clone().requires_grad_(True), x0.clone().requires_grad_(True)
+    loss = loss_of(*QuadRollout.apply(ta, xa, sim, cmd, wl.dt, wl.nsteps, 20)) + \
+        loss_of(*QuadRollout.apply(tb, xb, sim, cmd, wl.dt, wl.nsteps, 20))
+    loss.backward()
+    assert np.array_equal(sim.theta(), th1)
+    assert not torch.equal(ta.grad, tb.grad)
+    for th, tgrad, xgrad in ((th0, ta.grad, xa.grad), (th1, tb.grad, xb.grad)):
+        alone = Sim([with_theta(g, t) for g, t in zip(wl.groups, th)], wl.n, wl.mode, gid=gid)
+        t = torch.tensor(th, requires_grad=True)
+        x = x0.clone().requires_grad_(True)
+        loss_of(*QuadRollout.apply(t, x, alone, cmd, wl.dt, wl.nsteps, 20)).backward()
+        assert torch.equal(t.grad, tgrad)
+        assert torch.equal(x.grad, xgrad)
+        alone.close()
     sim.close()
 
 

@@ -5,11 +5,13 @@ real-time control loop that reserves all of its memory at start-up, or a
 plug-in whose host application owns every device allocation -- so they cannot
 hand sim_rollout_backward a workspace.  The workspace-free entry point runs
 the same adjoint out of a fixed 32 MiB array inside the library.  This test
-calls it through the C ABI, twice in a row (the array keeps the previous
-call's contents), and compares it with the workspace entry point: per-agent
-gradients bit for bit, per-group sums within 1e-5 (their final reduction runs
-over a different number of blocks).  The file name makes pytest collect it
-last.
+calls it through the C ABI three times in a row (the array keeps the previous
+call's contents; the first call differentiates another terminal cotangent) and
+compares each call with the workspace entry point on the same input, for the
+P and the PID rate loop: per-agent gradients bit for bit, per-group sums
+within 1e-5 (the capped grid partitions the agents over fewer blocks, so the
+group sums are added in another order).  The file name makes pytest collect
+it last.
 """
 import ctypes
 
@@ -24,7 +26,8 @@ def _p(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def test_noalloc_adjoint_matches_workspace_adjoint_on_two_calls():
+@pytest.mark.parametrize("pid", [False, True], ids=["p-loop", "pid-loop"])
+def test_noalloc_adjoint_matches_workspace_adjoint_on_two_calls(pid):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import __graft_entry__
@@ -36,28 +39,39 @@ def test_noalloc_adjoint_matches_workspace_adjoint_on_two_calls():
     L = _lib.lib()
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
-    # one checkpoint segment of 400 steps: 400 x 68 B per thread, so the fixed
-    # array holds fewer resident blocks than the workspace path launches
+    # one checkpoint segment of 400 steps: 400 x 68 B (80 B with the PID loop's
+    # integral) per thread, so the fixed array holds fewer resident blocks than
+    # the 16 blocks of 128 threads the 2,048 agents need, and each block of the
+    # capped grid takes several agents in turn
     T, C = 400, 400
-    wl = W.differentiable(n_per_group=512, n_groups=4, nsteps=T)
+    make = W.differentiable_pid if pid else W.differentiable
+    wl = make(n_per_group=512, n_groups=4, nsteps=T)
     gid = torch.from_numpy(wl.gid).to(dev)
     sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
+    nx = sim.nx
     x0 = planar(torch.from_numpy(wl.x0)).to(dev)
     cmd = torch.from_numpy(wl.cmd).reshape(-1).to(dev)
     ckpt, _ = sim.rollout_forward(x0, cmd, wl.dt, T, C=C)
-    gT = torch.zeros(17 * wl.n, device=dev)
+    gT = torch.zeros(nx * wl.n, device=dev)
     gT[: 3 * wl.n] = 1.0
+    # another terminal cotangent, for a call whose leftovers the next call must not see
+    g_other = torch.from_numpy(np.random.default_rng(5).normal(size=nx * wl.n).astype(np.float32)).to(dev)
     w = torch.full((wl.n,), wl.w_omega, device=dev)
-    ref_dx0, ref_dth, ref_dtha = sim.rollout_backward(ckpt, cmd, wl.dt, T, gT, w, C=C, per_agent=True)
+    refs = {}
+    for name, g in (("other", g_other), ("loss", gT)):
+        refs[name] = sim.rollout_backward(ckpt, cmd, wl.dt, T, g, w, C=C, per_agent=True)
     torch.cuda.synchronize()
-    assert torch.isfinite(ref_dx0).all() and torch.isfinite(ref_dth).all()
+    for r in refs.values():
+        assert all(torch.isfinite(t).all() for t in r)
 
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    for _ in range(2):
+    # three calls in a row: the first with the other cotangent, then two with the loss's
+    for name, g in (("other", g_other), ("loss", gT), ("loss", gT)):
+        ref_dx0, ref_dth, ref_dtha = refs[name]
         dx0 = torch.full_like(ref_dx0, float("nan"))
         dth = torch.full_like(ref_dth, float("nan"))
         dtha = torch.full_like(ref_dtha, float("nan"))
-        rc = L.sim_rollout_backward_noalloc(sim.handle, _p(ckpt), _p(cmd), wl.dt, T, C, _p(gT), _p(w), _p(dx0),
+        rc = L.sim_rollout_backward_noalloc(sim.handle, _p(ckpt), _p(cmd), wl.dt, T, C, _p(g), _p(w), _p(dx0),
                                             _p(dth), _p(dtha), stream)
         assert rc == _lib.SIM_OK, L.sim_error_string(rc)
         torch.cuda.synchronize()
@@ -67,8 +81,8 @@ def test_noalloc_adjoint_matches_workspace_adjoint_on_two_calls():
         np.testing.assert_allclose(dth.cpu().numpy(), ref_dth.cpu().numpy(), rtol=1e-5, atol=1e-6 * scale)
 
     # a checkpoint interval whose scratch cannot fit even one block is refused
-    dx0 = torch.empty_like(ref_dx0)
-    dth = torch.empty_like(ref_dth)
+    dx0 = torch.empty_like(refs["loss"][0])
+    dth = torch.empty_like(refs["loss"][1])
     rc = L.sim_rollout_backward_noalloc(sim.handle, _p(ckpt), _p(cmd), wl.dt, 100_000, 100_000, _p(gT), _p(w),
                                         _p(dx0), _p(dth), None, stream)
     assert rc == _lib.SIM_ERR_WORKSPACE
