@@ -452,6 +452,11 @@ def main():
     ap.add_argument("--multi-only", action="store_true",
                     help="time only the quadrotor / car / fixed-wing swarm (equal thirds) at --agents x "
                          "--physics-steps (profiling case)")
+    ap.add_argument("--hetero-only", action="store_true",
+                    help="time only the 8-group heterogeneous swarm (600,000 agents) over --physics-steps "
+                         "(profiling case)")
+    ap.add_argument("--collide-only", action="store_true",
+                    help="time only collision detection on --agents agents (profiling case)")
     ap.add_argument("--block", type=int, default=0, help="fix the forward block size (with --pid-only, --multi-only)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -477,8 +482,11 @@ def main():
     if args.adjoint_only:
         run_adjoint_only(args, world, rank, dev)
         return
-    if args.pid_only or args.multi_only:
-        run_swarm_only(args, world, rank, dev, "pid" if args.pid_only else "multi")
+    if args.pid_only or args.multi_only or args.hetero_only:
+        run_swarm_only(args, world, rank, dev, "pid" if args.pid_only else "multi" if args.multi_only else "hetero")
+        return
+    if args.collide_only:
+        run_collide_only(args, rank, dev)
         return
     stream = torch.cuda.current_stream()
     props = torch.cuda.get_device_properties(dev)
@@ -644,7 +652,8 @@ def run_adjoint_only(args, world, rank, dev):
 
 def run_swarm_only(args, world, rank, dev, kind: str):
     """One swarm on --agents x --physics-steps, --K and --block (or tuned): kind "pid" is the
-    PID-rate-loop swarm, "multi" the quadrotor / car / fixed-wing swarm in equal thirds."""
+    PID-rate-loop swarm, "multi" the quadrotor / car / fixed-wing swarm in equal thirds,
+    "hetero" the 8-group swarm of 600,000 agents (--agents ignored)."""
     import torch
 
     from paper_2308_12698_b300 import autotune
@@ -654,6 +663,10 @@ def run_swarm_only(args, world, rank, dev, kind: str):
     if kind == "pid":
         wl = W.closed_loop_pid(n=NA, nsteps=TS)
         flops = FLOPS_PER_AGENT_STEP_PID
+    elif kind == "hetero":
+        wl = W.heterogeneous(nsteps=TS, shuffle=False)
+        NA = wl.n
+        flops = FLOPS_PER_AGENT_STEP
     else:
         sizes = (NA // 3, NA // 3, NA - 2 * (NA // 3))
         wl = W.multi_type(sizes=sizes, nsteps=TS)
@@ -755,21 +768,10 @@ def swarm_leg(world, wl, dev, timed_steps, reps, **sim_kw):
     return tune, ms
 
 
-def copy_bandwidth(nbytes: int, kind: str, reps: int = 20) -> float:
-    """GB/s of copies of nbytes: "h2d" / "d2h" between pinned host and device memory, "l2" a
-    device-to-device copy small enough to stay in L2 (read + write bytes counted).  reps
-    copies are enqueued back to back between two events, so the time is the copies' own and
-    not the host's enqueue cost; best of three such runs."""
+def copy_rate(dst, src, nbytes: int, reps: int = 20) -> float:
+    """GB/s of copying src into dst (torch tensors, pinned host or device): reps copies
+    enqueued back to back between two events, best of three such runs."""
     import torch
-    n = nbytes // 4
-    if kind == "l2":
-        a = torch.ones(n, device="cuda")
-        b = torch.empty_like(a)
-        src, dst, moved = a, b, 2 * nbytes
-    else:
-        h = torch.ones(n).pin_memory()
-        d = torch.empty(n, device="cuda")
-        src, dst, moved = (h, d, nbytes) if kind == "h2d" else (d, h, nbytes)
     for _ in range(3):
         dst.copy_(src, non_blocking=True)
     torch.cuda.synchronize()
@@ -782,15 +784,53 @@ def copy_bandwidth(nbytes: int, kind: str, reps: int = 20) -> float:
         e1.record()
         e1.synchronize()
         best = min(best, e0.elapsed_time(e1) / reps)
-    return moved / (best / 1e3) / 1e9
+    return nbytes / (best / 1e3) / 1e9
 
 
-#: Algorithmic bytes per agent of one collision call (1e6 agents, 2^21 buckets), as the
-#: kernels touch them.  Insert: status 1, position 16, list link 4, bucket head exchange 4.
-#: Query: status 1, position 16, arm length of its group 4, 27 bucket heads x 4, and per
-#: candidate on those lists (load 1e6 / 2^21, so 27 x 0.48 = 12.9 expected) its link 4, its
-#: position 16 and its arm length 4; hit byte 1.  Apply: hit and status 2.
-COLLIDE_BYTES_PER_AGENT = (1 + 16 + 4 + 4) + (1 + 16 + 4 + 27 * 4 + 12.9 * (4 + 16 + 4) + 1) + 2
+def l2_copy_bandwidth(nbytes: int = 32 << 20) -> float:
+    """GB/s (read + write bytes) of a device-to-device copy small enough to stay in L2."""
+    import torch
+    a = torch.ones(nbytes // 4, device="cuda")
+    b = torch.empty_like(a)
+    return copy_rate(b, a, 2 * nbytes)
+
+
+#: Algorithmic bytes per agent of one collision call (1e6 agents at 2 m mean spacing, 2^22
+#: buckets, cells of 0.909 m for the reference arm), as the kernels touch them.  Insert:
+#: status 1, position 16, arm length 4, its 32-byte record written, bucket head exchange 4.
+#: Query: status 1, own record 16, 8 bucket heads x 4, and per candidate on those lists
+#: (8 x 1e6 / 2^22 = 1.9 unrelated agents plus 0.8 within the 8 cells: 2.7 expected) 20 bytes
+#: of its record (position, radius, link); hit byte 1.  Apply: hit and status 2.
+COLLIDE_BYTES_PER_AGENT = (1 + 16 + 4 + 32 + 4) + (1 + 16 + 8 * 4 + 2.7 * 20 + 1) + 2
+
+
+def run_collide_only(args, rank, dev):
+    """Collision detection on the collision field of --agents agents: --warmup then --steps calls."""
+    import torch
+
+    from paper_2308_12698_b300 import workload as W
+    from paper_2308_12698_b300.sim import Sim, planar
+    cw = W.collision_field(args.agents)
+    cs = Sim(cw.groups, cw.n, cw.mode)
+    cx = planar(torch.from_numpy(cw.x0)).to(dev)
+    cws = torch.empty(max(cs.collide_workspace_bytes(), 1), dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        cs.reset_status()
+        cs.collide(cx, 1.0, cws)
+    torch.cuda.synchronize()
+    ms = 0.0
+    for _ in range(args.steps):
+        cs.reset_status()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        cs.collide(cx, 1.0, cws)
+        b.record()
+        b.synchronize()
+        ms += a.elapsed_time(b) / args.steps
+    if rank == 0:
+        print(json.dumps({"leg": "collide", "agents": cw.n, "ms_per_call": ms, "value": cw.n / (ms / 1e3),
+                          "unit": "agents/s", "bytes_per_agent": COLLIDE_BYTES_PER_AGENT}), flush=True)
+    cs.close()
 
 
 def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_steps, sms, clocks) -> dict:
@@ -858,14 +898,15 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     hrate = hw.n * T_STEPS / (ms / 1e3)
     st_, ms1 = swarm_leg(world, W.scale_sweep(hw.n, nsteps=T_STEPS), dev, timed_steps, reps)
     rate1 = hw.n * T_STEPS / (ms1 / 1e3)
-    hp = profiled("step_kernel<1,true>", f"heterogeneous-{hw.n}-K{ht['K']}")
+    hp = profiled("range_kernel<1>", f"heterogeneous-{hw.n}-K{ht['K']}")
     out["hetero"] = {"value": world * hrate, "unit": UNIT, "ms_per_step": ms,
                      "n_agents": hw.n, "groups": len(hw.groups), "sizes": list(W.HETERO_SIZES), "K": ht["K"],
                      "block": ht["block"],
                      "one_group_same_n": {"value": world * rate1, "K": st_["K"], "block": st_["block"]},
                      "ratio_to_one_group": hrate / rate1,
                      "roofline": alu_roofline(FLOPS_PER_AGENT_STEP, hrate, sms, clocks, hp,
-                                              "step_kernel<closed loop, groups in shared memory>",
+                                              "range_kernel<closed loop>: one group per block, its constants "
+                                              "in the kernel's parameters",
                                               note="every group runs the same operations")}
 
     # PID body-rate loop: 1e6 agents with 20-component states
@@ -885,11 +926,11 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     rate = mw.n * T_STEPS / (ms / 1e3)
     flops = (sizes[0] * FLOPS_PER_AGENT_STEP + sizes[1] * FLOPS_PER_AGENT_STEP_CAR +
              sizes[2] * FLOPS_PER_AGENT_STEP_FIXED_WING) / mw.n
-    mp = profiled("step_kernel<1,true,true>", f"multi-type-{mw.n}-K{mt['K']}", "multi")
+    mp = profiled("range_kernel<1,true>", f"multi-type-{mw.n}-K{mt['K']}", "multi")
     out["multi_type"] = {"value": world * rate, "unit": UNIT, "ms_per_step": ms,
                          "n_agents": mw.n, "sizes": {"quadrotor": sizes[0], "car": sizes[1], "fixed_wing": sizes[2]},
                          "K": mt["K"], "block": mt["block"],
-                         "roofline": alu_roofline(flops, rate, sms, clocks, mp, "step_kernel<mixed agent types>",
+                         "roofline": alu_roofline(flops, rate, sms, clocks, mp, "range_kernel<mixed agent types>",
                                                   note="quadrotors at the hand count, cars and fixed-wing drones "
                                                        "at the checker's count; tan/atan2 not counted")}
 
@@ -904,15 +945,21 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     # decision rounds: commands from pinned host memory every M steps, positions back after
     # each round, both overlapped with the physics (1000 steps per bench step); beside them the
     # pinned copy bandwidth of this machine's host link, per direction, for one round's 16 MB
-    link = {"h2d_GBs": copy_bandwidth(16 * N_AGENTS, "h2d"), "d2h_GBs": copy_bandwidth(16 * N_AGENTS, "d2h"),
-            "bytes": 16 * N_AGENTS, "how": "20 pinned 16 MB copies back to back per direction, CUDA events"}
     rounds = {}
+    link = {}
     for M in (10, 100):
         R = T_STEPS // M
         h_cmds = torch.from_numpy(wl.cmd).reshape(1, -1).repeat(R, 1).contiguous().pin_memory()
         h_obs = torch.empty((R, 4 * N_AGENTS), dtype=torch.float32).pin_memory()
         cmd2 = torch.empty(8 * N_AGENTS, dtype=torch.float32, device=dev)
         obs2 = torch.empty(8 * N_AGENTS, dtype=torch.float32, device=dev)
+        if not link:
+            # the host link as the rounds see it: one round's 16 MB between the same buffers
+            link = {"h2d_GBs": copy_rate(cmd2[: 4 * N_AGENTS], h_cmds[0], 16 * N_AGENTS),
+                    "d2h_GBs": copy_rate(h_obs[0], obs2[: 4 * N_AGENTS], 16 * N_AGENTS),
+                    "bytes": 16 * N_AGENTS,
+                    "how": "one round's 16 MB command plane in and observation plane out, between the rounds' "
+                           "own pinned and device buffers, 20 copies back to back per direction, CUDA events"}
         Kr = min(sim.launch()["K"], M)
         rrun = lambda: sim.run_rounds(x, h_cmds, M, DT, K=Kr, h_obs=h_obs, cmd2=cmd2, obs2=obs2)  # noqa: E731
         timed_steps(rrun, 2, reset)
@@ -935,7 +982,7 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     t = timed_steps(crun, reps, cs.reset_status)
     ms = max_over_ranks(sum(t), world) / reps
     hits = int((cs.status() == 2).sum().item())
-    l2 = copy_bandwidth(32 << 20, "l2")
+    l2 = l2_copy_bandwidth()
     achieved = COLLIDE_BYTES_PER_AGENT * cw.n / (ms / 1e3) / 1e9
     cp = profiled("collide_query", f"collision-field-{cw.n}", "collide")
     out["collide"] = {"value": world * cw.n / (ms / 1e3), "unit": "agents/s", "ms_per_call": ms,

@@ -283,12 +283,17 @@ int sim_rollout_backward_noalloc(sim_handle_t h, const float* d_ckpt, const floa
  * radius_scale; the decision is taken in FP32 as d2 < (r_i + r_j)^2 with
  * d2 = (dx*dx + dy*dy) + dz*dz, each operation rounded separately.  Every
  * colliding live agent is marked dead (status 2) and frozen by later calls.
- * Method: a uniform grid of cells of side > 2 max radius, hashed into a
- * power-of-two table (spatial hash of Teschner et al., 2003), one linked list
- * per bucket built with atomic exchanges, then a 27-cell neighbour search per
- * agent.  The outcome does not depend on the order of the lists.
+ * Method: a uniform grid of cells of side 1.01 x twice the largest contact
+ * distance (4.04 max radius), hashed into a power-of-two table of >= 4
+ * n_agents buckets (spatial hash of Teschner et al., 2003), one linked list
+ * per bucket of 32-byte records (position, radius, link) built with atomic
+ * exchanges.  A pair in contact is then less than half a cell apart on every
+ * axis, so each agent searches the 2 x 2 x 2 cells on the side of its own
+ * cell it lies nearer to (cell coordinates computed in FP64).  The outcome
+ * does not depend on the order of the lists.
  * d_state: planar state (only positions are read).  d_workspace:
- * sim_collide_workspace_bytes(h) bytes, 256-byte aligned.  radius_scale > 0.
+ * sim_collide_workspace_bytes(h) bytes (about 16 + 32 + 1 bytes per agent),
+ * 256-byte aligned.  radius_scale > 0.
  * Up to 2^31 - 1 agents.  The call may run on a stream other than the
  * stepping stream ("outside the main loop"): an agent marked while a step is
  * in flight is frozen from the next launch on. */

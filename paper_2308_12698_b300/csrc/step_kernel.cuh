@@ -176,6 +176,51 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 1) step_kernel(StepArgs A, co
   }
 }
 
+// Contiguous agent ranges, each of one parameter group, for range_kernel,
+// cut into chunks of blockDim agents, one chunk per block.  The table travels
+// in the kernel's parameters (__grid_constant__); the range index, and with
+// it the group, is then uniform over a block, and the compiler reads the
+// group's constants from the constant bank instead of holding them in
+// registers (79-80 registers against 115-127 for the shared-memory table of
+// step_kernel's heterogeneous form).
+struct RangeTable {
+  DevGroup g[32];          // the range's group's constants
+  int64_t start[32];       // first agent of the range
+  int64_t end[32];         // one past its last agent
+  int first_block[33];     // block at which each range starts; [n_ranges] = the grid
+  int n_ranges;
+};
+
+// K fused RK4 steps per launch for agents in contiguous per-group ranges,
+// one agent per thread, one block per chunk (not persistent: the hardware
+// scheduler evens out the last wave better than a resident grid taking whole
+// chunks in turn, measured 3.5 % faster on 8 groups of 600,000 agents).
+// Same arithmetic, results and status marks as step_kernel's fused form.
+template <int MODE, bool MULTI = false>
+__global__ void __launch_bounds__(256) range_kernel(StepArgs A, const __grid_constant__ RangeTable T) {
+  int r = 0;
+  for (int k = 1; k < T.n_ranges; ++k) r += (int)(blockIdx.x >= (unsigned)T.first_block[k]);
+  const int64_t i = T.start[r] + (int64_t)(blockIdx.x - T.first_block[r]) * blockDim.x + threadIdx.x;
+  if (i >= T.end[r] || A.status[i]) return;  // dead agents are frozen
+  const DevGroup& P = T.g[r];
+  constexpr int NS = state_dim<MODE>();
+  St x;
+  load_state<NS>(A.state, A.n, i, x);
+  const float4 c = A.cmd[i];
+  const Hd hd = heading(MODE != 0 ? c.w : 0.f);
+  if (MULTI && P.vt != (float)TYPE_QUAD) {
+    for (int k = 0; k < A.K; ++k) vehicle_step(P, x, c, A.H);
+  } else {
+    const LagCoef L = lag_coef(P.inv_tau, A.H);
+#pragma unroll 2
+    for (int k = 0; k < A.K; ++k) step<MODE>(P, x, c, hd, A.H, L);
+  }
+  if (all_finite<NS>(x))
+    store_state<NS>(A.state, A.n, i, x);
+  else
+    A.status[i] = kStatusDiverged;  // refreeze_kernel finds its last finite state
+}
+
 // After a call's K-step launches (same state, command and step size): each
 // agent marked kStatusDiverged is still at the start state of the launch in
 // which its state went non-finite.  That state is stepped again one step at a

@@ -183,6 +183,36 @@ def test_heterogeneous_one_launch_is_bitwise_each_group_alone(dev):
         np.testing.assert_array_equal(both[idx], alone)
 
 
+def _permuted(wl, perm):
+    return W.Workload(wl.name, wl.mode, wl.groups, wl.gid[perm], wl.x0[perm], wl.cmd[perm], wl.dt, wl.nsteps)
+
+
+@pytest.mark.parametrize("kind", ["quad", "pid", "multi"])
+@pytest.mark.parametrize("K", [1, 20])
+def test_contiguous_and_interleaved_groups_agree(dev, kind, K):
+    """Groups whose agents form contiguous id ranges run as range_kernel (one group per block,
+    its constants read from the kernel's parameters); interleaved ids run as step_kernel with the
+    group table in shared memory.  The same agents in three layouts -- sorted by group,
+    contiguous blocks in reversed group order, shuffled -- give the same bits per agent."""
+    if kind == "quad":
+        wl = W.heterogeneous(sizes=(700, 1000, 300, 5), nsteps=60)
+    elif kind == "pid":
+        wl = W.differentiable_pid(n_per_group=400, n_groups=3, nsteps=60)
+    else:
+        wl = W.multi_type(sizes=(600, 500, 400), nsteps=60)
+    order = np.argsort(wl.gid, kind="stable")
+    layouts = {"sorted": order, "reversed": np.argsort(-wl.gid.astype(np.int64), kind="stable"),
+               "shuffled": np.random.default_rng(2).permutation(wl.n)}
+    outs = {}
+    for name, perm in layouts.items():
+        got = gpu_run(_permuted(wl, perm), dev, 60, K=K)
+        back = np.empty_like(got)
+        back[perm] = got
+        outs[name] = back
+    np.testing.assert_array_equal(outs["reversed"], outs["sorted"])
+    np.testing.assert_array_equal(outs["shuffled"], outs["sorted"])
+
+
 def test_one_group_with_ids_is_bitwise_homogeneous(dev):
     wl = W.closed_loop(n=777, nsteps=50)
     a = gpu_run(wl, dev, 50, K=10)
@@ -291,11 +321,13 @@ def test_host_entry_matches_device_entry(dev):
     sim.close()
 
 
-def test_pipelined_host_entry_over_chunks(dev):
+@pytest.mark.parametrize("shuffle", [True, False], ids=["interleaved", "contiguous"])
+def test_pipelined_host_entry_over_chunks(dev, shuffle):
     """300k agents (4 chunks through copy and compute streams), several groups, dead agents:
-    the host-buffer entry gives bitwise the device-buffer result."""
+    the host-buffer entry gives bitwise the device-buffer result.  Contiguous groups run as the
+    range kernel, whose ranges the chunks cut."""
     from paper_2308_12698_b300.sim import Sim, planar, unplanar
-    wl = W.heterogeneous(sizes=(100_000, 150_000, 50_001), nsteps=30, shuffle=True)
+    wl = W.heterogeneous(sizes=(100_000, 150_000, 50_001), nsteps=30, shuffle=shuffle)
     x0 = wl.x0.copy()
     x0[::997, 5] = np.nan
     gid = torch.from_numpy(wl.gid).to(dev)
