@@ -787,6 +787,33 @@ def copy_rate(dst, src, nbytes: int, reps: int = 20) -> float:
     return nbytes / (best / 1e3) / 1e9
 
 
+def duplex_rate(d_in, h_in, h_out, d_out, nbytes: int, reps: int = 20) -> float:
+    """GB/s per direction with host-to-device copies (h_in -> d_in) and device-to-host copies
+    (d_out -> h_out) on two streams at once: reps of each, timed from the first start to the
+    last end; best of three."""
+    import torch
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    best = float("inf")
+    for _ in range(4):
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        s1.wait_event(e0)
+        s2.wait_event(e0)
+        with torch.cuda.stream(s1):
+            for _ in range(reps):
+                d_in.copy_(h_in, non_blocking=True)
+            e1.record(s1)
+        with torch.cuda.stream(s2):
+            for _ in range(reps):
+                h_out.copy_(d_out, non_blocking=True)
+            e2.record(s2)
+        e1.synchronize()
+        e2.synchronize()
+        best = min(best, max(e0.elapsed_time(e1), e0.elapsed_time(e2)) / reps)
+    return nbytes / (best / 1e3) / 1e9
+
+
 def l2_copy_bandwidth(nbytes: int = 32 << 20) -> float:
     """GB/s (read + write bytes) of a device-to-device copy small enough to stay in L2."""
     import torch
@@ -954,12 +981,16 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
         cmd2 = torch.empty(8 * N_AGENTS, dtype=torch.float32, device=dev)
         obs2 = torch.empty(8 * N_AGENTS, dtype=torch.float32, device=dev)
         if not link:
-            # the host link as the rounds see it: one round's 16 MB between the same buffers
+            # the host link as the rounds see it: one round's 16 MB between the same buffers,
+            # each direction alone and both at once (the rounds move both at once)
             link = {"h2d_GBs": copy_rate(cmd2[: 4 * N_AGENTS], h_cmds[0], 16 * N_AGENTS),
                     "d2h_GBs": copy_rate(h_obs[0], obs2[: 4 * N_AGENTS], 16 * N_AGENTS),
+                    "both_directions_GBs_each": duplex_rate(cmd2[: 4 * N_AGENTS], h_cmds[0], h_obs[0],
+                                                            obs2[: 4 * N_AGENTS], 16 * N_AGENTS),
                     "bytes": 16 * N_AGENTS,
                     "how": "one round's 16 MB command plane in and observation plane out, between the rounds' "
-                           "own pinned and device buffers, 20 copies back to back per direction, CUDA events"}
+                           "own pinned and device buffers, 20 copies back to back per direction (alone, then "
+                           "both directions on two streams at once), CUDA events"}
         Kr = min(sim.launch()["K"], M)
         rrun = lambda: sim.run_rounds(x, h_cmds, M, DT, K=Kr, h_obs=h_obs, cmd2=cmd2, obs2=obs2)  # noqa: E731
         timed_steps(rrun, 2, reset)
@@ -969,7 +1000,8 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
         rounds[f"M{M}"] = {"value": world * N_AGENTS * T_STEPS / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
                            "rounds": R, "K": Kr, "h2d_bytes_per_round": 16 * N_AGENTS,
                            "d2h_bytes_per_round": 16 * N_AGENTS, "link_GBs_per_direction": per_dir,
-                           "h2d_frac_of_link": per_dir / link["h2d_GBs"], "d2h_frac_of_link": per_dir / link["d2h_GBs"]}
+                           "h2d_frac_of_link": per_dir / link["h2d_GBs"], "d2h_frac_of_link": per_dir / link["d2h_GBs"],
+                           "frac_of_link_both_directions": per_dir / link["both_directions_GBs_each"]}
     out["decision_rounds"] = dict(rounds, link=link)
 
     # collision detection: 1e6 agents at 2 m mean spacing, 1 % planted near pairs
@@ -987,7 +1019,8 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     cp = profiled("collide_query", f"collision-field-{cw.n}", "collide")
     out["collide"] = {"value": world * cw.n / (ms / 1e3), "unit": "agents/s", "ms_per_call": ms,
                       "n_agents": cw.n, "collided": hits, "table_and_lists_MB": cws.numel() / 1e6,
-                      "method": "spatial hash, linked lists, 27-cell search",
+                      "method": "spatial hash of cells twice the contact distance, 32-byte records in "
+                                "linked lists, 2 x 2 x 2-cell search",
                       "roofline": {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s",
                                    "frac": achieved / l2, "bytes_per_agent": COLLIDE_BYTES_PER_AGENT,
                                    "peak_basis": "measured in this run: 32 MB device-to-device copies that stay "

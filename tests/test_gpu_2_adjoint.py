@@ -254,6 +254,17 @@ def test_full_size_adjoint_sampled_against_fd(dev, orc):
     _, rdx0, rdth = orc.grad(groups_sub, sub(wl.gid), sub(wl.x0), sub(wl.cmd), wl.dt, wl.nsteps, wl.mode,
                              sub(wl.goal), wl.w_omega)
     fd = _fd_theta(orc, wl, agents)
+    # worst component error as a fraction of the strict bar 1e-3 |r| + 1e-4 max|r| (1 = at the bar)
+    rel = lambda g, r: float(np.max(np.abs(g - r) / (1e-3 * np.abs(r) + 1e-4 * np.abs(r).max())))  # noqa: E731
+    cosine = lambda g, r: float(g @ r / (np.linalg.norm(g) * np.linalg.norm(r)))  # noqa: E731
+    strict = [j for j in range(len(agents)) if not fla[j]]
+    print(f"differentiable workload: {fl.mean():.3f} of 256 sampled agents flagged at a kink; unflagged agents, "
+          f"worst error as a fraction of the strict bar: theta vs FP64 reverse "
+          f"{max(rel(dth_a[agents[j]], rdth[j]) for j in strict):.3f} "
+          f"(cosine >= {min(cosine(dth_a[agents[j]], rdth[j]) for j in strict):.7f}), theta vs FD "
+          f"{max(rel(dth_a[agents[j]], fd[j]) for j in strict):.3f}, x0 vs reverse "
+          f"{max(rel(dx0[agents[j]], rdx0[j]) for j in strict):.3f}; flagged agents theta vs reverse "
+          f"{max(rel(dth_a[agents[j]], rdth[j]) for j in range(len(agents)) if fla[j]):.3f} of the strict bar")
     for j, a in enumerate(agents):
         if fla[j]:
             # FD itself straddles the kink for these; reverse mode is the reference
