@@ -175,9 +175,9 @@ int sim_step(sim_handle_t h, float* d_state, const float* d_cmd, float dt, int64
 /* sim_step for callers whose state lives in host memory: copies h_state and
  * h_cmd into the caller's device buffers d_state / d_cmd, steps, copies the
  * state back into h_state, then waits for `stream` (bounded wait).  The agents
- * are processed in up to 16 chunks whose host-to-device copies, steps and
- * device-to-host copies run on library-owned streams, so copies overlap
- * compute; the call is ordered after earlier work on `stream`.  Host buffers
+ * are processed in up to 32 chunks whose host-to-device copies, steps (over 4
+ * compute streams) and device-to-host copies run on library-owned streams, so
+ * copies overlap compute; the call is ordered after earlier work on `stream`.  Host buffers
  * should be pinned for the copies to be asynchronous.  Not capturable in a
  * CUDA graph (it waits).  On SIM_ERR_TIMEOUT the copies may still be running:
  * keep every buffer alive until `stream` is idle. */
