@@ -144,7 +144,11 @@ typedef struct sim_graph_s* sim_graph_t;
  * d_group_id: device array of n_agents uint8 group ids, or NULL when
  * n_groups == 1.  The handle keeps the pointer (the caller keeps the buffer
  * alive and unchanged); sim_create checks every id once (synchronously) and
- * returns SIM_ERR_GROUP if one is out of range.  mode: SIM_OPEN_LOOP,
+ * returns SIM_ERR_GROUP if one is out of range.  It also reads the ids once to
+ * see whether each group's agents form one contiguous range (sorted ids, or
+ * contiguous blocks in any order): if so, the fused steps run one group per
+ * thread block with the group's constants in the kernel's parameters, which
+ * is faster than the general form (the results are the same bit for bit).  mode: SIM_OPEN_LOOP,
  * SIM_CLOSED_LOOP or SIM_CLOSED_LOOP_PID (kI, kD, xi_max are read only in the
  * last; they must be finite, xi_max >= 0, in every mode).  Groups of car or
  * fixed-wing type need SIM_CLOSED_LOOP; such a handle steps (sim_step and
