@@ -213,6 +213,19 @@ def test_contiguous_and_interleaved_groups_agree(dev, kind, K):
     np.testing.assert_array_equal(outs["shuffled"], outs["sorted"])
 
 
+def test_contiguous_groups_with_an_empty_group(dev):
+    """A group with no agents between two contiguous ones (ids 0 and 2 only): the range kernel
+    skips it; the same agents interleaved give the same bits."""
+    wl = W.heterogeneous(sizes=(700, 0, 300), nsteps=40)
+    assert set(np.unique(wl.gid)) == {0, 2}
+    a = gpu_run(wl, dev, 40, K=20)
+    perm = np.random.default_rng(4).permutation(wl.n)
+    got = gpu_run(_permuted(wl, perm), dev, 40, K=20)
+    back = np.empty_like(got)
+    back[perm] = got
+    np.testing.assert_array_equal(back, a)
+
+
 def test_one_group_with_ids_is_bitwise_homogeneous(dev):
     wl = W.closed_loop(n=777, nsteps=50)
     a = gpu_run(wl, dev, 50, K=10)
@@ -485,8 +498,10 @@ def _diverging_swarm(kind):
     300 steps, mostly in the middle of a 100-step launch.  The other agents stay finite."""
     if kind == "open":
         wl = W.open_loop(n=64, nsteps=300)
-    elif kind == "hetero":
+    elif kind == "hetero":  # interleaved ids: the persistent kernel, table in shared memory
         wl = W.heterogeneous(sizes=(32, 32), nsteps=300, shuffle=True)
+    elif kind == "hetero_contiguous":  # contiguous ids: the range kernel
+        wl = W.heterogeneous(sizes=(32, 32), nsteps=300, shuffle=False)
     else:
         wl = W.closed_loop_pid(n=64, nsteps=300)
     x0 = wl.x0.copy()
@@ -496,7 +511,7 @@ def _diverging_swarm(kind):
     return W.Workload(wl.name, wl.mode, wl.groups, wl.gid, x0, wl.cmd, wl.dt, 300), spin
 
 
-@pytest.mark.parametrize("kind", ["open", "hetero", "pid"])
+@pytest.mark.parametrize("kind", ["open", "hetero", "hetero_contiguous", "pid"])
 def test_nonfinite_freeze_does_not_depend_on_K(dev, kind):
     """An agent that turns non-finite in the middle of a K-step launch keeps its last finite
     state, the same bits that one-step launches keep: 300 steps as 300 launches of one step, 3 of
