@@ -578,8 +578,7 @@ int sim_set_params(sim_handle_t h, const sim_group_params_t* groups, int n_group
     arm[g] = groups[g].L;
     max_arm = std::max(max_arm, arm[g]);
   }
-  // take the new groups only once the device copies have succeeded
-
+  // the host copies change only once the device copies have succeeded
   if (cudaMemcpy(h->d_groups, tbl, sizeof(DevGroup) * n_groups, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(h->d_arm, arm, sizeof(float) * n_groups, cudaMemcpyHostToDevice) != cudaSuccess)
     return SIM_ERR_CUDA;
