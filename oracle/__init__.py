@@ -13,6 +13,11 @@ The cascaded controller is the build's own reading (the paper defers it to a
 reference it does not include); it is pinned by hand-solved special cases and
 by the closed-loop spectrum at hover, not by any printed value, so its parity
 against the paper itself is unpinned.
+
+``rollout_f32`` evaluates the same model on float (every operation rounded to
+single precision).  It is not a reference for values: its distance from the
+FP64 rollout sizes the tolerance of the FP32 CUDA path over long rollouts, and
+``tests/test_oracle_fp32.py`` pins it to the FP64 model.
 """
 from __future__ import annotations
 
@@ -66,6 +71,8 @@ def lib():
         P = ctypes.c_void_p
         L.oracle_rollout.argtypes = [P, ctypes.c_int, P, ctypes.c_int64, P, P, ctypes.c_double,
                                      ctypes.c_int64, ctypes.c_int, ctypes.c_int, P]
+        L.oracle_rollout_f32.argtypes = [P, ctypes.c_int, P, ctypes.c_int64, P, P, ctypes.c_double,
+                                         ctypes.c_int64, ctypes.c_int, ctypes.c_int]
         L.oracle_grad.argtypes = [P, ctypes.c_int, P, ctypes.c_int64, P, P, ctypes.c_double,
                                   ctypes.c_int64, ctypes.c_int, P, ctypes.c_double, ctypes.c_int, P, P, P]
         L.oracle_derivative.argtypes = [P, P, P, P]
@@ -133,6 +140,24 @@ def rollout(groups, gid, x0, cmd, h, nsteps, mode, nthreads=None, with_cost=Fals
     if rcode != 0:
         raise ValueError("oracle_rollout rejected its arguments")
     return (x, rc) if with_cost else x
+
+
+def rollout_f32(groups, gid, x0, cmd, h, nsteps, mode, nthreads=None):
+    """The same rollout with the model evaluated in FP32 (every operation rounded to single
+    precision, the state kept as float32 between steps); quadrotor groups only.  Returns the
+    (n, state_dim) float32 final state.  Its distance from ``rollout`` measures what FP32 rounding
+    does to the equations, independently of the CUDA path."""
+    x = np.ascontiguousarray(np.asarray(x0, dtype=np.float32)).copy()
+    if x.ndim != 2 or x.shape[1] != state_dim(mode):
+        raise ValueError(f"states must be (n, {state_dim(mode)}) in mode {mode}")
+    c = np.ascontiguousarray(np.asarray(cmd, dtype=np.float64))
+    gi = np.ascontiguousarray(np.asarray(gid, dtype=np.int32))
+    pg = pack_groups(groups)
+    rcode = lib().oracle_rollout_f32(_p(pg), len(groups), _p(gi), x.shape[0], _p(x), _p(c), float(h),
+                                     int(nsteps), int(mode), _threads(nthreads))
+    if rcode != 0:
+        raise ValueError("oracle_rollout_f32 rejected its arguments")
+    return x
 
 
 def grad(groups, gid, x0, cmd, h, nsteps, mode, goal, w_omega, nthreads=None):

@@ -193,6 +193,37 @@ int oracle_rollout(const double* groups, int n_groups, const int32_t* gid, int64
   return 0;
 }
 
+// The same rollout of quadrotor groups evaluated in FP32: the model above
+// instantiated on float, every operation rounded to single precision (the
+// library is compiled without contraction), the state stored as float between
+// steps.  Its distance from the FP64 rollout is what FP32 rounding alone does
+// to these equations over nsteps steps; tests use it to size the bar of the
+// FP32 CUDA path beyond the stated 1000-step one.  x is n x state_dim floats.
+int oracle_rollout_f32(const double* groups, int n_groups, const int32_t* gid, int64_t n, float* x,
+                       const double* cmd, double h, int64_t nsteps, int mode, int nthreads) {
+  if (n < 0 || nsteps < 0 || n_groups < 1 || mode < OPEN_LOOP || mode > CLOSED_LOOP_PID) return -1;
+  const GroupSet S(groups, n_groups);
+  std::vector<Group<float>> P32;
+  for (int g = 0; g < n_groups; ++g) {
+    if (S.P[g].type != TYPE_QUAD) return -1;
+    P32.push_back(cast_group<float>(S.P[g]));
+  }
+  const int nx = state_dim(mode);
+  parallel_for(n, nthreads, [&](int64_t lo, int64_t hi) {
+    for (int64_t a = lo; a < hi; ++a) {
+      const int g = gid ? gid[a] : 0;
+      float cur[NXP], nxt[NXP];
+      std::memcpy(cur, x + a * nx, nx * sizeof(float));
+      for (int64_t s = 0; s < nsteps; ++s) {
+        step_any(P32[g], S.F[g], mode, cur, cmd + a * 4, h, nxt);
+        std::memcpy(cur, nxt, nx * sizeof(float));
+      }
+      std::memcpy(x + a * nx, cur, nx * sizeof(float));
+    }
+  });
+  return 0;
+}
+
 // Per-agent loss L_a = |p_T - goal_a|^2 + w_omega * sum_{n=1..T} sum_i Omega_{n,i}^2
 // and its exact discrete gradient by reverse mode: dL/dx0 (n x 17; n x 20 in
 // the PID mode) and

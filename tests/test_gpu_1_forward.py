@@ -113,30 +113,45 @@ def test_closed_loop_1000_steps(dev, orc, K):
     check_traj(gpu_run(wl, dev, 1000, K=K), ref_run(orc, wl, 1000))
 
 
+def _quantiles(e):
+    return np.array([np.median(e), np.quantile(e, 0.9), np.quantile(e, 0.99), e.max()])
+
+
 def test_closed_loop_full_length(dev, orc):
     """The closed-loop case at its full length: 5,000 agents x 10,000 steps (10 s of flight towards
-    waypoints up to 87 m away).  The 1e-3 m / 1e-3 rad bar is stated after 1000 steps.  FP32 rounding
-    adds a bounded error every step and the stable closed loop carries it forward without amplifying
-    it: the error grows about linearly in the step count (worst agent 5.8e-5 m after 1000 steps, 1.2e-3
-    after 10,000 here).  So the bar after n steps is (n / 1000) x 1e-3, and 99 % of the agents must still
-    be inside the 1000-step bar itself."""
+    waypoints up to 87 m away).  The 1e-3 m / 1e-3 rad bar is stated after 1000 steps; beyond that the
+    FP32 path is held to what FP32 rounding itself does to the same equations.  The checker evaluates
+    the model a second time in FP32 (every operation rounded, the state stored as float between
+    steps, its own operation order), and at 1000, 5000 and 10,000 steps the kernel's distance from
+    the FP64 rollout must stay within 1.5 times that evaluation's distance, quantile by quantile
+    (median, p90, p99, worst agent), for position, attitude and the quaternion's norm (nothing
+    renormalises it).  Both are FP32 evaluations of the same equations with different operation
+    orders, so the two distributions agree up to the sampling spread of a quantile over 5,000
+    agents (measured ratios 0.95 to 1.11).  The stated bar itself holds for every agent after the
+    first 1000 steps."""
     wl = W.closed_loop(n=5000)
     assert wl.nsteps == 10_000
-    got = gpu_run(wl, dev, wl.nsteps, K=1000)
-    ref = ref_run(orc, wl, wl.nsteps)
-    check_traj(got, ref, tol=1e-3 * wl.nsteps / 1000)
-    perr = np.abs(got[:, 0:3].astype(np.float64) - ref[:, 0:3]).max(axis=1)
-    aerr = attitude_err(got[:, 6:10].astype(np.float64), ref[:, 6:10])
-    assert np.quantile(perr, 0.99) <= 1e-3 and np.quantile(aerr, 0.99) <= 1e-3, \
-        (np.quantile(perr, 0.99), np.quantile(aerr, 0.99))
-    # no renormalisation anywhere: the quaternion's norm after 10,000 FP32 steps.  Each step rounds
-    # the four components once (about 2^-24 relative), and the roundings pile up over the steps in
-    # the agents that turn fastest: median ~1e-6, worst of 5,000 agents 2.4e-5
-    dn = np.abs(np.linalg.norm(got[:, 6:10].astype(np.float64), axis=1) - 1)
-    print(f"10,000 steps: | |q| - 1 | median {np.median(dn):.1e}, p99 {np.quantile(dn, 0.99):.1e}, max {dn.max():.1e}")
-    assert np.quantile(dn, 0.99) <= 1e-5 and dn.max() <= 5e-5, (np.quantile(dn, 0.99), dn.max())
-    # the first 1000 steps of the same run meet the stated bar for every agent
-    check_traj(gpu_run(wl, dev, 1000, K=1000), ref_run(orc, wl, 1000))
+    xg = np.ascontiguousarray(wl.x0, dtype=np.float32)
+    x64 = np.asarray(wl.x0, dtype=np.float64)
+    x32 = xg.copy()
+    done = 0
+    for n in (1000, 5000, 10_000):
+        xg = gpu_run(wl, dev, n - done, K=1000, x0=xg)
+        x64 = ref_run(orc, wl, n - done, x0=x64)
+        x32 = orc.rollout_f32(wl.groups, wl.gid, x32, wl.cmd, wl.dt, n - done, wl.mode)
+        done = n
+        if n == 1000:
+            check_traj(xg, x64)
+        errs = {
+            "position m": lambda x: np.abs(x[:, 0:3].astype(np.float64) - x64[:, 0:3]).max(axis=1),
+            "attitude rad": lambda x: attitude_err(x[:, 6:10].astype(np.float64), x64[:, 6:10]),
+            "| |q| - 1 |": lambda x: np.abs(np.linalg.norm(x[:, 6:10].astype(np.float64), axis=1) - 1),
+        }
+        for name, err in errs.items():
+            qg, q32 = _quantiles(err(xg)), _quantiles(err(x32))
+            print(f"{n:6d} steps {name:12s} kernel {qg} FP32 checker {q32} ratio {qg / q32}")
+            # an absolute floor of a few FP32 roundings for agents that barely move
+            assert (qg <= 1.5 * q32 + 4 * 2.0**-24).all(), (n, name, qg, q32)
 
 
 def test_fused_substeps_are_bitwise_plain_steps(dev):
