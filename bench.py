@@ -746,6 +746,12 @@ def fwd_adj_entry(world, sim, x0, cmd, nsteps, C, timed_steps, reps, sms, clocks
             "roofline": roof}
 
 
+def sm_fill(n: int, block: int, sms: int) -> str:
+    """How a swarm of n agents lands on the GPU at this block size."""
+    blocks = -(-n // block)
+    return f"{n:,} agents in {blocks} blocks of {block} fill {min(blocks, sms)} of the {sms} SMs"
+
+
 def swarm_leg(world, wl, dev, timed_steps, reps, **sim_kw):
     """A tuned swarm in one graph per bench step: (sim, tuned config, ms per bench step)."""
     import torch
@@ -913,7 +919,8 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     c4.update(groups=len(dw.groups), kink_share=kinks.get("share"), kinks_by_kind=kinks.get("by_kind"),
               kink_note="agents whose FP64 trajectory passes next to a controller kink (held to the looser "
                         "gradient bar); counted by the checker, tests/golden/kinks_differentiable.json",
-              note="4,096 agents fill 32 of the SMs: latency-bound, not a throughput figure")
+              note=sm_fill(dw.n, c4["block_adj"], sms) + " in the reverse sweep, one warp each: "
+                   "latency-bound, not a throughput figure")
     out["fwd_adjoint_config4"] = c4
     ds.close()
     del dx0, dcmd
@@ -967,7 +974,7 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     out["closed_loop_5000"] = {"value": world * cw1.n * cw1.nsteps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
                                "n_agents": cw1.n, "physics_steps": cw1.nsteps, "K": c1t["K"],
                                "block": c1t["block"],
-                               "note": "5,000 agents fill 20 of the SMs at the tuned block: latency-bound"}
+                               "note": sm_fill(cw1.n, c1t["block"], sms) + " at the tuned block: latency-bound"}
 
     # decision rounds: commands from pinned host memory every M steps, positions back after
     # each round, both overlapped with the physics (1000 steps per bench step); beside them the
@@ -1077,7 +1084,8 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     pw = W.scale_sweep(1000, nsteps=T_STEPS)
     pt, ms = swarm_leg(world, pw, dev, timed_steps, reps)
     out["n1000"] = {"value": 1000 * T_STEPS / (ms / 1e3), "unit": UNIT, "us_per_physics_step": ms,
-                    "K": pt["K"], "note": "latency bound: 1000 agents fill 4 of the SMs",
+                    "K": pt["K"], "block": pt["block"],
+                    "note": "latency bound: " + sm_fill(1000, pt["block"], sms),
                     "paper_context": PAPER_1000}
     return out
 

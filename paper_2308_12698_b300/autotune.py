@@ -15,7 +15,7 @@ import torch
 
 from .sim import Sim
 
-BLOCKS = (64, 128, 256)
+BLOCKS = (32, 64, 128, 256)
 KS = (10, 50, 100, 250, 1000)
 CS = (1, 2, 4, 8, 16, 25, 50, 100)
 
@@ -25,9 +25,9 @@ def _cache_path() -> str:
     return os.path.join(base, "quadsim_b300", "autotune.json")
 
 
-def _key(sim: Sim, kind: str, nsteps: int) -> str:
+def _key(sim: Sim, kind: str, nsteps: int, candidates) -> str:
     name = torch.cuda.get_device_name()
-    return f"{kind}|n={sim.n}|g={sim.n_groups}|mode={sim.mode}|T={nsteps}|{name}"
+    return f"{kind}|n={sim.n}|g={sim.n_groups}|mode={sim.mode}|T={nsteps}|{name}|{candidates}"
 
 
 def _load() -> dict:
@@ -67,7 +67,7 @@ def tune_step(sim: Sim, state: torch.Tensor, cmd: torch.Tensor, dt: float, nstep
               blocks=BLOCKS, ks=KS) -> dict:
     """Pick (block, K) for sim_step over nsteps; applies and returns it."""
     cache = _load() if use_cache else {}
-    key = _key(sim, "step", nsteps)
+    key = _key(sim, "step", nsteps, (tuple(blocks), tuple(ks)))
     if key in cache:
         cfg = cache[key]
     else:
@@ -90,10 +90,10 @@ def tune_step(sim: Sim, state: torch.Tensor, cmd: torch.Tensor, dt: float, nstep
 
 
 def tune_adjoint(sim: Sim, x0: torch.Tensor, cmd: torch.Tensor, dt: float, nsteps: int, use_cache: bool = True,
-                 cs=CS, blocks=(64, 128)) -> dict:
+                 cs=CS, blocks=(32, 64, 128)) -> dict:
     """Pick (block, C) for the checkpointed forward + adjoint; applies and returns it."""
     cache = _load() if use_cache else {}
-    key = _key(sim, "adjoint", nsteps)
+    key = _key(sim, "adjoint", nsteps, (tuple(blocks), tuple(cs)))
     if key in cache:
         cfg = cache[key]
     else:

@@ -27,6 +27,17 @@ namespace {
 
 constexpr int kDefaultBlockFwd = 256;
 constexpr int kDefaultBlockAdj = 128;
+
+// Default threads per block for n agents on sms SMs: the largest of `largest`,
+// largest/2, ... 32 that still gives every SM a block.  A swarm too small for
+// that runs 32-thread blocks, one warp per SM, so that no scheduler holds two
+// of its warps (4,096 agents: 128 single-warp blocks rather than 16 blocks of
+// 256, whose eight warps share four schedulers on each of 16 SMs).
+int spread_block(int64_t n, int sms, int largest) {
+  int b = largest;
+  while (b > 32 && (n + b - 1) / b < sms) b /= 2;
+  return b;
+}
 constexpr int kDefaultK = 10;
 constexpr int kDefaultC = 100;
 
@@ -528,6 +539,10 @@ int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents,
       cudaMalloc(&h->status, std::max<int64_t>(n_agents, 1)) != cudaSuccess ||
       cudaMemset(h->status, 0, std::max<int64_t>(n_agents, 1)) != cudaSuccess) {
     rc = SIM_ERR_CUDA;
+  }
+  if (rc == SIM_OK) {
+    h->block_fwd = spread_block(n_agents, h->sms, kDefaultBlockFwd);
+    h->block_adj = spread_block(n_agents, h->sms, kDefaultBlockAdj);
   }
   if (rc == SIM_OK && n_groups > 1 && n_agents > 0) {
     unsigned int* d_max = nullptr;

@@ -485,6 +485,28 @@ def test_autotuner_pick_is_bitwise_any_other(dev, tmp_path, monkeypatch):
     sim.close()
 
 
+def _spread(n, sms, largest):
+    # the largest power-of-two block (largest down to 32) that still gives every SM a block
+    for b in (256, 128, 64, 32):
+        if b <= largest and -(-n // b) >= sms:
+            return b
+    return 32
+
+
+@pytest.mark.parametrize("n", [1000, 4096, 20_000, 100_000])
+def test_default_block_spreads_small_swarms(dev, n):
+    """sim_create's block sizes spread a small swarm one warp per SM; forward results do not
+    depend on the block size."""
+    from paper_2308_12698_b300.sim import Sim
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    wl = W.closed_loop(n=n, nsteps=50)
+    sim = Sim(wl.groups, wl.n, wl.mode)
+    got = sim.launch()
+    sim.close()
+    assert got["block"] == _spread(n, sms, 256) and got["block_adj"] == _spread(n, sms, 128), got
+    np.testing.assert_array_equal(gpu_run(wl, dev, 50, K=25), gpu_run(wl, dev, 50, K=25, block=256))
+
+
 def test_nonfinite_agent_is_frozen_and_counted(dev):
     from paper_2308_12698_b300.sim import Sim, planar, unplanar
     wl = W.closed_loop(n=500, nsteps=10)

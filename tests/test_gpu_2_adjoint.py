@@ -342,6 +342,7 @@ def test_shared_and_global_scratch_agree(dev):
     wl = W.differentiable(n_per_group=500, n_groups=3, nsteps=240)
     gid = torch.from_numpy(wl.gid).to(dev)
     sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
+    sim.set_launch(block_adj=128)  # 40 steps x 68 B x 128 threads exceed the shared-memory scratch
     x0 = planar(torch.from_numpy(wl.x0)).to(dev)
     cmd = torch.from_numpy(wl.cmd).reshape(-1).to(dev)
     gT = torch.zeros(17 * wl.n, device=dev)

@@ -48,6 +48,7 @@ def test_noalloc_adjoint_matches_workspace_adjoint_on_two_calls(pid):
     wl = make(n_per_group=512, n_groups=4, nsteps=T)
     gid = torch.from_numpy(wl.gid).to(dev)
     sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
+    sim.set_launch(block_adj=128)
     nx = sim.nx
     x0 = planar(torch.from_numpy(wl.x0)).to(dev)
     cmd = torch.from_numpy(wl.cmd).reshape(-1).to(dev)
