@@ -26,8 +26,9 @@ def _p(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+@pytest.mark.parametrize("block_adj", [128, 0], ids=["block128", "default-block"])
 @pytest.mark.parametrize("pid", [False, True], ids=["p-loop", "pid-loop"])
-def test_noalloc_adjoint_matches_workspace_adjoint_on_two_calls(pid):
+def test_noalloc_adjoint_matches_workspace_adjoint_on_two_calls(pid, block_adj):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import __graft_entry__
@@ -41,14 +42,15 @@ def test_noalloc_adjoint_matches_workspace_adjoint_on_two_calls(pid):
     torch.cuda.set_device(dev)
     # one checkpoint segment of 400 steps: 400 x 68 B (80 B with the PID loop's
     # integral) per thread, so the fixed array holds fewer resident blocks than
-    # the 16 blocks of 128 threads the 2,048 agents need, and each block of the
-    # capped grid takes several agents in turn
+    # the 16 blocks of 128 threads (or the 64 blocks of 32 threads that the
+    # default block size gives 2,048 agents) the agents need, and each block of
+    # the capped grid takes several agents in turn
     T, C = 400, 400
     make = W.differentiable_pid if pid else W.differentiable
     wl = make(n_per_group=512, n_groups=4, nsteps=T)
     gid = torch.from_numpy(wl.gid).to(dev)
     sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
-    sim.set_launch(block_adj=128)
+    sim.set_launch(block_adj=block_adj)
     nx = sim.nx
     x0 = planar(torch.from_numpy(wl.x0)).to(dev)
     cmd = torch.from_numpy(wl.cmd).reshape(-1).to(dev)
