@@ -942,6 +942,11 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
                                               "range_kernel<closed loop>: one group per block, its constants "
                                               "in the kernel's parameters",
                                               note="every group runs the same operations")}
+    # the same agents with the groups' ids interleaved at random: the handle's group-sorted order
+    hi, msi = swarm_leg(world, W.heterogeneous(nsteps=T_STEPS, shuffle=True), dev, timed_steps, reps)
+    out["hetero"]["interleaved"] = {"value": world * hw.n * T_STEPS / (msi / 1e3), "ms_per_step": msi,
+                                    "K": hi["K"], "block": hi["block"], "ratio_to_contiguous": ms / msi,
+                                    "how": "ids in random order; range_kernel through the group-sorted order"}
 
     # PID body-rate loop: 1e6 agents with 20-component states
     pw = W.closed_loop_pid(n=N_AGENTS, nsteps=T_STEPS)
@@ -953,7 +958,7 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
                   "roofline": alu_roofline(FLOPS_PER_AGENT_STEP_PID, rate, sms, clocks, pp,
                                            "step_kernel<PID rate loop, one group>")}
 
-    # quadrotors, cars and fixed-wing drones (200,000 each) in one persistent launch
+    # quadrotors, cars and fixed-wing drones (200,000 each) in one launch
     mw = W.multi_type(nsteps=T_STEPS)
     mt, ms = swarm_leg(world, mw, dev, timed_steps, reps)
     sizes = W.MULTI_TYPE_SIZES
@@ -967,6 +972,12 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
                          "roofline": alu_roofline(flops, rate, sms, clocks, mp, "range_kernel<mixed agent types>",
                                                   note="quadrotors at the hand count, cars and fixed-wing drones "
                                                        "at the checker's count; tan/atan2 not counted")}
+    # the same swarm with the agent types interleaved at random: the group-sorted order keeps each
+    # warp on one type
+    mi, msi = swarm_leg(world, W.multi_type(nsteps=T_STEPS, shuffle=True), dev, timed_steps, reps)
+    out["multi_type"]["interleaved"] = {"value": world * mw.n * T_STEPS / (msi / 1e3), "ms_per_step": msi,
+                                        "K": mi["K"], "block": mi["block"], "ratio_to_contiguous": ms / msi,
+                                        "how": "ids in random order; range_kernel through the group-sorted order"}
 
     # the closed-loop configuration at its own shape: 5,000 agents x 10,000 steps, tuned
     cw1 = W.closed_loop()

@@ -148,7 +148,14 @@ typedef struct sim_graph_s* sim_graph_t;
  * see whether each group's agents form one contiguous range (sorted ids, or
  * contiguous blocks in any order): if so, the fused steps run one group per
  * thread block with the group's constants in the kernel's parameters, which
- * is faster than the general form (the results are the same bit for bit).  mode: SIM_OPEN_LOOP,
+ * is faster than the general form (the results are the same bit for bit).
+ * When the groups interleave (and n_agents < 2^32), the handle keeps a
+ * group-sorted order of the agents (4 bytes per agent, device memory it owns)
+ * and the fused steps reach the agents through it, still one group per block:
+ * always when the groups mix agent types (a warp of mixed types would run
+ * every type's model), and for launches of 32 fused steps or more otherwise
+ * (below that, the order's scattered loads cost more than they save).  The
+ * caller's buffers keep their layout.  mode: SIM_OPEN_LOOP,
  * SIM_CLOSED_LOOP or SIM_CLOSED_LOOP_PID (kI, kD, xi_max are read only in the
  * last; they must be finite, xi_max >= 0, in every mode).  Groups of car or
  * fixed-wing type need SIM_CLOSED_LOOP; such a handle steps (sim_step and

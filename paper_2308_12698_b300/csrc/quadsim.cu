@@ -172,6 +172,24 @@ constexpr int kHostChunks = 32;
 constexpr int kComputeStreams = 4;
 constexpr int64_t kHostChunkMin = 32768;
 
+// The host pipeline's chunks of n agents: m chunks of `chunk` agents (the last
+// one shorter).  A function of n alone, so that the group-sorted order built at
+// creation can keep each chunk's agents together.
+static void host_chunks(int64_t n, int* m, int64_t* chunk) {
+  *m = (int)std::max<int64_t>(1, std::min<int64_t>(kHostChunks, n / kHostChunkMin));
+  *chunk = (n + *m - 1) / *m;
+}
+
+// Fused launches of K steps or more take the group-sorted order when the
+// groups' ids interleave.  Measured on 8 quadrotor groups of 600,000 agents in
+// random order: the order's scattered loads and stores cost 8.7 us per launch,
+// and warps of one group gain 0.33 us per step (1000 steps at K = 1000: 7.44
+// -> 7.11 ms; at K = 1: 16.2 -> 24.9 ms), so it pays from K ~ 26.  Swarms that
+// mix agent types take it at any K: a warp of mixed types runs every type's
+// model (200,000 each of quadrotors, cars and fixed-wing drones in random
+// order: 13.1 -> 4.1 ms at K = 1000, 21.5 -> 19.9 ms at K = 1).
+constexpr int kOrderMinK = 32;
+
 struct sim_s {
   int device = 0;
   int sms = 1;
@@ -193,6 +211,14 @@ struct sim_s {
   // creation from the ids): the fused steps then run as range_kernel
   bool ranged = false;
   int64_t g_start[SIM_MAX_GROUPS] = {}, g_end[SIM_MAX_GROUPS] = {};
+  // ids in which the groups interleave: the agents sorted by (group, host
+  // pipeline chunk, index) in d_order (owned); the agents of group g and chunk
+  // c sit at positions [g_off[g][c], g_off[g][c + 1]), and range_kernel steps
+  // any run of whole chunks through it
+  uint32_t* d_order = nullptr;
+  int n_chunks = 1;
+  int64_t chunk = 0;
+  std::vector<int64_t> g_off;  // [n_groups][n_chunks + 1]
   // host-buffer pipeline (sim_step_host): created on first use
   cudaStream_t s_h2d = nullptr, s_d2h = nullptr, s_comp[kComputeStreams] = {};
   cudaEvent_t ev_start = nullptr, ev_end = nullptr, ev_in[kHostChunks] = {}, ev_done[kHostChunks] = {};
@@ -326,26 +352,65 @@ int find_ranges(sim_s* h) {
     last[g] = i;
     ++cnt[g];
   }
-  for (int g = 0; g < h->n_groups; ++g)
-    if (cnt[g] && last[g] - first[g] + 1 != cnt[g]) return SIM_OK;  // a group is split: persistent kernel
-  for (int g = 0; g < h->n_groups; ++g) {
-    h->g_start[g] = cnt[g] ? first[g] : 0;
-    h->g_end[g] = cnt[g] ? last[g] + 1 : 0;
+  bool split = false;
+  for (int g = 0; g < h->n_groups; ++g) split = split || (cnt[g] && last[g] - first[g] + 1 != cnt[g]);
+  if (!split) {
+    for (int g = 0; g < h->n_groups; ++g) {
+      h->g_start[g] = cnt[g] ? first[g] : 0;
+      h->g_end[g] = cnt[g] ? last[g] + 1 : 0;
+    }
+    h->ranged = true;
+    return SIM_OK;
   }
-  h->ranged = true;
+  // the groups interleave: a counting sort by (group, chunk), stable in the
+  // index; positions fit 32 bits (more agents keep the persistent kernel)
+  if (h->n > (int64_t)UINT32_MAX) return SIM_OK;
+  host_chunks(h->n, &h->n_chunks, &h->chunk);
+  const int nc = h->n_chunks, G = h->n_groups;
+  std::vector<int64_t> count((size_t)G * nc, 0);
+  for (int64_t i = 0; i < h->n; ++i) ++count[(size_t)ids[(size_t)i] * nc + (size_t)(i / h->chunk)];
+  h->g_off.assign((size_t)G * (nc + 1), 0);
+  int64_t pos = 0;
+  for (int g = 0; g < G; ++g)
+    for (int c = 0; c <= nc; ++c) {
+      h->g_off[(size_t)g * (nc + 1) + c] = pos;
+      if (c < nc) pos += count[(size_t)g * nc + c];
+    }
+  std::vector<int64_t> next((size_t)G * nc);
+  for (int g = 0; g < G; ++g)
+    for (int c = 0; c < nc; ++c) next[(size_t)g * nc + c] = h->g_off[(size_t)g * (nc + 1) + c];
+  std::vector<uint32_t> order((size_t)h->n);
+  for (int64_t i = 0; i < h->n; ++i) order[(size_t)next[(size_t)ids[(size_t)i] * nc + (size_t)(i / h->chunk)]++] = (uint32_t)i;
+  if (cudaMalloc(&h->d_order, sizeof(uint32_t) * (size_t)h->n) != cudaSuccess ||
+      cudaMemcpy(h->d_order, order.data(), sizeof(uint32_t) * (size_t)h->n, cudaMemcpyHostToDevice) != cudaSuccess)
+    return SIM_ERR_CUDA;
   return SIM_OK;
 }
 
+// Whether [first, first + count) is a run of whole host-pipeline chunks, the
+// launches the group-sorted order can serve.
+bool whole_chunks(const sim_s* h, int64_t first, int64_t count) {
+  const int64_t end = first + count;
+  return first % h->chunk == 0 && (end == h->n || end % h->chunk == 0);
+}
+
 // The fused steps as range_kernel: one block per chunk of block_fwd agents of
-// one group, over the groups' ranges clipped to [first, first + count).
+// one group, over the groups' ranges clipped to [first, first + count); with
+// the group-sorted order (a run of whole chunks), over each group's positions
+// for those chunks.
 int launch_ranged(sim_s* h, const StepArgs& A, cudaStream_t st, int64_t first, int64_t count) {
   static_assert(SIM_MAX_GROUPS <= 32, "RangeTable holds 32 ranges");
+  const bool ordered = h->d_order != nullptr;
+  const int64_t ca = ordered ? first / h->chunk : 0;
+  const int64_t cb = ordered ? (first + count == h->n ? h->n_chunks : (first + count) / h->chunk) : 0;
   RangeTable T;
   std::memset(&T, 0, sizeof(T));
   int64_t blocks = 0;
   int r = 0;
   for (int g = 0; g < h->n_groups; ++g) {
-    const int64_t a = std::max(h->g_start[g], first), b = std::min(h->g_end[g], first + count);
+    const int64_t* off = ordered ? &h->g_off[(size_t)g * (h->n_chunks + 1)] : nullptr;
+    const int64_t a = ordered ? off[ca] : std::max(h->g_start[g], first);
+    const int64_t b = ordered ? off[cb] : std::min(h->g_end[g], first + count);
     if (b <= a) continue;
     T.g[r] = h->host_groups[g];
     T.start[r] = a;
@@ -359,11 +424,27 @@ int launch_ranged(sim_s* h, const StepArgs& A, cudaStream_t st, int64_t first, i
   T.first_block[r] = (int)blocks;
   T.n_ranges = r;
   const int grid = (int)blocks, bd = h->block_fwd;
-  if (h->multi) range_kernel<1, true><<<grid, bd, 0, st>>>(A, T);
-  else if (h->mode == SIM_CLOSED_LOOP_PID) range_kernel<2><<<grid, bd, 0, st>>>(A, T);
-  else if (h->mode == SIM_CLOSED_LOOP) range_kernel<1><<<grid, bd, 0, st>>>(A, T);
-  else range_kernel<0><<<grid, bd, 0, st>>>(A, T);
+  if (ordered) {
+    if (h->multi) range_kernel<1, true, true><<<grid, bd, 0, st>>>(A, T);
+    else if (h->mode == SIM_CLOSED_LOOP_PID) range_kernel<2, false, true><<<grid, bd, 0, st>>>(A, T);
+    else if (h->mode == SIM_CLOSED_LOOP) range_kernel<1, false, true><<<grid, bd, 0, st>>>(A, T);
+    else range_kernel<0, false, true><<<grid, bd, 0, st>>>(A, T);
+  } else {
+    if (h->multi) range_kernel<1, true><<<grid, bd, 0, st>>>(A, T);
+    else if (h->mode == SIM_CLOSED_LOOP_PID) range_kernel<2><<<grid, bd, 0, st>>>(A, T);
+    else if (h->mode == SIM_CLOSED_LOOP) range_kernel<1><<<grid, bd, 0, st>>>(A, T);
+    else range_kernel<0><<<grid, bd, 0, st>>>(A, T);
+  }
   return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ERR_CUDA;
+}
+
+// Whether a fused launch of K steps over [first, first + count) runs as
+// range_kernel: contiguous groups always; interleaved groups through the
+// group-sorted order for runs of whole chunks, mixed agent types at any K and
+// one type from kOrderMinK steps.
+bool use_ranges(const sim_s* h, int K, int64_t first, int64_t count) {
+  if (h->ranged) return true;
+  return h->d_order && whole_chunks(h, first, count) && (h->multi || K >= kOrderMinK);
 }
 
 int launch_step(sim_s* h, float* d_state, const float* d_cmd, StepH H, int K, cudaStream_t st, int64_t first,
@@ -380,8 +461,9 @@ int launch_step(sim_s* h, float* d_state, const float* d_cmd, StepH H, int K, cu
   A.n_groups = h->n_groups;
   A.H = H;
   A.groups = h->d_groups;
+  A.order = h->d_order;
   const bool plain = plain_path(h, K);
-  if (!plain && h->ranged) return launch_ranged(h, A, st, first, count);
+  if (!plain && use_ranges(h, K, first, count)) return launch_ranged(h, A, st, first, count);
   const size_t smem = plain ? plain_smem(h) : group_smem(h);
   const int grid = fwd_grid(h, smem, count, plain);
   const DevGroup& P0 = h->host_group0;
@@ -426,6 +508,7 @@ int launch_refreeze(sim_s* h, float* d_state, const float* d_cmd, StepH H, int64
   A.n_groups = h->n_groups;
   A.H = H;
   A.groups = h->d_groups;
+  A.order = nullptr;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, (int64_t)h->sms * 4));
   if (h->multi) refreeze_kernel<1, true><<<grid, 256, 0, st>>>(A);
   else if (h->mode == SIM_CLOSED_LOOP_PID) refreeze_kernel<2><<<grid, 256, 0, st>>>(A);
@@ -661,8 +744,9 @@ int sim_step_host(sim_handle_t h, float* h_state, const float* h_cmd, float* d_s
   // Chunks of agents flow through H2D copy -> steps -> D2H copy on separate
   // streams, so the copies of one chunk overlap the steps of the others, and
   // the compute streams run several chunks' launches at once.
-  const int m = (int)std::max<int64_t>(1, std::min<int64_t>(kHostChunks, n / kHostChunkMin));
-  const int64_t chunk = (n + m - 1) / m;
+  int m;
+  int64_t chunk;
+  host_chunks(n, &m, &chunk);
   const int K = substeps_K > 0 ? substeps_K : h->K;
   const StepH H = make_h(dt);
   const size_t fs = sizeof(float);
@@ -1109,6 +1193,7 @@ void sim_destroy(sim_handle_t h) {
   if (h->d_arm) cudaFree(h->d_arm);
   if (h->d_count) cudaFree(h->d_count);
   if (h->h_count) cudaFreeHost(h->h_count);
+  if (h->d_order) cudaFree(h->d_order);
   delete h;
 }
 

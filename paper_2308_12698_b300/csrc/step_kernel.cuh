@@ -26,6 +26,7 @@ struct StepArgs {
   int n_groups;
   StepH H;
   const DevGroup* groups;  // device table (several groups)
+  const uint32_t* order;   // range_kernel<..., ORDER>: agent at each group-sorted position
 };
 
 // Asynchronous global -> shared copies (cp.async, sm_80 and later), each
@@ -196,12 +197,17 @@ struct RangeTable {
 // scheduler evens out the last wave better than a resident grid taking whole
 // chunks in turn, measured 3.5 % faster on 8 groups of 600,000 agents).
 // Same arithmetic, results and status marks as step_kernel's fused form.
-template <int MODE, bool MULTI = false>
+// ORDER: the ranges are of positions in a group-sorted order of the agents
+// (A.order), for ids in which the groups interleave; a warp then still holds
+// agents of one group, and of one agent type.
+template <int MODE, bool MULTI = false, bool ORDER = false>
 __global__ void __launch_bounds__(256) range_kernel(StepArgs A, const __grid_constant__ RangeTable T) {
   int r = 0;
   for (int k = 1; k < T.n_ranges; ++k) r += (int)(blockIdx.x >= (unsigned)T.first_block[k]);
-  const int64_t i = T.start[r] + (int64_t)(blockIdx.x - T.first_block[r]) * blockDim.x + threadIdx.x;
-  if (i >= T.end[r] || A.status[i]) return;  // dead agents are frozen
+  const int64_t j = T.start[r] + (int64_t)(blockIdx.x - T.first_block[r]) * blockDim.x + threadIdx.x;
+  if (j >= T.end[r]) return;
+  const int64_t i = ORDER ? (int64_t)A.order[j] : j;
+  if (A.status[i]) return;  // dead agents are frozen
   const DevGroup& P = T.g[r];
   constexpr int NS = state_dim<MODE>();
   St x;

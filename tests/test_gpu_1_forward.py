@@ -203,12 +203,14 @@ def _permuted(wl, perm):
 
 
 @pytest.mark.parametrize("kind", ["quad", "pid", "multi"])
-@pytest.mark.parametrize("K", [1, 20])
+@pytest.mark.parametrize("K", [1, 20, 60])
 def test_contiguous_and_interleaved_groups_agree(dev, kind, K):
     """Groups whose agents form contiguous id ranges run as range_kernel (one group per block,
-    its constants read from the kernel's parameters); interleaved ids run as step_kernel with the
-    group table in shared memory.  The same agents in three layouts -- sorted by group,
-    contiguous blocks in reversed group order, shuffled -- give the same bits per agent."""
+    its constants read from the kernel's parameters).  Interleaved ids run through the handle's
+    group-sorted order as the same kernel for mixed agent types at any K and for launches of 32
+    steps or more (K = 60 here), otherwise as step_kernel with the group table in shared memory.
+    The same agents in three layouts -- sorted by group, contiguous blocks in reversed group
+    order, shuffled -- give the same bits per agent."""
     if kind == "quad":
         wl = W.heterogeneous(sizes=(700, 1000, 300, 5), nsteps=60)
     elif kind == "pid":
@@ -349,20 +351,25 @@ def test_host_entry_matches_device_entry(dev):
     sim.close()
 
 
-@pytest.mark.parametrize("shuffle", [True, False], ids=["interleaved", "contiguous"])
-def test_pipelined_host_entry_over_chunks(dev, shuffle):
-    """300k agents (4 chunks through copy and compute streams), several groups, dead agents:
+@pytest.mark.parametrize("layout,K", [("interleaved", 7), ("interleaved", 40), ("contiguous", 7),
+                                      ("mixed_types", 7)])
+def test_pipelined_host_entry_over_chunks(dev, layout, K):
+    """300k agents (9 chunks through copy and compute streams), several groups, dead agents:
     the host-buffer entry gives bitwise the device-buffer result.  Contiguous groups run as the
-    range kernel, whose ranges the chunks cut."""
+    range kernel, whose ranges the chunks cut; interleaved groups at K = 40 and interleaved agent
+    types run it through the group-sorted order, whose positions the chunks cut."""
     from paper_2308_12698_b300.sim import Sim, planar, unplanar
-    wl = W.heterogeneous(sizes=(100_000, 150_000, 50_001), nsteps=30, shuffle=shuffle)
+    if layout == "mixed_types":
+        wl = W.multi_type(sizes=(100_000, 150_000, 50_001), nsteps=80, shuffle=True)
+    else:
+        wl = W.heterogeneous(sizes=(100_000, 150_000, 50_001), nsteps=80, shuffle=layout == "interleaved")
     x0 = wl.x0.copy()
     x0[::997, 5] = np.nan
     gid = torch.from_numpy(wl.gid).to(dev)
     ref_sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
     xd = planar(torch.from_numpy(x0)).to(dev)
     cmd = torch.from_numpy(wl.cmd).reshape(-1).to(dev)
-    ref_sim.step(xd, cmd, wl.dt, 30, K=7)
+    ref_sim.step(xd, cmd, wl.dt, 80, K=K)
     ref = unplanar(xd, wl.n).cpu().numpy()
     sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
     h_state = planar(torch.from_numpy(x0)).pin_memory()
@@ -372,7 +379,7 @@ def test_pipelined_host_entry_over_chunks(dev, shuffle):
     for _ in range(2):  # the second call reuses the library's streams and events
         h_state.copy_(planar(torch.from_numpy(x0)))
         sim.reset_status()
-        sim.step_host(h_state, h_cmd, d_state, d_cmd, wl.dt, 30, K=7)
+        sim.step_host(h_state, h_cmd, d_state, d_cmd, wl.dt, 80, K=K)
         np.testing.assert_array_equal(unplanar(h_state, wl.n).numpy(), ref)
         assert sim.n_dead() == ref_sim.n_dead() == len(range(0, wl.n, 997))
     sim.close()
@@ -535,7 +542,7 @@ def _diverging_swarm(kind):
     300 steps, mostly in the middle of a 100-step launch.  The other agents stay finite."""
     if kind == "open":
         wl = W.open_loop(n=64, nsteps=300)
-    elif kind == "hetero":  # interleaved ids: the persistent kernel, table in shared memory
+    elif kind == "hetero":  # interleaved ids: the persistent kernel at K = 1, the group-sorted order from 32
         wl = W.heterogeneous(sizes=(32, 32), nsteps=300, shuffle=True)
     elif kind == "hetero_contiguous":  # contiguous ids: the range kernel
         wl = W.heterogeneous(sizes=(32, 32), nsteps=300, shuffle=False)
