@@ -987,6 +987,34 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
                                "block": c1t["block"],
                                "note": sm_fill(cw1.n, c1t["block"], sms) + " at the tuned block: latency-bound"}
 
+    # half of the agents dead at random (as collisions leave them): live agent-steps/s with the
+    # dead agents skipped by the threads that hold them, then after sim_compact
+    import numpy as np
+    dwl = W.scale_sweep(N_AGENTS, nsteps=T_STEPS)
+    dead = np.zeros(dwl.n, np.uint8)
+    dead[np.random.default_rng(7).random(dwl.n) < 0.5] = 2
+    live = int((dead == 0).sum())
+    dx0 = planar(torch.from_numpy(dwl.x0)).to(dev)
+    dcmd = torch.from_numpy(dwl.cmd).reshape(-1).to(dev)
+    dh = {}
+    for compact in (False, True):
+        ds = Sim(dwl.groups, dwl.n, dwl.mode)
+        ds.load_status(torch.from_numpy(dead).to(dev))
+        if compact:
+            ds.compact()
+        dxx = dx0.clone()
+        dg = ds.graph(dxx, dcmd, DT, T_STEPS, K=T_STEPS)
+        dreset = lambda: dxx.copy_(dx0)  # noqa: E731
+        timed_steps(dg.launch, 2, dreset)
+        dms = max_over_ranks(sum(timed_steps(dg.launch, reps, dreset)), world) / reps
+        dh["compacted" if compact else "in_place"] = {"value": world * live * T_STEPS / (dms / 1e3),
+                                                      "ms_per_step": dms}
+        dg.close()
+        ds.close()
+    out["half_dead"] = dict(dh, unit=UNIT, n_agents=dwl.n, live_agents=live, K=T_STEPS,
+                            note="live agent-steps/s; 50 % of the agents dead at random positions in the ids")
+    del dx0, dcmd
+
     # decision rounds: commands from pinned host memory every M steps, positions back after
     # each round, both overlapped with the physics (1000 steps per bench step); beside them the
     # pinned copy bandwidth of this machine's host link, per direction, for one round's 16 MB

@@ -108,6 +108,7 @@ extern "C" {
 #define SIM_ERR_WORKSPACE (-3) /* workspace too small */
 #define SIM_ERR_TIMEOUT (-4)   /* a bounded host wait ran out */
 #define SIM_ERR_GROUP (-5)     /* a group id >= n_groups was found */
+#define SIM_ERR_STALE (-6)     /* a graph captured before the handle's agent order changed */
 
 #define SIM_OPEN_LOOP 0
 #define SIM_CLOSED_LOOP 1
@@ -341,12 +342,34 @@ int sim_get_launch(sim_handle_t h, int* block_fwd, int* block_adj, int* K, int* 
 /* Number of agents marked dead (non-finite state).  Synchronises the stream
  * with a bounded wait (SIM_ERR_TIMEOUT after timeout_ms). */
 int sim_status(sim_handle_t h, int64_t* n_dead, int timeout_ms, void* stream);
-/* Marks every agent alive again. */
+/* Marks every agent alive again (and drops a sim_compact order). */
 int sim_reset_status(sim_handle_t h, void* stream);
+
+/* Steps only the live agents from now on (Sec. III-A: agents marked dead are
+ * excluded from the computation).  Dead agents are otherwise skipped by the
+ * thread that holds them, so a swarm whose dead agents are spread over the ids
+ * (after collisions, say) keeps its full launch time: with half of 1e6 agents
+ * dead at random, half the throughput per live agent.  sim_compact reads the
+ * status bytes (ordered after earlier work on `stream`, then waiting for it,
+ * bounded) and builds an order of the live agents alone, sorted by group
+ * (4 bytes per agent of device memory the handle owns).  Fused launches that
+ * an order serves -- 32 steps or more, or any number when the groups mix agent
+ * types, over the whole swarm or whole sim_step_host chunks -- then step only
+ * those agents, one group per block.  Results are the same bit for bit.
+ * Agents that die later are skipped as before; sim_reset_status and
+ * sim_load_status drop the order (dead agents may come alive).  Each of these
+ * changes of the order makes graphs captured before it stale: sim_graph_launch
+ * refuses them with SIM_ERR_STALE (capture again).  Work of this handle on
+ * other streams must be finished first.  More than 2^32 agents: no order,
+ * SIM_OK. */
+int sim_compact(sim_handle_t h, void* stream);
 
 /* Capture ceil(nsteps/K) sim_step launches on d_state/d_cmd into a CUDA
  * graph (stream capture on `stream`, which must not be the legacy default
- * stream); sim_graph_launch replays them on any stream. */
+ * stream); sim_graph_launch replays them on any stream, or returns
+ * SIM_ERR_STALE when sim_compact (or a status reset that dropped its order)
+ * has changed the handle's agent order since the capture.  A graph must not
+ * outlive its handle. */
 int sim_graph_create(sim_handle_t h, float* d_state, const float* d_cmd, float dt, int64_t nsteps, int substeps_K,
                      void* stream, sim_graph_t* out);
 int sim_graph_launch(sim_graph_t g, void* stream);

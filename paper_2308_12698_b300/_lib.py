@@ -13,6 +13,7 @@ SIM_ERR_CUDA = -2
 SIM_ERR_WORKSPACE = -3
 SIM_ERR_TIMEOUT = -4
 SIM_ERR_GROUP = -5
+SIM_ERR_STALE = -6
 SIM_OPEN_LOOP = 0
 SIM_CLOSED_LOOP = 1
 SIM_CLOSED_LOOP_PID = 2
@@ -26,7 +27,7 @@ EXPORTS = ("sim_create", "sim_set_params", "sim_step", "sim_step_host", "sim_rol
            "sim_workspace_bytes", "sim_rollout_backward", "sim_set_launch", "sim_get_launch", "sim_status",
            "sim_reset_status", "sim_graph_create", "sim_graph_launch", "sim_graph_destroy", "sim_step_launches",
            "sim_destroy", "sim_error_string", "sim_rollout_backward_noalloc",
-           "sim_collide_workspace_bytes", "sim_collide", "sim_copy_status", "sim_run_rounds", "sim_load_status")
+           "sim_collide_workspace_bytes", "sim_collide", "sim_copy_status", "sim_run_rounds", "sim_load_status", "sim_compact")
 
 
 class GroupParams(ctypes.Structure):
@@ -91,6 +92,7 @@ def lib():
         "sim_get_launch": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
         "sim_status": (I, [P, ctypes.POINTER(I64), I, P]),
         "sim_reset_status": (I, [P, P]),
+        "sim_compact": (I, [P, P]),
         "sim_graph_create": (I, [P, P, P, F, I64, I, P, ctypes.POINTER(P)]),
         "sim_graph_launch": (I, [P, P]),
         "sim_graph_destroy": (None, [P]),

@@ -219,6 +219,13 @@ struct sim_s {
   int n_chunks = 1;
   int64_t chunk = 0;
   std::vector<int64_t> g_off;  // [n_groups][n_chunks + 1]
+  // sim_compact: the live agents alone in the same (group, chunk, index) order
+  // (d_live, owned; live_off as g_off), used while `live` holds; `epoch` counts
+  // the changes of the agent order that graphs captured before must not outlive
+  uint32_t* d_live = nullptr;
+  bool live = false;
+  std::vector<int64_t> live_off;
+  uint64_t epoch = 0;
   // host-buffer pipeline (sim_step_host): created on first use
   cudaStream_t s_h2d = nullptr, s_d2h = nullptr, s_comp[kComputeStreams] = {};
   cudaEvent_t ev_start = nullptr, ev_end = nullptr, ev_in[kHostChunks] = {}, ev_done[kHostChunks] = {};
@@ -233,11 +240,21 @@ struct sim_s {
 struct sim_graph_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  const sim_s* h = nullptr;  // the handle it steps, and that handle's agent-order epoch at capture
+  uint64_t epoch = 0;
 };
 
 namespace {
 
 bool hetero(const sim_s* h) { return h->n_groups > 1; }
+
+// Agents may come alive again: the live agents' order no longer covers them.
+void drop_live(sim_s* h) {
+  if (h->live) {
+    h->live = false;
+    ++h->epoch;
+  }
+}
 
 size_t group_smem(const sim_s* h) { return hetero(h) ? sizeof(DevGroup) * h->n_groups : 0; }
 
@@ -336,6 +353,7 @@ size_t scratch_bytes(const sim_s* h, int C, int grid) {
 // (ids interleaved) as step_kernel with the table in shared memory.
 int find_ranges(sim_s* h) {
   h->ranged = false;
+  host_chunks(h->n, &h->n_chunks, &h->chunk);
   // one group: its constants are kernel parameters of step_kernel already, and
   // that kernel's persistent grid of 32-agent chunks ends its last wave more
   // evenly (range_kernel measured 1-3 % slower at 6e5 and 1e6 agents)
@@ -365,7 +383,6 @@ int find_ranges(sim_s* h) {
   // the groups interleave: a counting sort by (group, chunk), stable in the
   // index; positions fit 32 bits (more agents keep the persistent kernel)
   if (h->n > (int64_t)UINT32_MAX) return SIM_OK;
-  host_chunks(h->n, &h->n_chunks, &h->chunk);
   const int nc = h->n_chunks, G = h->n_groups;
   std::vector<int64_t> count((size_t)G * nc, 0);
   for (int64_t i = 0; i < h->n; ++i) ++count[(size_t)ids[(size_t)i] * nc + (size_t)(i / h->chunk)];
@@ -391,16 +408,23 @@ int find_ranges(sim_s* h) {
 // launches the group-sorted order can serve.
 bool whole_chunks(const sim_s* h, int64_t first, int64_t count) {
   const int64_t end = first + count;
-  return first % h->chunk == 0 && (end == h->n || end % h->chunk == 0);
+  return h->chunk > 0 && first % h->chunk == 0 && (end == h->n || end % h->chunk == 0);
 }
 
 // The fused steps as range_kernel: one block per chunk of block_fwd agents of
 // one group, over the groups' ranges clipped to [first, first + count); with
 // the group-sorted order (a run of whole chunks), over each group's positions
 // for those chunks.
-int launch_ranged(sim_s* h, const StepArgs& A, cudaStream_t st, int64_t first, int64_t count) {
+// How a fused launch runs: the persistent kernel, the range kernel over
+// contiguous groups, or the range kernel through the group-sorted order or the
+// live agents' order.
+enum RangeMode { kPersistent, kContiguous, kGroupOrder, kLiveOrder };
+
+int launch_ranged(sim_s* h, StepArgs A, cudaStream_t st, int64_t first, int64_t count, RangeMode mode) {
   static_assert(SIM_MAX_GROUPS <= 32, "RangeTable holds 32 ranges");
-  const bool ordered = h->d_order != nullptr;
+  const bool ordered = mode != kContiguous;
+  A.order = mode == kLiveOrder ? h->d_live : h->d_order;
+  const std::vector<int64_t>& offs = mode == kLiveOrder ? h->live_off : h->g_off;
   const int64_t ca = ordered ? first / h->chunk : 0;
   const int64_t cb = ordered ? (first + count == h->n ? h->n_chunks : (first + count) / h->chunk) : 0;
   RangeTable T;
@@ -408,7 +432,7 @@ int launch_ranged(sim_s* h, const StepArgs& A, cudaStream_t st, int64_t first, i
   int64_t blocks = 0;
   int r = 0;
   for (int g = 0; g < h->n_groups; ++g) {
-    const int64_t* off = ordered ? &h->g_off[(size_t)g * (h->n_chunks + 1)] : nullptr;
+    const int64_t* off = ordered ? &offs[(size_t)g * (h->n_chunks + 1)] : nullptr;
     const int64_t a = ordered ? off[ca] : std::max(h->g_start[g], first);
     const int64_t b = ordered ? off[cb] : std::min(h->g_end[g], first + count);
     if (b <= a) continue;
@@ -438,13 +462,17 @@ int launch_ranged(sim_s* h, const StepArgs& A, cudaStream_t st, int64_t first, i
   return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ERR_CUDA;
 }
 
-// Whether a fused launch of K steps over [first, first + count) runs as
-// range_kernel: contiguous groups always; interleaved groups through the
-// group-sorted order for runs of whole chunks, mixed agent types at any K and
-// one type from kOrderMinK steps.
-bool use_ranges(const sim_s* h, int K, int64_t first, int64_t count) {
-  if (h->ranged) return true;
-  return h->d_order && whole_chunks(h, first, count) && (h->multi || K >= kOrderMinK);
+// How a fused launch of K steps over [first, first + count) runs.  An order
+// serves runs of whole chunks, for mixed agent types at any K and for one type
+// from kOrderMinK steps: the live agents' order after sim_compact, else the
+// group-sorted order of interleaved ids.  Contiguous groups take the range
+// kernel directly; everything else the persistent kernel.
+RangeMode range_mode(const sim_s* h, int K, int64_t first, int64_t count) {
+  const bool order_pays = (h->multi || K >= kOrderMinK) && whole_chunks(h, first, count);
+  if (h->live && order_pays) return kLiveOrder;
+  if (h->ranged) return kContiguous;
+  if (h->d_order && order_pays) return kGroupOrder;
+  return kPersistent;
 }
 
 int launch_step(sim_s* h, float* d_state, const float* d_cmd, StepH H, int K, cudaStream_t st, int64_t first,
@@ -461,9 +489,10 @@ int launch_step(sim_s* h, float* d_state, const float* d_cmd, StepH H, int K, cu
   A.n_groups = h->n_groups;
   A.H = H;
   A.groups = h->d_groups;
-  A.order = h->d_order;
+  A.order = nullptr;
   const bool plain = plain_path(h, K);
-  if (!plain && use_ranges(h, K, first, count)) return launch_ranged(h, A, st, first, count);
+  const RangeMode rm = plain ? kPersistent : range_mode(h, K, first, count);
+  if (rm != kPersistent) return launch_ranged(h, A, st, first, count, rm);
   const size_t smem = plain ? plain_smem(h) : group_smem(h);
   const int grid = fwd_grid(h, smem, count, plain);
   const DevGroup& P0 = h->host_group0;
@@ -576,6 +605,7 @@ const char* sim_error_string(int code) {
     case SIM_ERR_WORKSPACE: return "workspace too small";
     case SIM_ERR_TIMEOUT: return "timed out waiting for the stream";
     case SIM_ERR_GROUP: return "group id out of range";
+    case SIM_ERR_STALE: return "graph captured before the agent order changed (capture it again)";
     default: return "unknown error";
   }
 }
@@ -1104,6 +1134,7 @@ int sim_load_status(sim_handle_t h, const uint8_t* d_status_in, void* stream) {
   if (!h) return SIM_ERR_ARG;
   if (h->n == 0) return SIM_OK;
   if (!d_status_in) return SIM_ERR_ARG;
+  drop_live(h);
   return cudaMemcpyAsync(h->status, d_status_in, (size_t)h->n, cudaMemcpyDeviceToDevice,
                          reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
              ? SIM_OK
@@ -1130,8 +1161,56 @@ int sim_status(sim_handle_t h, int64_t* n_dead, int timeout_ms, void* stream) {
 int sim_reset_status(sim_handle_t h, void* stream) {
   if (!h) return SIM_ERR_ARG;
   if (h->n == 0) return SIM_OK;
+  drop_live(h);
   return cudaMemsetAsync(h->status, 0, h->n, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? SIM_OK
                                                                                                    : SIM_ERR_CUDA;
+}
+
+int sim_compact(sim_handle_t h, void* stream) {
+  if (!h) return SIM_ERR_ARG;
+  if (h->n == 0 || h->n > (int64_t)UINT32_MAX) return SIM_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // the status bytes as the stream's earlier work leaves them
+  std::vector<uint8_t> status((size_t)h->n), ids;
+  if (cudaMemcpyAsync(status.data(), h->status, (size_t)h->n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return SIM_ERR_CUDA;
+  if (h->n_groups > 1) {
+    ids.resize((size_t)h->n);
+    if (cudaMemcpyAsync(ids.data(), h->gid, (size_t)h->n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      return SIM_ERR_CUDA;
+  }
+  const int rc = wait_stream(st, 600000);
+  if (rc != SIM_OK) return rc;
+  // counting sort of the live agents by (group, chunk), stable in the index
+  const int nc = h->n_chunks, G = h->n_groups;
+  std::vector<int64_t> count((size_t)G * nc, 0);
+  for (int64_t i = 0; i < h->n; ++i)
+    if (!status[(size_t)i]) ++count[(size_t)(G > 1 ? ids[(size_t)i] : 0) * nc + (size_t)(i / h->chunk)];
+  std::vector<int64_t> off((size_t)G * (nc + 1), 0), next((size_t)G * nc);
+  int64_t pos = 0;
+  for (int g = 0; g < G; ++g)
+    for (int c = 0; c <= nc; ++c) {
+      off[(size_t)g * (nc + 1) + c] = pos;
+      if (c < nc) {
+        next[(size_t)g * nc + c] = pos;
+        pos += count[(size_t)g * nc + c];
+      }
+    }
+  std::vector<uint32_t> order((size_t)std::max<int64_t>(pos, 1));
+  for (int64_t i = 0; i < h->n; ++i)
+    if (!status[(size_t)i]) order[(size_t)next[(size_t)(G > 1 ? ids[(size_t)i] : 0) * nc + (size_t)(i / h->chunk)]++] = (uint32_t)i;
+  if (!h->d_live && cudaMalloc(&h->d_live, sizeof(uint32_t) * (size_t)h->n) != cudaSuccess) return SIM_ERR_CUDA;
+  // ordered after the launches already enqueued on `stream` (which may read the
+  // previous order); work of this handle on other streams must have finished
+  if (cudaMemcpyAsync(h->d_live, order.data(), sizeof(uint32_t) * (size_t)pos, cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return SIM_ERR_CUDA;
+  const int rc2 = wait_stream(st, 600000);
+  if (rc2 != SIM_OK) return rc2;
+  h->live_off.swap(off);
+  h->live = true;
+  ++h->epoch;
+  return SIM_OK;
 }
 
 int sim_graph_create(sim_handle_t h, float* d_state, const float* d_cmd, float dt, int64_t nsteps, int substeps_K,
@@ -1157,12 +1236,15 @@ int sim_graph_create(sim_handle_t h, float* d_state, const float* d_cmd, float d
     delete g;
     return SIM_ERR_CUDA;
   }
+  g->h = h;
+  g->epoch = h->epoch;
   *out = g;
   return SIM_OK;
 }
 
 int sim_graph_launch(sim_graph_t g, void* stream) {
   if (!g) return SIM_ERR_ARG;
+  if (g->h->epoch != g->epoch) return SIM_ERR_STALE;  // the agent order it captured has changed
   return cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? SIM_OK : SIM_ERR_CUDA;
 }
 
@@ -1194,6 +1276,7 @@ void sim_destroy(sim_handle_t h) {
   if (h->d_count) cudaFree(h->d_count);
   if (h->h_count) cudaFreeHost(h->h_count);
   if (h->d_order) cudaFree(h->d_order);
+  if (h->d_live) cudaFree(h->d_live);
   delete h;
 }
 

@@ -261,6 +261,10 @@ class Sim:
     def reset_status(self, stream=None):
         check(lib().sim_reset_status(self._h, _stream(stream)), "sim_reset_status")
 
+    def compact(self, stream=None):
+        """Step only the live agents from now on (sim_compact); graphs captured before go stale."""
+        check(lib().sim_compact(self._h, _stream(stream)), "sim_compact")
+
     # -- graphs --
     def graph(self, state: torch.Tensor, cmd: torch.Tensor, dt: float, nsteps: int, K: int = 0) -> "Graph":
         return Graph(self, state, cmd, dt, nsteps, K)
