@@ -1001,7 +1001,10 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
         ds = Sim(dwl.groups, dwl.n, dwl.mode)
         ds.load_status(torch.from_numpy(dead).to(dev))
         if compact:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             ds.compact()
+            dh["compact_ms"] = (time.perf_counter() - t0) * 1e3
         dxx = dx0.clone()
         dg = ds.graph(dxx, dcmd, DT, T_STEPS, K=T_STEPS)
         dreset = lambda: dxx.copy_(dx0)  # noqa: E731

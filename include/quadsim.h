@@ -349,10 +349,12 @@ int sim_reset_status(sim_handle_t h, void* stream);
  * excluded from the computation).  Dead agents are otherwise skipped by the
  * thread that holds them, so a swarm whose dead agents are spread over the ids
  * (after collisions, say) keeps its full launch time: with half of 1e6 agents
- * dead at random, half the throughput per live agent.  sim_compact reads the
- * status bytes (ordered after earlier work on `stream`, then waiting for it,
- * bounded) and builds an order of the live agents alone, sorted by group
- * (4 bytes per agent of device memory the handle owns).  Fused launches that
+ * dead at random, half the throughput per live agent.  sim_compact builds,
+ * from the status bytes, an order of the live agents alone, sorted by group
+ * (4 bytes per agent of device memory the handle owns): two passes on the
+ * device ordered after earlier work on `stream`, with one bounded wait for
+ * the per-group counts between them and one at the end (0.14 ms for 1e6
+ * agents).  Fused launches that
  * an order serves -- 32 steps or more, or any number when the groups mix agent
  * types, over the whole swarm or whole sim_step_host chunks -- then step only
  * those agents, one group per block.  Results are the same bit for bit.

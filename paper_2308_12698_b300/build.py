@@ -9,7 +9,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libquadsim.so")
 SOURCES = [os.path.join(CSRC, f) for f in ("quadsim.cu", "model_fwd.cuh", "model_adj.cuh", "step_kernel.cuh",
-                                           "vehicles.cuh", "adjoint_kernel.cuh", "collide.cuh")] + \
+                                           "vehicles.cuh", "adjoint_kernel.cuh", "collide.cuh", "compact.cuh")] + \
     [os.path.join(ROOT, "include", "quadsim.h")]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",

@@ -18,6 +18,7 @@
 #include "../../include/quadsim.h"
 #include "adjoint_kernel.cuh"
 #include "collide.cuh"
+#include "compact.cuh"
 #include "model_fwd.cuh"
 #include "step_kernel.cuh"
 
@@ -225,6 +226,10 @@ struct sim_s {
   uint32_t* d_live = nullptr;
   bool live = false;
   std::vector<int64_t> live_off;
+  unsigned int* d_live_cnt = nullptr;  // owned: the counting pass's output, and its pinned host copy
+  unsigned int* h_live_cnt = nullptr;
+  int64_t* d_live_off = nullptr;       // owned: the positions the scatter pass writes from, and theirs
+  int64_t* h_live_off = nullptr;
   uint64_t epoch = 0;
   // host-buffer pipeline (sim_step_host): created on first use
   cudaStream_t s_h2d = nullptr, s_d2h = nullptr, s_comp[kComputeStreams] = {};
@@ -1170,44 +1175,49 @@ int sim_compact(sim_handle_t h, void* stream) {
   if (!h) return SIM_ERR_ARG;
   if (h->n == 0 || h->n > (int64_t)UINT32_MAX) return SIM_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  // the status bytes as the stream's earlier work leaves them
-  std::vector<uint8_t> status((size_t)h->n), ids;
-  if (cudaMemcpyAsync(status.data(), h->status, (size_t)h->n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    return SIM_ERR_CUDA;
-  if (h->n_groups > 1) {
-    ids.resize((size_t)h->n);
-    if (cudaMemcpyAsync(ids.data(), h->gid, (size_t)h->n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-      return SIM_ERR_CUDA;
-  }
-  const int rc = wait_stream(st, 600000);
-  if (rc != SIM_OK) return rc;
-  // counting sort of the live agents by (group, chunk), stable in the index
   const int nc = h->n_chunks, G = h->n_groups;
-  std::vector<int64_t> count((size_t)G * nc, 0);
-  for (int64_t i = 0; i < h->n; ++i)
-    if (!status[(size_t)i]) ++count[(size_t)(G > 1 ? ids[(size_t)i] : 0) * nc + (size_t)(i / h->chunk)];
-  std::vector<int64_t> off((size_t)G * (nc + 1), 0), next((size_t)G * nc);
+  const size_t ncnt = (size_t)G * nc, noff = (size_t)G * (nc + 1);
+  // each buffer on its own, so that a failed call leaves none half-made
+  if ((!h->d_live && cudaMalloc(&h->d_live, sizeof(uint32_t) * (size_t)h->n) != cudaSuccess) ||
+      (!h->d_live_cnt && cudaMalloc(&h->d_live_cnt, sizeof(unsigned int) * ncnt) != cudaSuccess) ||
+      (!h->d_live_off && cudaMalloc(&h->d_live_off, sizeof(int64_t) * noff) != cudaSuccess) ||
+      (!h->h_live_cnt && cudaMallocHost(&h->h_live_cnt, sizeof(unsigned int) * ncnt) != cudaSuccess) ||
+      (!h->h_live_off && cudaMallocHost(&h->h_live_off, sizeof(int64_t) * noff) != cudaSuccess))
+    return SIM_ERR_CUDA;
+  LiveArgs A;
+  A.status = h->status;
+  A.gid = G > 1 ? h->gid : nullptr;
+  A.n = h->n;
+  A.chunk = h->chunk;
+  A.n_groups = G;
+  A.n_chunks = nc;
+  A.counts = h->d_live_cnt;
+  A.off = h->d_live_off;
+  A.order = h->d_live;
+  // pass 1 (ordered after earlier work on `stream`): live agents per (group, chunk)
+  live_order_kernel<false><<<nc, kLiveBlock, 0, st>>>(A);
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(h->h_live_cnt, h->d_live_cnt, sizeof(unsigned int) * ncnt, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess)
+    return SIM_ERR_CUDA;
+  int rc = wait_stream(st, 600000);
+  if (rc != SIM_OK) return rc;
   int64_t pos = 0;
   for (int g = 0; g < G; ++g)
     for (int c = 0; c <= nc; ++c) {
-      off[(size_t)g * (nc + 1) + c] = pos;
-      if (c < nc) {
-        next[(size_t)g * nc + c] = pos;
-        pos += count[(size_t)g * nc + c];
-      }
+      h->h_live_off[(size_t)g * (nc + 1) + c] = pos;
+      if (c < nc) pos += h->h_live_cnt[(size_t)g * nc + c];
     }
-  std::vector<uint32_t> order((size_t)std::max<int64_t>(pos, 1));
-  for (int64_t i = 0; i < h->n; ++i)
-    if (!status[(size_t)i]) order[(size_t)next[(size_t)(G > 1 ? ids[(size_t)i] : 0) * nc + (size_t)(i / h->chunk)]++] = (uint32_t)i;
-  if (!h->d_live && cudaMalloc(&h->d_live, sizeof(uint32_t) * (size_t)h->n) != cudaSuccess) return SIM_ERR_CUDA;
-  // ordered after the launches already enqueued on `stream` (which may read the
-  // previous order); work of this handle on other streams must have finished
-  if (cudaMemcpyAsync(h->d_live, order.data(), sizeof(uint32_t) * (size_t)pos, cudaMemcpyHostToDevice, st) !=
+  // pass 2: each live agent's index at its position
+  if (cudaMemcpyAsync(h->d_live_off, h->h_live_off, sizeof(int64_t) * noff, cudaMemcpyHostToDevice, st) !=
       cudaSuccess)
     return SIM_ERR_CUDA;
-  const int rc2 = wait_stream(st, 600000);
-  if (rc2 != SIM_OK) return rc2;
-  h->live_off.swap(off);
+  live_order_kernel<true><<<nc, kLiveBlock, 0, st>>>(A);
+  if (cudaGetLastError() != cudaSuccess) return SIM_ERR_CUDA;
+  // the call returns with the order in place, so that launches on any stream may use it
+  rc = wait_stream(st, 600000);
+  if (rc != SIM_OK) return rc;
+  h->live_off.assign(h->h_live_off, h->h_live_off + noff);
   h->live = true;
   ++h->epoch;
   return SIM_OK;
@@ -1277,6 +1287,10 @@ void sim_destroy(sim_handle_t h) {
   if (h->h_count) cudaFreeHost(h->h_count);
   if (h->d_order) cudaFree(h->d_order);
   if (h->d_live) cudaFree(h->d_live);
+  if (h->d_live_cnt) cudaFree(h->d_live_cnt);
+  if (h->d_live_off) cudaFree(h->d_live_off);
+  if (h->h_live_cnt) cudaFreeHost(h->h_live_cnt);
+  if (h->h_live_off) cudaFreeHost(h->h_live_off);
   delete h;
 }
 
