@@ -1001,6 +1001,7 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
         ds = Sim(dwl.groups, dwl.n, dwl.mode)
         ds.load_status(torch.from_numpy(dead).to(dev))
         if compact:
+            ds.compact()  # the first call also allocates the order's buffers
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             ds.compact()
