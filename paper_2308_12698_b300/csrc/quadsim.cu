@@ -356,6 +356,57 @@ size_t scratch_bytes(const sim_s* h, int C, int grid) {
 // synchronously, from the caller's id buffer (which the handle's contract
 // keeps unchanged).  If so the fused steps run as range_kernel; otherwise
 // (ids interleaved) as step_kernel with the table in shared memory.
+int wait_stream(cudaStream_t st, int timeout_ms);
+
+// The agents whose status byte is 0, sorted by (group, host-pipeline chunk,
+// index), written to out (n entries) by the two passes of live_order_kernel,
+// with off[g][c] the first position of (group g, chunk c).  Ordered after
+// earlier work on st; returns after the order is written (bounded waits).
+int order_live(sim_s* h, cudaStream_t st, uint32_t* out, std::vector<int64_t>& off) {
+  const int nc = h->n_chunks, G = h->n_groups;
+  const size_t ncnt = (size_t)G * nc, noff = (size_t)G * (nc + 1);
+  // each buffer on its own, so that a failed call leaves none half-made
+  if ((!h->d_live_cnt && cudaMalloc(&h->d_live_cnt, sizeof(unsigned int) * ncnt) != cudaSuccess) ||
+      (!h->d_live_off && cudaMalloc(&h->d_live_off, sizeof(int64_t) * noff) != cudaSuccess) ||
+      (!h->h_live_cnt && cudaMallocHost(&h->h_live_cnt, sizeof(unsigned int) * ncnt) != cudaSuccess) ||
+      (!h->h_live_off && cudaMallocHost(&h->h_live_off, sizeof(int64_t) * noff) != cudaSuccess))
+    return SIM_ERR_CUDA;
+  LiveArgs A;
+  A.status = h->status;
+  A.gid = G > 1 ? h->gid : nullptr;
+  A.n = h->n;
+  A.chunk = h->chunk;
+  A.n_groups = G;
+  A.n_chunks = nc;
+  A.counts = h->d_live_cnt;
+  A.off = h->d_live_off;
+  A.order = out;
+  // pass 1: live agents per (group, chunk), back to the host
+  live_order_kernel<false><<<nc, kLiveBlock, 0, st>>>(A);
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(h->h_live_cnt, h->d_live_cnt, sizeof(unsigned int) * ncnt, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess)
+    return SIM_ERR_CUDA;
+  int rc = wait_stream(st, 600000);
+  if (rc != SIM_OK) return rc;
+  int64_t pos = 0;
+  for (int g = 0; g < G; ++g)
+    for (int c = 0; c <= nc; ++c) {
+      h->h_live_off[(size_t)g * (nc + 1) + c] = pos;
+      if (c < nc) pos += h->h_live_cnt[(size_t)g * nc + c];
+    }
+  // pass 2: each agent's index at its position
+  if (cudaMemcpyAsync(h->d_live_off, h->h_live_off, sizeof(int64_t) * noff, cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return SIM_ERR_CUDA;
+  live_order_kernel<true><<<nc, kLiveBlock, 0, st>>>(A);
+  if (cudaGetLastError() != cudaSuccess) return SIM_ERR_CUDA;
+  rc = wait_stream(st, 600000);
+  if (rc != SIM_OK) return rc;
+  off.assign(h->h_live_off, h->h_live_off + noff);
+  return SIM_OK;
+}
+
 int find_ranges(sim_s* h) {
   h->ranged = false;
   host_chunks(h->n, &h->n_chunks, &h->chunk);
@@ -385,28 +436,12 @@ int find_ranges(sim_s* h) {
     h->ranged = true;
     return SIM_OK;
   }
-  // the groups interleave: a counting sort by (group, chunk), stable in the
-  // index; positions fit 32 bits (more agents keep the persistent kernel)
+  // the groups interleave: the agents sorted by (group, chunk, index), every
+  // status byte being 0 at creation; positions fit 32 bits (more agents keep
+  // the persistent kernel)
   if (h->n > (int64_t)UINT32_MAX) return SIM_OK;
-  const int nc = h->n_chunks, G = h->n_groups;
-  std::vector<int64_t> count((size_t)G * nc, 0);
-  for (int64_t i = 0; i < h->n; ++i) ++count[(size_t)ids[(size_t)i] * nc + (size_t)(i / h->chunk)];
-  h->g_off.assign((size_t)G * (nc + 1), 0);
-  int64_t pos = 0;
-  for (int g = 0; g < G; ++g)
-    for (int c = 0; c <= nc; ++c) {
-      h->g_off[(size_t)g * (nc + 1) + c] = pos;
-      if (c < nc) pos += count[(size_t)g * nc + c];
-    }
-  std::vector<int64_t> next((size_t)G * nc);
-  for (int g = 0; g < G; ++g)
-    for (int c = 0; c < nc; ++c) next[(size_t)g * nc + c] = h->g_off[(size_t)g * (nc + 1) + c];
-  std::vector<uint32_t> order((size_t)h->n);
-  for (int64_t i = 0; i < h->n; ++i) order[(size_t)next[(size_t)ids[(size_t)i] * nc + (size_t)(i / h->chunk)]++] = (uint32_t)i;
-  if (cudaMalloc(&h->d_order, sizeof(uint32_t) * (size_t)h->n) != cudaSuccess ||
-      cudaMemcpy(h->d_order, order.data(), sizeof(uint32_t) * (size_t)h->n, cudaMemcpyHostToDevice) != cudaSuccess)
-    return SIM_ERR_CUDA;
-  return SIM_OK;
+  if (cudaMalloc(&h->d_order, sizeof(uint32_t) * (size_t)h->n) != cudaSuccess) return SIM_ERR_CUDA;
+  return order_live(h, 0, h->d_order, h->g_off);
 }
 
 // Whether [first, first + count) is a run of whole host-pipeline chunks, the
@@ -1174,50 +1209,13 @@ int sim_reset_status(sim_handle_t h, void* stream) {
 int sim_compact(sim_handle_t h, void* stream) {
   if (!h) return SIM_ERR_ARG;
   if (h->n == 0 || h->n > (int64_t)UINT32_MAX) return SIM_OK;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int nc = h->n_chunks, G = h->n_groups;
-  const size_t ncnt = (size_t)G * nc, noff = (size_t)G * (nc + 1);
-  // each buffer on its own, so that a failed call leaves none half-made
-  if ((!h->d_live && cudaMalloc(&h->d_live, sizeof(uint32_t) * (size_t)h->n) != cudaSuccess) ||
-      (!h->d_live_cnt && cudaMalloc(&h->d_live_cnt, sizeof(unsigned int) * ncnt) != cudaSuccess) ||
-      (!h->d_live_off && cudaMalloc(&h->d_live_off, sizeof(int64_t) * noff) != cudaSuccess) ||
-      (!h->h_live_cnt && cudaMallocHost(&h->h_live_cnt, sizeof(unsigned int) * ncnt) != cudaSuccess) ||
-      (!h->h_live_off && cudaMallocHost(&h->h_live_off, sizeof(int64_t) * noff) != cudaSuccess))
-    return SIM_ERR_CUDA;
-  LiveArgs A;
-  A.status = h->status;
-  A.gid = G > 1 ? h->gid : nullptr;
-  A.n = h->n;
-  A.chunk = h->chunk;
-  A.n_groups = G;
-  A.n_chunks = nc;
-  A.counts = h->d_live_cnt;
-  A.off = h->d_live_off;
-  A.order = h->d_live;
-  // pass 1 (ordered after earlier work on `stream`): live agents per (group, chunk)
-  live_order_kernel<false><<<nc, kLiveBlock, 0, st>>>(A);
-  if (cudaGetLastError() != cudaSuccess ||
-      cudaMemcpyAsync(h->h_live_cnt, h->d_live_cnt, sizeof(unsigned int) * ncnt, cudaMemcpyDeviceToHost, st) !=
-          cudaSuccess)
-    return SIM_ERR_CUDA;
-  int rc = wait_stream(st, 600000);
-  if (rc != SIM_OK) return rc;
-  int64_t pos = 0;
-  for (int g = 0; g < G; ++g)
-    for (int c = 0; c <= nc; ++c) {
-      h->h_live_off[(size_t)g * (nc + 1) + c] = pos;
-      if (c < nc) pos += h->h_live_cnt[(size_t)g * nc + c];
-    }
-  // pass 2: each live agent's index at its position
-  if (cudaMemcpyAsync(h->d_live_off, h->h_live_off, sizeof(int64_t) * noff, cudaMemcpyHostToDevice, st) !=
-      cudaSuccess)
-    return SIM_ERR_CUDA;
-  live_order_kernel<true><<<nc, kLiveBlock, 0, st>>>(A);
-  if (cudaGetLastError() != cudaSuccess) return SIM_ERR_CUDA;
-  // the call returns with the order in place, so that launches on any stream may use it
-  rc = wait_stream(st, 600000);
-  if (rc != SIM_OK) return rc;
-  h->live_off.assign(h->h_live_off, h->h_live_off + noff);
+  if (!h->d_live && cudaMalloc(&h->d_live, sizeof(uint32_t) * (size_t)h->n) != cudaSuccess) return SIM_ERR_CUDA;
+  // returns with the order in place, so that launches on any stream may use it
+  const int rc = order_live(h, reinterpret_cast<cudaStream_t>(stream), h->d_live, h->live_off);
+  if (rc != SIM_OK) {
+    drop_live(h);
+    return rc;
+  }
   h->live = true;
   ++h->epoch;
   return SIM_OK;
