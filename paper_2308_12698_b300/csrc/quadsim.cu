@@ -407,7 +407,10 @@ int order_live(sim_s* h, cudaStream_t st, uint32_t* out, std::vector<int64_t>& o
   return SIM_OK;
 }
 
-int find_ranges(sim_s* h) {
+// How the fused steps reach the groups, decided once from the ids at
+// creation: contiguous ranges (range_kernel directly), a group-sorted order
+// (interleaved ids), or neither (one group).
+int plan_groups(sim_s* h) {
   h->ranged = false;
   host_chunks(h->n, &h->n_chunks, &h->chunk);
   // one group: its constants are kernel parameters of step_kernel already, and
@@ -713,7 +716,7 @@ int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents,
     }
     if (d_max) cudaFree(d_max);
   }
-  if (rc == SIM_OK) rc = find_ranges(h);
+  if (rc == SIM_OK) rc = plan_groups(h);
   if (rc == SIM_OK) {
     // allow the shared-memory scratch variant of the adjoint its full size
     const int big = (int)(kSmemScratchMax + 64 * 1024);
