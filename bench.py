@@ -458,6 +458,8 @@ def main():
     ap.add_argument("--collide-only", action="store_true",
                     help="time only collision detection on --agents agents (profiling case)")
     ap.add_argument("--block", type=int, default=0, help="fix the forward block size (with --pid-only, --multi-only)")
+    ap.add_argument("--interleaved", action="store_true",
+                    help="with --multi-only or --hetero-only: the groups' ids in random order")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -664,12 +666,12 @@ def run_swarm_only(args, world, rank, dev, kind: str):
         wl = W.closed_loop_pid(n=NA, nsteps=TS)
         flops = FLOPS_PER_AGENT_STEP_PID
     elif kind == "hetero":
-        wl = W.heterogeneous(nsteps=TS, shuffle=False)
+        wl = W.heterogeneous(nsteps=TS, shuffle=args.interleaved)
         NA = wl.n
         flops = FLOPS_PER_AGENT_STEP
     else:
         sizes = (NA // 3, NA // 3, NA - 2 * (NA // 3))
-        wl = W.multi_type(sizes=sizes, nsteps=TS)
+        wl = W.multi_type(sizes=sizes, nsteps=TS, shuffle=args.interleaved)
         flops = (sizes[0] * FLOPS_PER_AGENT_STEP + sizes[1] * FLOPS_PER_AGENT_STEP_CAR +
                  sizes[2] * FLOPS_PER_AGENT_STEP_FIXED_WING) / NA
     gid = torch.from_numpy(wl.gid).to(dev) if len(wl.groups) > 1 else None
@@ -944,9 +946,13 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
                                               note="every group runs the same operations")}
     # the same agents with the groups' ids interleaved at random: the handle's group-sorted order
     hi, msi = swarm_leg(world, W.heterogeneous(nsteps=T_STEPS, shuffle=True), dev, timed_steps, reps)
-    out["hetero"]["interleaved"] = {"value": world * hw.n * T_STEPS / (msi / 1e3), "ms_per_step": msi,
+    hirate = hw.n * T_STEPS / (msi / 1e3)
+    hip = profiled("range_kernel<1,false,true>", f"heterogeneous-interleaved-{hw.n}-K{hi['K']}")
+    out["hetero"]["interleaved"] = {"value": world * hirate, "ms_per_step": msi,
                                     "K": hi["K"], "block": hi["block"], "ratio_to_contiguous": ms / msi,
-                                    "how": "ids in random order; range_kernel through the group-sorted order"}
+                                    "how": "ids in random order; range_kernel through the group-sorted order",
+                                    "roofline": alu_roofline(FLOPS_PER_AGENT_STEP, hirate, sms, clocks, hip,
+                                                             "range_kernel<closed loop, ORDER>")}
 
     # PID body-rate loop: 1e6 agents with 20-component states
     pw = W.closed_loop_pid(n=N_AGENTS, nsteps=T_STEPS)
@@ -975,9 +981,13 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     # the same swarm with the agent types interleaved at random: the group-sorted order keeps each
     # warp on one type
     mi, msi = swarm_leg(world, W.multi_type(nsteps=T_STEPS, shuffle=True), dev, timed_steps, reps)
-    out["multi_type"]["interleaved"] = {"value": world * mw.n * T_STEPS / (msi / 1e3), "ms_per_step": msi,
+    mirate = mw.n * T_STEPS / (msi / 1e3)
+    mip = profiled("range_kernel<1,true,true>", f"multi-type-interleaved-{mw.n}-K{mi['K']}", "multi")
+    out["multi_type"]["interleaved"] = {"value": world * mirate, "ms_per_step": msi,
                                         "K": mi["K"], "block": mi["block"], "ratio_to_contiguous": ms / msi,
-                                        "how": "ids in random order; range_kernel through the group-sorted order"}
+                                        "how": "ids in random order; range_kernel through the group-sorted order",
+                                        "roofline": alu_roofline(flops, mirate, sms, clocks, mip,
+                                                                 "range_kernel<mixed agent types, ORDER>")}
 
     # the closed-loop configuration at its own shape: 5,000 agents x 10,000 steps, tuned
     cw1 = W.closed_loop()
