@@ -386,6 +386,20 @@ int64_t sim_step_launches(sim_handle_t h, int64_t nsteps, int substeps_K);
 void sim_destroy(sim_handle_t h);
 const char* sim_error_string(int code);
 
+/* Device bounds checks (a stand-in for a memory checker).  The library can be
+ * built a second time with its kernels' index checks compiled in
+ * (libquadsim_checked.so): each instrumented access first tests its index
+ * against the extent of its buffer; a failed test records the first failure
+ * in a device word, site << 48 | index (low 48 bits), and skips the access --
+ * no trap, no assert, so the context stays usable.  sim_bounds_checks waits
+ * for the device, stores that word in *first_failure (0: no failure) and
+ * clears it, and returns 1; the product library returns 0 with
+ * *first_failure = 0.  Sites: 1-3 planar state loads, stores and prefetches,
+ * 4 agent indices, 5 group ids, 6-7 range-kernel ranges and order entries,
+ * 8 checkpoint indices, 9 adjoint scratch steps and theta rows, 10 collision
+ * records, 11 live-order positions, 12 partial sums. */
+int sim_bounds_checks(uint64_t* first_failure);
+
 #ifdef __cplusplus
 }
 #endif

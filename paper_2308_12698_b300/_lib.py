@@ -5,7 +5,9 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libquadsim.so")
+#: QUADSIM_LIB points the binding at another build of the same sources (the
+#: bounds-checked build, libquadsim_checked.so).
+LIB_PATH = os.environ.get("QUADSIM_LIB") or os.path.join(HERE, "libquadsim.so")
 
 SIM_OK = 0
 SIM_ERR_ARG = -1
@@ -27,7 +29,7 @@ EXPORTS = ("sim_create", "sim_set_params", "sim_step", "sim_step_host", "sim_rol
            "sim_workspace_bytes", "sim_rollout_backward", "sim_set_launch", "sim_get_launch", "sim_status",
            "sim_reset_status", "sim_graph_create", "sim_graph_launch", "sim_graph_destroy", "sim_step_launches",
            "sim_destroy", "sim_error_string", "sim_rollout_backward_noalloc",
-           "sim_collide_workspace_bytes", "sim_collide", "sim_copy_status", "sim_run_rounds", "sim_load_status", "sim_compact")
+           "sim_collide_workspace_bytes", "sim_collide", "sim_copy_status", "sim_run_rounds", "sim_load_status", "sim_compact", "sim_bounds_checks")
 
 
 class GroupParams(ctypes.Structure):
@@ -93,6 +95,7 @@ def lib():
         "sim_status": (I, [P, ctypes.POINTER(I64), I, P]),
         "sim_reset_status": (I, [P, P]),
         "sim_compact": (I, [P, P]),
+        "sim_bounds_checks": (I, [ctypes.POINTER(ctypes.c_uint64)]),
         "sim_graph_create": (I, [P, P, P, F, I64, I, P, ctypes.POINTER(P)]),
         "sim_graph_launch": (I, [P, P]),
         "sim_graph_destroy": (None, [P]),

@@ -44,6 +44,9 @@ __global__ void __launch_bounds__(256) ckpt_kernel(CkptArgs A, const DevGroup P0
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t cstride = ckpt_stride(NS, A.n);
   for (int64_t i = first_agent(); i < A.n; i += stride) {
+#ifdef QS_CHECKED
+    if (HETERO && !QS_OK(A.gid[i] < A.n_groups, 5, A.gid[i])) continue;
+#endif
     St x;
     load_state<NS>(A.x0, A.n, i, x);
     store_state<NS>(A.ckpt, A.n, i, x);
@@ -64,6 +67,9 @@ __global__ void __launch_bounds__(256) ckpt_kernel(CkptArgs A, const DevGroup P0
         step<MODE>(P, x, c, hd, A.H, L);
         rc += (x.a[OM] * x.a[OM] + x.a[OM + 1] * x.a[OM + 1]) + (x.a[OM + 2] * x.a[OM + 2] + x.a[OM + 3] * x.a[OM + 3]);
         dst += cstride;
+#ifdef QS_CHECKED
+        if (!QS_OK(s + 1 <= A.S, 8, s + 1)) break;
+#endif
         store_state<NS>(dst, A.n, i, x);
       }
     } else {
@@ -75,6 +81,9 @@ __global__ void __launch_bounds__(256) ckpt_kernel(CkptArgs A, const DevGroup P0
           rc += (x.a[OM] * x.a[OM] + x.a[OM + 1] * x.a[OM + 1]) + (x.a[OM + 2] * x.a[OM + 2] + x.a[OM + 3] * x.a[OM + 3]);
         }
         dst += cstride;
+#ifdef QS_CHECKED
+        if (!QS_OK(s + 1 <= A.S, 8, s + 1)) break;
+#endif
         store_state<NS>(dst, A.n, i, x);
       }
     }
@@ -109,6 +118,12 @@ struct AdjArgs {
 // four bytes).
 template <int NS>
 __device__ __forceinline__ void prefetch_state(float4* dst, int bd, const float* src, int64_t n, int64_t i) {
+#ifdef QS_CHECKED
+  if (!QS_OK(i >= 0 && i < n, 3, i)) {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    return;
+  }
+#endif
   const float4* P = reinterpret_cast<const float4*>(src);
 #pragma unroll
   for (int k = 0; k < 4; ++k) cp_async16(dst + k * bd, P + k * n + i);
@@ -169,7 +184,13 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
 #pragma unroll
     for (int q = 0; q < NDC; ++q) dc[q] = 0.f;
     int g = -1;
-    if (i < A.n && A.status[i] == 0) {
+#ifdef QS_CHECKED
+    // a failed check leaves the lane in the loop (the warp's reduction below needs every lane)
+    const bool skip = i < A.n && A.gid && !QS_OK(A.gid[i] < A.n_groups, 5, A.gid[i]);
+#else
+    constexpr bool skip = false;
+#endif
+    if (!skip && i < A.n && A.status[i] == 0) {
       g = A.gid ? (int)A.gid[i] : 0;
       const DevGroup& P = sg[g];  // read from shared memory where used: keeps registers for the adjoint
       const LagCoef L = lag_coef(P.inv_tau, A.H);
@@ -185,6 +206,9 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
       for (int s = A.S - 1; s >= 0; --s) {
         const int64_t n0 = (int64_t)s * A.C;
         const int len = (int)min((int64_t)A.C, A.nsteps - n0);
+#ifdef QS_CHECKED
+        if (!QS_OK(s < A.S && len >= 1 && len <= A.C, 9, len)) break;
+#endif
         if (SMEMS) {
           // this segment's checkpoint has arrived; start fetching the next one
           const int b = (A.S - 1 - s) & 1;
@@ -233,11 +257,11 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
       }
       theta_from_derived(P, dc, tb);
       store_state<NS>(A.dLdx0, A.n, i, lam);
-      if (A.th_agent) {
+      if (A.th_agent && QS_OK(i < A.n, 9, i)) {
 #pragma unroll
         for (int q = 0; q < NTH; ++q) A.th_agent[i * NTH + q] = tb[q];
       }
-    } else if (i < A.n) {
+    } else if (!skip && i < A.n) {
       // a dead agent is frozen over the rollout (x_T = x_0, no running
       // cost): dL/dx_0 = dL/dx_T, and it adds nothing to theta
       St lam;
@@ -259,7 +283,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
         float v = mine ? tb[q] : 0.f;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane == 0) wacc[(warp * A.n_groups + gl) * NTH + q] += v;
+        if (lane == 0 && QS_OK(gl >= 0 && gl < A.n_groups, 5, gl)) wacc[(warp * A.n_groups + gl) * NTH + q] += v;
       }
     }
   }
@@ -276,6 +300,9 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
 __global__ void __launch_bounds__(256) reduce_partials(const float* partials, int nblocks, int width, float* out) {
   __shared__ float buf[256];
   const int e = blockIdx.x;
+#ifdef QS_CHECKED
+  if (!QS_OK(e < width, 12, e)) return;  // uniform over the block: no barrier is left waiting
+#endif
   float s = 0.f;
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partials[(int64_t)b * width + e];
   buf[threadIdx.x] = s;

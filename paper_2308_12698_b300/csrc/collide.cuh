@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "checks.cuh"
+
 namespace qs {
 
 struct __align__(32) CollRec {
@@ -89,6 +91,9 @@ __global__ void __launch_bounds__(256) collide_query(CollArgs A) {
       for (int b = 0; b < 8 && !h; ++b) {
         int j = A.head[cell_key(cx + ((b & 1) ? sx : 0), cy + ((b & 2) ? sy : 0), cz + ((b & 4) ? sz : 0), A.mask)];
         while (j >= 0 && budget-- > 0) {
+#ifdef QS_CHECKED
+          if (!QS_OK(j < A.n, 10, j)) break;
+#endif
           const float4* r4 = reinterpret_cast<const float4*>(A.rec + j);
           const float4 pj = r4[0];
           const int nj = __float_as_int(r4[1].x);

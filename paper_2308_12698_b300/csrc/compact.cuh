@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "checks.cuh"
+
 namespace qs {
 
 constexpr int kLiveBlock = 1024;  // threads of live_order_kernel: 32 warps
@@ -50,7 +52,8 @@ __global__ void __launch_bounds__(kLiveBlock) live_order_kernel(LiveArgs A) {
       int64_t pos = next[g] + __popc(below);
       for (int v = 0; v < w; ++v) pos += wcnt[v][g];
       // the bucket's end bounds the write even if the status changed between the passes
-      if (pos < A.off[g * (A.n_chunks + 1) + c + 1]) A.order[pos] = (uint32_t)i;
+      if (pos < A.off[g * (A.n_chunks + 1) + c + 1] && QS_OK(pos >= 0 && pos < A.n, 11, pos))
+        A.order[pos] = (uint32_t)i;
     }
     __syncthreads();
     if (threadIdx.x < A.n_groups) {

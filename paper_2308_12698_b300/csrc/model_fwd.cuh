@@ -32,6 +32,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "checks.cuh"
+
 namespace qs {
 
 enum { PX = 0, VX = 3, QW = 6, QX = 7, QY = 8, QZ = 9, WX = 10, OM = 13, NX = 17, NRB = 13, XI = 17, NXP = 20 };
@@ -117,6 +119,12 @@ __device__ __forceinline__ LagCoef lag_coef(float inv_tau, const StepH& H) {
 // agent) when the state has 20 components.
 template <int NS = NX>
 __device__ __forceinline__ void load_state(const float* __restrict__ base, int64_t n, int64_t i, St& x) {
+#ifdef QS_CHECKED
+  if (!QS_OK(i >= 0 && i < n, 1, i)) {
+    for (int k = 0; k < NS; ++k) x.a[k] = 0.f;
+    return;
+  }
+#endif
   const float4* P = reinterpret_cast<const float4*>(base);
   const float4 a = P[i], b = P[n + i], c = P[2 * n + i], d = P[3 * n + i];
   x.a[0] = a.x; x.a[1] = a.y; x.a[2] = a.z; x.a[3] = a.w;
@@ -133,6 +141,9 @@ __device__ __forceinline__ void load_state(const float* __restrict__ base, int64
 
 template <int NS = NX>
 __device__ __forceinline__ void store_state(float* __restrict__ base, int64_t n, int64_t i, const St& x) {
+#ifdef QS_CHECKED
+  if (!QS_OK(i >= 0 && i < n, 2, i)) return;
+#endif
   float4* P = reinterpret_cast<float4*>(base);
   P[i] = make_float4(x.a[0], x.a[1], x.a[2], x.a[3]);
   P[n + i] = make_float4(x.a[4], x.a[5], x.a[6], x.a[7]);

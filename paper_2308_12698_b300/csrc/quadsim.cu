@@ -640,6 +640,21 @@ int wait_stream(cudaStream_t st, int timeout_ms) {
 
 extern "C" {
 
+int sim_bounds_checks(uint64_t* first_failure) {
+  if (!first_failure) return SIM_ERR_ARG;
+  *first_failure = 0;
+#ifdef QS_CHECKED
+  unsigned long long w = 0, zero = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpyFromSymbol(&w, g_check_word, sizeof(w)) != cudaSuccess ||
+      cudaMemcpyToSymbol(g_check_word, &zero, sizeof(zero)) != cudaSuccess)
+    return SIM_ERR_CUDA;
+  *first_failure = w;
+  return 1;
+#else
+  return 0;
+#endif
+}
+
 const char* sim_error_string(int code) {
   switch (code) {
     case SIM_OK: return "ok";

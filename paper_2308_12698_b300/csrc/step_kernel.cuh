@@ -90,6 +90,12 @@ constexpr int kPlainSlotF4 = 6;
 // load in flight through its arithmetic.  Same arithmetic and results as the
 // register path.
 __device__ __forceinline__ void fetch_agent(float4* slot, int bd, const StepArgs& A, int64_t i) {
+#ifdef QS_CHECKED
+  if (!QS_OK(i >= 0 && i < A.n, 3, i)) {
+    cp_async_commit();
+    return;
+  }
+#endif
   const float4* P = reinterpret_cast<const float4*>(A.state);
 #pragma unroll
   for (int k = 0; k < 4; ++k) cp_async16(slot + k * bd, P + k * A.n + i);
@@ -110,6 +116,9 @@ __device__ __forceinline__ void plain_loop(const StepArgs& A, const DevGroup& P0
   for (int b = 0; i < end; i += stride, b ^= 1) {
     cp_async_wait_all();  // agent i has arrived in buffer b
     if (i + stride < end) fetch_agent(slot + (b ^ 1) * kPlainSlotF4 * bd, bd, A, i + stride);
+#ifdef QS_CHECKED
+    if (!QS_OK(i >= 0 && i < A.n, 4, i)) continue;
+#endif
     if (A.status[i]) continue;  // dead agents are frozen
     const float4* s = slot + b * kPlainSlotF4 * bd;
     const float4 p0 = s[0], p1 = s[bd], p2 = s[2 * bd], p3 = s[3 * bd], c = s[5 * bd];
@@ -150,6 +159,10 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 1) step_kernel(StepArgs A, co
   const int64_t end = A.first + A.count;
   const int K = PLAIN ? 1 : A.K;
   for (int64_t i = A.first + first_agent(); i < end; i += stride) {
+#ifdef QS_CHECKED
+    if (!QS_OK(i >= 0 && i < A.n, 4, i)) continue;
+    if (HETERO && !QS_OK(A.gid[i] < A.n_groups, 5, A.gid[i])) continue;
+#endif
     if (A.status[i]) continue;  // dead agents are frozen
     St x;
     load_state<state_dim<MODE>()>(A.state, A.n, i, x);
@@ -204,8 +217,15 @@ template <int MODE, bool MULTI = false, bool ORDER = false>
 __global__ void __launch_bounds__(256) range_kernel(StepArgs A, const __grid_constant__ RangeTable T) {
   int r = 0;
   for (int k = 1; k < T.n_ranges; ++k) r += (int)(blockIdx.x >= (unsigned)T.first_block[k]);
+#ifdef QS_CHECKED
+  if (!QS_OK(r >= 0 && r < T.n_ranges, 6, r)) return;
+#endif
   const int64_t j = T.start[r] + (int64_t)(blockIdx.x - T.first_block[r]) * blockDim.x + threadIdx.x;
   if (j >= T.end[r]) return;
+#ifdef QS_CHECKED
+  if (!QS_OK(j >= 0 && j < A.n, 6, j)) return;
+  if (ORDER && !QS_OK(A.order[j] < A.n, 7, A.order[j])) return;
+#endif
   const int64_t i = ORDER ? (int64_t)A.order[j] : j;
   if (A.status[i]) return;  // dead agents are frozen
   const DevGroup& P = T.g[r];
@@ -241,6 +261,10 @@ __global__ void __launch_bounds__(256) refreeze_kernel(StepArgs A) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t end = A.first + A.count;
   for (int64_t i = A.first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end; i += stride) {
+#ifdef QS_CHECKED
+    if (!QS_OK(i >= 0 && i < A.n, 4, i)) continue;
+    if (A.n_groups > 1 && !QS_OK(A.gid[i] < A.n_groups, 5, A.gid[i])) continue;
+#endif
     if (A.status[i] != kStatusDiverged) continue;
     const DevGroup& P = A.groups[A.n_groups > 1 ? A.gid[i] : 0];
     const float4 c = A.cmd[i];

@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_error_strings(L):
-    for code in (0, -1, -2, -3, -4, -5, -99):
+    for code in (0, -1, -2, -3, -4, -5, -6, -99):
         assert isinstance(L.sim_error_string(code), bytes)
     assert L.sim_error_string(-1) == b"invalid argument"
 
@@ -69,3 +69,18 @@ def test_null_handle_calls_fail_cleanly(L):
     assert L.sim_graph_launch(None, None) == _lib.SIM_ERR_ARG
     L.sim_destroy(None)
     L.sim_graph_destroy(None)
+
+
+def test_checked_build_exports_the_same_entry_points(L):
+    from paper_2308_12698_b300 import build
+    checked = ctypes.CDLL(build.LIB_CHECKED)
+    for n in declared():
+        assert hasattr(checked, n), n
+
+
+def test_product_build_has_no_device_checks(L):
+    # the product library answers without touching the device: checks not compiled in
+    word = ctypes.c_uint64(123)
+    assert L.sim_bounds_checks(ctypes.byref(word)) == 0
+    assert word.value == 0
+    assert L.sim_bounds_checks(None) == _lib.SIM_ERR_ARG
