@@ -345,6 +345,15 @@ int sim_status(sim_handle_t h, int64_t* n_dead, int timeout_ms, void* stream);
 /* Marks every agent alive again (and drops a sim_compact order). */
 int sim_reset_status(sim_handle_t h, void* stream);
 
+/* Per-group diagnostics of the swarm in d_state (planar, 16-byte aligned): for
+ * each group g, h_out[6 g .. 6 g + 5] = the number of live agents, of agents
+ * frozen non-finite (status 1), of agents marked collided (status 2), and the
+ * mean position x, y, z of the live agents (0 when none is live; z is the
+ * altitude).  FP64 sums reduced in a fixed order (the same result on every
+ * run); ordered after earlier work on `stream`, then waits for it (bounded).
+ * h_out: host memory of 6 n_groups doubles. */
+int sim_group_stats(sim_handle_t h, const float* d_state, double* h_out, void* stream);
+
 /* Steps only the live agents from now on (Sec. III-A: agents marked dead are
  * excluded from the computation).  Dead agents are otherwise skipped by the
  * thread that holds them, so a swarm whose dead agents are spread over the ids

@@ -29,7 +29,8 @@ EXPORTS = ("sim_create", "sim_set_params", "sim_step", "sim_step_host", "sim_rol
            "sim_workspace_bytes", "sim_rollout_backward", "sim_set_launch", "sim_get_launch", "sim_status",
            "sim_reset_status", "sim_graph_create", "sim_graph_launch", "sim_graph_destroy", "sim_step_launches",
            "sim_destroy", "sim_error_string", "sim_rollout_backward_noalloc",
-           "sim_collide_workspace_bytes", "sim_collide", "sim_copy_status", "sim_run_rounds", "sim_load_status", "sim_compact", "sim_bounds_checks")
+           "sim_collide_workspace_bytes", "sim_collide", "sim_copy_status", "sim_run_rounds", "sim_load_status", "sim_compact", "sim_bounds_checks",
+           "sim_group_stats")
 
 
 class GroupParams(ctypes.Structure):
@@ -95,6 +96,7 @@ def lib():
         "sim_status": (I, [P, ctypes.POINTER(I64), I, P]),
         "sim_reset_status": (I, [P, P]),
         "sim_compact": (I, [P, P]),
+        "sim_group_stats": (I, [P, P, P, P]),
         "sim_bounds_checks": (I, [ctypes.POINTER(ctypes.c_uint64)]),
         "sim_graph_create": (I, [P, P, P, F, I64, I, P, ctypes.POINTER(P)]),
         "sim_graph_launch": (I, [P, P]),

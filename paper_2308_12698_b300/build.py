@@ -12,7 +12,7 @@ LIB = os.path.join(HERE, "libquadsim.so")
 LIB_CHECKED = os.path.join(HERE, "libquadsim_checked.so")
 SOURCES = [os.path.join(CSRC, f) for f in ("quadsim.cu", "model_fwd.cuh", "model_adj.cuh", "step_kernel.cuh",
                                            "vehicles.cuh", "adjoint_kernel.cuh", "collide.cuh", "compact.cuh",
-                                           "checks.cuh")] + \
+                                           "checks.cuh", "stats.cuh")] + \
     [os.path.join(ROOT, "include", "quadsim.h")]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",

@@ -19,6 +19,7 @@
 #include "adjoint_kernel.cuh"
 #include "collide.cuh"
 #include "compact.cuh"
+#include "stats.cuh"
 #include "model_fwd.cuh"
 #include "step_kernel.cuh"
 
@@ -230,6 +231,10 @@ struct sim_s {
   unsigned int* h_live_cnt = nullptr;
   int64_t* d_live_off = nullptr;       // owned: the positions the scatter pass writes from, and theirs
   int64_t* h_live_off = nullptr;
+  // sim_group_stats: per-block partial rows and the summed row (device, owned), its pinned copy
+  double* d_stat = nullptr;
+  double* h_stat = nullptr;
+  int stat_blocks = 0;
   uint64_t epoch = 0;
   // host-buffer pipeline (sim_step_host): created on first use
   cudaStream_t s_h2d = nullptr, s_d2h = nullptr, s_comp[kComputeStreams] = {};
@@ -1224,6 +1229,52 @@ int sim_reset_status(sim_handle_t h, void* stream) {
                                                                                                    : SIM_ERR_CUDA;
 }
 
+int sim_group_stats(sim_handle_t h, const float* d_state, double* h_out, void* stream) {
+  if (!h || !h_out) return SIM_ERR_ARG;
+  const int G = h->n_groups, width = G * kStatFields;
+  for (int e = 0; e < width; ++e) h_out[e] = 0.0;
+  if (h->n == 0) return SIM_OK;
+  if (!d_state || !aligned16(d_state)) return SIM_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((h->n + kStatBlock - 1) / kStatBlock,
+                                                                 (int64_t)h->sms * 8));
+  if (!h->d_stat) {
+    h->stat_blocks = std::max(blocks, h->sms * 8);
+    if (cudaMalloc(&h->d_stat, sizeof(double) * (size_t)(h->stat_blocks + 1) * width) != cudaSuccess) {
+      h->d_stat = nullptr;
+      return SIM_ERR_CUDA;
+    }
+  }
+  if (!h->h_stat && cudaMallocHost(&h->h_stat, sizeof(double) * width) != cudaSuccess) {
+    h->h_stat = nullptr;
+    return SIM_ERR_CUDA;
+  }
+  StatArgs A;
+  A.pos = reinterpret_cast<const float4*>(d_state);
+  A.status = h->status;
+  A.gid = G > 1 ? h->gid : nullptr;
+  A.n = h->n;
+  A.n_groups = G;
+  A.partials = h->d_stat;
+  double* sums = h->d_stat + (size_t)h->stat_blocks * width;
+  group_stats_kernel<<<blocks, kStatBlock, 0, st>>>(A);
+  group_stats_finish<<<1, 256, 0, st>>>(h->d_stat, blocks, width, sums);
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(h->h_stat, sums, sizeof(double) * width, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return SIM_ERR_CUDA;
+  const int rc = wait_stream(st, 600000);
+  if (rc != SIM_OK) return rc;
+  for (int g = 0; g < G; ++g) {
+    const double* r = h->h_stat + g * kStatFields;
+    double* o = h_out + g * kStatFields;
+    o[0] = r[0];
+    o[1] = r[1];
+    o[2] = r[2];
+    for (int k = 3; k < 6; ++k) o[k] = r[0] > 0 ? r[k] / r[0] : 0.0;
+  }
+  return SIM_OK;
+}
+
 int sim_compact(sim_handle_t h, void* stream) {
   if (!h) return SIM_ERR_ARG;
   if (h->n == 0 || h->n > (int64_t)UINT32_MAX) return SIM_OK;
@@ -1303,6 +1354,8 @@ void sim_destroy(sim_handle_t h) {
   if (h->h_count) cudaFreeHost(h->h_count);
   if (h->d_order) cudaFree(h->d_order);
   if (h->d_live) cudaFree(h->d_live);
+  if (h->d_stat) cudaFree(h->d_stat);
+  if (h->h_stat) cudaFreeHost(h->h_stat);
   if (h->d_live_cnt) cudaFree(h->d_live_cnt);
   if (h->d_live_off) cudaFree(h->d_live_off);
   if (h->h_live_cnt) cudaFreeHost(h->h_live_cnt);

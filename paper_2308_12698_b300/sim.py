@@ -261,6 +261,15 @@ class Sim:
     def reset_status(self, stream=None):
         check(lib().sim_reset_status(self._h, _stream(stream)), "sim_reset_status")
 
+    def group_stats(self, state: torch.Tensor, stream=None):
+        """Per group: live, non-finite and collided counts and the live agents' mean position,
+        as a (n_groups, 6) float64 numpy array (sim_group_stats)."""
+        _check_f32(state, self.nx * self.n, "state")
+        out = np.zeros((self.n_groups, 6), dtype=np.float64)
+        check(lib().sim_group_stats(self._h, _ptr(state) if self.n else None,
+                                    out.ctypes.data_as(ctypes.c_void_p), _stream(stream)), "sim_group_stats")
+        return out
+
     def compact(self, stream=None):
         """Step only the live agents from now on (sim_compact); graphs captured before go stale."""
         check(lib().sim_compact(self._h, _stream(stream)), "sim_compact")

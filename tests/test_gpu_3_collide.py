@@ -157,3 +157,34 @@ def test_detection_between_rounds_of_flight(dev, orc):
         prev_x, prev_st = xs, st
     assert all(d > 0 for d in deaths), deaths
     sim.close()
+
+
+@pytest.mark.parametrize("n_per", [0, 5000, 70_000])
+def test_group_stats(dev, n_per):
+    """sim_group_stats against numpy on the same state and status bytes: counts exact, means
+    within FP64 summation-order rounding, and bitwise the same on a second call.  Groups
+    interleaved, one of them empty when n_per = 0, agents non-finite and collided."""
+    from paper_2308_12698_b300.sim import Sim, planar
+    sizes = (n_per, 3000, 2 * n_per + 17) if n_per else (0, 3000, 17)
+    wl = W.heterogeneous(sizes=sizes, nsteps=1, shuffle=True)
+    x0 = wl.x0.copy()
+    status = np.zeros(wl.n, np.uint8)
+    rng = np.random.default_rng(11)
+    status[rng.random(wl.n) < 0.1] = 1
+    status[rng.random(wl.n) < 0.1] = 2
+    gid = torch.from_numpy(wl.gid).to(dev)
+    sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
+    sim.load_status(torch.from_numpy(status).to(dev))
+    x = planar(torch.from_numpy(x0)).to(dev)
+    got = sim.group_stats(x)
+    again = sim.group_stats(x)
+    np.testing.assert_array_equal(got, again)
+    for g in range(len(wl.groups)):
+        m = wl.gid == g
+        live = m & (status == 0)
+        assert got[g, 0] == live.sum()
+        assert got[g, 1] == (m & (status == 1)).sum()
+        assert got[g, 2] == (m & (status == 2)).sum()
+        mean = x0[live, 0:3].astype(np.float64).mean(axis=0) if live.any() else np.zeros(3)
+        np.testing.assert_allclose(got[g, 3:6], mean, rtol=1e-12, atol=1e-12)
+    sim.close()
