@@ -389,7 +389,8 @@ void sim_graph_destroy(sim_graph_t g);
 /* Number of kernel launches one sim_step call makes for these arguments:
  * ceil(nsteps / K) step launches, plus one pass that replays agents which
  * went non-finite in the middle of a launch (none when every launch is a
- * single step of one open- or P-closed-loop quadrotor group). */
+ * single step of one open- or P-closed-loop quadrotor group).  An upper
+ * bound after sim_compact: a step launch over no live agent is skipped. */
 int64_t sim_step_launches(sim_handle_t h, int64_t nsteps, int substeps_K);
 
 void sim_destroy(sim_handle_t h);
