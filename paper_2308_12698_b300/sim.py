@@ -297,6 +297,8 @@ class Graph:
         self._g = g
 
     def launch(self, stream=None):
+        if not self.sim.handle:  # the graph's kernels use the handle's buffers: it must outlive the graph
+            raise SimError("graph launch after its Sim was closed")
         check(lib().sim_graph_launch(self._g, _stream(stream)), "sim_graph_launch")
 
     def close(self):
