@@ -169,18 +169,20 @@ def test_heterogeneous_parity(dev, orc, shuffle):
     check_traj(gpu_run(wl, dev, 1000, K=50), ref_run(orc, wl, 1000))
 
 
-def test_heterogeneous_full_size_sampled(dev, orc):
-    """The bench's heterogeneous batch (8 groups, 600,000 agents, one launch of K = 1000): 2048
-    sampled agents against the checker."""
+@pytest.mark.parametrize("shuffle", [False, True], ids=["contiguous", "interleaved"])
+def test_heterogeneous_full_size_sampled(dev, orc, shuffle):
+    """The bench's heterogeneous batch (8 groups, 600,000 agents, one launch of K = 1000; ids
+    contiguous, or in random order through the group-sorted order): 2048 sampled agents and the
+    first agent of every group against the checker."""
     from paper_2308_12698_b300.sim import Sim, planar, unplanar
-    wl = W.heterogeneous(nsteps=1000)
+    wl = W.heterogeneous(nsteps=1000, shuffle=shuffle)
     gid = torch.from_numpy(wl.gid).to(dev)
     sim = Sim(wl.groups, wl.n, wl.mode, gid=gid)
     x = planar(torch.from_numpy(wl.x0)).to(dev)
     cmd = torch.from_numpy(wl.cmd).reshape(-1).to(dev)
     sim.step(x, cmd, wl.dt, 1000, K=1000)
-    idx = np.concatenate([np.random.default_rng(13).choice(wl.n, 2048, replace=False),
-                          np.searchsorted(wl.gid, np.arange(8))])  # the first agent of every group
+    firsts = np.array([np.flatnonzero(wl.gid == g)[0] for g in range(8)])  # the first agent of every group
+    idx = np.concatenate([np.random.default_rng(13).choice(wl.n, 2048, replace=False), firsts])
     got = unplanar(x, wl.n)[torch.from_numpy(idx).to(dev)].cpu().numpy()
     ref = orc.rollout(wl.groups, wl.gid[idx], wl.x0[idx], wl.cmd[idx], wl.dt, 1000, wl.mode)
     check_traj(got, ref)

@@ -197,11 +197,13 @@ def test_mixed_swarm_host_entry_and_rounds_are_bitwise_sim_step(dev):
     sim.close()
 
 
-def test_mixed_swarm_full_size_sampled(dev, orc):
-    """The bench's mixed-type leg (600,000 agents, one launch of K = 1000): 1000 sampled agents
-    of each type against the checker."""
+@pytest.mark.parametrize("shuffle", [False, True], ids=["contiguous", "interleaved"])
+def test_mixed_swarm_full_size_sampled(dev, orc, shuffle):
+    """The bench's mixed-type legs (600,000 agents, one launch of K = 1000; the types' ids
+    contiguous, or in random order through the group-sorted order): 1000 sampled agents of each
+    type against the checker."""
     from paper_2308_12698_b300.sim import Sim, planar, unplanar
-    wl = W.multi_type(nsteps=1000)
+    wl = W.multi_type(nsteps=1000, shuffle=shuffle)
     sim = Sim(wl.groups, wl.n, wl.mode, gid=torch.from_numpy(wl.gid).to(dev))
     x = planar(torch.from_numpy(wl.x0)).to(dev)
     sim.step(x, torch.from_numpy(wl.cmd).to(dev).reshape(-1), wl.dt, 1000, K=1000)
