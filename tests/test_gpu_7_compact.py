@@ -182,3 +182,14 @@ def test_all_dead_and_empty(dev):
     empty = Sim([W.base_group()], 0, W.CLOSED_LOOP)
     empty.compact()
     empty.close()
+
+
+def test_full_size_half_dead_bitwise(dev):
+    """The bench's half-dead leg in its launch shape: 1e6 agents, half dead at random, one launch
+    of K = 1000; compacted and in place give the same bits."""
+    wl = W.scale_sweep(1_000_000, nsteps=1000)
+    status = _dead(wl.n, 0.5, 7)
+    a, sa = _run(wl, dev, status, 1000, 1000, compact=False)
+    b, sb = _run(wl, dev, status, 1000, 1000, compact=True)
+    np.testing.assert_array_equal(b, a)
+    np.testing.assert_array_equal(sb, sa)
