@@ -363,10 +363,9 @@ int sim_group_stats(sim_handle_t h, const float* d_state, double* h_out, void* s
  * (4 bytes per agent of device memory the handle owns): two passes on the
  * device ordered after earlier work on `stream`, with one bounded wait for
  * the per-group counts between them and one at the end (0.14 ms for 1e6
- * agents).  Fused launches that
- * an order serves -- 32 steps or more, or any number when the groups mix agent
- * types, over the whole swarm or whole sim_step_host chunks -- then step only
- * those agents, one group per block.  Results are the same bit for bit.
+ * agents).  Fused launches of 2 steps or more (any number when the groups mix
+ * agent types), over the whole swarm or whole sim_step_host chunks, then step
+ * only those agents, one group per block.  Results are the same bit for bit.
  * Agents that die later are skipped as before; sim_reset_status and
  * sim_load_status drop the order (dead agents may come alive).  Each of these
  * changes of the order makes graphs captured before it stale: sim_graph_launch

@@ -3,8 +3,8 @@ excluded from the computation).
 
 The live agents' order changes which warp holds which agent, never an agent's
 arithmetic: every case compares a compacted handle with an uncompacted one bit
-for bit, state and status bytes, over launches that take the order (32 steps or
-more, any K for mixed agent types) and launches that do not.
+for bit, state and status bytes, over launches that take the order (2 steps or
+more, any K for mixed agent types) and launches that do not (K = 1).
 """
 import numpy as np
 import pytest
@@ -67,8 +67,7 @@ def _run(wl, dev, status, nsteps, K, compact, x0=None):
 @pytest.mark.parametrize("kind", ["one_group", "contiguous", "interleaved", "mixed_types", "pid"])
 @pytest.mark.parametrize("K", [1, 40, 100])
 def test_compacted_steps_are_bitwise_the_same(dev, kind, K):
-    """Half the agents dead at random; 100 steps (K = 40: launches of 40, 40 and 20, the last
-    one below the order's 32 steps for one agent type)."""
+    """Half the agents dead at random; 100 steps (K = 40: launches of 40, 40 and 20)."""
     wl = _workload(kind)
     status = _dead(wl.n, 0.5, 1)
     a, sa = _run(wl, dev, status, 100, K, compact=False)
