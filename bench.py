@@ -912,6 +912,11 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     dx0 = planar(torch.from_numpy(dw.x0)).to(dev)
     dcmd = torch.from_numpy(dw.cmd).reshape(-1).to(dev)
     c4 = fwd_adj_entry(world, ds, dx0, dcmd, dw.nsteps, 100, timed_steps, reps, sms, clocks)
+    # beside the workload's own interval, the tuner's pick of C and block for this swarm
+    c4t = autotune.tune_adjoint(ds, dx0, dcmd, DT, dw.nsteps)
+    tuned = fwd_adj_entry(world, ds, dx0, dcmd, dw.nsteps, c4t["C"], timed_steps, reps, sms, clocks)
+    c4["tuned"] = {k: tuned[k] for k in ("value", "ms_per_step", "C", "block_adj", "checkpoint_MB")}
+    c4["tuned"]["frac"] = tuned["roofline"]["frac"]
     kinks = {}
     try:
         with open(os.path.join(ROOT, "tests", "golden", "kinks_differentiable.json")) as f:
