@@ -362,11 +362,6 @@ size_t scratch_bytes(const sim_s* h, int C, int grid) {
   return align256((size_t)C * h->nx * sizeof(float) * (size_t)grid * h->block_adj);
 }
 
-// Several groups: whether each group's agents form one contiguous range of
-// ids (sorted ids, or contiguous blocks in any order), read once,
-// synchronously, from the caller's id buffer (which the handle's contract
-// keeps unchanged).  If so the fused steps run as range_kernel; otherwise
-// (ids interleaved) as step_kernel with the table in shared memory.
 int wait_stream(cudaStream_t st, int timeout_ms);
 
 // The agents whose status byte is 0, sorted by (group, host-pipeline chunk,
@@ -418,8 +413,10 @@ int order_live(sim_s* h, cudaStream_t st, uint32_t* out, std::vector<int64_t>& o
   return SIM_OK;
 }
 
-// How the fused steps reach the groups, decided once from the ids at
-// creation: contiguous ranges (range_kernel directly), a group-sorted order
+// How the fused steps reach the groups, decided once at creation from the
+// caller's id buffer (read synchronously; the handle's contract keeps it
+// unchanged): contiguous ranges, one per group (sorted ids, or contiguous
+// blocks in any order: range_kernel directly), a group-sorted order
 // (interleaved ids), or neither (one group).
 int plan_groups(sim_s* h) {
   h->ranged = false;
