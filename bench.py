@@ -1029,6 +1029,11 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
         dh["compacted" if compact else "in_place"] = {"value": world * live * T_STEPS / (dms / 1e3),
                                                       "ms_per_step": dms}
         dg.close()
+        # forward with checkpoints + adjoint over the same swarm (C = 100)
+        fms, _, _ = timed_fwd_adj(ds, dx0, dcmd, T_STEPS, 100, timed_steps, reps)
+        fms = max_over_ranks(fms, world)
+        dh.setdefault("fwd_adjoint_C100", {})["compacted" if compact else "in_place"] = {
+            "value": world * live * T_STEPS / (fms / 1e3), "ms_per_step": fms}
         ds.close()
     out["half_dead"] = dict(dh, unit=UNIT, n_agents=dwl.n, live_agents=live, K=T_STEPS,
                             note="live agent-steps/s; 50 % of the agents dead at random positions in the ids")

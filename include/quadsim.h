@@ -365,7 +365,10 @@ int sim_group_stats(sim_handle_t h, const float* d_state, double* h_out, void* s
  * the per-group counts between them and one at the end (0.14 ms for 1e6
  * agents).  Fused launches of 2 steps or more (any number when the groups mix
  * agent types), over the whole swarm or whole sim_step_host chunks, then step
- * only those agents, one group per block.  Results are the same bit for bit.
+ * only those agents, one group per block; sim_rollout_forward and the adjoint
+ * (sim_rollout_backward, sim_rollout_backward_noalloc) sweep only those agents
+ * too, and a memory-bound pass writes the frozen results of the dead ones
+ * (their checkpoints, dL/dx0 = dL/dx_T, zero theta rows).  Results are the same bit for bit.
  * Agents that die later are skipped as before; sim_reset_status and
  * sim_load_status drop the order (dead agents may come alive).  Each of these
  * changes of the order makes graphs captured before it stale: sim_graph_launch

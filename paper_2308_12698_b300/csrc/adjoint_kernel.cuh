@@ -23,6 +23,8 @@ struct CkptArgs {
   int n_groups;
   StepH H;
   const DevGroup* groups;
+  const uint32_t* order;  // null, or the live agents' order: agent order[j] for j < count
+  int64_t count;          // agents the kernel visits: n, or the order's length
 };
 
 // Floats from one checkpoint to the next: a planar state (NS N floats)
@@ -43,8 +45,10 @@ __global__ void __launch_bounds__(256) ckpt_kernel(CkptArgs A, const DevGroup P0
   constexpr int NS = state_dim<MODE>();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t cstride = ckpt_stride(NS, A.n);
-  for (int64_t i = first_agent(); i < A.n; i += stride) {
+  for (int64_t j = first_agent(); j < A.count; j += stride) {
+    const int64_t i = A.order ? (int64_t)A.order[j] : j;
 #ifdef QS_CHECKED
+    if (!QS_OK(i >= 0 && i < A.n, 4, i)) continue;
     if (HETERO && !QS_OK(A.gid[i] < A.n_groups, 5, A.gid[i])) continue;
 #endif
     St x;
@@ -92,6 +96,24 @@ __global__ void __launch_bounds__(256) ckpt_kernel(CkptArgs A, const DevGroup P0
   }
 }
 
+// With the live agents' order, ckpt_kernel visits only those agents: every
+// agent dead at the start of the rollout gets its frozen checkpoints here (the
+// start state at every checkpoint, no running cost), as ckpt_kernel writes them
+// for the dead agents it visits.
+template <int MODE>
+__global__ void __launch_bounds__(256) ckpt_frozen_kernel(CkptArgs A) {
+  constexpr int NS = state_dim<MODE>();
+  const int64_t cstride = ckpt_stride(NS, A.n);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) {
+    if (!A.status[i]) continue;
+    St x;
+    load_state<NS>(A.x0, A.n, i, x);
+    for (int s = 0; s <= A.S; ++s) store_state<NS>(A.ckpt + s * cstride, A.n, i, x);
+    if (A.run_cost) A.run_cost[i] = 0.f;
+  }
+}
+
 struct AdjArgs {
   const float* ckpt;
   const float4* cmd;
@@ -110,6 +132,8 @@ struct AdjArgs {
   int n_groups;
   StepH H;
   const DevGroup* groups;
+  const uint32_t* order;  // null, or the live agents' order: agent order[j] for j < count
+  int64_t count;          // agents the kernel visits: n, or the order's length
 };
 
 // Starts copying agent i's state out of the planar checkpoint `src` (n
@@ -154,7 +178,9 @@ __device__ __forceinline__ void read_prefetched(const float4* src, int bd, St& x
 // rather than in the global scratch, and each segment's checkpoint is
 // prefetched into shared memory (cp.async, double-buffered) while the
 // segment before it in the sweep is being processed.
-template <int MODE, bool SMEMS>
+// ORDER: the agents of the live agents' order (A.order, A.count) rather than
+// all n in index order.
+template <int MODE, bool SMEMS, bool ORDER = false>
 __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
   extern __shared__ float4 smem4[];
   DevGroup* sg = reinterpret_cast<DevGroup*>(smem4);
@@ -176,8 +202,10 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
   // checkpoints; global scratch: for the segment's step-start states)
   const int bd = blockDim.x;
   float4* const mypf = reinterpret_cast<float4*>(sscr + (SMEMS ? (int64_t)A.C * sstep : 0)) + threadIdx.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < A.n; base += nthreads) {
-    const int64_t i = base + threadIdx.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < A.count; base += nthreads) {
+    const int64_t j = base + threadIdx.x;
+    const bool in = j < A.count;  // every lane stays in the loop for the warp's reduction below
+    const int64_t i = ORDER ? (in ? (int64_t)A.order[j] : A.n) : j;
     float tb[NTH], dc[NDC];
 #pragma unroll
     for (int q = 0; q < NTH; ++q) tb[q] = 0.f;
@@ -186,11 +214,11 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
     int g = -1;
 #ifdef QS_CHECKED
     // a failed check leaves the lane in the loop (the warp's reduction below needs every lane)
-    const bool skip = i < A.n && A.gid && !QS_OK(A.gid[i] < A.n_groups, 5, A.gid[i]);
+    const bool skip = in && (!QS_OK(i >= 0 && i < A.n, 4, i) || (A.gid && !QS_OK(A.gid[i] < A.n_groups, 5, A.gid[i])));
 #else
     constexpr bool skip = false;
 #endif
-    if (!skip && i < A.n && A.status[i] == 0) {
+    if (!skip && in && A.status[i] == 0) {
       g = A.gid ? (int)A.gid[i] : 0;
       const DevGroup& P = sg[g];  // read from shared memory where used: keeps registers for the adjoint
       const LagCoef L = lag_coef(P.inv_tau, A.H);
@@ -261,7 +289,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
 #pragma unroll
         for (int q = 0; q < NTH; ++q) A.th_agent[i * NTH + q] = tb[q];
       }
-    } else if (!skip && i < A.n) {
+    } else if (!skip && in) {
       // a dead agent is frozen over the rollout (x_T = x_0, no running
       // cost): dL/dx_0 = dL/dx_T, and it adds nothing to theta
       St lam;
@@ -292,6 +320,24 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
     float s = 0.f;
     for (int w = 0; w < nw; ++w) s += wacc[w * A.n_groups * NTH + e];
     A.partials[(int64_t)blockIdx.x * A.n_groups * NTH + e] = s;
+  }
+}
+
+// With the live agents' order, adjoint_kernel visits only those agents: every
+// agent dead when the sweep runs gets the frozen map's gradient here (dL/dx0 =
+// dL/dx_T, a zero theta row), as adjoint_kernel writes it for the dead agents
+// it visits.
+template <int MODE>
+__global__ void __launch_bounds__(256) adjoint_frozen_kernel(AdjArgs A) {
+  constexpr int NS = state_dim<MODE>();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) {
+    if (!A.status[i]) continue;
+    St lam;
+    load_state<NS>(A.dLdxT, A.n, i, lam);
+    store_state<NS>(A.dLdx0, A.n, i, lam);
+    if (A.th_agent)
+      for (int q = 0; q < NTH; ++q) A.th_agent[i * NTH + q] = 0.f;
   }
 }
 

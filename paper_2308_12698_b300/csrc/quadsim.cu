@@ -339,18 +339,38 @@ int adj_grid(const sim_s* h, int C) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)occ * h->sms));
 }
 
+// The agents a rollout kernel visits: the live agents' order after
+// sim_compact, else all n in index order.
+void live_visit(const sim_s* h, const uint32_t** order, int64_t* count) {
+  *order = h->live ? h->d_live : nullptr;
+  *count = h->live ? h->live_off.back() : h->n;
+}
+
 int launch_adjoint(const sim_s* h, const AdjArgs& A, int C, int grid, cudaStream_t st) {
   const size_t smem = adj_smem(h, C);
   const bool sm = adj_smem_scratch(h, C);
+  if (A.order) {
+    const int fgrid = (int)std::max<int64_t>(1, std::min<int64_t>((h->n + 255) / 256, (int64_t)h->sms * 8));
+    if (h->mode == SIM_CLOSED_LOOP_PID) adjoint_frozen_kernel<2><<<fgrid, 256, 0, st>>>(A);
+    else if (h->mode == SIM_CLOSED_LOOP) adjoint_frozen_kernel<1><<<fgrid, 256, 0, st>>>(A);
+    else adjoint_frozen_kernel<0><<<fgrid, 256, 0, st>>>(A);
+  }
+  const bool o = A.order != nullptr;
   if (h->mode == SIM_CLOSED_LOOP_PID) {
-    if (sm) adjoint_kernel<2, true><<<grid, h->block_adj, smem, st>>>(A);
-    else adjoint_kernel<2, false><<<grid, h->block_adj, smem, st>>>(A);
+    if (sm) o ? adjoint_kernel<2, true, true><<<grid, h->block_adj, smem, st>>>(A)
+              : adjoint_kernel<2, true><<<grid, h->block_adj, smem, st>>>(A);
+    else o ? adjoint_kernel<2, false, true><<<grid, h->block_adj, smem, st>>>(A)
+           : adjoint_kernel<2, false><<<grid, h->block_adj, smem, st>>>(A);
   } else if (h->mode == SIM_CLOSED_LOOP) {
-    if (sm) adjoint_kernel<1, true><<<grid, h->block_adj, smem, st>>>(A);
-    else adjoint_kernel<1, false><<<grid, h->block_adj, smem, st>>>(A);
+    if (sm) o ? adjoint_kernel<1, true, true><<<grid, h->block_adj, smem, st>>>(A)
+              : adjoint_kernel<1, true><<<grid, h->block_adj, smem, st>>>(A);
+    else o ? adjoint_kernel<1, false, true><<<grid, h->block_adj, smem, st>>>(A)
+           : adjoint_kernel<1, false><<<grid, h->block_adj, smem, st>>>(A);
   } else {
-    if (sm) adjoint_kernel<0, true><<<grid, h->block_adj, smem, st>>>(A);
-    else adjoint_kernel<0, false><<<grid, h->block_adj, smem, st>>>(A);
+    if (sm) o ? adjoint_kernel<0, true, true><<<grid, h->block_adj, smem, st>>>(A)
+              : adjoint_kernel<0, true><<<grid, h->block_adj, smem, st>>>(A);
+    else o ? adjoint_kernel<0, false, true><<<grid, h->block_adj, smem, st>>>(A)
+           : adjoint_kernel<0, false><<<grid, h->block_adj, smem, st>>>(A);
   }
   return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ERR_CUDA;
 }
@@ -746,7 +766,13 @@ int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents,
     const int big = (int)(kSmemScratchMax + 64 * 1024);
     if (cudaFuncSetAttribute(adjoint_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) != cudaSuccess ||
         cudaFuncSetAttribute(adjoint_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) != cudaSuccess ||
-        cudaFuncSetAttribute(adjoint_kernel<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) != cudaSuccess)
+        cudaFuncSetAttribute(adjoint_kernel<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) != cudaSuccess ||
+        cudaFuncSetAttribute(adjoint_kernel<2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(adjoint_kernel<1, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(adjoint_kernel<0, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
+            cudaSuccess)
       rc = SIM_ERR_CUDA;
   }
   if (rc != SIM_OK) {
@@ -972,10 +998,18 @@ int sim_rollout_forward(sim_handle_t h, const float* d_state0, const float* d_cm
   A.n_groups = h->n_groups;
   A.H = make_h(dt);
   A.groups = h->d_groups;
+  live_visit(h, &A.order, &A.count);
   const size_t smem = group_smem(h);
   const int grid = fwd_grid(h, smem, h->n);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const DevGroup& P0 = h->host_group0;
+  if (A.order) {
+    // the agents dead at the start first: ckpt_kernel marks the ones that die on the way
+    const int fgrid = (int)std::max<int64_t>(1, std::min<int64_t>((h->n + 255) / 256, (int64_t)h->sms * 8));
+    if (h->mode == SIM_CLOSED_LOOP_PID) ckpt_frozen_kernel<2><<<fgrid, 256, 0, st>>>(A);
+    else if (h->mode == SIM_CLOSED_LOOP) ckpt_frozen_kernel<1><<<fgrid, 256, 0, st>>>(A);
+    else ckpt_frozen_kernel<0><<<fgrid, 256, 0, st>>>(A);
+  }
   if (h->mode == SIM_CLOSED_LOOP_PID) {
     if (hetero(h)) ckpt_kernel<2, true><<<grid, h->block_fwd, smem, st>>>(A, P0);
     else ckpt_kernel<2, false><<<grid, h->block_fwd, smem, st>>>(A, P0);
@@ -1034,6 +1068,7 @@ int sim_rollout_backward(sim_handle_t h, const float* d_ckpt, const float* d_cmd
   A.n_groups = h->n_groups;
   A.H = make_h(dt);
   A.groups = h->d_groups;
+  live_visit(h, &A.order, &A.count);
   if (launch_adjoint(h, A, C, grid, st) != SIM_OK) return SIM_ERR_CUDA;
   reduce_partials<<<h->n_groups * NTH, 256, 0, st>>>(A.partials, grid, h->n_groups * NTH, d_dL_dtheta);
   return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ERR_CUDA;
@@ -1123,6 +1158,7 @@ int sim_rollout_backward_noalloc(sim_handle_t h, const float* d_ckpt, const floa
   A.n_groups = h->n_groups;
   A.H = make_h(dt);
   A.groups = h->d_groups;
+  live_visit(h, &A.order, &A.count);
   if (launch_adjoint(h, A, C, grid, st) != SIM_OK) return SIM_ERR_CUDA;
   reduce_partials<<<h->n_groups * NTH, 256, 0, st>>>(A.partials, grid, h->n_groups * NTH, d_dL_dtheta);
   return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ERR_CUDA;

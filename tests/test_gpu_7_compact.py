@@ -192,3 +192,48 @@ def test_full_size_half_dead_bitwise(dev):
     b, sb = _run(wl, dev, status, 1000, 1000, compact=True)
     np.testing.assert_array_equal(b, a)
     np.testing.assert_array_equal(sb, sa)
+
+
+def _rollout(wl, dev, status, C, compact, x0, gT):
+    from paper_2308_12698_b300.sim import planar
+    sim = _sim(wl, dev)
+    sim.load_status(torch.from_numpy(status).to(dev))
+    if compact:
+        sim.compact()
+    x = planar(torch.from_numpy(x0)).to(dev)
+    cmd = torch.from_numpy(wl.cmd).reshape(-1).to(dev)
+    w = torch.full((wl.n,), wl.w_omega, device=dev)
+    ckpt, rc = sim.rollout_forward(x, cmd, wl.dt, wl.nsteps, C=C)
+    st_fwd = sim.status().cpu().numpy()
+    dx0, dth, dtha = sim.rollout_backward(ckpt, cmd, wl.dt, wl.nsteps, gT, w, C=C, per_agent=True)
+    torch.cuda.synchronize()
+    out = [t.cpu().numpy() for t in (ckpt, rc, dx0, dth, dtha)] + [st_fwd]
+    sim.close()
+    return out
+
+
+@pytest.mark.parametrize("pid", [False, True], ids=["p-loop", "pid-loop"])
+@pytest.mark.parametrize("C", [1, 8, 40])
+def test_compacted_rollout_and_adjoint(dev, pid, C):
+    """Checkpointed rollout and adjoint over the live agents' order: checkpoints, running costs,
+    status, dL/dx0 and per-agent theta rows bit for bit as without the order, group sums within
+    summation-order rounding.  Half the agents dead before the rollout; eight more spin past
+    RK4's stability bound and die during it (their checkpoints are the kernel's, not the
+    frozen pass's, which runs first)."""
+    make = W.differentiable_pid if pid else W.differentiable
+    wl = make(n_per_group=500, n_groups=4, nsteps=240)
+    x0 = wl.x0.copy()
+    status = _dead(wl.n, 0.5, 8)
+    spin = np.flatnonzero(status == 0)[:8]
+    x0[spin, 10:13] = 0.0
+    x0[spin, 12] = np.linspace(8000.0, 12000.0, 8)
+    nx = x0.shape[1]
+    gT = torch.zeros(nx * wl.n, device=dev)
+    gT[: 3 * wl.n] = 1.0
+    a = _rollout(wl, dev, status, C, False, x0, gT)
+    b = _rollout(wl, dev, status, C, True, x0, gT)
+    for k, name in ((0, "checkpoints"), (1, "running cost"), (2, "dL/dx0"), (4, "theta rows"), (5, "status")):
+        np.testing.assert_array_equal(b[k], a[k], err_msg=name)
+    assert (a[5][spin] == 1).sum() >= 6, a[5][spin]
+    scale = np.abs(a[3]).max()
+    np.testing.assert_allclose(b[3], a[3], rtol=1e-5, atol=1e-6 * scale)
