@@ -25,6 +25,7 @@ struct CkptArgs {
   const DevGroup* groups;
   const uint32_t* order;  // null, or the live agents' order: agent order[j] for j < count
   int64_t count;          // agents the kernel visits: n, or the order's length
+  LinCoef coef;           // one group: its RK4 weights of the linear parts (lin_coef, on the host)
 };
 
 // Floats from one checkpoint to the next: a planar state (NS N floats)
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(256) ckpt_kernel(CkptArgs A, const DevGroup P0
     const float4 c = A.cmd[i];
     const Hd hd = heading(MODE != 0 ? c.w : 0.f);
     const DevGroup P = HETERO ? sg[A.gid[i]] : P0;
-    const LagCoef L = lag_coef(P.inv_tau, A.H);
+    const LinCoef L = HETERO ? lin_coef(P.inv_tau, P.cd_m, A.H) : A.coef;
     float rc = 0.f;
     float* dst = A.ckpt;  // checkpoint s + 1 follows checkpoint s at cstride floats
     if (A.C == 1) {
@@ -183,13 +184,18 @@ __device__ __forceinline__ void read_prefetched(const float4* src, int bd, St& x
 template <int MODE, bool SMEMS, bool ORDER = false>
 __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
   extern __shared__ float4 smem4[];
+  // shared memory: the group table, each group's RK4 weights, the per-warp
+  // accumulators, then (16-byte aligned) the scratch and prefetch slots
   DevGroup* sg = reinterpret_cast<DevGroup*>(smem4);
-  float* wacc = reinterpret_cast<float*>(sg + A.n_groups);
+  LinCoef* scoef = reinterpret_cast<LinCoef*>(sg + A.n_groups);
+  float* wacc = reinterpret_cast<float*>(scoef + A.n_groups);
   const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int e = threadIdx.x; e < nw * A.n_groups * NTH; e += blockDim.x) wacc[e] = 0.f;
   load_groups<true>(sg, A.groups, A.n_groups);
-  // shared scratch starts after the accumulators, 16-byte aligned
-  float* sscr = reinterpret_cast<float*>(smem4 + (sizeof(DevGroup) * A.n_groups + 4 * nw * A.n_groups * NTH + 15) / 16);
+  for (int g = threadIdx.x; g < A.n_groups; g += blockDim.x) scoef[g] = lin_coef(sg[g].inv_tau, sg[g].cd_m, A.H);
+  __syncthreads();
+  float* sscr = reinterpret_cast<float*>(
+      smem4 + (sizeof(DevGroup) * A.n_groups + sizeof(LinCoef) * A.n_groups + 4 * nw * A.n_groups * NTH + 15) / 16);
   float* const scratch = SMEMS ? sscr : A.scratch;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;  // grid stride over agents
   // scratch column of this thread: its own slot in the block (shared) or in the grid (global)
@@ -221,7 +227,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
     if (!skip && in && A.status[i] == 0) {
       g = A.gid ? (int)A.gid[i] : 0;
       const DevGroup& P = sg[g];  // read from shared memory where used: keeps registers for the adjoint
-      const LagCoef L = lag_coef(P.inv_tau, A.H);
+      const LinCoef& L = scoef[g];
       const float4 c = A.cmd[i];
       const Hd hd = heading(MODE != 0 ? c.w : 0.f);
       const float w = A.w_run ? A.w_run[i] : 0.f;

@@ -194,7 +194,7 @@ __device__ __forceinline__ void controller_vjp(const DevGroup& P, const float* x
 // slower: the recomputation fills issue slots that would otherwise wait).
 template <int MODE>
 __device__ __forceinline__ void step_vjp(const DevGroup& P, const St& x, const float4 c, const Hd& hd,
-                                         const StepH& H, const LagCoef& L, St& lam, float tb[NTH], float dc[NDC]) {
+                                         const StepH& H, const LinCoef& L, St& lam, float tb[NTH], float dc[NDC]) {
   float u[4];
   float wdot[3], e[3];  // PID: omega' at x and the rate error
   if (MODE == 2) {

@@ -4,8 +4,11 @@
 //                   plus linear drag, for the 13 rigid-body components
 //   rotor lag       Omega' = (Omega_cmd - Omega)/tau_m; linear and decoupled, so
 //                   its four RK4 stages and the RK4 update are applied through
-//                   their exact coefficients (LagCoef) instead of four
+//                   their exact coefficients (LinCoef) instead of four
 //                   derivative evaluations -- the same RK4 map, fewer operations
+//   drag            linear in v with a forcing that does not depend on v: the
+//                   translation's RK4 update is likewise a fixed weighting of
+//                   v and the four stages' thrust and gravity (LinCoef)
 //   controller      cascaded position PD -> attitude P -> normalised rate P ->
 //                   G^-1 -> rotor clamp (the paper's inner body-rate loop,
 //                   Sec. III-B, completed as documented in quadsim.h).  The
@@ -98,18 +101,67 @@ struct StepH {
 
 __device__ __forceinline__ float coef(int i, float a, float aq) { return (i >= QW && i <= QZ) ? aq : a; }
 
-// Exact RK4 coefficients of Omega' = (u - Omega)/tau: stage k sees
-// Omega + c_k (u - Omega) (c_1 = 0), and the step ends at Omega + c5 (u - Omega).
-struct LagCoef {
+// Correctly rounded FP32 operations, one rounding each, the same on the host
+// and the device (the device would otherwise contract a * b + c into an FMA):
+// coefficients computed with them agree bit for bit wherever they are made.
+__host__ __device__ __forceinline__ float rmul(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+__host__ __device__ __forceinline__ float radd(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+__host__ __device__ __forceinline__ float rsub(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fsub_rn(a, b);
+#else
+  return a - b;
+#endif
+}
+
+// Exact RK4 weights of the step's linear parts, per group and step size.
+// Rotor lag Omega' = (u - Omega)/tau: stage k sees Omega + c_k (u - Omega)
+// (c_1 = 0), and the step ends at Omega + c5 (u - Omega).
+// Drag: v' = f_k - a v with a = c_d / m and f_k the stage's thrust and
+// gravity, which do not depend on v, so RK4's stage velocities and sums reduce
+// to v_new = v + (am1 v + b1 f1 + b2 f2 + b3 f3 + b4 f4) and
+// p_new = p + (g v + d1 f1 + d2 f2 + d3 f3), with z = a h:
+//   am1 = -z + z^2/2 - z^3/6 + z^4/24   (RK4's e^-z - 1)
+//   b = h/6 (1 - z + z^2/2 - z^3/4, 2 - z + z^2/2, 2 - z, 1)
+//   g = h/6 (6 - 3z + z^2 - z^3/4),  d = h^2/6 (1 - z/2 + z^2/4, 1 - z/2, 1)
+// the same map as the four stages, in fewer operations.  One-group launches
+// take them from the kernel's parameters (computed on the host), so that the
+// step's multiply-adds read them from the constant bank, not registers.
+struct LinCoef {
   float c2, c3, c4, c5;
+  float am1, b1, b2, b3, b4;
+  float g, d1, d2, d3;
 };
 
-__device__ __forceinline__ LagCoef lag_coef(float inv_tau, const StepH& H) {
-  LagCoef L;
-  L.c2 = H.h2 * inv_tau;
-  L.c3 = L.c2 * (1.f - L.c2);
-  L.c4 = H.h * inv_tau * (1.f - L.c3);
-  L.c5 = H.h6 * inv_tau * ((3.f - 2.f * L.c2) + (3.f - 2.f * L.c3 - L.c4));
+__host__ __device__ __forceinline__ LinCoef lin_coef(float inv_tau, float cd_m, const StepH& H) {
+  LinCoef L;
+  L.c2 = rmul(H.h2, inv_tau);
+  L.c3 = rmul(L.c2, rsub(1.f, L.c2));
+  L.c4 = rmul(rmul(H.h, inv_tau), rsub(1.f, L.c3));
+  L.c5 = rmul(rmul(H.h6, inv_tau), radd(rsub(3.f, rmul(2.f, L.c2)), rsub(rsub(3.f, rmul(2.f, L.c3)), L.c4)));
+  const float z = rmul(H.h, cd_m);
+  L.am1 = rmul(-z, rsub(1.f, rmul(z, rsub(0.5f, rmul(z, rsub(1.f / 6.f, rmul(z, 1.f / 24.f)))))));
+  L.b1 = rmul(H.h6, rsub(1.f, rmul(z, rsub(1.f, rmul(z, rsub(0.5f, rmul(z, 0.25f)))))));
+  L.b2 = rmul(H.h6, rsub(2.f, rmul(z, rsub(1.f, rmul(z, 0.5f)))));
+  L.b3 = rmul(H.h6, rsub(2.f, z));
+  L.b4 = H.h6;
+  L.g = rmul(H.h6, rsub(6.f, rmul(z, rsub(3.f, rmul(z, rsub(1.f, rmul(z, 0.25f)))))));
+  const float hh6 = rmul(H.h, H.h6);
+  L.d1 = rmul(hh6, rsub(1.f, rmul(z, rsub(0.5f, rmul(z, 0.25f)))));
+  L.d2 = rmul(hh6, rsub(1.f, rmul(z, 0.5f)));
+  L.d3 = hh6;
   return L;
 }
 
@@ -203,6 +255,40 @@ __device__ __forceinline__ void rb_derivative(const DevGroup& P, const float* y,
   d[WX] = P.gx * (wy * wz) + tx;
   d[WX + 1] = P.gy * (wz * wx) + ty;
   d[WX + 2] = P.gz * (wx * wy) + tz;
+}
+
+// The same derivative at an RK4 stage, for the forward step: the rotation's
+// components (2 q' and omega') and the velocity's forcing f = thrust along body
+// z over m plus gravity, without the drag, which lin_coef's weights carry.
+// Wherever two products meet one sum the multiply-add is written out (fmaf,
+// __fmul_rn), so that each kernel that steps agents computes the same bits: the
+// checkpoints of one kernel and the states another recomputes from them must
+// agree, and a compiler free to fuse either product could round differently
+// in different kernels.
+__device__ __forceinline__ void rb_stage(const DevGroup& P, const float q[4], const float w[3], const float Om[4],
+                                         float f[3], float dq[4], float dw[3]) {
+  // s_i = Omega_i^2 enter only as sums and differences of pairs, each one
+  // multiply-add: s1 +- s2 = fma(Om1, Om1, +-s2), s3 +- s4 likewise
+  const float s2 = __fmul_rn(Om[1], Om[1]), s4 = __fmul_rn(Om[3], Om[3]);
+  const float s12 = fmaf(Om[0], Om[0], s2), d12 = fmaf(Om[0], Om[0], -s2);
+  const float s34 = fmaf(Om[2], Om[2], s4), d34 = fmaf(Om[2], Om[2], -s4);
+  const float T2 = __fmul_rn(P.T2c, __fadd_rn(s12, s34));
+  const float tx = __fmul_rn(P.txc, __fsub_rn(d12, d34));
+  const float ty = __fmul_rn(P.tyc, __fsub_rn(s34, s12));
+  const float tz = __fmul_rn(P.tzc, __fadd_rn(d12, d34));
+  const float bx = fmaf(q[1], q[3], __fmul_rn(q[0], q[2]));
+  const float by = fmaf(q[2], q[3], -__fmul_rn(q[0], q[1]));
+  const float bxy = fmaf(q[1], q[1], __fmul_rn(q[2], q[2]));
+  f[0] = __fmul_rn(T2, bx);
+  f[1] = __fmul_rn(T2, by);
+  f[2] = fmaf(-T2, bxy, fmaf(0.5f, T2, -P.g));
+  dq[0] = fmaf(-q[3], w[2], fmaf(-q[2], w[1], -__fmul_rn(q[1], w[0])));
+  dq[1] = fmaf(-q[3], w[1], fmaf(q[2], w[2], __fmul_rn(q[0], w[0])));
+  dq[2] = fmaf(-q[1], w[2], fmaf(q[3], w[0], __fmul_rn(q[0], w[1])));
+  dq[3] = fmaf(-q[2], w[0], fmaf(q[1], w[1], __fmul_rn(q[0], w[2])));
+  dw[0] = fmaf(P.gx, __fmul_rn(w[1], w[2]), tx);
+  dw[1] = fmaf(P.gy, __fmul_rn(w[2], w[0]), ty);
+  dw[2] = fmaf(P.gz, __fmul_rn(w[0], w[1]), tz);
 }
 
 // ---------------------------------------------------------- the controller --
@@ -305,52 +391,70 @@ __device__ __forceinline__ void controller(const DevGroup& P, const float* x, co
 }
 
 // ------------------------------------------------------------------ RK4 --
-// RK4 with the first stage's derivative k (rb_derivative at x) already known.
-__device__ __forceinline__ void rk4_k1(const DevGroup& P, St& x, const float u[4], const StepH& H, const LagCoef& L,
-                                       float k[NRB]) {
-  float dOm[4], Om[4];
+// One classical RK4 step with the rotor command u held, from the first
+// stage's rb_stage values at x (f1, dq1, dw1).  The rotation and the rotor
+// lag go through the four stages; the translation takes lin_coef's weights.
+// Each update is one product and one sum, written as the multiply-add it is.
+__device__ __forceinline__ void rk4_from(const DevGroup& P, St& x, const float u[4], const StepH& H, const LinCoef& L,
+                                         const float f1[3], const float dq1[4], const float dw1[3]) {
+  float dOm[4], Om[4], q[4], w[3], aq[4], aw[3], f2[3], f3[3], f4[3], dq[4], dw[3];
 #pragma unroll
   for (int i = 0; i < 4; ++i) dOm[i] = u[i] - x.a[OM + i];
-  float y[NRB], acc[NRB];
 #pragma unroll
-  for (int i = 0; i < NRB; ++i) { acc[i] = k[i]; y[i] = x.a[i] + coef(i, H.h2, H.h2q) * k[i]; }
+  for (int i = 0; i < 4; ++i) { aq[i] = dq1[i]; q[i] = fmaf(H.h2q, dq1[i], x.a[QW + i]); }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) Om[i] = x.a[OM + i] + L.c2 * dOm[i];
-  rb_derivative(P, y, Om, k);
+  for (int i = 0; i < 3; ++i) { aw[i] = dw1[i]; w[i] = fmaf(H.h2, dw1[i], x.a[WX + i]); }
 #pragma unroll
-  for (int i = 0; i < NRB; ++i) { acc[i] += 2.f * k[i]; y[i] = x.a[i] + coef(i, H.h2, H.h2q) * k[i]; }
+  for (int i = 0; i < 4; ++i) Om[i] = fmaf(L.c2, dOm[i], x.a[OM + i]);
+  rb_stage(P, q, w, Om, f2, dq, dw);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) Om[i] = x.a[OM + i] + L.c3 * dOm[i];
-  rb_derivative(P, y, Om, k);
+  for (int i = 0; i < 4; ++i) { aq[i] = fmaf(2.f, dq[i], aq[i]); q[i] = fmaf(H.h2q, dq[i], x.a[QW + i]); }
 #pragma unroll
-  for (int i = 0; i < NRB; ++i) { acc[i] += 2.f * k[i]; y[i] = x.a[i] + coef(i, H.h, H.hq) * k[i]; }
+  for (int i = 0; i < 3; ++i) { aw[i] = fmaf(2.f, dw[i], aw[i]); w[i] = fmaf(H.h2, dw[i], x.a[WX + i]); }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) Om[i] = x.a[OM + i] + L.c4 * dOm[i];
-  rb_derivative(P, y, Om, k);
+  for (int i = 0; i < 4; ++i) Om[i] = fmaf(L.c3, dOm[i], x.a[OM + i]);
+  rb_stage(P, q, w, Om, f3, dq, dw);
 #pragma unroll
-  for (int i = 0; i < NRB; ++i) { acc[i] += k[i]; x.a[i] = x.a[i] + coef(i, H.h6, H.h6q) * acc[i]; }
+  for (int i = 0; i < 4; ++i) { aq[i] = fmaf(2.f, dq[i], aq[i]); q[i] = fmaf(H.hq, dq[i], x.a[QW + i]); }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) x.a[OM + i] = x.a[OM + i] + L.c5 * dOm[i];
+  for (int i = 0; i < 3; ++i) { aw[i] = fmaf(2.f, dw[i], aw[i]); w[i] = fmaf(H.h, dw[i], x.a[WX + i]); }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) Om[i] = fmaf(L.c4, dOm[i], x.a[OM + i]);
+  rb_stage(P, q, w, Om, f4, dq, dw);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) x.a[QW + i] = fmaf(H.h6q, aq[i] + dq[i], x.a[QW + i]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) x.a[WX + i] = fmaf(H.h6, aw[i] + dw[i], x.a[WX + i]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) x.a[OM + i] = fmaf(L.c5, dOm[i], x.a[OM + i]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float v = x.a[VX + i];
+    const float dp = fmaf(L.g, v, fmaf(L.d1, f1[i], fmaf(L.d2, f2[i], __fmul_rn(L.d3, f3[i]))));
+    const float dv = fmaf(L.am1, v, fmaf(L.b1, f1[i], fmaf(L.b2, f2[i], fmaf(L.b3, f3[i], __fmul_rn(L.b4, f4[i])))));
+    x.a[PX + i] = __fadd_rn(x.a[PX + i], dp);
+    x.a[VX + i] = __fadd_rn(v, dv);
+  }
 }
 
-__device__ __forceinline__ void rk4(const DevGroup& P, St& x, const float u[4], const StepH& H, const LagCoef& L) {
-  float k[NRB];
-  rb_derivative(P, x.a, x.a + OM, k);
-  rk4_k1(P, x, u, H, L, k);
+__device__ __forceinline__ void rk4(const DevGroup& P, St& x, const float u[4], const StepH& H, const LinCoef& L) {
+  float f[3], dq[4], dw[3];
+  rb_stage(P, x.a + QW, x.a + WX, x.a + OM, f, dq, dw);
+  rk4_from(P, x, u, H, L, f, dq, dw);
 }
 
 template <int MODE>
 __device__ __forceinline__ void step(const DevGroup& P, St& x, const float4 c, const Hd& hd, const StepH& H,
-                                     const LagCoef& L) {
-  float u[4];
+                                     const LinCoef& L) {
+  // the first RK4 stage at x before the controller: the PID rate loop's
+  // derivative term takes its omega', and both loops then run the same code
+  float u[4], f[3], dq[4], dw[3];
+  rb_stage(P, x.a + QW, x.a + WX, x.a + OM, f, dq, dw);
   if (MODE == 2) {
-    // omega' at the step start is the first RK4 stage's; the controller's
-    // derivative term takes it, then RK4 goes on from it
-    float k[NRB], e[3];
-    rb_derivative(P, x.a, x.a + OM, k);
+    float e[3];
     Ctl C;
-    controller_fwd<true>(P, x.a, c, hd, C, u, k + WX, e);
-    rk4_k1(P, x, u, H, L, k);
+    controller_fwd<true>(P, x.a, c, hd, C, u, dw, e);
+    rk4_from(P, x, u, H, L, f, dq, dw);
 #pragma unroll
     for (int i = 0; i < 3; ++i) x.a[XI + i] = clampf(x.a[XI + i] + H.h * e[i], -P.xim[i], P.xim[i]);
     return;
@@ -360,7 +464,7 @@ __device__ __forceinline__ void step(const DevGroup& P, St& x, const float4 c, c
   } else {
     u[0] = c.x; u[1] = c.y; u[2] = c.z; u[3] = c.w;
   }
-  rk4(P, x, u, H, L);
+  rk4_from(P, x, u, H, L, f, dq, dw);
 }
 
 }  // namespace qs

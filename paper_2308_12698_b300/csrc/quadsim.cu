@@ -315,12 +315,13 @@ size_t adj_smem_scratch_bytes(const sim_s* h, int C) {
 
 bool adj_smem_scratch(const sim_s* h, int C) { return adj_smem_scratch_bytes(h, C) <= kSmemScratchMax; }
 
-// Dynamic shared memory of one adjoint block: the group table and the
-// per-warp accumulators, then (16-byte aligned) the segment scratch with the
+// Dynamic shared memory of one adjoint block: the group table, the groups'
+// RK4 weights and the per-warp accumulators, then (16-byte aligned) the segment scratch with the
 // checkpoint prefetch slots when they fit, else the prefetch slots alone
 // (for the step-start states read back from the global scratch).
 size_t adj_smem(const sim_s* h, int C) {
-  size_t b = sizeof(DevGroup) * h->n_groups + (size_t)(h->block_adj / 32) * h->n_groups * NTH * sizeof(float);
+  size_t b = (sizeof(DevGroup) + sizeof(LinCoef)) * h->n_groups +
+             (size_t)(h->block_adj / 32) * h->n_groups * NTH * sizeof(float);
   b = (b + 15) & ~(size_t)15;
   return b + (adj_smem_scratch(h, C) ? adj_smem_scratch_bytes(h, C) : 2 * 5 * sizeof(float4) * h->block_adj);
 }
@@ -508,6 +509,7 @@ int launch_ranged(sim_s* h, StepArgs A, cudaStream_t st, int64_t first, int64_t 
     const int64_t b = ordered ? off[cb] : std::min(h->g_end[g], first + count);
     if (b <= a) continue;
     T.g[r] = h->host_groups[g];
+    T.coef[r] = lin_coef(h->host_groups[g].inv_tau, h->host_groups[g].cd_m, A.H);
     T.start[r] = a;
     T.end[r] = b;
     T.first_block[r] = (int)blocks;
@@ -562,6 +564,7 @@ int launch_step(sim_s* h, float* d_state, const float* d_cmd, StepH H, int K, cu
   A.H = H;
   A.groups = h->d_groups;
   A.order = nullptr;
+  A.coef = lin_coef(h->host_group0.inv_tau, h->host_group0.cd_m, H);
   const bool plain = plain_path(h, K);
   const RangeMode rm = plain ? kPersistent : range_mode(h, K, first, count);
   if (rm != kPersistent) return launch_ranged(h, A, st, first, count, rm);
@@ -999,6 +1002,7 @@ int sim_rollout_forward(sim_handle_t h, const float* d_state0, const float* d_cm
   A.H = make_h(dt);
   A.groups = h->d_groups;
   live_visit(h, &A.order, &A.count);
+  A.coef = lin_coef(h->host_group0.inv_tau, h->host_group0.cd_m, A.H);
   const size_t smem = group_smem(h);
   const int grid = fwd_grid(h, smem, h->n);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -27,6 +27,7 @@ struct StepArgs {
   StepH H;
   const DevGroup* groups;  // device table (several groups)
   const uint32_t* order;   // range_kernel<..., ORDER>: agent at each group-sorted position
+  LinCoef coef;            // one group: its RK4 weights of the linear parts (lin_coef, on the host)
 };
 
 // Asynchronous global -> shared copies (cp.async, sm_80 and later), each
@@ -110,7 +111,7 @@ __device__ __forceinline__ void plain_loop(const StepArgs& A, const DevGroup& P0
   float4* const slot = smem + threadIdx.x;  // [2 buffers][kPlainSlotF4][bd]
   const int64_t stride = (int64_t)gridDim.x * bd;
   const int64_t end = A.first + A.count;
-  const LagCoef L = lag_coef(P0.inv_tau, A.H);
+  const LinCoef& L = A.coef;
   int64_t i = A.first + first_agent();
   if (i < end) fetch_agent(slot, bd, A, i);
   for (int b = 0; i < end; i += stride, b ^= 1) {
@@ -173,10 +174,10 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 1) step_kernel(StepArgs A, co
       for (int k = 0; k < K; ++k) vehicle_step(P, x, c, A.H);
     } else if (HETERO) {
       const DevGroup P = sg[A.gid[i]];
-      const LagCoef L = lag_coef(P.inv_tau, A.H);
+      const LinCoef L = lin_coef(P.inv_tau, P.cd_m, A.H);
       for (int k = 0; k < K; ++k) step<MODE>(P, x, c, hd, A.H, L);
     } else {
-      const LagCoef L = lag_coef(P0.inv_tau, A.H);
+      const LinCoef& L = A.coef;
 #pragma unroll 2
       for (int k = 0; k < K; ++k) step<MODE>(P0, x, c, hd, A.H, L);  // unrolled: +0.5-1 %
     }
@@ -199,6 +200,7 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 1) step_kernel(StepArgs A, co
 // step_kernel's heterogeneous form).
 struct RangeTable {
   DevGroup g[32];          // the range's group's constants
+  LinCoef coef[32];        // and its RK4 weights of the linear parts (lin_coef, on the host)
   int64_t start[32];       // first agent of the range
   int64_t end[32];         // one past its last agent
   int first_block[33];     // block at which each range starts; [n_ranges] = the grid
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(256) range_kernel(StepArgs A, const __grid_con
   if (MULTI && P.vt != (float)TYPE_QUAD) {
     for (int k = 0; k < A.K; ++k) vehicle_step(P, x, c, A.H);
   } else {
-    const LagCoef L = lag_coef(P.inv_tau, A.H);
+    const LinCoef& L = T.coef[r];
 #pragma unroll 2
     for (int k = 0; k < A.K; ++k) step<MODE>(P, x, c, hd, A.H, L);
   }
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(256) refreeze_kernel(StepArgs A) {
     const DevGroup& P = A.groups[A.n_groups > 1 ? A.gid[i] : 0];
     const float4 c = A.cmd[i];
     const Hd hd = heading(MODE != 0 ? c.w : 0.f);
-    const LagCoef L = lag_coef(P.inv_tau, A.H);
+    const LinCoef L = lin_coef(P.inv_tau, P.cd_m, A.H);
     St x;
     load_state<NS>(A.state, A.n, i, x);
     for (int k = 0; k < A.K; ++k) {
