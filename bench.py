@@ -1142,6 +1142,10 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     big = sweep[-1]["plain"]
     out["plain"]["hbm_case"] = {"n_agents": sweep[-1]["n_agents"], "value": big["value"],
                                 "achieved_GBs": big["hbm_gbs_equiv"], "frac": big.get("hbm_frac")}
+    pl = profiled("step_kernel<1,false,plain>", f"closed-loop-{sweep[-1]['n_agents']}-K1")
+    if pl:  # DRAM bytes of one launch from the committed ncu summary, against the algorithmic bytes
+        out["plain"]["hbm_case"].update(traffic=pl["bytes_per_launch"], profile=pl["profile"],
+                                        algorithmic_bytes=BYTES_PER_AGENT_STEP_PLAIN * sweep[-1]["n_agents"])
 
     # the paper's own measurement point: 1000 quadrotors, per-round time (context only)
     pw = W.scale_sweep(1000, nsteps=T_STEPS)

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) ckpt_kernel(CkptArgs A, const DevGroup P0
     const float4 c = A.cmd[i];
     const Hd hd = heading(MODE != 0 ? c.w : 0.f);
     const DevGroup P = HETERO ? sg[A.gid[i]] : P0;
-    const LinCoef L = HETERO ? lin_coef(P.inv_tau, P.cd_m, A.H) : A.coef;
+    const LinCoef L = HETERO ? lin_coef(P, A.H) : A.coef;
     float rc = 0.f;
     float* dst = A.ckpt;  // checkpoint s + 1 follows checkpoint s at cstride floats
     if (A.C == 1) {
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs A) {
   const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int e = threadIdx.x; e < nw * A.n_groups * NTH; e += blockDim.x) wacc[e] = 0.f;
   load_groups<true>(sg, A.groups, A.n_groups);
-  for (int g = threadIdx.x; g < A.n_groups; g += blockDim.x) scoef[g] = lin_coef(sg[g].inv_tau, sg[g].cd_m, A.H);
+  for (int g = threadIdx.x; g < A.n_groups; g += blockDim.x) scoef[g] = lin_coef(sg[g], A.H);
   __syncthreads();
   float* sscr = reinterpret_cast<float*>(
       smem4 + (sizeof(DevGroup) * A.n_groups + sizeof(LinCoef) * A.n_groups + 4 * nw * A.n_groups * NTH + 15) / 16);

@@ -95,12 +95,13 @@ template <bool PID = false>
 __device__ __forceinline__ void controller_vjp(const DevGroup& P, const float* x, const Hd& hd, const Ctl& C,
                                                const float ub[4], float* xb, float tb[NTH],
                                                const float* eb = nullptr, float* wdb = nullptr) {
-  // sqrt(clamp(S)): gradient passes on 0 < S <= om2max (sqrt'(0) taken as 0)
+  // u = omega_max sqrt(clamp(S, 0, 1)) (S in units of omega_max^2): gradient
+  // passes on 0 < S <= 1 (sqrt'(0) taken as 0)
   float Sb[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const float s = C.S[i];
-    Sb[i] = (s > 0.f && s <= P.om2max) ? ub[i] * 0.5f * rsqrtf(s) : 0.f;
+    Sb[i] = (s > 0.f && s <= 1.f) ? ub[i] * (0.5f * P.omax) * rsqrtf(s) : 0.f;
   }
   const float f0b = (Sb[0] + Sb[1]) + (Sb[2] + Sb[3]);
   float fb[3];
@@ -160,8 +161,8 @@ __device__ __forceinline__ void controller_vjp(const DevGroup& P, const float* x
   const float N2b = M2b + 0.5f * Nb * C.rN;
   Bb += 2.f * C.B * N2b;
   Fzb += 2.f * C.F[2] * N2b;
-  // (A, B) = heading rotation of (F_x, F_y); f0 = f0c (F . b3), f0c = m / (4 kt)
-  const float fcb = f0b * P.f0c;
+  // (A, B) = heading rotation of (F_x, F_y); f0 = f0c (F . b3) / 2, f0c = m / (2 kt omega_max^2)
+  const float fcb = 0.5f * f0b * P.f0c;
   tb[TH_M] += f0b * C.fc * P.mix0;
   float Fb[3];
   Fb[0] = hd.c * Ab - hd.s * Bb + fcb * C.b3[0];
@@ -195,29 +196,32 @@ __device__ __forceinline__ void controller_vjp(const DevGroup& P, const float* x
 template <int MODE>
 __device__ __forceinline__ void step_vjp(const DevGroup& P, const St& x, const float4 c, const Hd& hd,
                                          const StepH& H, const LinCoef& L, St& lam, float tb[NTH], float dc[NDC]) {
-  float u[4];
+  float dOm[4], bq[3];
   float wdot[3], e[3];  // PID: omega' at x and the rate error
-  if (MODE == 2) {
-    // omega' at x (the first RK4 stage's) feeds the derivative term
-    float k0[NRB];
-    rb_derivative(P, x.a, x.a + OM, k0);
-    wdot[0] = k0[WX]; wdot[1] = k0[WX + 1]; wdot[2] = k0[WX + 2];
-    Ctl C;
-    controller_fwd<true>(P, x.a, c, hd, C, u, wdot, e);
-  } else if (MODE == 1) {
-    controller(P, x.a, c, hd, u);
+  thrust_axis(x.a + QW, bq);
+  if (MODE == 0) {
+    dOm[0] = c.x - x.a[OM]; dOm[1] = c.y - x.a[OM + 1]; dOm[2] = c.z - x.a[OM + 2]; dOm[3] = c.w - x.a[OM + 3];
   } else {
-    u[0] = c.x; u[1] = c.y; u[2] = c.z; u[3] = c.w;
+    float r[4];
+    if (MODE == 2) {
+      // omega' at x (the first RK4 stage's) feeds the derivative term
+      float k0[NRB];
+      rb_derivative(P, x.a, x.a + OM, k0);
+      wdot[0] = k0[WX]; wdot[1] = k0[WX + 1]; wdot[2] = k0[WX + 2];
+      Ctl C;
+      controller_fwd<true>(P, x.a, c, hd, bq, C, r, wdot, e);
+    } else {
+      controller(P, x.a, c, hd, bq, r);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) dOm[i] = fmaf(P.omax, r[i], -x.a[OM + i]);  // u = omega_max r
   }
   // rotor lag: stage k sees Omega + c_k (u - Omega) (c_1 = 0); the step ends
   // at Omega + c5 (u - Omega).  Stage rotor speeds are recomputed where used
   // and each stage's cotangent is folded into ub / xb at once.
-  float dOm[4], Om[4];
+  float Om[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    dOm[i] = u[i] - x.a[OM + i];
-    Om[i] = x.a[OM + i] + L.c2 * dOm[i];
-  }
+  for (int i = 0; i < 4; ++i) Om[i] = x.a[OM + i] + L.c2 * dOm[i];
   float k[NRB], y2[NRB], y3[NRB], y4[NRB];
   rb_derivative(P, x.a, x.a + OM, k);
 #pragma unroll
@@ -294,8 +298,8 @@ __device__ __forceinline__ void step_vjp(const DevGroup& P, const St& x, const f
       eb[i] = pass ? H.h * lam.a[XI + i] : 0.f;
     }
     Ctl C;
-    float u2[4], e2[3];
-    controller_fwd<true>(P, x.a, c, hd, C, u2, wdot, e2);
+    float r2[4], e2[3];
+    controller_fwd<true>(P, x.a, c, hd, bq, C, r2, wdot, e2);
     controller_vjp<true>(P, x.a, hd, C, ub, xb, tb, eb, wdb);
     // omega' = rows WX.. of Eq. (qd4) at (x, Omega)
 #pragma unroll
@@ -308,8 +312,8 @@ __device__ __forceinline__ void step_vjp(const DevGroup& P, const St& x, const f
     for (int i = 0; i < 4; ++i) xb[OM + i] += Ob[i];
   } else if (MODE == 1) {
     Ctl C;
-    float u2[4];
-    controller_fwd(P, x.a, c, hd, C, u2);
+    float r2[4];
+    controller_fwd(P, x.a, c, hd, bq, C, r2);
     controller_vjp(P, x.a, hd, C, ub, xb, tb);
   }
 #pragma unroll

@@ -8,9 +8,11 @@
 //                   derivative evaluations -- the same RK4 map, fewer operations
 //   drag            linear in v with a forcing that does not depend on v: the
 //                   translation's RK4 update is likewise a fixed weighting of
-//                   v and the four stages' thrust and gravity (LinCoef)
+//                   v and the four stages' thrust S b (LinCoef, whose weights
+//                   also carry the thrust constant and gravity)
 //   controller      cascaded position PD -> attitude P -> normalised rate P ->
-//                   G^-1 -> rotor clamp (the paper's inner body-rate loop,
+//                   G^-1 -> rotor clamp, the mixer in units of omega_max^2 so
+//                   that the clamp is a saturating add (the paper's inner body-rate loop,
 //                   Sec. III-B, completed as documented in quadsim.h).  The
 //                   desired attitude (body z along the demanded force, body y
 //                   normal to it and to the heading) is the rotation
@@ -47,16 +49,18 @@ enum { TH_KP = 0, TH_KD = 3, TH_KATT = 6, TH_KRATE = 9, TH_M = 12, TH_J = 13, NT
 struct __align__(16) DevGroup {
   // forward: dynamics
   float T2c, cd_m, g, inv_tau;  // 2 kt / m, c_d / m, gravity, 1 / tau_m
-  float txc, tyc, tzc, om2max;  // kt L sin(a) / Jx, kt L cos(a) / Jy, kq / Jz, omega_max^2
+  float txc, tyc, tzc, omax;    // kt L sin(a) / Jx, kt L cos(a) / Jy, kq / Jz, omega_max
   float gx, gy, gz, m;          // (Jy - Jz)/Jx, (Jz - Jx)/Jy, (Jx - Jy)/Jz, mass
-  // forward: controller
+  // forward: controller.  The mixer works in units of omega_max^2 (its
+  // constants below are divided by omega_max^2), so the rotor clamp
+  // [0, omega_max^2] is a saturation to [0, 1].
   float kp[3], a_max;
-  float kd[3], f0c;             // f0c = m / (4 kt): collective thrust demand -> Omega^2 per rotor
-  float qa[3], pad0;            // mix_i krate_i taumax_i 2 katt_i: error-quaternion component -> Omega^2
-  float wa[3], pad1;            // mix_i krate_i taumax_i: body rate -> Omega^2
+  float kd[3], f0c;             // f0c = m / (2 kt omega_max^2): F . R(q) e3 / 2 -> Omega^2 per rotor
+  float qa[3], az_lo;           // mix_i krate_i taumax_i 2 katt_i: error-quaternion component -> Omega^2; g - a_max
+  float wa[3], az_hi;           // mix_i krate_i taumax_i: body rate -> Omega^2; g + a_max
   // adjoint
   float inv_m, Jx, Jy, Jz;
-  float iJx, iJy, iJz, mix0;    // mix0 = 1 / (4 kt)
+  float iJx, iJy, iJz, mix0;    // mix0 = 1 / (4 kt omega_max^2)
   float krate[3], pad2;
   float katt2[3], pad3;         // 2 katt
   float mt[3], pad4;            // mix_i taumax_i  (mix = 1/(4 kt L sin a), 1/(4 kt L cos a), 1/(4 kq))
@@ -129,10 +133,13 @@ __host__ __device__ __forceinline__ float rsub(float a, float b) {
 // Exact RK4 weights of the step's linear parts, per group and step size.
 // Rotor lag Omega' = (u - Omega)/tau: stage k sees Omega + c_k (u - Omega)
 // (c_1 = 0), and the step ends at Omega + c5 (u - Omega).
-// Drag: v' = f_k - a v with a = c_d / m and f_k the stage's thrust and
-// gravity, which do not depend on v, so RK4's stage velocities and sums reduce
-// to v_new = v + (am1 v + b1 f1 + b2 f2 + b3 f3 + b4 f4) and
-// p_new = p + (g v + d1 f1 + d2 f2 + d3 f3), with z = a h:
+// Drag: v' = T2c f_k - g e3 - a v with a = c_d / m and f_k = S_k b_k the
+// stage's thrust (rb_stage), which does not depend on v, so RK4's stage
+// velocities and sums reduce to
+//   v_new = v + (am1 v + B1 f1 + B2 f2 + B3 f3 + B4 f4 + gb e3)
+//   p_new = p + (g v + D1 f1 + D2 f2 + D3 f3 + gd e3)
+// with B_k = T2c b_k, D_k = T2c d_k, gb = -g (b1 + b2 + b3 + b4),
+// gd = -g (d1 + d2 + d3) and, for z = a h,
 //   am1 = -z + z^2/2 - z^3/6 + z^4/24   (RK4's e^-z - 1)
 //   b = h/6 (1 - z + z^2/2 - z^3/4, 2 - z + z^2/2, 2 - z, 1)
 //   g = h/6 (6 - 3z + z^2 - z^3/4),  d = h^2/6 (1 - z/2 + z^2/4, 1 - z/2, 1)
@@ -141,27 +148,32 @@ __host__ __device__ __forceinline__ float rsub(float a, float b) {
 // step's multiply-adds read them from the constant bank, not registers.
 struct LinCoef {
   float c2, c3, c4, c5;
-  float am1, b1, b2, b3, b4;
-  float g, d1, d2, d3;
+  float am1, b1, b2, b3, b4;  // B_k: times T2c
+  float g, d1, d2, d3;        // D_k: times T2c
+  float gb, gd;               // gravity's share of the v and p updates (z only)
 };
 
-__host__ __device__ __forceinline__ LinCoef lin_coef(float inv_tau, float cd_m, const StepH& H) {
+__host__ __device__ __forceinline__ LinCoef lin_coef(const DevGroup& P, const StepH& H) {
   LinCoef L;
-  L.c2 = rmul(H.h2, inv_tau);
+  L.c2 = rmul(H.h2, P.inv_tau);
   L.c3 = rmul(L.c2, rsub(1.f, L.c2));
-  L.c4 = rmul(rmul(H.h, inv_tau), rsub(1.f, L.c3));
-  L.c5 = rmul(rmul(H.h6, inv_tau), radd(rsub(3.f, rmul(2.f, L.c2)), rsub(rsub(3.f, rmul(2.f, L.c3)), L.c4)));
-  const float z = rmul(H.h, cd_m);
+  L.c4 = rmul(rmul(H.h, P.inv_tau), rsub(1.f, L.c3));
+  L.c5 = rmul(rmul(H.h6, P.inv_tau), radd(rsub(3.f, rmul(2.f, L.c2)), rsub(rsub(3.f, rmul(2.f, L.c3)), L.c4)));
+  const float z = rmul(H.h, P.cd_m);
   L.am1 = rmul(-z, rsub(1.f, rmul(z, rsub(0.5f, rmul(z, rsub(1.f / 6.f, rmul(z, 1.f / 24.f)))))));
-  L.b1 = rmul(H.h6, rsub(1.f, rmul(z, rsub(1.f, rmul(z, rsub(0.5f, rmul(z, 0.25f)))))));
-  L.b2 = rmul(H.h6, rsub(2.f, rmul(z, rsub(1.f, rmul(z, 0.5f)))));
-  L.b3 = rmul(H.h6, rsub(2.f, z));
-  L.b4 = H.h6;
+  const float b1 = rmul(H.h6, rsub(1.f, rmul(z, rsub(1.f, rmul(z, rsub(0.5f, rmul(z, 0.25f)))))));
+  const float b2 = rmul(H.h6, rsub(2.f, rmul(z, rsub(1.f, rmul(z, 0.5f)))));
+  const float b3 = rmul(H.h6, rsub(2.f, z));
+  const float b4 = H.h6;
   L.g = rmul(H.h6, rsub(6.f, rmul(z, rsub(3.f, rmul(z, rsub(1.f, rmul(z, 0.25f)))))));
   const float hh6 = rmul(H.h, H.h6);
-  L.d1 = rmul(hh6, rsub(1.f, rmul(z, rsub(0.5f, rmul(z, 0.25f)))));
-  L.d2 = rmul(hh6, rsub(1.f, rmul(z, 0.5f)));
-  L.d3 = hh6;
+  const float d1 = rmul(hh6, rsub(1.f, rmul(z, rsub(0.5f, rmul(z, 0.25f)))));
+  const float d2 = rmul(hh6, rsub(1.f, rmul(z, 0.5f)));
+  const float d3 = hh6;
+  L.b1 = rmul(P.T2c, b1); L.b2 = rmul(P.T2c, b2); L.b3 = rmul(P.T2c, b3); L.b4 = rmul(P.T2c, b4);
+  L.d1 = rmul(P.T2c, d1); L.d2 = rmul(P.T2c, d2); L.d3 = rmul(P.T2c, d3);
+  L.gb = rmul(-P.g, radd(radd(radd(b1, b2), b3), b4));
+  L.gd = rmul(-P.g, radd(radd(d1, d2), d3));
   return L;
 }
 
@@ -257,31 +269,39 @@ __device__ __forceinline__ void rb_derivative(const DevGroup& P, const float* y,
   d[WX + 2] = P.gz * (wx * wy) + tz;
 }
 
+// Half the body z axis, b = R(q) e3 / 2 = (qx qz + w qy, qy qz - w qx,
+// 1/2 - qx^2 - qy^2): the thrust direction of Eq. (qd2), at each RK4 stage and
+// in the controller at the step start (the same bits: the step shares them).
+__device__ __forceinline__ void thrust_axis(const float q[4], float b[3]) {
+  b[0] = fmaf(q[1], q[3], __fmul_rn(q[0], q[2]));
+  b[1] = fmaf(q[2], q[3], -__fmul_rn(q[0], q[1]));
+  b[2] = fmaf(-q[1], q[1], fmaf(-q[2], q[2], 0.5f));
+}
+
 // The same derivative at an RK4 stage, for the forward step: the rotation's
-// components (2 q' and omega') and the velocity's forcing f = thrust along body
-// z over m plus gravity, without the drag, which lin_coef's weights carry.
+// components (2 q' and omega'), and the thrust as f = S b with S the sum of
+// the Omega_i^2 and b = thrust_axis(q) (also returned): v' = T2c f - g e3 -
+// cd_m v, whose constants lin_coef's weights carry.
 // Wherever two products meet one sum the multiply-add is written out (fmaf,
 // __fmul_rn), so that each kernel that steps agents computes the same bits: the
 // checkpoints of one kernel and the states another recomputes from them must
 // agree, and a compiler free to fuse either product could round differently
 // in different kernels.
 __device__ __forceinline__ void rb_stage(const DevGroup& P, const float q[4], const float w[3], const float Om[4],
-                                         float f[3], float dq[4], float dw[3]) {
+                                         float f[3], float dq[4], float dw[3], float b[3]) {
   // s_i = Omega_i^2 enter only as sums and differences of pairs, each one
   // multiply-add: s1 +- s2 = fma(Om1, Om1, +-s2), s3 +- s4 likewise
   const float s2 = __fmul_rn(Om[1], Om[1]), s4 = __fmul_rn(Om[3], Om[3]);
   const float s12 = fmaf(Om[0], Om[0], s2), d12 = fmaf(Om[0], Om[0], -s2);
   const float s34 = fmaf(Om[2], Om[2], s4), d34 = fmaf(Om[2], Om[2], -s4);
-  const float T2 = __fmul_rn(P.T2c, __fadd_rn(s12, s34));
+  const float S = __fadd_rn(s12, s34);
   const float tx = __fmul_rn(P.txc, __fsub_rn(d12, d34));
   const float ty = __fmul_rn(P.tyc, __fsub_rn(s34, s12));
   const float tz = __fmul_rn(P.tzc, __fadd_rn(d12, d34));
-  const float bx = fmaf(q[1], q[3], __fmul_rn(q[0], q[2]));
-  const float by = fmaf(q[2], q[3], -__fmul_rn(q[0], q[1]));
-  const float bxy = fmaf(q[1], q[1], __fmul_rn(q[2], q[2]));
-  f[0] = __fmul_rn(T2, bx);
-  f[1] = __fmul_rn(T2, by);
-  f[2] = fmaf(-T2, bxy, fmaf(0.5f, T2, -P.g));
+  thrust_axis(q, b);
+  f[0] = __fmul_rn(S, b[0]);
+  f[1] = __fmul_rn(S, b[1]);
+  f[2] = __fmul_rn(S, b[2]);
   dq[0] = fmaf(-q[3], w[2], fmaf(-q[2], w[1], -__fmul_rn(q[1], w[0])));
   dq[1] = fmaf(-q[3], w[1], fmaf(q[2], w[2], __fmul_rn(q[0], w[0])));
   dq[2] = fmaf(-q[1], w[2], fmaf(q[3], w[0], __fmul_rn(q[0], w[1])));
@@ -291,9 +311,22 @@ __device__ __forceinline__ void rb_stage(const DevGroup& P, const float q[4], co
   dw[2] = fmaf(P.gz, __fmul_rn(w[0], w[1]), tz);
 }
 
+// a + b and a - b saturated to [0, 1], NaN to 0 (PTX add.sat / sub.sat): the
+// mixer's last add and the rotor clamp in one instruction.
+__device__ __forceinline__ float add_sat(float a, float b) {
+  float r;
+  asm("add.rn.sat.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float sub_sat(float a, float b) {
+  float r;
+  asm("sub.rn.sat.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+
 // ---------------------------------------------------------- the controller --
 struct Ctl {
-  float e[3], a[3];
+  float e[3];
   bool pass[3];  // acceleration clamp passes the gradient
   float F[3];    // desired acceleration plus gravity (the desired force / m)
   float b3[3], fc;
@@ -307,31 +340,37 @@ struct Ctl {
   float E[4];    // conj(q) o Q
   float s;       // sign(E_w) / |Q|
   float qe[4];
-  float S[4];    // Omega^2 demanded by the mixer, before the clamp
+  float S[4];    // Omega^2 / omega_max^2 demanded by the mixer, before the clamp
 };
 
+// b: thrust_axis(q) at x (the first RK4 stage's).  r receives the rotor
+// commands as fractions of omega_max, sqrt(clamp(S, 0, 1)).
 // PID: also the integral and derivative terms of the rate loop (x holds xi at
 // XI..XI+2, wdot is omega' at x); e receives the rate error omega_des - omega.
 template <bool PID = false>
 __device__ __forceinline__ void controller_fwd(const DevGroup& P, const float* x, const float4 c, const Hd& hd,
-                                               Ctl& C, float u[4], const float* wdot = nullptr,
+                                               const float b[3], Ctl& C, float r[4], const float* wdot = nullptr,
                                                float* e = nullptr) {
   const float cc[3] = {c.x, c.y, c.z};
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 2; ++i) {
     C.e[i] = cc[i] - x[PX + i];
     const float ar = P.kp[i] * C.e[i] - P.kd[i] * x[VX + i];
     C.pass[i] = (ar >= -P.a_max) && (ar <= P.a_max);
-    C.a[i] = clampf(ar, -P.a_max, P.a_max);
+    C.F[i] = clampf(ar, -P.a_max, P.a_max);
   }
-  C.F[0] = C.a[0];
-  C.F[1] = C.a[1];
-  C.F[2] = C.a[2] + P.g;
+  // z: gravity added before the clamp, whose bounds are then g -+ a_max
+  C.e[2] = cc[2] - x[PX + 2];
+  const float az = fmaf(P.kp[2], C.e[2], fmaf(-P.kd[2], x[VX + 2], P.g));
+  C.pass[2] = (az >= P.az_lo) && (az <= P.az_hi);
+  C.F[2] = clampf(az, P.az_lo, P.az_hi);
   const float w = x[QW], qx = x[QX], qy = x[QY], qz = x[QZ];
-  C.b3[0] = 2.f * (qx * qz + w * qy);
-  C.b3[1] = 2.f * (qy * qz - w * qx);
-  C.b3[2] = 1.f - 2.f * (qx * qx + qy * qy);
-  C.fc = C.F[0] * C.b3[0] + C.F[1] * C.b3[1] + C.F[2] * C.b3[2];
+  // collective thrust demand F . R(q) e3 = 2 (F . b)
+  C.b3[0] = 2.f * b[0];
+  C.b3[1] = 2.f * b[1];
+  C.b3[2] = 2.f * b[2];
+  const float fh = fmaf(C.F[0], b[0], fmaf(C.F[1], b[1], __fmul_rn(C.F[2], b[2])));
+  C.fc = 2.f * fh;
   // R_des = Rz(psi) Rx(phi) Ry(theta): in the heading frame the desired z axis is
   // (A, B, F_z) / |F| = (sin theta, -sin phi cos theta, cos phi cos theta)
   C.A = hd.c * C.F[0] + hd.s * C.F[1];
@@ -343,10 +382,11 @@ __device__ __forceinline__ void controller_fwd(const DevGroup& P, const float* x
   C.rM = rsqrt_sfu(M2);
   C.M = M2 * C.rM;
   // half angles as unnormalised (cos, sin) pairs: (N + F_z, -B) ~ (1 + cos phi, sin phi),
-  // or (-B, N - F_z) ~ (sin phi, 1 - cos phi) when F_z < 0; (M + N, A) for theta
+  // or (-B, N - F_z) ~ (sin phi, 1 - cos phi) when F_z < 0 (both N + |F_z|); (M + N, A) for theta
   C.up = C.F[2] >= 0.f;
-  C.X[0] = C.up ? C.N + C.F[2] : -C.B;
-  C.X[1] = C.up ? -C.B : C.N - C.F[2];
+  const float Xa = C.N + fabsf(C.F[2]);
+  C.X[0] = C.up ? Xa : -C.B;
+  C.X[1] = C.up ? -C.B : Xa;
   C.Y[0] = C.M + C.N;
   C.Y[1] = C.A;
   // q_d ~ q_z(psi) o q_x(phi) o q_y(theta)
@@ -364,7 +404,7 @@ __device__ __forceinline__ void controller_fwd(const DevGroup& P, const float* x
   const float rQ = rsqrt_sfu(dw * dw + dx * dx + dy * dy + dz * dz);
   C.s = copysignf(rQ, C.E[0]);  // sign fix folded into the normalisation
   C.qe[0] = C.s * C.E[0]; C.qe[1] = C.s * C.E[1]; C.qe[2] = C.s * C.E[2]; C.qe[3] = C.s * C.E[3];
-  const float f0 = P.f0c * C.fc;
+  const float f0 = P.f0c * fh;
   float f1 = P.qa[0] * C.qe[1] - P.wa[0] * x[WX];
   float f2 = P.qa[1] * C.qe[2] - P.wa[1] * x[WX + 1];
   float f3 = P.qa[2] * C.qe[3] - P.wa[2] * x[WX + 2];
@@ -376,51 +416,55 @@ __device__ __forceinline__ void controller_fwd(const DevGroup& P, const float* x
 #pragma unroll
     for (int i = 0; i < 3; ++i) e[i] = P.katt2[i] * C.qe[1 + i] - x[WX + i];
   }
-  C.S[0] = (f0 + f1) + (f3 - f2);
-  C.S[1] = (f0 - f1) - (f2 + f3);
-  C.S[2] = (f0 - f1) + (f2 + f3);
-  C.S[3] = (f0 + f1) + (f2 - f3);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) u[i] = sqrt_sfu(clampf(C.S[i], 0.f, P.om2max));
+  // G^-1: rotor i takes f0 + (+-f1) + (+-f2) + (+-f3); the last add saturates
+  const float a = f0 + f1, d = f0 - f1, g3 = f3 - f2, h3 = f2 + f3;
+  C.S[0] = a + g3;
+  C.S[1] = d - h3;
+  C.S[2] = d + h3;
+  C.S[3] = a - g3;
+  r[0] = sqrt_sfu(add_sat(a, g3));
+  r[1] = sqrt_sfu(sub_sat(d, h3));
+  r[2] = sqrt_sfu(add_sat(d, h3));
+  r[3] = sqrt_sfu(sub_sat(a, g3));
 }
 
 __device__ __forceinline__ void controller(const DevGroup& P, const float* x, const float4 c, const Hd& hd,
-                                           float u[4]) {
+                                           const float b[3], float r[4]) {
   Ctl C;
-  controller_fwd(P, x, c, hd, C, u);
+  controller_fwd(P, x, c, hd, b, C, r);
 }
 
 // ------------------------------------------------------------------ RK4 --
-// One classical RK4 step with the rotor command u held, from the first
-// stage's rb_stage values at x (f1, dq1, dw1).  The rotation and the rotor
-// lag go through the four stages; the translation takes lin_coef's weights.
-// Each update is one product and one sum, written as the multiply-add it is.
-__device__ __forceinline__ void rk4_from(const DevGroup& P, St& x, const float u[4], const StepH& H, const LinCoef& L,
-                                         const float f1[3], const float dq1[4], const float dw1[3]) {
-  float dOm[4], Om[4], q[4], w[3], aq[4], aw[3], f2[3], f3[3], f4[3], dq[4], dw[3];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) dOm[i] = u[i] - x.a[OM + i];
+// One classical RK4 step with the rotor command held, from the first stage's
+// rb_stage values at x (f1, dq1, dw1) and dOm = u - Omega.  The rotation and
+// the rotor lag go through the four stages; the translation takes lin_coef's
+// weights.  Each update is one product and one sum, written as the
+// multiply-add it is.
+__device__ __forceinline__ void rk4_from(const DevGroup& P, St& x, const float dOm[4], const StepH& H,
+                                         const LinCoef& L, const float f1[3], const float dq1[4],
+                                         const float dw1[3]) {
+  float Om[4], q[4], w[3], aq[4], aw[3], f2[3], f3[3], f4[3], dq[4], dw[3], b[3];
 #pragma unroll
   for (int i = 0; i < 4; ++i) { aq[i] = dq1[i]; q[i] = fmaf(H.h2q, dq1[i], x.a[QW + i]); }
 #pragma unroll
   for (int i = 0; i < 3; ++i) { aw[i] = dw1[i]; w[i] = fmaf(H.h2, dw1[i], x.a[WX + i]); }
 #pragma unroll
   for (int i = 0; i < 4; ++i) Om[i] = fmaf(L.c2, dOm[i], x.a[OM + i]);
-  rb_stage(P, q, w, Om, f2, dq, dw);
+  rb_stage(P, q, w, Om, f2, dq, dw, b);
 #pragma unroll
   for (int i = 0; i < 4; ++i) { aq[i] = fmaf(2.f, dq[i], aq[i]); q[i] = fmaf(H.h2q, dq[i], x.a[QW + i]); }
 #pragma unroll
   for (int i = 0; i < 3; ++i) { aw[i] = fmaf(2.f, dw[i], aw[i]); w[i] = fmaf(H.h2, dw[i], x.a[WX + i]); }
 #pragma unroll
   for (int i = 0; i < 4; ++i) Om[i] = fmaf(L.c3, dOm[i], x.a[OM + i]);
-  rb_stage(P, q, w, Om, f3, dq, dw);
+  rb_stage(P, q, w, Om, f3, dq, dw, b);
 #pragma unroll
   for (int i = 0; i < 4; ++i) { aq[i] = fmaf(2.f, dq[i], aq[i]); q[i] = fmaf(H.hq, dq[i], x.a[QW + i]); }
 #pragma unroll
   for (int i = 0; i < 3; ++i) { aw[i] = fmaf(2.f, dw[i], aw[i]); w[i] = fmaf(H.h, dw[i], x.a[WX + i]); }
 #pragma unroll
   for (int i = 0; i < 4; ++i) Om[i] = fmaf(L.c4, dOm[i], x.a[OM + i]);
-  rb_stage(P, q, w, Om, f4, dq, dw);
+  rb_stage(P, q, w, Om, f4, dq, dw, b);
 #pragma unroll
   for (int i = 0; i < 4; ++i) x.a[QW + i] = fmaf(H.h6q, aq[i] + dq[i], x.a[QW + i]);
 #pragma unroll
@@ -430,41 +474,38 @@ __device__ __forceinline__ void rk4_from(const DevGroup& P, St& x, const float u
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const float v = x.a[VX + i];
-    const float dp = fmaf(L.g, v, fmaf(L.d1, f1[i], fmaf(L.d2, f2[i], __fmul_rn(L.d3, f3[i]))));
-    const float dv = fmaf(L.am1, v, fmaf(L.b1, f1[i], fmaf(L.b2, f2[i], fmaf(L.b3, f3[i], __fmul_rn(L.b4, f4[i])))));
+    // gravity's share, a constant of the step, in the innermost term of z
+    const float p3 = i == 2 ? fmaf(L.d3, f3[i], L.gd) : __fmul_rn(L.d3, f3[i]);
+    const float v4 = i == 2 ? fmaf(L.b4, f4[i], L.gb) : __fmul_rn(L.b4, f4[i]);
+    const float dp = fmaf(L.g, v, fmaf(L.d1, f1[i], fmaf(L.d2, f2[i], p3)));
+    const float dv = fmaf(L.am1, v, fmaf(L.b1, f1[i], fmaf(L.b2, f2[i], fmaf(L.b3, f3[i], v4))));
     x.a[PX + i] = __fadd_rn(x.a[PX + i], dp);
     x.a[VX + i] = __fadd_rn(v, dv);
   }
 }
 
-__device__ __forceinline__ void rk4(const DevGroup& P, St& x, const float u[4], const StepH& H, const LinCoef& L) {
-  float f[3], dq[4], dw[3];
-  rb_stage(P, x.a + QW, x.a + WX, x.a + OM, f, dq, dw);
-  rk4_from(P, x, u, H, L, f, dq, dw);
-}
-
 template <int MODE>
 __device__ __forceinline__ void step(const DevGroup& P, St& x, const float4 c, const Hd& hd, const StepH& H,
                                      const LinCoef& L) {
-  // the first RK4 stage at x before the controller: the PID rate loop's
-  // derivative term takes its omega', and both loops then run the same code
-  float u[4], f[3], dq[4], dw[3];
-  rb_stage(P, x.a + QW, x.a + WX, x.a + OM, f, dq, dw);
-  if (MODE == 2) {
-    float e[3];
-    Ctl C;
-    controller_fwd<true>(P, x.a, c, hd, C, u, dw, e);
-    rk4_from(P, x, u, H, L, f, dq, dw);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) x.a[XI + i] = clampf(x.a[XI + i] + H.h * e[i], -P.xim[i], P.xim[i]);
+  // the first RK4 stage at x before the controller: the controller takes its
+  // thrust axis, and the PID rate loop's derivative term its omega'
+  float f[3], dq[4], dw[3], b[3], dOm[4];
+  rb_stage(P, x.a + QW, x.a + WX, x.a + OM, f, dq, dw, b);
+  if (MODE == 0) {
+    dOm[0] = c.x - x.a[OM]; dOm[1] = c.y - x.a[OM + 1]; dOm[2] = c.z - x.a[OM + 2]; dOm[3] = c.w - x.a[OM + 3];
+    rk4_from(P, x, dOm, H, L, f, dq, dw);
     return;
   }
-  if (MODE == 1) {
-    controller(P, x.a, c, hd, u);
-  } else {
-    u[0] = c.x; u[1] = c.y; u[2] = c.z; u[3] = c.w;
+  float r[4], e[3];
+  Ctl C;
+  controller_fwd<MODE == 2>(P, x.a, c, hd, b, C, r, dw, e);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) dOm[i] = fmaf(P.omax, r[i], -x.a[OM + i]);  // u = omega_max r
+  rk4_from(P, x, dOm, H, L, f, dq, dw);
+  if (MODE == 2) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) x.a[XI + i] = clampf(x.a[XI + i] + H.h * e[i], -P.xim[i], P.xim[i]);
   }
-  rk4_from(P, x, u, H, L, f, dq, dw);
 }
 
 }  // namespace qs

@@ -80,7 +80,7 @@ DevGroup derive(const sim_group_params_t& p) {
   d.txc = (float)(kt * Ls / Jx);
   d.tyc = (float)(kt * Lc / Jy);
   d.tzc = (float)(kq / Jz);
-  d.om2max = (float)om2;
+  d.omax = p.omega_max;
   d.gx = (float)((Jy - Jz) / Jx);
   d.gy = (float)((Jz - Jx) / Jy);
   d.gz = (float)((Jx - Jy) / Jz);
@@ -88,13 +88,14 @@ DevGroup derive(const sim_group_params_t& p) {
   for (int i = 0; i < 3; ++i) {
     d.kp[i] = p.kp[i];
     d.kd[i] = p.kd[i];
-    d.qa[i] = (float)(mix[i] * p.krate[i] * taumax[i] * 2.0 * p.katt[i]);
-    d.wa[i] = (float)(mix[i] * p.krate[i] * taumax[i]);
+    // the mixer's constants in units of omega_max^2 (mix_i taumax_i / omega_max^2 = 1/2)
+    d.qa[i] = (float)(mix[i] * p.krate[i] * taumax[i] * 2.0 * p.katt[i] / om2);
+    d.wa[i] = (float)(mix[i] * p.krate[i] * taumax[i] / om2);
     d.krate[i] = p.krate[i];
     d.katt2[i] = (float)(2.0 * p.katt[i]);
-    d.mt[i] = (float)(mix[i] * taumax[i]);
-    d.kic[i] = (float)(mix[i] * taumax[i] * p.kI[i]);
-    d.kdc[i] = (float)(mix[i] * taumax[i] * p.kD[i]);
+    d.mt[i] = (float)(mix[i] * taumax[i] / om2);
+    d.kic[i] = (float)(mix[i] * taumax[i] * p.kI[i] / om2);
+    d.kdc[i] = (float)(mix[i] * taumax[i] * p.kD[i] / om2);
     d.xim[i] = p.xi_max[i];
   }
   d.vt = (float)p.type;
@@ -107,11 +108,13 @@ DevGroup derive(const sim_group_params_t& p) {
     for (int i = 0; i < 6; ++i) d.vk[i] = p.veh[i];
   }
   d.a_max = p.a_max;
-  d.f0c = (float)(m / (4.0 * kt));
+  d.az_lo = (float)((double)p.g - p.a_max);  // the z clamp with gravity added: g -+ a_max
+  d.az_hi = (float)((double)p.g + p.a_max);
+  d.f0c = (float)(m / (2.0 * kt * om2));
   d.inv_m = (float)(1.0 / m);
   d.Jx = p.Jxx; d.Jy = p.Jyy; d.Jz = p.Jzz;
   d.iJx = (float)(1.0 / Jx); d.iJy = (float)(1.0 / Jy); d.iJz = (float)(1.0 / Jz);
-  d.mix0 = (float)(1.0 / (4.0 * kt));
+  d.mix0 = (float)(1.0 / (4.0 * kt * om2));
   return d;
 }
 
@@ -509,7 +512,7 @@ int launch_ranged(sim_s* h, StepArgs A, cudaStream_t st, int64_t first, int64_t 
     const int64_t b = ordered ? off[cb] : std::min(h->g_end[g], first + count);
     if (b <= a) continue;
     T.g[r] = h->host_groups[g];
-    T.coef[r] = lin_coef(h->host_groups[g].inv_tau, h->host_groups[g].cd_m, A.H);
+    T.coef[r] = lin_coef(h->host_groups[g], A.H);
     T.start[r] = a;
     T.end[r] = b;
     T.first_block[r] = (int)blocks;
@@ -564,7 +567,7 @@ int launch_step(sim_s* h, float* d_state, const float* d_cmd, StepH H, int K, cu
   A.H = H;
   A.groups = h->d_groups;
   A.order = nullptr;
-  A.coef = lin_coef(h->host_group0.inv_tau, h->host_group0.cd_m, H);
+  A.coef = lin_coef(h->host_group0, H);
   const bool plain = plain_path(h, K);
   const RangeMode rm = plain ? kPersistent : range_mode(h, K, first, count);
   if (rm != kPersistent) return launch_ranged(h, A, st, first, count, rm);
@@ -1002,7 +1005,7 @@ int sim_rollout_forward(sim_handle_t h, const float* d_state0, const float* d_cm
   A.H = make_h(dt);
   A.groups = h->d_groups;
   live_visit(h, &A.order, &A.count);
-  A.coef = lin_coef(h->host_group0.inv_tau, h->host_group0.cd_m, A.H);
+  A.coef = lin_coef(h->host_group0, A.H);
   const size_t smem = group_smem(h);
   const int grid = fwd_grid(h, smem, h->n);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

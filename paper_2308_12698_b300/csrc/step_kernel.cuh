@@ -142,13 +142,16 @@ __device__ __forceinline__ void plain_loop(const StepArgs& A, const DevGroup& P0
 // K fused RK4 steps per launch; the state touches HBM once per launch.
 // MULTI: some groups are cars or fixed-wing drones (closed loop only); each
 // agent runs its group's model.  PLAIN (1 or 2): one step per launch (K =
-// 1), where HBM bounds the kernel: registers capped so that 3 blocks of 256
-// stay resident and keep more loads in flight (the fused form runs faster
-// with the few more registers it takes uncapped).  PLAIN 2 prefetches each
-// thread's next agent (plain_loop); the host takes it when the agents exceed
-// one resident wave, PLAIN 1 (nothing to overlap) otherwise.
+// 1), where HBM bounds the kernel.  Registers are capped so that 3 blocks of
+// 256 stay resident: the plain form keeps more loads in flight, and the fused
+// one-group form fits in 80 without spilling (uncapped it takes 88 in the
+// closed loop, the same speed, and the PID loop runs 3 % slower).  The
+// heterogeneous form, which holds its group's constants in registers, is left
+// uncapped: capped it spills.  PLAIN 2 prefetches each thread's next agent
+// (plain_loop); the host takes it when the agents exceed one resident wave,
+// PLAIN 1 (nothing to overlap) otherwise.
 template <int MODE, bool HETERO, bool MULTI = false, int PLAIN = 0>
-__global__ void __launch_bounds__(256, PLAIN ? 3 : 1) step_kernel(StepArgs A, const DevGroup P0) {
+__global__ void __launch_bounds__(256, (PLAIN || !HETERO) ? 3 : 1) step_kernel(StepArgs A, const DevGroup P0) {
   extern __shared__ float4 smem4[];
   if (PLAIN == 2) {
     plain_loop<MODE>(A, P0, smem4);
@@ -174,7 +177,7 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 1) step_kernel(StepArgs A, co
       for (int k = 0; k < K; ++k) vehicle_step(P, x, c, A.H);
     } else if (HETERO) {
       const DevGroup P = sg[A.gid[i]];
-      const LinCoef L = lin_coef(P.inv_tau, P.cd_m, A.H);
+      const LinCoef L = lin_coef(P, A.H);
       for (int k = 0; k < K; ++k) step<MODE>(P, x, c, hd, A.H, L);
     } else {
       const LinCoef& L = A.coef;
@@ -271,7 +274,7 @@ __global__ void __launch_bounds__(256) refreeze_kernel(StepArgs A) {
     const DevGroup& P = A.groups[A.n_groups > 1 ? A.gid[i] : 0];
     const float4 c = A.cmd[i];
     const Hd hd = heading(MODE != 0 ? c.w : 0.f);
-    const LinCoef L = lin_coef(P.inv_tau, P.cd_m, A.H);
+    const LinCoef L = lin_coef(P, A.H);
     St x;
     load_state<NS>(A.state, A.n, i, x);
     for (int k = 0; k < A.K; ++k) {
