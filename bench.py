@@ -932,32 +932,33 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     ds.close()
     del dx0, dcmd
 
-    # heterogeneous: 8 groups, uneven sizes (600k), one persistent launch per K steps, graph;
+    # heterogeneous: 8 groups, uneven sizes (600k), a launch per group range per K steps, side by side
+    # on the handle's streams, in a graph;
     # beside it the one-group swarm at the same agent count
     hw = W.heterogeneous(nsteps=T_STEPS, shuffle=False)
     ht, ms = swarm_leg(world, hw, dev, timed_steps, reps)
     hrate = hw.n * T_STEPS / (ms / 1e3)
     st_, ms1 = swarm_leg(world, W.scale_sweep(hw.n, nsteps=T_STEPS), dev, timed_steps, reps)
     rate1 = hw.n * T_STEPS / (ms1 / 1e3)
-    hp = profiled("range_kernel<1>", f"heterogeneous-{hw.n}-K{ht['K']}")
+    hp = profiled("group_kernel<1>", f"heterogeneous-{hw.n}-K{ht['K']}")
     out["hetero"] = {"value": world * hrate, "unit": UNIT, "ms_per_step": ms,
                      "n_agents": hw.n, "groups": len(hw.groups), "sizes": list(W.HETERO_SIZES), "K": ht["K"],
                      "block": ht["block"],
                      "one_group_same_n": {"value": world * rate1, "K": st_["K"], "block": st_["block"]},
                      "ratio_to_one_group": hrate / rate1,
                      "roofline": alu_roofline(FLOPS_PER_AGENT_STEP, hrate, sms, clocks, hp,
-                                              "range_kernel<closed loop>: one group per block, its constants "
-                                              "in the kernel's parameters",
+                                              "group_kernel<closed loop>: a launch per group range, side by "
+                                              "side; the group's constants in the kernel's parameters",
                                               note="every group runs the same operations")}
     # the same agents with the groups' ids interleaved at random: the handle's group-sorted order
     hi, msi = swarm_leg(world, W.heterogeneous(nsteps=T_STEPS, shuffle=True), dev, timed_steps, reps)
     hirate = hw.n * T_STEPS / (msi / 1e3)
-    hip = profiled("range_kernel<1,false,true>", f"heterogeneous-interleaved-{hw.n}-K{hi['K']}")
+    hip = profiled("group_kernel<1,false,true>", f"heterogeneous-interleaved-{hw.n}-K{hi['K']}")
     out["hetero"]["interleaved"] = {"value": world * hirate, "ms_per_step": msi,
                                     "K": hi["K"], "block": hi["block"], "ratio_to_contiguous": ms / msi,
-                                    "how": "ids in random order; range_kernel through the group-sorted order",
+                                    "how": "ids in random order; group_kernel through the group-sorted order",
                                     "roofline": alu_roofline(FLOPS_PER_AGENT_STEP, hirate, sms, clocks, hip,
-                                                             "range_kernel<closed loop, ORDER>")}
+                                                             "group_kernel<closed loop, ORDER>")}
 
     # PID body-rate loop: 1e6 agents with 20-component states
     pw = W.closed_loop_pid(n=N_AGENTS, nsteps=T_STEPS)
@@ -969,30 +970,30 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
                   "roofline": alu_roofline(FLOPS_PER_AGENT_STEP_PID, rate, sms, clocks, pp,
                                            "step_kernel<PID rate loop, one group>")}
 
-    # quadrotors, cars and fixed-wing drones (200,000 each) in one launch
+    # quadrotors, cars and fixed-wing drones (200,000 each): a launch per type's group, side by side
     mw = W.multi_type(nsteps=T_STEPS)
     mt, ms = swarm_leg(world, mw, dev, timed_steps, reps)
     sizes = W.MULTI_TYPE_SIZES
     rate = mw.n * T_STEPS / (ms / 1e3)
     flops = (sizes[0] * FLOPS_PER_AGENT_STEP + sizes[1] * FLOPS_PER_AGENT_STEP_CAR +
              sizes[2] * FLOPS_PER_AGENT_STEP_FIXED_WING) / mw.n
-    mp = profiled("range_kernel<1,true>", f"multi-type-{mw.n}-K{mt['K']}", "multi")
+    mp = profiled("group_kernel<1,multi>", f"multi-type-{mw.n}-K{mt['K']}", "multi")
     out["multi_type"] = {"value": world * rate, "unit": UNIT, "ms_per_step": ms,
                          "n_agents": mw.n, "sizes": {"quadrotor": sizes[0], "car": sizes[1], "fixed_wing": sizes[2]},
                          "K": mt["K"], "block": mt["block"],
-                         "roofline": alu_roofline(flops, rate, sms, clocks, mp, "range_kernel<mixed agent types>",
+                         "roofline": alu_roofline(flops, rate, sms, clocks, mp, "group_kernel<mixed agent types>: a launch per type's group",
                                                   note="quadrotors at the hand count, cars and fixed-wing drones "
                                                        "at the checker's count; tan/atan2 not counted")}
     # the same swarm with the agent types interleaved at random: the group-sorted order keeps each
     # warp on one type
     mi, msi = swarm_leg(world, W.multi_type(nsteps=T_STEPS, shuffle=True), dev, timed_steps, reps)
     mirate = mw.n * T_STEPS / (msi / 1e3)
-    mip = profiled("range_kernel<1,true,true>", f"multi-type-interleaved-{mw.n}-K{mi['K']}", "multi")
+    mip = profiled("group_kernel<1,multi,true>", f"multi-type-interleaved-{mw.n}-K{mi['K']}", "multi")
     out["multi_type"]["interleaved"] = {"value": world * mirate, "ms_per_step": msi,
                                         "K": mi["K"], "block": mi["block"], "ratio_to_contiguous": ms / msi,
-                                        "how": "ids in random order; range_kernel through the group-sorted order",
+                                        "how": "ids in random order; group_kernel through the group-sorted order",
                                         "roofline": alu_roofline(flops, mirate, sms, clocks, mip,
-                                                                 "range_kernel<mixed agent types, ORDER>")}
+                                                                 "group_kernel<mixed agent types, ORDER>")}
 
     # the closed-loop configuration at its own shape: 5,000 agents x 10,000 steps, tuned
     cw1 = W.closed_loop()

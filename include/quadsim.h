@@ -389,10 +389,14 @@ int sim_graph_launch(sim_graph_t g, void* stream);
 void sim_graph_destroy(sim_graph_t g);
 
 /* Number of kernel launches one sim_step call makes for these arguments:
- * ceil(nsteps / K) step launches, plus one pass that replays agents which
- * went non-finite in the middle of a launch (none when every launch is a
- * single step of one open- or P-closed-loop quadrotor group).  An upper
- * bound after sim_compact: a step launch over no live agent is skipped. */
+ * ceil(nsteps / K) fused step launches, each one kernel launch per group
+ * range when several groups run by range or order (contiguous ids, a
+ * group-sorted order, or sim_compact's live order: one launch per group with
+ * agents there, each on a stream of the handle's own, forked from and joined
+ * back to the caller's stream), plus one pass that replays agents which went
+ * non-finite in the middle of a launch (none when every launch is a single
+ * step of one open- or P-closed-loop quadrotor group).  An upper bound: a
+ * launch over no agent is skipped, and counted as if each group had agents. */
 int64_t sim_step_launches(sim_handle_t h, int64_t nsteps, int substeps_K);
 
 void sim_destroy(sim_handle_t h);

@@ -12,8 +12,8 @@
 //   3 prefetch_state  agent index outside [0, n) of a planar state (cp.async)
 //   4 step kernels    agent index outside [0, n) (status, command, group id)
 //   5 group tables    group id outside [0, n_groups)
-//   6 range_kernel    range outside [0, n_ranges) or position outside [0, n)
-//   7 range_kernel    order[position] outside [0, n)
+//   6 group_kernel    position outside [0, n)
+//   7 group_kernel    order[position] outside [0, n)
 //   8 checkpoints     checkpoint index outside [0, S]
 //   9 adjoint         scratch step outside [0, C), or per-agent theta row outside [0, n)
 //  10 collisions      bucket outside the table, record outside [0, n)

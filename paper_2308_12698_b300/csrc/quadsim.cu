@@ -219,12 +219,12 @@ struct sim_s {
   DevGroup host_group0;
   DevGroup host_groups[SIM_MAX_GROUPS];
   // each group's agents form one contiguous range [g_start, g_end) (found at
-  // creation from the ids): the fused steps then run as range_kernel
+  // creation from the ids): the fused steps then run as group_kernel launches, one per range
   bool ranged = false;
   int64_t g_start[SIM_MAX_GROUPS] = {}, g_end[SIM_MAX_GROUPS] = {};
   // ids in which the groups interleave: the agents sorted by (group, host
   // pipeline chunk, index) in d_order (owned); the agents of group g and chunk
-  // c sit at positions [g_off[g][c], g_off[g][c + 1]), and range_kernel steps
+  // c sit at positions [g_off[g][c], g_off[g][c + 1]), and group_kernel steps
   // any run of whole chunks through it
   uint32_t* d_order = nullptr;
   int n_chunks = 1;
@@ -250,6 +250,10 @@ struct sim_s {
   cudaEvent_t ev_start = nullptr, ev_end = nullptr, ev_in[kHostChunks] = {}, ev_done[kHostChunks] = {};
   // decision rounds (sim_run_rounds): per command plane and observation plane
   cudaEvent_t ev_cmd[2] = {}, ev_cmd_free[2] = {}, ev_obs[2] = {}, ev_obs_free[2] = {};
+  // several groups: a stream per group range of a fused launch (launch_ranged),
+  // forked from the caller's stream and joined back to it; created with the handle
+  cudaStream_t s_grp[SIM_MAX_GROUPS] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[SIM_MAX_GROUPS] = {};
   int block_fwd = kDefaultBlockFwd;
   int block_adj = kDefaultBlockAdj;
   int K = kDefaultK;
@@ -440,14 +444,14 @@ int order_live(sim_s* h, cudaStream_t st, uint32_t* out, std::vector<int64_t>& o
 // How the fused steps reach the groups, decided once at creation from the
 // caller's id buffer (read synchronously; the handle's contract keeps it
 // unchanged): contiguous ranges, one per group (sorted ids, or contiguous
-// blocks in any order: range_kernel directly), a group-sorted order
+// blocks in any order: a group_kernel launch per range), a group-sorted order
 // (interleaved ids), or neither (one group).
 int plan_groups(sim_s* h) {
   h->ranged = false;
   host_chunks(h->n, &h->n_chunks, &h->chunk);
   // one group: its constants are kernel parameters of step_kernel already, and
   // that kernel's persistent grid of 32-agent chunks ends its last wave more
-  // evenly (range_kernel measured 1-3 % slower at 6e5 and 1e6 agents)
+  // evenly (one block per 256-agent chunk measured 1-3 % slower at 6e5 and 1e6 agents)
   if (h->n_groups == 1) return SIM_OK;
   if (h->n == 0) return SIM_OK;
   std::vector<uint8_t> ids((size_t)h->n);
@@ -486,56 +490,72 @@ bool whole_chunks(const sim_s* h, int64_t first, int64_t count) {
   return h->chunk > 0 && first % h->chunk == 0 && (end == h->n || end % h->chunk == 0);
 }
 
-// The fused steps as range_kernel: one block per chunk of block_fwd agents of
-// one group, over the groups' ranges clipped to [first, first + count); with
-// the group-sorted order (a run of whole chunks), over each group's positions
-// for those chunks.
-// How a fused launch runs: the persistent kernel, the range kernel over
-// contiguous groups, or the range kernel through the group-sorted order or the
-// live agents' order.
+// How a fused launch runs: the persistent kernel, one launch per group range
+// of contiguous groups, or one per group range of the group-sorted order or of
+// the live agents' order.
 enum RangeMode { kPersistent, kContiguous, kGroupOrder, kLiveOrder };
 
+template <bool ORDER>
+void launch_group(const sim_s* h, const StepArgs& A, const DevGroup& P, int grid, cudaStream_t s) {
+  const int bd = h->block_fwd;
+  if (P.vt != (float)TYPE_QUAD) group_kernel<1, true, ORDER><<<grid, bd, 0, s>>>(A, P);
+  else if (h->mode == SIM_CLOSED_LOOP_PID) group_kernel<2, false, ORDER><<<grid, bd, 0, s>>>(A, P);
+  else if (h->mode == SIM_CLOSED_LOOP) group_kernel<1, false, ORDER><<<grid, bd, 0, s>>>(A, P);
+  else group_kernel<0, false, ORDER><<<grid, bd, 0, s>>>(A, P);
+}
+
+// The fused steps of several groups as group_kernel launches, one per group
+// range clipped to [first, first + count), or, with an order (a run of whole
+// chunks), one per group over its positions in the order for those chunks.
+// With more than one range each runs on its group's stream, forked from st
+// and joined back to it (the same form inside a graph capture: parallel
+// branches).  The ranges' launches then run side by side; a small group's
+// launch, whose blocks each take K whole steps, overlaps the large ones.
 int launch_ranged(sim_s* h, StepArgs A, cudaStream_t st, int64_t first, int64_t count, RangeMode mode) {
-  static_assert(SIM_MAX_GROUPS <= 32, "RangeTable holds 32 ranges");
   const bool ordered = mode != kContiguous;
   A.order = mode == kLiveOrder ? h->d_live : h->d_order;
   const std::vector<int64_t>& offs = mode == kLiveOrder ? h->live_off : h->g_off;
   const int64_t ca = ordered ? first / h->chunk : 0;
   const int64_t cb = ordered ? (first + count == h->n ? h->n_chunks : (first + count) / h->chunk) : 0;
-  RangeTable T;
-  std::memset(&T, 0, sizeof(T));
-  int64_t blocks = 0;
-  int r = 0;
+  int gs[SIM_MAX_GROUPS];
+  int64_t ra[SIM_MAX_GROUPS], rb[SIM_MAX_GROUPS];
+  int nr = 0;
   for (int g = 0; g < h->n_groups; ++g) {
     const int64_t* off = ordered ? &offs[(size_t)g * (h->n_chunks + 1)] : nullptr;
     const int64_t a = ordered ? off[ca] : std::max(h->g_start[g], first);
     const int64_t b = ordered ? off[cb] : std::min(h->g_end[g], first + count);
     if (b <= a) continue;
-    T.g[r] = h->host_groups[g];
-    T.coef[r] = lin_coef(h->host_groups[g], A.H);
-    T.start[r] = a;
-    T.end[r] = b;
-    T.first_block[r] = (int)blocks;
-    blocks += (b - a + h->block_fwd - 1) / h->block_fwd;
-    if (blocks > INT32_MAX) return SIM_ERR_ARG;
-    ++r;
+    if ((b - a + h->block_fwd - 1) / h->block_fwd > INT32_MAX) return SIM_ERR_ARG;
+    gs[nr] = g;
+    ra[nr] = a;
+    rb[nr] = b;
+    ++nr;
   }
-  if (r == 0) return SIM_OK;
-  T.first_block[r] = (int)blocks;
-  T.n_ranges = r;
-  const int grid = (int)blocks, bd = h->block_fwd;
-  if (ordered) {
-    if (h->multi) range_kernel<1, true, true><<<grid, bd, 0, st>>>(A, T);
-    else if (h->mode == SIM_CLOSED_LOOP_PID) range_kernel<2, false, true><<<grid, bd, 0, st>>>(A, T);
-    else if (h->mode == SIM_CLOSED_LOOP) range_kernel<1, false, true><<<grid, bd, 0, st>>>(A, T);
-    else range_kernel<0, false, true><<<grid, bd, 0, st>>>(A, T);
-  } else {
-    if (h->multi) range_kernel<1, true><<<grid, bd, 0, st>>>(A, T);
-    else if (h->mode == SIM_CLOSED_LOOP_PID) range_kernel<2><<<grid, bd, 0, st>>>(A, T);
-    else if (h->mode == SIM_CLOSED_LOOP) range_kernel<1><<<grid, bd, 0, st>>>(A, T);
-    else range_kernel<0><<<grid, bd, 0, st>>>(A, T);
+  if (nr == 0) return SIM_OK;
+  const bool fork = nr > 1;
+  if (fork && cudaEventRecord(h->ev_fork, st) != cudaSuccess) return SIM_ERR_CUDA;
+  int rc = SIM_OK;
+  for (int r = 0; r < nr; ++r) {
+    const int g = gs[r];
+    const cudaStream_t s = fork ? h->s_grp[g] : st;
+    if (fork && cudaStreamWaitEvent(s, h->ev_fork, 0) != cudaSuccess) {
+      rc = SIM_ERR_CUDA;
+      break;  // nothing launched on s: nothing to join
+    }
+    const DevGroup& P = h->host_groups[g];
+    A.first = ra[r];
+    A.count = rb[r] - ra[r];
+    A.coef = lin_coef(P, A.H);
+    const int grid = (int)((A.count + h->block_fwd - 1) / h->block_fwd);
+    if (ordered) launch_group<true>(h, A, P, grid, s);
+    else launch_group<false>(h, A, P, grid, s);
+    if (cudaGetLastError() != cudaSuccess) rc = SIM_ERR_CUDA;
+    // join even after a failed launch: a capture must get every forked stream back
+    if (fork && (cudaEventRecord(h->ev_join[g], s) != cudaSuccess ||
+                 cudaStreamWaitEvent(st, h->ev_join[g], 0) != cudaSuccess))
+      rc = SIM_ERR_CUDA;
   }
-  return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ERR_CUDA;
+  return rc;
 }
 
 // How a fused launch of K steps over [first, first + count) runs.  An order
@@ -767,6 +787,13 @@ int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents,
     if (d_max) cudaFree(d_max);
   }
   if (rc == SIM_OK) rc = plan_groups(h);
+  if (rc == SIM_OK && n_groups > 1) {
+    if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess) rc = SIM_ERR_CUDA;
+    for (int g = 0; g < n_groups && rc == SIM_OK; ++g)
+      if (cudaStreamCreateWithFlags(&h->s_grp[g], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->ev_join[g], cudaEventDisableTiming) != cudaSuccess)
+        rc = SIM_ERR_CUDA;
+  }
   if (rc == SIM_OK) {
     // allow the shared-memory scratch variant of the adjoint its full size
     const int big = (int)(kSmemScratchMax + 64 * 1024);
@@ -839,7 +866,11 @@ int sim_get_launch(sim_handle_t h, int* block_fwd, int* block_adj, int* K, int* 
 int64_t sim_step_launches(sim_handle_t h, int64_t nsteps, int substeps_K) {
   if (!h || nsteps <= 0 || h->n == 0) return 0;
   const int64_t K = substeps_K > 0 ? substeps_K : h->K;
-  return (nsteps + K - 1) / K + (plain_path(h, (int)std::min(K, nsteps)) ? 0 : 1);  // + the refreeze pass
+  // a fused launch over several groups' ranges is one launch per range (at most one per group)
+  const int64_t per = h->n_groups > 1 && range_mode(h, (int)std::min(K, nsteps), 0, h->n) != kPersistent
+                          ? h->n_groups : 1;
+  const bool plain = plain_path(h, (int)std::min(K, nsteps));
+  return (nsteps + K - 1) / K * (plain ? 1 : per) + (plain ? 0 : 1);  // + the refreeze pass
 }
 
 int sim_step(sim_handle_t h, float* d_state, const float* d_cmd, float dt, int64_t nsteps, int substeps_K,
@@ -1385,7 +1416,11 @@ void sim_destroy(sim_handle_t h) {
     if (st) cudaStreamDestroy(st);
   for (cudaStream_t st : h->s_comp)
     if (st) cudaStreamDestroy(st);
-  for (cudaEvent_t e : {h->ev_start, h->ev_end})
+  for (cudaStream_t st : h->s_grp)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t e : h->ev_join)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : {h->ev_start, h->ev_end, h->ev_fork})
     if (e) cudaEventDestroy(e);
   for (int c = 0; c < kHostChunks; ++c) {
     if (h->ev_in[c]) cudaEventDestroy(h->ev_in[c]);

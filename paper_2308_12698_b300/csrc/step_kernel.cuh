@@ -26,7 +26,7 @@ struct StepArgs {
   int n_groups;
   StepH H;
   const DevGroup* groups;  // device table (several groups)
-  const uint32_t* order;   // range_kernel<..., ORDER>: agent at each group-sorted position
+  const uint32_t* order;   // group_kernel<..., ORDER>: agent at each group-sorted position
   LinCoef coef;            // one group: its RK4 weights of the linear parts (lin_coef, on the host)
 };
 
@@ -194,55 +194,39 @@ __global__ void __launch_bounds__(256, (PLAIN || !HETERO) ? 3 : 1) step_kernel(S
   }
 }
 
-// Contiguous agent ranges, each of one parameter group, for range_kernel,
-// cut into chunks of blockDim agents, one chunk per block.  The table travels
-// in the kernel's parameters (__grid_constant__); the range index, and with
-// it the group, is then uniform over a block, and the compiler reads the
-// group's constants from the constant bank instead of holding them in
-// registers (79-80 registers against 115-127 for the shared-memory table of
-// step_kernel's heterogeneous form).
-struct RangeTable {
-  DevGroup g[32];          // the range's group's constants
-  LinCoef coef[32];        // and its RK4 weights of the linear parts (lin_coef, on the host)
-  int64_t start[32];       // first agent of the range
-  int64_t end[32];         // one past its last agent
-  int first_block[33];     // block at which each range starts; [n_ranges] = the grid
-  int n_ranges;
-};
-
-// K fused RK4 steps per launch for agents in contiguous per-group ranges,
-// one agent per thread, one block per chunk (not persistent: the hardware
-// scheduler evens out the last wave better than a resident grid taking whole
-// chunks in turn, measured 3.5 % faster on 8 groups of 600,000 agents).
-// Same arithmetic, results and status marks as step_kernel's fused form.
-// ORDER: the ranges are of positions in a group-sorted order of the agents
-// (A.order), for ids in which the groups interleave; a warp then still holds
-// agents of one group, and of one agent type.
-template <int MODE, bool MULTI = false, bool ORDER = false>
-__global__ void __launch_bounds__(256) range_kernel(StepArgs A, const __grid_constant__ RangeTable T) {
-  int r = 0;
-  for (int k = 1; k < T.n_ranges; ++k) r += (int)(blockIdx.x >= (unsigned)T.first_block[k]);
-#ifdef QS_CHECKED
-  if (!QS_OK(r >= 0 && r < T.n_ranges, 6, r)) return;
-#endif
-  const int64_t j = T.start[r] + (int64_t)(blockIdx.x - T.first_block[r]) * blockDim.x + threadIdx.x;
-  if (j >= T.end[r]) return;
+// K fused RK4 steps for one range of one group: [A.first, A.first + A.count)
+// of agent ids, or of positions in a group-sorted order of the agents
+// (ORDER: A.order, for ids in which the groups interleave; a warp then still
+// holds agents of one group, and of one agent type).  One agent per thread,
+// one block per chunk (not persistent: the hardware scheduler evens out the
+// last wave better than a resident grid taking whole chunks in turn).  The
+// group's constants (P) and RK4 weights (A.coef) are kernel parameters at
+// fixed offsets, which the step's operations read from the constant bank as
+// operands.  The host launches one per range, each on a stream of its own, so
+// that the ranges run side by side.  (One launch over a table of all ranges,
+// indexed by a block-uniform range, spent 17 more thread instructions per
+// agent-step reading the constants: 3-5 % slower.)  Same arithmetic, results
+// and status marks as step_kernel's fused form.  VEH: the group is a car or
+// fixed-wing group (vehicle_step).
+template <int MODE, bool VEH = false, bool ORDER = false>
+__global__ void __launch_bounds__(256, 3) group_kernel(StepArgs A, const DevGroup P) {
+  const int64_t j = A.first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= A.first + A.count) return;
 #ifdef QS_CHECKED
   if (!QS_OK(j >= 0 && j < A.n, 6, j)) return;
   if (ORDER && !QS_OK(A.order[j] < A.n, 7, A.order[j])) return;
 #endif
   const int64_t i = ORDER ? (int64_t)A.order[j] : j;
   if (A.status[i]) return;  // dead agents are frozen
-  const DevGroup& P = T.g[r];
   constexpr int NS = state_dim<MODE>();
   St x;
   load_state<NS>(A.state, A.n, i, x);
   const float4 c = A.cmd[i];
-  const Hd hd = heading(MODE != 0 ? c.w : 0.f);
-  if (MULTI && P.vt != (float)TYPE_QUAD) {
+  if (VEH) {
     for (int k = 0; k < A.K; ++k) vehicle_step(P, x, c, A.H);
   } else {
-    const LinCoef& L = T.coef[r];
+    const Hd hd = heading(MODE != 0 ? c.w : 0.f);
+    const LinCoef& L = A.coef;
 #pragma unroll 2
     for (int k = 0; k < A.K; ++k) step<MODE>(P, x, c, hd, A.H, L);
   }

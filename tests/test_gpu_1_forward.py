@@ -207,10 +207,11 @@ def _permuted(wl, perm):
 @pytest.mark.parametrize("kind", ["quad", "pid", "multi"])
 @pytest.mark.parametrize("K", [1, 20, 60])
 def test_contiguous_and_interleaved_groups_agree(dev, kind, K):
-    """Groups whose agents form contiguous id ranges run as range_kernel (one group per block,
-    its constants read from the kernel's parameters).  Interleaved ids run through the handle's
-    group-sorted order as the same kernel for mixed agent types at any K and for launches of 32
-    steps or more (K = 60 here), otherwise as step_kernel with the group table in shared memory.
+    """Groups whose agents form contiguous id ranges run as group_kernel, a launch per range on
+    the handle's streams, side by side, each with its group's constants in the kernel's
+    parameters.  Interleaved ids run through the handle's group-sorted order as the same launches
+    for mixed agent types at any K and for launches of 32 steps or more (K = 60 here), otherwise
+    as step_kernel with the group table in shared memory.
     The same agents in three layouts -- sorted by group, contiguous blocks in reversed group
     order, shuffled -- give the same bits per agent."""
     if kind == "quad":
@@ -233,8 +234,8 @@ def test_contiguous_and_interleaved_groups_agree(dev, kind, K):
 
 
 def test_contiguous_groups_with_an_empty_group(dev):
-    """A group with no agents between two contiguous ones (ids 0 and 2 only): the range kernel
-    skips it; the same agents interleaved give the same bits."""
+    """A group with no agents between two contiguous ones (ids 0 and 2 only): no launch for it;
+    the same agents interleaved give the same bits."""
     wl = W.heterogeneous(sizes=(700, 0, 300), nsteps=40)
     assert set(np.unique(wl.gid)) == {0, 2}
     a = gpu_run(wl, dev, 40, K=20)
@@ -357,9 +358,10 @@ def test_host_entry_matches_device_entry(dev):
                                       ("mixed_types", 7)])
 def test_pipelined_host_entry_over_chunks(dev, layout, K):
     """300k agents (9 chunks through copy and compute streams), several groups, dead agents:
-    the host-buffer entry gives bitwise the device-buffer result.  Contiguous groups run as the
-    range kernel, whose ranges the chunks cut; interleaved groups at K = 40 and interleaved agent
-    types run it through the group-sorted order, whose positions the chunks cut."""
+    the host-buffer entry gives bitwise the device-buffer result.  Contiguous groups run as a
+    launch per group range, whose ranges the chunks cut; interleaved groups at K = 40 and
+    interleaved agent types run them through the group-sorted order, whose positions the chunks
+    cut."""
     from paper_2308_12698_b300.sim import Sim, planar, unplanar
     if layout == "mixed_types":
         wl = W.multi_type(sizes=(100_000, 150_000, 50_001), nsteps=80, shuffle=True)
@@ -546,7 +548,7 @@ def _diverging_swarm(kind):
         wl = W.open_loop(n=64, nsteps=300)
     elif kind == "hetero":  # interleaved ids: the persistent kernel at K = 1, the group-sorted order from 32
         wl = W.heterogeneous(sizes=(32, 32), nsteps=300, shuffle=True)
-    elif kind == "hetero_contiguous":  # contiguous ids: the range kernel
+    elif kind == "hetero_contiguous":  # contiguous ids: a launch per group range
         wl = W.heterogeneous(sizes=(32, 32), nsteps=300, shuffle=False)
     else:
         wl = W.closed_loop_pid(n=64, nsteps=300)
