@@ -127,7 +127,7 @@ def test_closed_loop_full_length(dev, orc):
     (median, p90, p99, worst agent), for position, attitude and the quaternion's norm (nothing
     renormalises it).  Both are FP32 evaluations of the same equations with different operation
     orders, so the two distributions agree up to the sampling spread of a quantile over 5,000
-    agents (measured ratios 0.95 to 1.13).  The stated bar itself holds for every agent after the
+    agents (measured ratios 0.96 to 1.08).  The stated bar itself holds for every agent after the
     first 1000 steps."""
     wl = W.closed_loop(n=5000)
     assert wl.nsteps == 10_000
