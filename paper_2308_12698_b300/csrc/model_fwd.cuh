@@ -61,9 +61,9 @@ struct __align__(16) DevGroup {
   // adjoint
   float inv_m, Jx, Jy, Jz;
   float iJx, iJy, iJz, mix0;    // mix0 = 1 / (4 kt omega_max^2)
-  float krate[3], pad2;
-  float katt2[3], pad3;         // 2 katt
-  float mt[3], pad4;            // mix_i taumax_i  (mix = 1/(4 kt L sin a), 1/(4 kt L cos a), 1/(4 kq))
+  float krate[3], gxt;          // gxt, gyt, gzt: the gyroscopic coefficients over the torque ones,
+  float katt2[3], gyt;          // (Jy - Jz) / (kt L sin a), (Jz - Jx) / (kt L cos a), (Jx - Jy) / kq
+  float mt[3], gzt;             // mix_i taumax_i  (mix = 1/(4 kt L sin a), 1/(4 kt L cos a), 1/(4 kq))
   // forward: PID rate loop (MODE 2)
   float kic[3], pad5;           // mix_i taumax_i kI_i: rate-error integral -> Omega^2
   float kdc[3], pad6;           // mix_i taumax_i kD_i: angular acceleration -> Omega^2
@@ -151,6 +151,7 @@ struct LinCoef {
   float am1, b1, b2, b3, b4;  // B_k: times T2c
   float g, d1, d2, d3;        // D_k: times T2c
   float gb, gd;               // gravity's share of the v and p updates (z only)
+  float t2[3], t1[3], t6[3];  // h/2, h, h/6 times the torque coefficients txc, tyc, tzc
 };
 
 __host__ __device__ __forceinline__ LinCoef lin_coef(const DevGroup& P, const StepH& H) {
@@ -174,6 +175,12 @@ __host__ __device__ __forceinline__ LinCoef lin_coef(const DevGroup& P, const St
   L.d1 = rmul(P.T2c, d1); L.d2 = rmul(P.T2c, d2); L.d3 = rmul(P.T2c, d3);
   L.gb = rmul(-P.g, radd(radd(radd(b1, b2), b3), b4));
   L.gd = rmul(-P.g, radd(radd(d1, d2), d3));
+  const float tc[3] = {P.txc, P.tyc, P.tzc};
+  for (int i = 0; i < 3; ++i) {
+    L.t2[i] = rmul(H.h2, tc[i]);
+    L.t1[i] = rmul(H.h, tc[i]);
+    L.t6[i] = rmul(H.h6, tc[i]);
+  }
   return L;
 }
 
@@ -279,8 +286,11 @@ __device__ __forceinline__ void thrust_axis(const float q[4], float b[3]) {
 }
 
 // The same derivative at an RK4 stage, for the forward step: the rotation's
-// components (2 q' and omega'), and the thrust as f = S b with S the sum of
-// the Omega_i^2 and b = thrust_axis(q) (also returned): v' = T2c f - g e3 -
+// components, 2 q' and omega' over the torque coefficients (dw_i = omega'_i /
+// t_i with t = (txc, tyc, tzc): the gyroscopic term's coefficient divided by
+// t_i, and t_i carried by the RK4 weights of omega, lin_coef's t2, t1, t6:
+// three multiplies fewer per stage), and the thrust as f = S b with S the sum
+// of the Omega_i^2 and b = thrust_axis(q) (also returned): v' = T2c f - g e3 -
 // cd_m v, whose constants lin_coef's weights carry.
 // Wherever two products meet one sum the multiply-add is written out (fmaf,
 // __fmul_rn), so that each kernel that steps agents computes the same bits: the
@@ -295,9 +305,8 @@ __device__ __forceinline__ void rb_stage(const DevGroup& P, const float q[4], co
   const float s12 = fmaf(Om[0], Om[0], s2), d12 = fmaf(Om[0], Om[0], -s2);
   const float s34 = fmaf(Om[2], Om[2], s4), d34 = fmaf(Om[2], Om[2], -s4);
   const float S = __fadd_rn(s12, s34);
-  const float tx = __fmul_rn(P.txc, __fsub_rn(d12, d34));
-  const float ty = __fmul_rn(P.tyc, __fsub_rn(s34, s12));
-  const float tz = __fmul_rn(P.tzc, __fadd_rn(d12, d34));
+  // Eq. 3's torque rows without their coefficients
+  const float tx = __fsub_rn(d12, d34), ty = __fsub_rn(s34, s12), tz = __fadd_rn(d12, d34);
   thrust_axis(q, b);
   f[0] = __fmul_rn(S, b[0]);
   f[1] = __fmul_rn(S, b[1]);
@@ -306,9 +315,9 @@ __device__ __forceinline__ void rb_stage(const DevGroup& P, const float q[4], co
   dq[1] = fmaf(-q[3], w[1], fmaf(q[2], w[2], __fmul_rn(q[0], w[0])));
   dq[2] = fmaf(-q[1], w[2], fmaf(q[3], w[0], __fmul_rn(q[0], w[1])));
   dq[3] = fmaf(-q[2], w[0], fmaf(q[1], w[1], __fmul_rn(q[0], w[2])));
-  dw[0] = fmaf(P.gx, __fmul_rn(w[1], w[2]), tx);
-  dw[1] = fmaf(P.gy, __fmul_rn(w[2], w[0]), ty);
-  dw[2] = fmaf(P.gz, __fmul_rn(w[0], w[1]), tz);
+  dw[0] = fmaf(P.gxt, __fmul_rn(w[1], w[2]), tx);
+  dw[1] = fmaf(P.gyt, __fmul_rn(w[2], w[0]), ty);
+  dw[2] = fmaf(P.gzt, __fmul_rn(w[0], w[1]), tz);
 }
 
 // a + b and a - b saturated to [0, 1], NaN to 0 (PTX add.sat / sub.sat): the
@@ -436,7 +445,8 @@ __device__ __forceinline__ void controller(const DevGroup& P, const float* x, co
 
 // ------------------------------------------------------------------ RK4 --
 // One classical RK4 step with the rotor command held, from the first stage's
-// rb_stage values at x (f1, dq1, dw1) and dOm = u - Omega.  The rotation and
+// rb_stage values at x (f1, dq1, dw1: omega' over the torque coefficients)
+// and dOm = u - Omega.  The rotation and
 // the rotor lag go through the four stages; the translation takes lin_coef's
 // weights.  Each update is one product and one sum, written as the
 // multiply-add it is.
@@ -447,28 +457,28 @@ __device__ __forceinline__ void rk4_from(const DevGroup& P, St& x, const float d
 #pragma unroll
   for (int i = 0; i < 4; ++i) { aq[i] = dq1[i]; q[i] = fmaf(H.h2q, dq1[i], x.a[QW + i]); }
 #pragma unroll
-  for (int i = 0; i < 3; ++i) { aw[i] = dw1[i]; w[i] = fmaf(H.h2, dw1[i], x.a[WX + i]); }
+  for (int i = 0; i < 3; ++i) { aw[i] = dw1[i]; w[i] = fmaf(L.t2[i], dw1[i], x.a[WX + i]); }
 #pragma unroll
   for (int i = 0; i < 4; ++i) Om[i] = fmaf(L.c2, dOm[i], x.a[OM + i]);
   rb_stage(P, q, w, Om, f2, dq, dw, b);
 #pragma unroll
   for (int i = 0; i < 4; ++i) { aq[i] = fmaf(2.f, dq[i], aq[i]); q[i] = fmaf(H.h2q, dq[i], x.a[QW + i]); }
 #pragma unroll
-  for (int i = 0; i < 3; ++i) { aw[i] = fmaf(2.f, dw[i], aw[i]); w[i] = fmaf(H.h2, dw[i], x.a[WX + i]); }
+  for (int i = 0; i < 3; ++i) { aw[i] = fmaf(2.f, dw[i], aw[i]); w[i] = fmaf(L.t2[i], dw[i], x.a[WX + i]); }
 #pragma unroll
   for (int i = 0; i < 4; ++i) Om[i] = fmaf(L.c3, dOm[i], x.a[OM + i]);
   rb_stage(P, q, w, Om, f3, dq, dw, b);
 #pragma unroll
   for (int i = 0; i < 4; ++i) { aq[i] = fmaf(2.f, dq[i], aq[i]); q[i] = fmaf(H.hq, dq[i], x.a[QW + i]); }
 #pragma unroll
-  for (int i = 0; i < 3; ++i) { aw[i] = fmaf(2.f, dw[i], aw[i]); w[i] = fmaf(H.h, dw[i], x.a[WX + i]); }
+  for (int i = 0; i < 3; ++i) { aw[i] = fmaf(2.f, dw[i], aw[i]); w[i] = fmaf(L.t1[i], dw[i], x.a[WX + i]); }
 #pragma unroll
   for (int i = 0; i < 4; ++i) Om[i] = fmaf(L.c4, dOm[i], x.a[OM + i]);
   rb_stage(P, q, w, Om, f4, dq, dw, b);
 #pragma unroll
   for (int i = 0; i < 4; ++i) x.a[QW + i] = fmaf(H.h6q, aq[i] + dq[i], x.a[QW + i]);
 #pragma unroll
-  for (int i = 0; i < 3; ++i) x.a[WX + i] = fmaf(H.h6, aw[i] + dw[i], x.a[WX + i]);
+  for (int i = 0; i < 3; ++i) x.a[WX + i] = fmaf(L.t6[i], aw[i] + dw[i], x.a[WX + i]);
 #pragma unroll
   for (int i = 0; i < 4; ++i) x.a[OM + i] = fmaf(L.c5, dOm[i], x.a[OM + i]);
 #pragma unroll
@@ -496,9 +506,14 @@ __device__ __forceinline__ void step(const DevGroup& P, St& x, const float4 c, c
     rk4_from(P, x, dOm, H, L, f, dq, dw);
     return;
   }
-  float r[4], e[3];
+  float r[4], e[3], wd[3];
+  if (MODE == 2) {  // the derivative term takes omega' itself
+    wd[0] = __fmul_rn(P.txc, dw[0]);
+    wd[1] = __fmul_rn(P.tyc, dw[1]);
+    wd[2] = __fmul_rn(P.tzc, dw[2]);
+  }
   Ctl C;
-  controller_fwd<MODE == 2>(P, x.a, c, hd, b, C, r, dw, e);
+  controller_fwd<MODE == 2>(P, x.a, c, hd, b, C, r, wd, e);
 #pragma unroll
   for (int i = 0; i < 4; ++i) dOm[i] = fmaf(P.omax, r[i], -x.a[OM + i]);  // u = omega_max r
   rk4_from(P, x, dOm, H, L, f, dq, dw);

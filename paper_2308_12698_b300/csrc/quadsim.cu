@@ -84,6 +84,9 @@ DevGroup derive(const sim_group_params_t& p) {
   d.gx = (float)((Jy - Jz) / Jx);
   d.gy = (float)((Jz - Jx) / Jy);
   d.gz = (float)((Jx - Jy) / Jz);
+  d.gxt = (float)((Jy - Jz) / (kt * Ls));  // the gyroscopic coefficients over the torque ones
+  d.gyt = (float)((Jz - Jx) / (kt * Lc));
+  d.gzt = (float)((Jx - Jy) / kq);
   d.m = p.m;
   for (int i = 0; i < 3; ++i) {
     d.kp[i] = p.kp[i];
