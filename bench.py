@@ -547,9 +547,9 @@ def main():
     step_launches = -(-TS // K)
     launch_s = (sum(times) / args.steps / step_launches) / 1e3
     kernel_rate = NA * min(K, TS) / launch_s
-    prof = profiled("step_kernel<1,false>", f"closed-loop-{NA}-K{K}")
+    prof = profiled("group_kernel<1,one_group>", f"closed-loop-{NA}-K{K}")
     roof = alu_roofline(FLOPS_PER_AGENT_STEP, kernel_rate, sms, clocks, prof,
-                        f"step_kernel<closed loop, one group>, K={K} fused steps, block {tune['block']}",
+                        f"group_kernel<closed loop, one group>, K={K} fused steps, block {tune['block']}",
                         avg_launch_us=launch_s * 1e6)
     roof["traffic"] = prof.get("bytes_per_launch")
     roof["frac_checker_count"] = CHECKER_FLOPS_PER_AGENT_STEP * kernel_rate / 1e12 / roof["peak"]
@@ -964,11 +964,11 @@ def side_measurements(args, world, sim, wl, x0, cmd, x, flush, stream, timed_ste
     pw = W.closed_loop_pid(n=N_AGENTS, nsteps=T_STEPS)
     pt, ms = swarm_leg(world, pw, dev, timed_steps, reps)
     rate = pw.n * T_STEPS / (ms / 1e3)
-    pp = profiled("step_kernel<2,false>", f"closed-loop-pid-{pw.n}-K{pt['K']}")
+    pp = profiled("group_kernel<2,one_group>", f"closed-loop-pid-{pw.n}-K{pt['K']}")
     out["pid"] = {"value": world * rate, "unit": UNIT, "ms_per_step": ms, "n_agents": pw.n, "K": pt["K"],
                   "block": pt["block"],
                   "roofline": alu_roofline(FLOPS_PER_AGENT_STEP_PID, rate, sms, clocks, pp,
-                                           "step_kernel<PID rate loop, one group>")}
+                                           "group_kernel<PID rate loop, one group>")}
 
     # quadrotors, cars and fixed-wing drones (200,000 each): a launch per type's group, side by side
     mw = W.multi_type(nsteps=T_STEPS)
