@@ -147,9 +147,12 @@ typedef struct sim_graph_s* sim_graph_t;
  * alive and unchanged); sim_create checks every id once (synchronously) and
  * returns SIM_ERR_GROUP if one is out of range.  It also reads the ids once to
  * see whether each group's agents form one contiguous range (sorted ids, or
- * contiguous blocks in any order): if so, the fused steps run one group per
- * thread block with the group's constants in the kernel's parameters, which
- * is faster than the general form (the results are the same bit for bit).
+ * contiguous blocks in any order): if so, the fused steps run as one kernel
+ * launch per group range with the group's constants in the kernel's
+ * parameters, the launches side by side on streams the handle creates (one
+ * per group; forked from the caller's stream by an event and joined back to
+ * it before the call's later work), which is faster than the general form
+ * (the results are the same bit for bit).
  * When the groups interleave (and n_agents < 2^32), the handle keeps a
  * group-sorted order of the agents (4 bytes per agent, device memory it owns)
  * and the fused steps reach the agents through it, still one group per block:
@@ -161,7 +164,9 @@ typedef struct sim_graph_s* sim_graph_t;
  * last; they must be finite, xi_max >= 0, in every mode).  Groups of car or
  * fixed-wing type need SIM_CLOSED_LOOP; such a handle steps (sim_step and
  * the calls built on it, collisions) but has no checkpointed rollout or
- * adjoint (SIM_ERR_ARG).  Runs on the current CUDA device. */
+ * adjoint (SIM_ERR_ARG).  Runs on the current CUDA device.  A handle's calls
+ * come from one host thread at a time: its calls reuse streams and events the
+ * handle owns. */
 int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents, const uint8_t* d_group_id,
                int mode, sim_handle_t* out);
 
