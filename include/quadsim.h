@@ -335,8 +335,8 @@ int sim_load_status(sim_handle_t h, const uint8_t* d_status_in, void* stream);
  * <= 128), and the defaults used when a call passes 0 for the steps fused
  * per launch (K) or the checkpoint interval (C).  A 0 argument leaves that
  * value unchanged; anything else out of range returns SIM_ERR_ARG.
- * sim_create sets the block sizes to the largest of 256 (128 for the
- * adjoint), 128, 64 and 32 that gives every SM at least one block, and to 32
+ * sim_create sets the block sizes to the largest of 128, 64 and 32 (forward
+ * and adjoint alike) that gives every SM at least one block, and to 32
  * for a swarm too small for that, so that a small swarm spreads one warp per
  * SM instead of sharing the schedulers of a few SMs.  Forward results do not
  * depend on the block size; group sums of the adjoint are summed in another

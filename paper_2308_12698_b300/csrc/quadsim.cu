@@ -27,7 +27,9 @@ using namespace qs;
 
 namespace {
 
-constexpr int kDefaultBlockFwd = 256;
+// forward 128: the fused step of one group 1.7 % faster than at 256, the plain step and the
+// per-range launches the same (1e6, 6e5 and 1e7 agents)
+constexpr int kDefaultBlockFwd = 128;
 constexpr int kDefaultBlockAdj = 128;
 
 // Default threads per block for n agents on sms SMs: the largest of `largest`,

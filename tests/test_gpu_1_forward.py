@@ -514,7 +514,7 @@ def test_default_block_spreads_small_swarms(dev, n):
     sim = Sim(wl.groups, wl.n, wl.mode)
     got = sim.launch()
     sim.close()
-    assert got["block"] == _spread(n, sms, 256) and got["block_adj"] == _spread(n, sms, 128), got
+    assert got["block"] == _spread(n, sms, 128) and got["block_adj"] == _spread(n, sms, 128), got
     np.testing.assert_array_equal(gpu_run(wl, dev, 50, K=25), gpu_run(wl, dev, 50, K=25, block=256))
 
 
