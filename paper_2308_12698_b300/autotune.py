@@ -63,6 +63,14 @@ def _time(fn, reps: int = 3) -> float:
     return best
 
 
+def pick_step(results, tie: float = 0.005):
+    """The (ms, block, K) to use from timed candidates: among those within `tie` of the fastest
+    (the timing's spread), the largest block, then the largest K -- fewer blocks per launch for
+    calls over part of the swarm."""
+    best = min(r[0] for r in results)
+    return max((r for r in results if r[0] <= best * (1.0 + tie)), key=lambda r: (r[1], r[2]))
+
+
 def tune_step(sim: Sim, state: torch.Tensor, cmd: torch.Tensor, dt: float, nsteps: int, use_cache: bool = True,
               blocks=BLOCKS, ks=KS) -> dict:
     """Pick (block, K) for sim_step over nsteps; applies and returns it."""
@@ -81,10 +89,7 @@ def tune_step(sim: Sim, state: torch.Tensor, cmd: torch.Tensor, dt: float, nstep
                 work.copy_(state)
                 ms = _time(lambda: sim.step(work, cmd, dt, nsteps, K=k))
                 results.append((ms, b, k))
-        # candidates within 0.5 % of the fastest (the timing's spread) go to the largest block,
-        # then the largest K: fewer blocks per launch for calls over part of the swarm
-        best = min(r[0] for r in results)
-        ms, b, k = max((r for r in results if r[0] <= best * 1.005), key=lambda r: (r[1], r[2]))
+        ms, b, k = pick_step(results)
         cfg = dict(block=b, K=k, ms=ms, candidates=[list(r) for r in results])
         cache[key] = cfg
         _store(cache)
