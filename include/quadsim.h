@@ -175,8 +175,9 @@ int sim_create(const sim_group_params_t* groups, int n_groups, int64_t n_agents,
  * SIM_ERR_ARG nothing changes.  Synchronous on the host, but it does not wait for work
  * of this handle already enqueued on other streams: synchronise those first,
  * or a launch in flight may see some blocks with the old groups and some
- * with the new.  CUDA graphs captured before keep the kernels and the
- * single-group parameters they captured: capture them again after this
+ * with the new.  CUDA graphs captured before keep the kernels and the group
+ * parameters their launches carry (one group, and the groups that run as a
+ * launch per range or through an order): capture them again after this
  * call. */
 int sim_set_params(sim_handle_t h, const sim_group_params_t* groups, int n_groups);
 
